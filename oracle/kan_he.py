@@ -1,0 +1,318 @@
+"""Encrypted KAN layer on the oracle CKKS (test infrastructure only).
+
+Follows the paper's Method section step by step:
+
+* Algorithm 1 (fast repeat packing): mask x to its n_i slots, then
+  ceil(log2(g+2k)) times add the ciphertext rotated right by n_i 2^(j-1).
+  Reading: the 1/(2R) input scaling of Algorithm 2 (line 4) is folded into
+  the mask, so the comparison inputs need no extra level.
+* Algorithm 2 (B-spline basis): ColTile'd knot vectors, PolyComp via the
+  composite f_{n_1} o ... o f_{n_d} (Cheon et al. closed form) with its last
+  stage returning (1 + f)/2, B0 = x1 (x) x2, then k recursion steps
+  b <- A1 (x_rep - t1) (x) b + A2 (t3 - x_rep) (x) rot(b, n_i). Reading: the two
+  products of a step share one relinearisation; A1, A2 are zero outside the
+  valid ColTile blocks.
+* Lazy combination and Algorithm 3: W_f = W' P (Eq. 13) with
+  W'[o, i(g+k) + m] = w_s[o, i] c[o, i, m].
+* SiLU (Eqs. 11-12): the fitted Chebyshev polynomial evaluated by a
+  Paterson-Stockmeyer-style baby-step / giant-step recursion.
+* Linear layers: baby-step giant-step diagonal matvec (Halevi-Shoup) with
+  hoisted baby-step rotations.
+"""
+import math
+
+import numpy as np
+
+from . import ckks
+from .kan_plain import fn_coeffs, knots
+
+
+def pow2ceil(n):
+    return 1 << max(0, (int(n) - 1).bit_length())
+
+
+# ------------------------------------------------------------------ Algorithm 3
+def permutation_matrix(n_r, n_c):
+    """Algorithm 3 (1-indexed in the paper): P[(r-1)n_c + c][(c-1)n_r + r] = 1."""
+    P = np.zeros((n_r * n_c, n_r * n_c))
+    for r in range(1, n_r + 1):
+        for c in range(1, n_c + 1):
+            j_c = (c - 1) * n_r + r
+            j_r = (r - 1) * n_c + c
+            P[j_r - 1, j_c - 1] = 1.0
+    return P
+
+
+def lazy_weights(layer):
+    """W' (n_o x n_i(g+k)), row-major basis index i(g+k) + m."""
+    n_o, n_i = layer["n_out"], layer["n_in"]
+    nb = layer["G"] + layer["k"]
+    Wp = (layer["w_s"][:, :, None] * layer["coef"]).reshape(n_o, n_i * nb)
+    return Wp
+
+
+def fused_weights(layer):
+    """Eq. 13: W_f = W' P (columns in ColTile order m n_i + i)."""
+    return lazy_weights(layer) @ permutation_matrix(layer["n_in"], layer["G"] + layer["k"])
+
+
+# ------------------------------------------------------------------ ColTile
+def coltile(Gm, l, r):
+    """ColTile(G, l, r): columns l..r-1 (1-indexed) of G concatenated column-major."""
+    return np.concatenate([Gm[:, c - 1] for c in range(l, r)]) if r > l else np.zeros(0)
+
+
+def grid_matrix(layer):
+    t = knots(layer)
+    return np.tile(t[None, :], (layer["n_in"], 1))
+
+
+# ------------------------------------------------------------------ BSGS plan
+def bsgs_plan(n_out, n, slots):
+    no = pow2ceil(n_out)
+    npad = pow2ceil(max(n, no))
+    if npad > slots:
+        raise ValueError("matrix does not fit the slots")
+    g1 = 1 << ((no.bit_length() - 1 + 1) // 2)
+    g2 = no // g1
+    folds = []
+    s = npad // 2
+    while s >= no:
+        folds.append(s)
+        s //= 2
+    return dict(no=no, npad=npad, g1=g1, g2=g2, folds=folds)
+
+
+def diagonals(M, plan, slots):
+    """d_t[s] = M[s mod no][(s+t) mod npad] for s < npad (zero where undefined)."""
+    n_out, n = M.shape
+    no, npad = plan["no"], plan["npad"]
+    Mp = np.zeros((no, npad))
+    Mp[:n_out, :n] = M
+    s = np.arange(npad)
+    D = np.zeros((no, slots))
+    for t in range(no):
+        D[t, :npad] = Mp[s % no, (s + t) % npad]
+    return D
+
+
+def bsgs_matvec(ctx, keys, v, M, plan):
+    """y[0:n_out] = M v; v must read v[(s+t) mod npad] at slot s+t for s < npad."""
+    S = ctx.slots
+    D = diagonals(M, plan, S)
+    g1, g2 = plan["g1"], plan["g2"]
+    baby = ckks.rotate_many(ctx, keys, v, list(range(g1)))
+    lv = v.level
+    z = None
+    for i in range(g2):
+        acc = None
+        Spt = ckks.plain_scale(ctx, v.scale, lv)
+        for j in range(g1):
+            d = np.roll(D[g1 * i + j], g1 * i)  # rot(d, -g1 i)
+            pt = ckks.encode(ctx, d, lv, Spt)
+            prod = np.zeros_like(v.data)
+            ctx.L_.or_mul_plain(ctx.h, baby[j].data.ctypes.data, pt.ctypes.data, 2, lv + 1,
+                                prod.ctypes.data)
+            if acc is None:
+                acc = prod
+            else:
+                o = np.zeros_like(acc)
+                ctx.L_.or_add(ctx.h, acc.ctypes.data, prod.ctypes.data, 2, lv + 1, 0, o.ctypes.data)
+                acc = o
+        inner = ckks.rescale(ctx, ckks.Ct(acc, lv, v.scale * Spt))
+        if i > 0:
+            inner = ckks.rotate(ctx, keys, inner, g1 * i)
+        z = inner if z is None else ckks.add(ctx, z, inner)
+    for s in plan["folds"]:
+        z = ckks.add(ctx, z, ckks.rotate(ctx, keys, z, s))
+    return z
+
+
+# ------------------------------------------------------------------ polynomials
+def eval_odd(ctx, keys, u, c, const=0.0):
+    """sum_l c[l] u^(2l+1) + const: each term is (c_l u) times the binary
+    powers u^2, u^4, ... of 2l in ascending order; terms summed at the lowest
+    level."""
+    pw = {1: u}
+    need = max(2 * l for l, cl in enumerate(c) if cl != 0.0)
+    b = 2
+    while b <= need:
+        pw[b] = ckks.mul(ctx, keys, pw[b // 2], pw[b // 2])
+        b *= 2
+    terms = []
+    for l, cl in enumerate(c):
+        if cl == 0.0:
+            continue
+        T = ckks.mul_const(ctx, u, cl)
+        e, b = 2 * l, 2
+        while e:
+            if e & b:
+                T = ckks.mul(ctx, keys, T, pw[b])
+                e ^= b
+            b *= 2
+        terms.append(T)
+    lv = min(t.level for t in terms)
+    out = None
+    for T in terms:
+        T = ckks.level_down(ctx, T, lv)
+        out = T if out is None else ckks.add(ctx, out, T)
+    if const != 0.0:
+        out = ckks.add_const(ctx, out, const)
+    return out
+
+
+def polycomp0(ctx, keys, a, stages):
+    """PolyComp(a, 0) = (1 + f(a))/2 with f = f_{n_d} o ... o f_{n_1}."""
+    u = a
+    for s, n in enumerate(stages):
+        c = fn_coeffs(n)
+        if s == len(stages) - 1:
+            u = eval_odd(ctx, keys, u, [0.5 * x for x in c], 0.5)
+        else:
+            u = eval_odd(ctx, keys, u, c)
+    return u
+
+
+def eval_cheb(ctx, keys, y, a):
+    """sum_j a_j T_j(y) by baby steps T_1..T_m (m a power of two with
+    m >= sqrt(d+1)) and giant steps T_{m 2^i}, splitting
+    p = q T_D + r with q_0 = a_D, q_i = 2 a_{D+i}, r_j = a_j - a_{2D-j}."""
+    a = [float(x) for x in a]
+    d = len(a) - 1
+    m = pow2ceil(math.ceil(math.sqrt(d + 1)))
+    T = {1: y}
+    for i in range(2, m + 1):
+        if i & (i - 1) == 0:
+            sq = ckks.mul(ctx, keys, T[i // 2], T[i // 2])
+            T[i] = ckks.add_const(ctx, ckks.mul_int(ctx, sq, 2), -1.0)
+        else:
+            hb = 1 << (i.bit_length() - 1)
+            lo = i - hb
+            pr = ckks.mul_int(ctx, ckks.mul(ctx, keys, T[hb], T[lo]), 2)
+            if hb - lo == 0:
+                T[i] = ckks.add_const(ctx, pr, -1.0)
+            else:
+                T[i] = ckks.sub(ctx, pr, ckks.level_down(ctx, T[hb - lo], pr.level))
+    Gs = {m: T[m]}
+    D = m
+    while 2 * D <= d:
+        sq = ckks.mul(ctx, keys, Gs[D], Gs[D])
+        Gs[2 * D] = ckks.add_const(ctx, ckks.mul_int(ctx, sq, 2), -1.0)
+        D *= 2
+
+    def rec(c):
+        deg = len(c) - 1
+        if deg < m:
+            if deg == 0:
+                return c[0]
+            return ckks.lincomb(ctx, [T[i] for i in range(1, deg + 1)], c[1:], c[0])
+        D = m
+        while 2 * D <= deg:
+            D *= 2
+        q = [c[D]] + [2.0 * c[D + i] for i in range(1, deg - D + 1)]
+        r = list(c[:D])
+        for i in range(1, deg - D + 1):
+            r[D - i] -= c[D + i]
+        Q = rec(q)
+        R = rec(r)
+        if isinstance(Q, float):
+            P = ckks.lincomb(ctx, [Gs[D]], [Q])
+        else:
+            P = ckks.mul(ctx, keys, Q, Gs[D])
+        if isinstance(R, float):
+            return ckks.add_const(ctx, P, R)
+        lv = min(P.level, R.level)
+        return ckks.add(ctx, ckks.level_down(ctx, P, lv), ckks.level_down(ctx, R, lv))
+
+    return rec(a)
+
+
+# ------------------------------------------------------------------ layer
+def layer_rotations(layer, slots):
+    """Every rotation step the layer schedule uses."""
+    n_i, n_o, G, k = layer["n_in"], layer["n_out"], layer["G"], layer["k"]
+    J = math.ceil(math.log2(G + 2 * k))
+    steps = {-n_i * 2 ** (j - 1) for j in range(1, J + 1)}
+    steps.add(n_i)
+    for n in (n_i * (G + k), n_i):
+        p = bsgs_plan(n_o, n, slots)
+        if p["npad"] < slots:
+            steps.add(-p["npad"])
+        steps.update(range(1, p["g1"]))
+        steps.update(p["g1"] * i for i in range(1, p["g2"]))
+        steps.update(p["folds"])
+    steps.discard(0)
+    return sorted(steps)
+
+
+def layer_eval(ctx, keys, x, layer):
+    S = ctx.slots
+    n_i, n_o, G, k = layer["n_in"], layer["n_out"], layer["G"], layer["k"]
+    R = layer["R"]
+    J = math.ceil(math.log2(G + 2 * k))
+    if n_i * 2 ** J > S:
+        raise ValueError("repeat packing needs n_i * 2^ceil(log2(g+2k)) <= N/2")
+    mask = np.ones(n_i)
+
+    # SiLU branch: y = affine(x) on the masked slots, replicated to period npad
+    lo, hi = layer["silu_lo"], layer["silu_hi"]
+    sa, sb = 2.0 / (hi - lo), -(hi + lo) / (hi - lo)
+    y = ckks.add_plain(ctx, ckks.mul_plain(ctx, x, sa * mask), sb * mask)
+    plan_b = bsgs_plan(n_o, n_i, S)
+    if plan_b["npad"] < S:
+        y = ckks.add(ctx, y, ckks.rotate(ctx, keys, y, -plan_b["npad"]))
+    v = eval_cheb(ctx, keys, y, layer["silu_cheb"])
+    yb = bsgs_matvec(ctx, keys, v, layer["w_b"], plan_b)
+
+    # Algorithm 1
+    xr = ckks.mul_plain(ctx, x, mask / (2.0 * R))
+    for j in range(1, J + 1):
+        xr = ckks.add(ctx, xr, ckks.rotate(ctx, keys, xr, -n_i * 2 ** (j - 1)))
+
+    # Algorithm 2
+    Gm = grid_matrix(layer)
+    r = G + 2 * k + 1
+    g1 = coltile(Gm, 1, r)
+    g2 = coltile(Gm, 2, r + 1)
+    a1 = ckks.add_plain(ctx, xr, -g1 / (2.0 * R))
+    a2 = ckks.add_plain(ctx, ckks.mul_int(ctx, xr, -1), g2 / (2.0 * R))
+    s1 = polycomp0(ctx, keys, a1, layer["comp"])
+    s2 = polycomp0(ctx, keys, a2, layer["comp"])
+    b = ckks.mul(ctx, keys, s1, s2)
+    for j in range(1, k + 1):
+        t1 = coltile(Gm, 1, r - j)
+        t2 = coltile(Gm, j + 1, r)
+        t3 = coltile(Gm, j + 2, r + 1)
+        t4 = coltile(Gm, 2, r - j + 1)
+        A1 = 1.0 / (t2 - t1)
+        A2 = 1.0 / (t3 - t4)
+        lb = b.level
+        xd = ckks.mod_drop(ctx, xr, lb + 1)
+        u1 = ckks.add_plain(ctx, ckks.mul_plain(ctx, xd, 2.0 * R * A1), -t1 * A1)
+        u2 = ckks.add_plain(ctx, ckks.mul_plain(ctx, xd, -2.0 * R * A2), t3 * A2)
+        rb = ckks.rotate(ctx, keys, b, n_i)
+        b = ckks.mul_sum(ctx, keys, [(u1, b), (u2, rb)])
+
+    # fused linear layer (Eq. 13) by BSGS
+    Wf = fused_weights(layer)
+    plan_s = bsgs_plan(n_o, n_i * (G + k), S)
+    if plan_s["npad"] < S:
+        b = ckks.add(ctx, b, ckks.rotate(ctx, keys, b, -plan_s["npad"]))
+    ys = bsgs_matvec(ctx, keys, b, Wf, plan_s)
+
+    lv = min(ys.level, yb.level)
+    return ckks.add(ctx, ckks.level_down(ctx, ys, lv), ckks.level_down(ctx, yb, lv))
+
+
+def infer(ctx, keys, x, model):
+    h = x
+    for layer in model:
+        h = layer_eval(ctx, keys, h, layer)
+    return h
+
+
+def model_rotations(model, slots):
+    s = set()
+    for layer in model:
+        s.update(layer_rotations(layer, slots))
+    return sorted(s)

@@ -1,0 +1,194 @@
+"""Pins for the oracle's KAN pieces (CPU only): Cox-de Boor (Eqs. 2-3)
+against scipy's B-spline and the cubic knot values, Algorithm 2's index
+algebra with exact comparisons, the f_n closed forms, Algorithm 3,
+Eq. 13, the SiLU fit (Eqs. 11-12) against numpy's weighted Chebyshev fit,
+the BSGS diagonal algebra by brute force, and the encrypted layer against
+the HE-friendly FP64 KAN."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import calibrate, ckks, kan_he, kan_plain, silu_fit
+from paper_2409_07751_gb300 import workloads as W
+
+
+def _layer(G=5, k=3, n_in=3, n_out=2, seed=0):
+    return W.make_model("t", seed=seed, widths=[n_in, n_out], G=G, k=k)[0]
+
+
+def test_cox_de_boor_matches_scipy():
+    si = pytest.importorskip("scipy.interpolate")
+    for G, k in [(5, 3), (3, 2), (10, 5), (4, 1)]:
+        L = _layer(G, k)
+        t = kan_plain.knots(L)
+        x = np.linspace(-1.0, 0.999, 101)
+        B = kan_plain.bspline_exact(x, t, k)
+        for m in range(G + k):
+            ref = si.BSpline.basis_element(t[m:m + k + 2], extrapolate=False)(x)
+            ref = np.nan_to_num(ref)
+            assert np.abs(B[:, m] - ref).max() < 1e-12
+
+
+def test_cubic_knot_values_and_partition_of_unity():
+    L = _layer(5, 3)
+    t = kan_plain.knots(L)
+    B = kan_plain.bspline_exact(t[1:4], t, 3)
+    # B_{0,3} at t_1, t_2, t_3 = 1/6, 2/3, 1/6
+    assert np.allclose(B[:, 0], [1 / 6, 2 / 3, 1 / 6], atol=1e-15)
+    x = np.linspace(-1, 0.99999, 1000)
+    assert np.abs(kan_plain.bspline_exact(x, t, 3).sum(-1) - 1).max() < 1e-14
+    # zero outside the extended grid
+    assert np.abs(kan_plain.bspline_exact(np.array([t[-1] + 0.1, t[0] - 0.1]), t, 3)).max() == 0
+
+
+def test_alg2_with_exact_comparison_is_cox_de_boor(monkeypatch):
+    """Algorithm 2 with PolyComp replaced by the exact step reproduces Eq. 3."""
+    monkeypatch.setattr(kan_plain, "polycomp0", lambda a, stages: (a > 0).astype(float))
+    for G, k in [(5, 3), (10, 5), (3, 2)]:
+        L = _layer(G, k)
+        t = kan_plain.knots(L)
+        x = np.random.default_rng(1).uniform(-1, 1, 300)
+        assert np.abs(kan_plain.bspline_hef(x, t, k, 2.0, [3]) - kan_plain.bspline_exact(x, t, k)).max() < 1e-13
+
+
+def test_fn_closed_forms():
+    assert kan_plain.fn_coeffs(1) == [1.5, -0.5]
+    assert kan_plain.fn_coeffs(2) == [15 / 8, -10 / 8, 3 / 8]
+    assert kan_plain.fn_coeffs(3) == [35 / 16, -35 / 16, 21 / 16, -5 / 16]
+    for n in (1, 2, 3, 4):
+        c = kan_plain.fn_coeffs(n)
+        p = np.polynomial.Polynomial([0] + sum([[cl, 0] for cl in c], [])[:-1])
+        assert abs(p(1.0) - 1) < 1e-15 and abs(p(-1.0) + 1) < 1e-15
+        assert abs(p.deriv()(1.0)) < 1e-12
+    s = kan_plain.polycomp0(np.array([-0.9, -0.3, 0.3, 0.9]), [3, 3, 3])
+    assert np.allclose(s, [0, 0, 1, 1], atol=1e-3)
+
+
+def test_alg3_permutation_and_eq13():
+    n_r, n_c = 4, 6
+    P = kan_he.permutation_matrix(n_r, n_c)
+    assert (P.sum(0) == 1).all() and (P.sum(1) == 1).all()
+    L = _layer(3, 3, n_in=n_r, n_out=3)
+    Bm = np.random.default_rng(2).normal(size=(n_r, n_c))  # B[i, m]
+    row_major = Bm.reshape(-1)                              # i*(g+k) + m
+    col_tile = Bm.T.reshape(-1)                              # m*n_i + i
+    assert np.allclose(P @ col_tile, row_major)
+    Wp, Wf = kan_he.lazy_weights(L), kan_he.fused_weights(L)
+    assert np.allclose(Wf @ col_tile, Wp @ row_major, atol=1e-14)
+    # and W' row-major is the einsum of the per-edge spline
+    y = np.einsum("im,oim,oi->o", Bm, L["coef"], L["w_s"])
+    assert np.allclose(Wp @ row_major, y)
+
+
+def test_coltile():
+    Gm = np.arange(12.0).reshape(3, 4)
+    assert list(kan_he.coltile(Gm, 2, 4)) == [1, 5, 9, 2, 6, 10]
+
+
+def test_silu_fit_matches_numpy_weighted_chebfit():
+    lo, hi, mu, sig = -6.0, 5.0, -0.3, 1.4
+    a = silu_fit.fit_silu(lo, hi, mu, sig, 12, 4000)
+    x = np.linspace(lo, hi, 4000)
+    y = (2 * x - (lo + hi)) / (hi - lo)
+    w = np.where(np.abs(x - mu) <= 3 * sig, 10.0, 1.0)
+    ref = np.polynomial.chebyshev.chebfit(y, kan_plain.silu(x), 12, w=np.sqrt(w))
+    assert np.abs(a - ref).max() < 1e-9
+    # weighted normal equations: V^T W r = 0
+    V = np.polynomial.chebyshev.chebvander(y, 12)
+    r = kan_plain.silu(x) - V @ a
+    assert np.abs(V.T @ (w * r)).max() < 1e-8
+    assert silu_fit.silu_range(0.0, 1.0, -3.0, 7.0) == (-3.0, 5.0)
+    assert silu_fit.silu_range(0.0, 1.0, -9.0, 2.0) == (-5.0, 2.0)
+
+
+def test_bsgs_diagonal_algebra_bruteforce():
+    S = 64
+    rng = np.random.default_rng(3)
+    for n_out, n in [(3, 20), (8, 8), (5, 32), (2, 3), (16, 64)]:
+        M = rng.normal(size=(n_out, n))
+        plan = kan_he.bsgs_plan(n_out, n, S)
+        D = kan_he.diagonals(M, plan, S)
+        v = np.zeros(S)
+        v[:n] = rng.normal(size=n)
+        npad = plan["npad"]
+        if npad < S:
+            v = v + np.roll(v, npad)  # rot(v, -npad)
+        rot = lambda a, t: np.roll(a, -t)
+        z = np.zeros(S)
+        for i in range(plan["g2"]):
+            inner = sum(np.roll(D[plan["g1"] * i + j], plan["g1"] * i) * rot(v, j) for j in range(plan["g1"]))
+            z += rot(inner, plan["g1"] * i)
+        for s in plan["folds"]:
+            z = z + rot(z, s)
+        assert np.allclose(z[:n_out], M @ v[:n])
+
+
+@pytest.fixture(scope="module")
+def he_small():
+    ctx = ckks.Ctx(ckks.Params(log_n=7, n_scale=17, n_special=2))
+    return ctx
+
+
+def test_alg1_repeat_packing(he_small):
+    ctx = he_small
+    n_i, G, k = 3, 5, 3
+    J = math.ceil(math.log2(G + 2 * k))
+    keys = ckks.Keys(ctx, 1, rot_steps=[-n_i * 2 ** (j - 1) for j in range(1, J + 1)])
+    x = np.zeros(ctx.slots)
+    x[:n_i] = [0.1, -0.2, 0.3]
+    x[n_i:] = 5.0  # garbage outside the input slots must be masked away
+    c = ckks.encrypt(ctx, keys, x, ctx.L, 2)
+    xr = ckks.mul_plain(ctx, c, np.ones(n_i))
+    for j in range(1, J + 1):
+        xr = ckks.add(ctx, xr, ckks.rotate(ctx, keys, xr, -n_i * 2 ** (j - 1)))
+    d = ckks.decrypt(ctx, keys, xr)
+    ref = np.zeros(ctx.slots)
+    ref[: n_i * 2 ** J] = np.tile(x[:n_i], 2 ** J)
+    assert np.abs(d - ref).max() < 1e-6
+
+
+def test_he_polynomials(he_small):
+    ctx = he_small
+    keys = ckks.Keys(ctx, 2)
+    rng = np.random.default_rng(4)
+    y = rng.uniform(-1, 1, ctx.slots)
+    c = ckks.encrypt(ctx, keys, y, ctx.L, 2)
+    for d in (3, 7, 15, 27):
+        a = rng.normal(size=d + 1) / (1 + np.arange(d + 1))
+        out = kan_he.eval_cheb(ctx, keys, c, a)
+        assert np.abs(ckks.decrypt(ctx, keys, out) - np.polynomial.chebyshev.chebval(y, a)).max() < 1e-5
+        assert ctx.L - out.level <= math.ceil(math.log2(d + 1)) + 1
+    for stages in ([1], [3], [3, 1]):
+        out = kan_he.polycomp0(ctx, keys, c, stages)
+        assert np.abs(ckks.decrypt(ctx, keys, out) - kan_plain.polycomp0(y, stages)).max() < 1e-5
+
+
+def test_he_bsgs_matvec(he_small):
+    ctx = he_small
+    rng = np.random.default_rng(5)
+    n_out, n = 5, 20
+    M = rng.normal(size=(n_out, n))
+    plan = kan_he.bsgs_plan(n_out, n, ctx.slots)
+    steps = [-plan["npad"]] + list(range(1, plan["g1"])) + [plan["g1"] * i for i in range(1, plan["g2"])] + plan["folds"]
+    keys = ckks.Keys(ctx, 3, rot_steps=steps)
+    v = np.zeros(ctx.slots)
+    v[:n] = rng.uniform(-1, 1, n)
+    c = ckks.encrypt(ctx, keys, v, ctx.L, 2)
+    c = ckks.add(ctx, c, ckks.rotate(ctx, keys, c, -plan["npad"]))
+    out = kan_he.bsgs_matvec(ctx, keys, c, M, plan)
+    assert np.abs(ckks.decrypt(ctx, keys, out, n_out) - M @ v[:n]).max() < 1e-6
+
+
+def test_he_kan_matches_hef(he_small):
+    ctx = he_small
+    model = W.make_model("t", widths=[3, 4, 2], G=3, k=2)
+    X = W.uniform_inputs(100, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    keys = ckks.Keys(ctx, 1, rot_steps=kan_he.model_rotations(m, ctx.slots))
+    for b in range(2):
+        c = ckks.encrypt(ctx, keys, X[b], ctx.L, 2, b)
+        out = kan_he.infer(ctx, keys, c, m)
+        dec = ckks.decrypt(ctx, keys, out, 2)
+        hef = kan_plain.forward(m, X[b:b + 1], "poly", "poly")[0]
+        assert np.abs(dec - hef).max() < 1e-5
