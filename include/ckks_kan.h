@@ -1,0 +1,194 @@
+/*
+ * ckks_kan.h — C ABI of the GB300 RNS-CKKS / encrypted-KAN library.
+ *
+ * Protocol (paper, Introduction and Threat Model): the client holds the
+ * secret key, raster-scans and encrypts its input x (length n_i), the server
+ * evaluates the KAN on the ciphertext with plaintext weights, and the client
+ * decrypts the n_o outputs from slots [0, n_o).
+ *
+ * Conventions for every entry point:
+ *  - Return value: CKKS_OK (0) or a negative CKKS_ERR_* code; no call aborts
+ *    or throws across the ABI. ckks_strerror() names a code; ckks_last_error()
+ *    gives the last failure's message on the calling thread.
+ *  - Handles (ckks_ctx, ckks_keys, ckks_ct, kan_model) are opaque and
+ *    library-owned; every `**out` handle is freed by its *_destroy call.
+ *    Ciphertext and key data live in device (HBM) memory on the context's
+ *    device.
+ *  - Host arrays passed in are caller-owned and only read (or written, for
+ *    outputs) during the call.
+ *  - Device pointers (uint64_t* d_...) must point into memory on the
+ *    context's device; the library does not take ownership.
+ *  - Work is queued on the context's stream; calls that return host data
+ *    (decrypt, export) synchronize that stream first.
+ *  - A ciphertext handle holds a batch of B >= 1 ciphertexts at one level l
+ *    (l + 1 RNS limbs), laid out [B][2][l+1][N] uint64 in NTT form.
+ */
+#ifndef CKKS_KAN_H
+#define CKKS_KAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CKKS_OK 0
+#define CKKS_ERR_INVALID_ARG -1
+#define CKKS_ERR_LEVEL -2        /* level exhausted or levels not compatible */
+#define CKKS_ERR_SCALE -3        /* operand scales differ by more than 2^-30 */
+#define CKKS_ERR_MISSING_KEY -4  /* no Galois key for a requested rotation */
+#define CKKS_ERR_OUT_OF_MEMORY -5
+#define CKKS_ERR_CUDA -6
+#define CKKS_ERR_OVERFLOW -7     /* a value does not fit its encoding scale */
+#define CKKS_ERR_TIMEOUT -8
+#define CKKS_ERR_UNSUPPORTED -9
+
+typedef struct ckks_ctx ckks_ctx;
+typedef struct ckks_keys ckks_keys;
+typedef struct ckks_ct ckks_ct;
+typedef struct kan_model kan_model;
+
+const char* ckks_strerror(int code);
+const char* ckks_last_error(void);
+
+/* ------------------------------------------------------------ context
+ * RNS-CKKS parameters (the scheme the paper builds on, HE section; the
+ * parameter rules are this library's own):
+ *   N = 2^log_n; q_0 = largest prime < 2^q0_bits with q_0 = 1 mod 2N;
+ *   n_special special primes below 2^p_bits; n_scale rescaling primes,
+ *   chosen top-down so that the canonical scale of level l,
+ *   Delta_L = 2^scale_bits, Delta_{l-1} = Delta_l^2 / q_l, stays at ~2^scale_bits.
+ * Key switching is hybrid with digits of n_special consecutive Q primes.
+ * device: CUDA ordinal. Errors: INVALID_ARG on out-of-range sizes
+ * (2 <= log_n <= 16, n_special >= 1, bit sizes <= 61), CUDA on device errors. */
+int ckks_context_create(int log_n, int q0_bits, int scale_bits, int n_scale, int p_bits,
+                        int n_special, int device, ckks_ctx** out);
+int ckks_context_destroy(ckks_ctx* ctx);
+/* moduli: n_qp = n_scale + 1 + n_special words (q_0..q_L, p_0..); delta: n_scale + 1
+ * canonical scales; either may be NULL. */
+int ckks_context_info(const ckks_ctx* ctx, uint64_t* moduli, double* delta, int* n_qp);
+/* Queue work on `stream` (a cudaStream_t) instead of the library's own stream. */
+int ckks_set_stream(ckks_ctx* ctx, void* stream);
+int ckks_synchronize(ckks_ctx* ctx);
+
+/* ------------------------------------------------------------ raw kernels
+ * Forward (inverse != 0: inverse) negacyclic NTT of n_rows rows of N uint64
+ * at device pointer d_rows, row r reduced mod q_{r % limbs}. Forward output
+ * is bit-reversed: A[j] = sum_i a[i] psi^((2 brv(j)+1) i) mod q, where psi is
+ * the first x^((q-1)/2N), x = 2,3,..., with psi^N = -1. Inputs must be < q. */
+int ckks_ntt(ckks_ctx* ctx, uint64_t* d_rows, size_t n_rows, int limbs, int inverse);
+
+/* ------------------------------------------------------------ keys
+ * Secret-key generation from `seed` (ternary secret, ChaCha20 stream), the
+ * relinearisation key, and one Galois key per rotation step in rot_steps
+ * (Eq. 10: step t > 0 rotates left). Key data: [digit][2][n_qp][N]. */
+int ckks_keygen(ckks_ctx* ctx, uint64_t seed, const int32_t* rot_steps, size_t n_steps,
+                ckks_keys** out);
+int ckks_keys_destroy(ckks_keys* keys);
+/* Copy the secret key (NTT form, n_qp x N words) or a switching key
+ * (galois = 0: relinearisation; beta_max x 2 x n_qp x N words) to host. */
+int ckks_keys_export_secret(const ckks_keys* keys, uint64_t* host, size_t cap_words);
+int ckks_keys_export_switch(const ckks_keys* keys, uint64_t galois, uint64_t* host,
+                            size_t cap_words);
+/* Galois element of a left rotation by `step`: 5^(step mod N/2) mod 2N. */
+uint64_t ckks_galois_element(const ckks_ctx* ctx, int32_t step);
+
+/* ------------------------------------------------------------ ciphertexts
+ * Encrypt `batch` vectors of n <= N/2 real values (values[b*n + j]) at
+ * `level` with scale Delta_level: c0 = -a s + m + e, c1 = a, where m is the
+ * canonical-embedding encoding, a ~ U(Z_q) and e centred-binomial (eta = 21),
+ * drawn from ChaCha20 streams keyed by `seed` and object id first_index + b.
+ * Errors: OVERFLOW if a value does not fit the scale. */
+int ckks_encrypt(ckks_ctx* ctx, const ckks_keys* keys, const double* values, size_t batch,
+                 size_t n, int level, uint64_t seed, uint64_t first_index, ckks_ct** out);
+/* Decrypt to host: out[b*n + j], n <= N/2. Uses limb 0 only, which is exact
+ * while |scale * value| < q_0 / 2. */
+int ckks_decrypt(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, double* out,
+                 size_t n);
+int ckks_ct_info(const ckks_ct* ct, size_t* batch, int* level, double* scale);
+/* Host copy of the batch, [B][2][level+1][N] words; cap_words must be >= that. */
+int ckks_ct_export(const ckks_ct* ct, uint64_t* host, size_t cap_words);
+int ckks_ct_import(ckks_ctx* ctx, const uint64_t* host, size_t batch, int level, double scale,
+                   ckks_ct** out);
+/* Sub-batch [first, first+count) of a batch, copied. */
+int ckks_ct_slice(ckks_ctx* ctx, const ckks_ct* ct, size_t first, size_t count, ckks_ct** out);
+int ckks_ct_destroy(ckks_ct* ct);
+
+/* ------------------------------------------------------------ homomorphic ops
+ * Eq. 6 / 7: slot-wise add / subtract. Equal batch, level and scale. */
+int ckks_add(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct** out);
+int ckks_sub(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct** out);
+/* Eq. 8 without rescale: tensor product then relinearisation (hybrid key
+ * switch of the s^2 component). Equal batch and level; scale = product. */
+int ckks_mul_relin(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const ckks_ct* b,
+                   ckks_ct** out);
+/* Divide by the top prime q_l with centred rounding; level - 1. */
+int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct** out);
+/* Eq. 8 complete: bring both to the lower level, multiply, relinearise, rescale. */
+int ckks_mul(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const ckks_ct* b,
+             ckks_ct** out);
+/* Eq. 9: slot-wise product with real vector v (n values, rest 0) encoded at
+ * the scale that lands on Delta_{l-1} after the included rescale. */
+int ckks_mul_plain(ckks_ctx* ctx, const ckks_ct* a, const double* v, size_t n, ckks_ct** out);
+/* a + v slot-wise (v encoded at a's scale). */
+int ckks_add_plain(ckks_ctx* ctx, const ckks_ct* a, const double* v, size_t n, ckks_ct** out);
+/* a * c (real scalar, rescaled) and a + c. */
+int ckks_mul_const(ckks_ctx* ctx, const ckks_ct* a, double c, ckks_ct** out);
+int ckks_add_const(ckks_ctx* ctx, const ckks_ct* a, double c, ckks_ct** out);
+/* Move to a lower level with the canonical scale Delta_level. */
+int ckks_level_down(ckks_ctx* ctx, const ckks_ct* a, int level, ckks_ct** out);
+/* Eq. 10: rotate left by `step` slots (right for step < 0). */
+int ckks_rotate(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, int32_t step,
+                ckks_ct** out);
+/* Several rotations of one input sharing a single ModUp (hoisting);
+ * outs[i] receives the rotation by steps[i]; bit-identical to ckks_rotate. */
+int ckks_rotate_hoisted(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in,
+                        const int32_t* steps, size_t n_steps, ckks_ct** outs);
+
+/* ------------------------------------------------------------ encrypted KAN
+ * One KAN layer (paper, Method): n_in -> n_out with a uniform grid of G
+ * intervals on [grid_lo, grid_hi] and order-k B-splines (Eqs. 1-4), spline
+ * coefficients coef[o][i][m] (m < G+k), spline scaler w_s[o][i] and base
+ * weights w_b[o][i]; the HE-friendly parameters are the comparison bound R
+ * (Algorithm 2), the SiLU polynomial (Eqs. 11-12) as Chebyshev coefficients
+ * on [silu_lo, silu_hi], and the comparison composite f_{comp[0]} o ... as
+ * the orders n of f_n(x) = sum_i 4^-i C(2i,i) x (1-x^2)^i. All arrays are
+ * row-major doubles, copied at model creation. */
+typedef struct {
+  int n_in, n_out, G, k;
+  double grid_lo, grid_hi;
+  const double* coef;
+  const double* w_s;
+  const double* w_b;
+  double R;
+  double silu_lo, silu_hi;
+  const double* silu_cheb;
+  int silu_degree;
+  const int* comp;
+  int n_comp;
+} kan_layer_desc;
+
+int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layers,
+                     kan_model** out);
+int kan_model_destroy(kan_model* model);
+/* Rotation steps the schedule uses (pass them to ckks_keygen); *n receives
+ * the count; at most cap are written. */
+int kan_model_rotations(const kan_model* model, int32_t* steps, size_t cap, size_t* n);
+/* Multiplicative depth (levels consumed) of one layer. */
+int kan_model_layer_depth(const kan_model* model, int layer, int* depth);
+/* One layer on a batch: repeat packing (Algorithm 1), B-spline basis
+ * (Algorithm 2), fused linear layer W_f = W'P (Algorithm 3, Eq. 13) and the
+ * polynomial SiLU branch, both linear maps by BSGS diagonal matvec with
+ * hoisted rotations. Output slots [0, n_out). */
+int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int layer,
+                   const ckks_ct* in, ckks_ct** out);
+/* Whole network on n_in input handles (batches, any levels): inputs are moved
+ * to the lowest level, concatenated into one batch and evaluated together. */
+int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model,
+              const ckks_ct* const* in, size_t n_in, ckks_ct** out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,333 @@
+"""ctypes binding of the C ABI in include/ckks_kan.h (argument marshalling only).
+
+Every computation runs in `libckks_kan.so`; this module converts numpy
+arrays to pointers and error codes to exceptions. Loading fails loudly if
+the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libckks_kan.so")
+
+_lib = None
+
+c_u64, c_i64, c_i32, c_dbl, c_vp, c_sz = (ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t)
+PP = ctypes.POINTER(ctypes.c_void_p)
+
+
+class KanLayerDesc(ctypes.Structure):
+    _fields_ = [("n_in", c_i32), ("n_out", c_i32), ("G", c_i32), ("k", c_i32),
+                ("grid_lo", c_dbl), ("grid_hi", c_dbl),
+                ("coef", c_vp), ("w_s", c_vp), ("w_b", c_vp),
+                ("R", c_dbl), ("silu_lo", c_dbl), ("silu_hi", c_dbl),
+                ("silu_cheb", c_vp), ("silu_degree", c_i32),
+                ("comp", c_vp), ("n_comp", c_i32)]
+
+
+SIGNATURES = {
+    "ckks_strerror": (ctypes.c_char_p, [c_i32]),
+    "ckks_last_error": (ctypes.c_char_p, []),
+    "ckks_context_create": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, PP]),
+    "ckks_context_destroy": (c_i32, [c_vp]),
+    "ckks_context_info": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "ckks_set_stream": (c_i32, [c_vp, c_vp]),
+    "ckks_synchronize": (c_i32, [c_vp]),
+    "ckks_ntt": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_i32]),
+    "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
+    "ckks_keys_destroy": (c_i32, [c_vp]),
+    "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
+    "ckks_keys_export_switch": (c_i32, [c_vp, c_u64, c_vp, c_sz]),
+    "ckks_galois_element": (c_u64, [c_vp, ctypes.c_int32]),
+    "ckks_encrypt": (c_i32, [c_vp, c_vp, c_vp, c_sz, c_sz, c_i32, c_u64, c_u64, PP]),
+    "ckks_decrypt": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz]),
+    "ckks_ct_info": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "ckks_ct_export": (c_i32, [c_vp, c_vp, c_sz]),
+    "ckks_ct_import": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_dbl, PP]),
+    "ckks_ct_slice": (c_i32, [c_vp, c_vp, c_sz, c_sz, PP]),
+    "ckks_ct_destroy": (c_i32, [c_vp]),
+    "ckks_add": (c_i32, [c_vp, c_vp, c_vp, PP]),
+    "ckks_sub": (c_i32, [c_vp, c_vp, c_vp, PP]),
+    "ckks_mul_relin": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
+    "ckks_rescale": (c_i32, [c_vp, c_vp, PP]),
+    "ckks_mul": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
+    "ckks_mul_plain": (c_i32, [c_vp, c_vp, c_vp, c_sz, PP]),
+    "ckks_add_plain": (c_i32, [c_vp, c_vp, c_vp, c_sz, PP]),
+    "ckks_mul_const": (c_i32, [c_vp, c_vp, c_dbl, PP]),
+    "ckks_add_const": (c_i32, [c_vp, c_vp, c_dbl, PP]),
+    "ckks_level_down": (c_i32, [c_vp, c_vp, c_i32, PP]),
+    "ckks_rotate": (c_i32, [c_vp, c_vp, c_vp, ctypes.c_int32, PP]),
+    "ckks_rotate_hoisted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "kan_model_create": (c_i32, [c_vp, c_vp, c_sz, PP]),
+    "kan_model_destroy": (c_i32, [c_vp]),
+    "kan_model_rotations": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
+    "kan_model_layer_depth": (c_i32, [c_vp, c_i32, c_vp]),
+    "kan_layer_eval": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, PP]),
+    "kan_infer": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, PP]),
+}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libckks_kan.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class CkksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (lib().ckks_strerror(code).decode(), code, msg))
+        self.code = code
+
+
+def check(rc):
+    if rc != 0:
+        raise CkksError(rc, lib().ckks_last_error().decode())
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+class Context:
+    def __init__(self, log_n, n_scale, n_special, q0_bits=60, scale_bits=40, p_bits=60, device=0):
+        h = c_vp()
+        check(lib().ckks_context_create(log_n, q0_bits, scale_bits, n_scale, p_bits, n_special,
+                                        device, ctypes.byref(h)))
+        self.h = h
+        self.log_n, self.N, self.slots = log_n, 1 << log_n, 1 << (log_n - 1)
+        self.L, self.alpha = n_scale, n_special
+        n = ctypes.c_int()
+        check(lib().ckks_context_info(h, None, None, ctypes.byref(n)))
+        self.n_qp = n.value
+        self.moduli = np.zeros(self.n_qp, np.uint64)
+        self.delta = np.zeros(self.L + 1)
+        check(lib().ckks_context_info(h, _p(self.moduli), _p(self.delta), None))
+        self.beta_max = (self.L + 1 + self.alpha - 1) // self.alpha
+
+    def close(self):
+        if self.h:
+            lib().ckks_context_destroy(self.h)
+            self.h = None
+
+    def synchronize(self):
+        check(lib().ckks_synchronize(self.h))
+
+    def set_stream(self, stream_ptr):
+        check(lib().ckks_set_stream(self.h, stream_ptr))
+
+    def galois(self, step):
+        return int(lib().ckks_galois_element(self.h, int(step)))
+
+    def ntt(self, dev_ptr, n_rows, limbs, inverse=False):
+        check(lib().ckks_ntt(self.h, dev_ptr, n_rows, limbs, 1 if inverse else 0))
+
+
+class Keys:
+    def __init__(self, ctx, seed, rot_steps=()):
+        steps = np.ascontiguousarray(list(rot_steps), dtype=np.int32)
+        h = c_vp()
+        check(lib().ckks_keygen(ctx.h, seed, _p(steps) if len(steps) else None, len(steps),
+                                ctypes.byref(h)))
+        self.h, self.ctx = h, ctx
+
+    def close(self):
+        if self.h:
+            lib().ckks_keys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export_secret(self):
+        out = np.zeros((self.ctx.n_qp, self.ctx.N), np.uint64)
+        check(lib().ckks_keys_export_secret(self.h, _p(out), out.size))
+        return out
+
+    def export_switch(self, galois=0):
+        out = np.zeros((self.ctx.beta_max, 2, self.ctx.n_qp, self.ctx.N), np.uint64)
+        check(lib().ckks_keys_export_switch(self.h, galois, _p(out), out.size))
+        return out
+
+
+class Ciphertext:
+    """Owns a ckks_ct handle: a batch of B ciphertexts at one level."""
+
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+        B, lv, sc = c_sz(), ctypes.c_int(), c_dbl()
+        check(lib().ckks_ct_info(h, ctypes.byref(B), ctypes.byref(lv), ctypes.byref(sc)))
+        self.batch, self.level, self.scale = B.value, lv.value, sc.value
+
+    def close(self):
+        if self.h:
+            lib().ckks_ct_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self):
+        out = np.zeros((self.batch, 2, self.level + 1, self.ctx.N), np.uint64)
+        check(lib().ckks_ct_export(self.h, _p(out), out.size))
+        return out
+
+    @staticmethod
+    def import_(ctx, data, level, scale):
+        data = np.ascontiguousarray(data, dtype=np.uint64)
+        if data.ndim == 3:
+            data = data[None]
+        h = c_vp()
+        check(lib().ckks_ct_import(ctx.h, _p(data), data.shape[0], level, scale, ctypes.byref(h)))
+        return Ciphertext(ctx, h)
+
+    def slice(self, first, count):
+        h = c_vp()
+        check(lib().ckks_ct_slice(self.ctx.h, self.h, first, count, ctypes.byref(h)))
+        return Ciphertext(self.ctx, h)
+
+
+def _out(ctx, fn, *args):
+    h = c_vp()
+    check(fn(*args, ctypes.byref(h)))
+    return Ciphertext(ctx, h)
+
+
+def encrypt(ctx, keys, values, level, seed, first_index=0):
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    if v.ndim == 1:
+        v = v[None]
+    return _out(ctx, lib().ckks_encrypt, ctx.h, keys.h, _p(v), v.shape[0], v.shape[1], level,
+                seed, first_index)
+
+
+def decrypt(ctx, keys, ct, n=None):
+    n = ctx.slots if n is None else n
+    out = np.zeros((ct.batch, n))
+    check(lib().ckks_decrypt(ctx.h, keys.h, ct.h, _p(out), n))
+    return out
+
+
+def add(ctx, a, b):
+    return _out(ctx, lib().ckks_add, ctx.h, a.h, b.h)
+
+
+def sub(ctx, a, b):
+    return _out(ctx, lib().ckks_sub, ctx.h, a.h, b.h)
+
+
+def mul_relin(ctx, keys, a, b):
+    return _out(ctx, lib().ckks_mul_relin, ctx.h, keys.h, a.h, b.h)
+
+
+def rescale(ctx, a):
+    return _out(ctx, lib().ckks_rescale, ctx.h, a.h)
+
+
+def mul(ctx, keys, a, b):
+    return _out(ctx, lib().ckks_mul, ctx.h, keys.h, a.h, b.h)
+
+
+def mul_plain(ctx, a, v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return _out(ctx, lib().ckks_mul_plain, ctx.h, a.h, _p(v), len(v))
+
+
+def add_plain(ctx, a, v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return _out(ctx, lib().ckks_add_plain, ctx.h, a.h, _p(v), len(v))
+
+
+def mul_const(ctx, a, c):
+    return _out(ctx, lib().ckks_mul_const, ctx.h, a.h, float(c))
+
+
+def add_const(ctx, a, c):
+    return _out(ctx, lib().ckks_add_const, ctx.h, a.h, float(c))
+
+
+def level_down(ctx, a, level):
+    return _out(ctx, lib().ckks_level_down, ctx.h, a.h, int(level))
+
+
+def rotate(ctx, keys, a, step):
+    return _out(ctx, lib().ckks_rotate, ctx.h, keys.h, a.h, int(step))
+
+
+def rotate_hoisted(ctx, keys, a, steps):
+    s = np.ascontiguousarray(list(steps), dtype=np.int32)
+    hs = (c_vp * len(s))()
+    check(lib().ckks_rotate_hoisted(ctx.h, keys.h, a.h, _p(s), len(s), hs))
+    return [Ciphertext(ctx, c_vp(h)) for h in hs]
+
+
+class Model:
+    """kan_model handle; `layers` are dicts as produced for the plaintext KAN
+    plus the HE keys R, silu_lo, silu_hi, silu_cheb and comp."""
+
+    def __init__(self, ctx, layers):
+        self.ctx = ctx
+        self._keep = []
+        descs = (KanLayerDesc * len(layers))()
+        for d, L in zip(descs, layers):
+            arrs = [np.ascontiguousarray(L[k], dtype=np.float64) for k in ("coef", "w_s", "w_b", "silu_cheb")]
+            comp = np.ascontiguousarray(L["comp"], dtype=np.int32)
+            self._keep += arrs + [comp]
+            d.n_in, d.n_out, d.G, d.k = L["n_in"], L["n_out"], L["G"], L["k"]
+            d.grid_lo, d.grid_hi = L["lo"], L["hi"]
+            d.coef, d.w_s, d.w_b = _p(arrs[0]), _p(arrs[1]), _p(arrs[2])
+            d.R, d.silu_lo, d.silu_hi = L["R"], L["silu_lo"], L["silu_hi"]
+            d.silu_cheb, d.silu_degree = _p(arrs[3]), len(arrs[3]) - 1
+            d.comp, d.n_comp = _p(comp), len(comp)
+        h = c_vp()
+        check(lib().kan_model_create(ctx.h, descs, len(layers), ctypes.byref(h)))
+        self.h = h
+        self.n_layers = len(layers)
+
+    def close(self):
+        if self.h:
+            lib().kan_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rotations(self):
+        n = c_sz()
+        check(lib().kan_model_rotations(self.h, None, 0, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1), np.int32)
+        check(lib().kan_model_rotations(self.h, _p(out), len(out), ctypes.byref(n)))
+        return [int(x) for x in out[: n.value]]
+
+    def layer_depth(self, layer):
+        d = ctypes.c_int()
+        check(lib().kan_model_layer_depth(self.h, layer, ctypes.byref(d)))
+        return d.value
+
+
+def kan_layer_eval(ctx, keys, model, layer, ct):
+    return _out(ctx, lib().kan_layer_eval, ctx.h, keys.h, model.h, int(layer), ct.h)
+
+
+def kan_infer(ctx, keys, model, cts):
+    hs = (c_vp * len(cts))(*[c.h.value if isinstance(c.h, c_vp) else c.h for c in cts])
+    return _out(ctx, lib().kan_infer, ctx.h, keys.h, model.h, hs, len(cts))

@@ -1,0 +1,281 @@
+// Elementwise kernels over ciphertext batches laid out [rows][N], where
+// row r belongs to RNS limb t = r % l (l limbs per polynomial).
+#include "modarith.cuh"
+
+namespace ck {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(size_t total) {
+  size_t g = (total + TPB - 1) / TPB;
+  const size_t cap = 152 * 32;
+  return (unsigned)(g < cap ? (g ? g : 1) : cap);
+}
+
+#define GRID_LOOP(idx, total) \
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (total); idx += (size_t)gridDim.x * blockDim.x)
+
+__global__ void add_kernel(const uint64_t* a, const uint64_t* b, uint64_t* out, size_t total,
+                           int log_n, int l, const Mod* mods, bool sub) {
+  GRID_LOOP(i, total) {
+    const int t = (int)((i >> log_n) % l);
+    const uint64_t q = mods[t].q;
+    out[i] = sub ? sub_mod(a[i], b[i], q) : add_mod(a[i], b[i], q);
+  }
+}
+
+__global__ void mul_pt_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t total,
+                              int log_n, int l, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, total) {
+    const size_t row = i >> log_n;
+    const int t = (int)(row % l);
+    out[i] = mul_mod(a[i], pt[(size_t)t * N + (i & (N - 1))], mods[t]);
+  }
+}
+
+struct Consts {
+  int64_t c[32];
+};
+
+__global__ void mul_int_kernel(const uint64_t* a, int64_t k, uint64_t* out, size_t total,
+                               int log_n, int l, const Mod* mods) {
+  GRID_LOOP(i, total) {
+    const int t = (int)((i >> log_n) % l);
+    out[i] = mul_mod(a[i], smod64(k, mods[t].q), mods[t]);
+  }
+}
+
+// poly 0 of each batch element += k (a constant polynomial is constant in NTT form)
+__global__ void add_int_c0_kernel(uint64_t* a, int64_t k, size_t B, int log_n, int l,
+                                  const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = (size_t)l * N;
+  GRID_LOOP(i, B * per) {
+    const size_t b = i / per, r = i % per;
+    const int t = (int)(r >> log_n);
+    uint64_t* p = a + b * 2 * per + r;
+    *p = add_mod(*p, smod64(k, mods[t].q), mods[t].q);
+  }
+}
+
+__global__ void add_pt_c0_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t B,
+                                 int log_n, int l, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = (size_t)l * N;
+  GRID_LOOP(i, B * 2 * per) {
+    const size_t b = i / (2 * per), r = i % (2 * per);
+    if (r < per) {
+      const int t = (int)(r >> log_n);
+      out[i] = add_mod(a[i], pt[r], mods[t].q);
+    } else {
+      out[i] = a[i];
+    }
+    (void)b;
+  }
+}
+
+// (a0, a1) x (b0, b1) -> (a0 b0, a0 b1 + a1 b0, a1 b1)
+__global__ void tensor_kernel(const uint64_t* a, const uint64_t* b, uint64_t* out, size_t B,
+                              int log_n, int l, const Mod* mods, bool acc) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = (size_t)l * N;
+  GRID_LOOP(i, B * per) {
+    const size_t bb = i / per, r = i % per;
+    const int t = (int)(r >> log_n);
+    const Mod m = mods[t];
+    const uint64_t* pa = a + bb * 2 * per + r;
+    const uint64_t* pb = b + bb * 2 * per + r;
+    const uint64_t a0 = pa[0], a1 = pa[per], b0 = pb[0], b1 = pb[per];
+    uint64_t d0 = mul_mod(a0, b0, m);
+    uint64_t d1 = add_mod(mul_mod(a0, b1, m), mul_mod(a1, b0, m), m.q);
+    uint64_t d2 = mul_mod(a1, b1, m);
+    uint64_t* po = out + bb * 3 * per + r;
+    if (acc) {
+      d0 = add_mod(d0, po[0], m.q);
+      d1 = add_mod(d1, po[per], m.q);
+      d2 = add_mod(d2, po[2 * per], m.q);
+    }
+    po[0] = d0;
+    po[per] = d1;
+    po[2 * per] = d2;
+  }
+}
+
+struct Ptrs {
+  const uint64_t* p[32];
+};
+
+__global__ void lincomb_kernel(Ptrs in, Consts k, int K, uint64_t* out, size_t total, int log_n,
+                               int l, const Mod* mods) {
+  GRID_LOOP(i, total) {
+    const int t = (int)((i >> log_n) % l);
+    const Mod m = mods[t];
+    uint64_t acc = 0;
+    for (int j = 0; j < K; j++) acc = add_mod(acc, mul_mod(in.p[j][i], smod64(k.c[j], m.q), m), m.q);
+    out[i] = acc;
+  }
+}
+
+__global__ void automorphism_kernel(const uint64_t* in, uint64_t* out, size_t total, int log_n,
+                                    const uint32_t* perm) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, total) {
+    const size_t row = i >> log_n;
+    out[i] = in[row * N + perm[i & (N - 1)]];
+  }
+}
+
+// out = (sigma(a0) + ks0, ks1) per batch element
+__global__ void rotate_finish_kernel(const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
+                                     uint64_t* out, size_t B, int log_n, int l, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = (size_t)l * N;
+  GRID_LOOP(i, B * per) {
+    const size_t b = i / per, r = i % per;
+    const int t = (int)(r >> log_n);
+    const size_t row0 = b * 2 * per + (r & ~(N - 1));
+    const uint64_t src = a[row0 + perm[r & (N - 1)]];
+    out[b * 2 * per + r] = add_mod(src, ks[b * 2 * per + r], mods[t].q);
+    out[b * 2 * per + per + r] = ks[b * 2 * per + per + r];
+  }
+}
+
+// R[p][t][n] = centred(last[p][n]) mod q_t, t < level (last limb mod q_level)
+__global__ void rescale_spread_kernel(const uint64_t* last, uint64_t* out, size_t polys,
+                                      int log_n, int level, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const uint64_t ql = mods[level].q;
+  GRID_LOOP(i, polys * level * N) {
+    const size_t p = i / ((size_t)level * N);
+    const size_t r = i % ((size_t)level * N);
+    const int t = (int)(r >> log_n);
+    const uint64_t x = last[p * N + (r & (N - 1))];
+    const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
+    out[i] = smod64(v, mods[t].q);
+  }
+}
+
+// out[p][t] = (in[p][t] - R[p][t]) * q_level^-1 mod q_t
+__global__ void rescale_finish_kernel(const uint64_t* in, const uint64_t* R, uint64_t* out,
+                                      size_t polys, int log_n, int level, const Mod* mods,
+                                      const uint64_t* inv, const uint64_t* invs) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, polys * level * N) {
+    const size_t p = i / ((size_t)level * N);
+    const size_t r = i % ((size_t)level * N);
+    const int t = (int)(r >> log_n);
+    const uint64_t q = mods[t].q;
+    const uint64_t x = in[p * (size_t)(level + 1) * N + r];
+    out[i] = mul_shoup(sub_mod(x, R[i], q), inv[t], invs[t], q);
+  }
+}
+
+__global__ void int_to_rns_kernel(const int64_t* v, uint64_t* out, size_t polys, int rows,
+                                  int log_n, const int16_t* pattern, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, polys * rows * N) {
+    const size_t p = i / ((size_t)rows * N);
+    const size_t r = (i / N) % rows;
+    const int mi = pattern[r];
+    out[i] = smod64(v[p * N + (i & (N - 1))], mods[mi].q);
+  }
+}
+
+}  // namespace
+
+void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,
+           bool sub) {
+  const size_t total = rows * c.N;
+  add_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, b, out, total, c.log_n, l, c.dmod(), sub);
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_mul_pt(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t rows, int l) {
+  const size_t total = rows * c.N;
+  mul_pt_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, out, total, c.log_n, l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows, int l) {
+  const size_t total = rows * c.N;
+  mul_int_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, k, out, total, c.log_n, l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l) {
+  add_int_c0_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, k, B, c.log_n, l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_add_pt_c0(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t B, int l) {
+  add_pt_c0_kernel<<<grid_for(B * 2 * l * c.N), TPB, 0, c.stream>>>(a, pt, out, B, c.log_n, l,
+                                                                     c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_tensor(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t B, int l,
+              bool accumulate) {
+  tensor_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, b, out, B, c.log_n, l, c.dmod(),
+                                                             accumulate);
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::vector<int64_t>& k,
+                   uint64_t* out, size_t rows, int l) {
+  if (in.size() > 32 || in.size() != k.size() || in.empty())
+    throw Error(CKKS_ERR_INVALID_ARG, "lincomb: 1..32 terms");
+  Ptrs P{};
+  Consts C{};
+  for (size_t j = 0; j < in.size(); j++) {
+    P.p[j] = in[j];
+    C.c[j] = k[j];
+  }
+  const size_t total = rows * c.N;
+  lincomb_kernel<<<grid_for(total), TPB, 0, c.stream>>>(P, C, (int)in.size(), out, total, c.log_n,
+                                                        l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_copy_limbs(Ctx& c, const uint64_t* in, int l_in, uint64_t* out, int l_out, size_t polys) {
+  const size_t w = (size_t)l_out * c.N * 8;
+  CK_CUDA(cudaMemcpy2DAsync(out, w, in, (size_t)l_in * c.N * 8, w, polys, cudaMemcpyDeviceToDevice,
+                            c.stream));
+}
+
+void k_automorphism(Ctx& c, const uint64_t* in, uint64_t* out, size_t rows, const uint32_t* perm) {
+  const size_t total = rows * c.N;
+  automorphism_kernel<<<grid_for(total), TPB, 0, c.stream>>>(in, out, total, c.log_n, perm);
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
+                     uint64_t* out, size_t B, int l) {
+  rotate_finish_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, ks, perm, out, B, c.log_n,
+                                                                    l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_rescale_spread(Ctx& c, const uint64_t* last, uint64_t* out, size_t polys, int level) {
+  rescale_spread_kernel<<<grid_for(polys * level * c.N), TPB, 0, c.stream>>>(last, out, polys,
+                                                                            c.log_n, level, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,
+                      int level, const uint64_t* inv, const uint64_t* invs) {
+  rescale_finish_kernel<<<grid_for(polys * level * c.N), TPB, 0, c.stream>>>(
+      in, r, out, polys, c.log_n, level, c.dmod(), inv, invs);
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_int_to_rns(Ctx& c, const int64_t* v, uint64_t* out, size_t polys, int rows,
+                  const int16_t* pattern) {
+  int_to_rns_kernel<<<grid_for(polys * rows * c.N), TPB, 0, c.stream>>>(v, out, polys, rows,
+                                                                       c.log_n, pattern, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+}  // namespace ck

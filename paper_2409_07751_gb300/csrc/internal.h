@@ -1,0 +1,171 @@
+// Internal types of the GB300 RNS-CKKS library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ckks_kan.h"
+
+namespace ck {
+
+// Per-modulus constants visible to kernels.
+struct Mod {
+  uint64_t q;
+  uint64_t mu;  // floor(2^(2s) / q), Barrett
+  uint32_t s;   // bit length of q
+  uint32_t pad;
+};
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char* what);
+#define CK_CUDA(x) ::ck::cuda_check((x), #x)
+
+struct Ctx;
+
+// Stream-ordered device allocation owned by a context.
+struct DevBuf {
+  Ctx* ctx = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(Ctx* c, size_t b);
+  ~DevBuf();
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept;
+  uint64_t* u64() const { return static_cast<uint64_t*>(p); }
+  void reset();
+};
+
+// Basis-conversion tables of one level (ModUp for every digit, ModDown).
+struct ConvTables {
+  int l = 0, beta = 0, rows = 0;  // rows = l + alpha
+  // ModUp: for digit j, local a < alpha: v = [x * Dhat^-1]_{q}; then for
+  // target row r: acc += v * [Dhat]_{m_r}.
+  DevBuf dhinv, dhinv_s;   // [beta][alpha]
+  DevBuf dh, dh_s;         // [beta][alpha][rows]
+  DevBuf ext_pattern;      // int16 [beta*rows]: modulus index of the row, -1 = digit row
+  DevBuf pq_pattern;       // int16 [rows]: -1 for Q rows, special modulus for P rows
+  DevBuf md_pinv, md_pinv_s;  // [l]: P^-1 mod q_i
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int log_n = 0;
+  uint64_t N = 0;
+  int L = 0, alpha = 0, n_qp = 0, beta_max = 0;
+  std::vector<uint64_t> mod, psi;
+  std::vector<double> delta;
+  // device tables
+  DevBuf d_mod;             // Mod[n_qp]
+  DevBuf d_tw, d_tws;       // [n_qp][N] psi^brv(k) and Shoup companions
+  DevBuf d_itw, d_itws;     // inverse
+  DevBuf d_ninv, d_ninvs;   // [n_qp]
+  DevBuf d_iota;            // int16 [n_qp]: 0..n_qp-1
+  DevBuf d_fft;             // double [2N][2]: cos, sin of 2 pi k / 2N
+  DevBuf d_slot;            // uint32 [N/2]: k_j = (5^j mod 2N - 1) / 4
+  DevBuf d_md_yinv, d_md_yinv_s;  // [alpha]: Phat_a^-1 mod p_a
+  DevBuf d_md_ph, d_md_ph_s;      // [alpha][L+1]: Phat_a mod q_i
+  std::map<int, std::unique_ptr<ConvTables>> conv;
+  std::map<uint64_t, std::unique_ptr<DevBuf>> perms;  // galois -> uint32[N]
+  DevBuf d_flag;            // int32 device status word (encoding overflow)
+  DevBuf d_rs_inv, d_rs_invs;     // [(L+1)][(L+1)]: q_l^-1 mod q_t at [l][t]
+  DevBuf d_pmod;                  // [L+1]: P mod q_t
+
+  ~Ctx();
+  const Mod* dmod() const { return static_cast<const Mod*>(d_mod.p); }
+  const int16_t* iota() const { return static_cast<const int16_t*>(d_iota.p); }
+  ConvTables& tables(int level);
+  const uint32_t* perm(uint64_t galois);
+  uint64_t galois(int64_t step) const;
+};
+
+}  // namespace ck
+
+// ABI handle types
+struct ckks_ctx {
+  ck::Ctx c;
+};
+
+struct ckks_keys {
+  ck::Ctx* ctx;
+  ck::DevBuf s;                                   // [n_qp][N] NTT form
+  ck::DevBuf relin;                               // [beta_max][2][n_qp][N]
+  std::map<uint64_t, std::unique_ptr<ck::DevBuf>> galois;
+};
+
+struct ckks_ct {
+  ck::Ctx* ctx;
+  ck::DevBuf d;  // [B][2][level+1][N]
+  size_t B;
+  int level;
+  double scale;
+  size_t words() const { return B * 2 * (size_t)(level + 1) * ctx->N; }
+};
+
+namespace ck {
+
+// ---- host helpers (context.cu)
+uint64_t mulmod_h(uint64_t a, uint64_t b, uint64_t q);
+uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t q);
+uint64_t invmod_h(uint64_t a, uint64_t q);
+uint64_t shoup_h(uint64_t w, uint64_t q);
+Mod make_mod(uint64_t q);
+bool is_prime_h(uint64_t n);
+int gen_chain(int log_n, int q0_bits, int scale_bits, int n_scale, int p_bits, int n_special,
+              std::vector<uint64_t>& mod, std::vector<double>& delta);
+void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p_bits,
+              int n_special, int device);
+
+// ---- NTT (ntt.cu): rows r at base + r*N use modulus pattern[r % P]; a
+// negative pattern entry skips the row.
+void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P);
+void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P);
+
+// ---- elementwise (elementwise.cu). Ciphertext batches are [B][polys][l][N].
+void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,
+           bool sub);
+void k_mul_pt(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t rows, int l);
+void k_add_pt_c0(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t B, int l);
+void k_tensor(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t B, int l,
+              bool accumulate);
+void k_copy_limbs(Ctx& c, const uint64_t* in, int l_in, uint64_t* out, int l_out, size_t polys);
+void k_automorphism(Ctx& c, const uint64_t* in, uint64_t* out, size_t rows, const uint32_t* perm);
+void k_rescale_spread(Ctx& c, const uint64_t* last, uint64_t* out, size_t polys, int level);
+void k_int_to_rns(Ctx& c, const int64_t* v, uint64_t* out, size_t polys, int rows,
+                  const int16_t* pattern);
+
+// ---- key switching (keyswitch.cu)
+// d: [B][l][N] NTT; ext out: [B][beta][l+alpha][N] NTT.
+void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext);
+// out[B][2][l][N] = ModDown(<sigma_g(ext), key>); galois 0 = no automorphism.
+void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
+                   uint64_t galois, uint64_t* out);
+
+// ---- encoding (encode.cu)
+// v: device doubles [B][nv]; writes pt [B][level+1][N] at `scale`. Returns
+// CKKS_ERR_OVERFLOW if a coefficient does not fit int64.
+int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double scale, uint64_t* pt);
+// m: [B][N] limb-0 coefficient values (uint64 mod q0); out: device doubles [B][nv]
+void decode_limb0(Ctx& c, const uint64_t* m, size_t B, double scale, double* d_out, size_t nv);
+
+// ---- sampling (sample.cu)
+void sample_ternary(Ctx& c, uint64_t seed, int64_t* out);
+void sample_cbd(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int64_t* out);
+void sample_uniform(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int rows,
+                    const int16_t* pattern, uint64_t* out);
+
+}  // namespace ck

@@ -1,0 +1,571 @@
+// Encrypted KAN layer schedule (paper, Method section).
+//
+//  SiLU branch (Eqs. 11-12): y = x (x) (mask * 2/(hi-lo)) + mask * (-(hi+lo)/(hi-lo)),
+//    replicated to the matvec period, the Chebyshev polynomial by baby/giant
+//    steps, then W_b by BSGS.
+//  Spline branch: Algorithm 1 (mask with 1/(2R) folded in, then doubling
+//    rotations by -n_i 2^(j-1)), Algorithm 2 (PolyComp through the composite
+//    f_n o ... whose last stage returns (1+f)/2, B0 = x1 (x) x2, k recursion
+//    steps sharing one relinearisation each), then W_f = W'P (Algorithm 3,
+//    Eq. 13) by BSGS.
+//  Output: both branches moved to the lower level and added.
+// Plaintext vectors are encoded once per (tag, level, scale) and cached on
+// the device; a batch shares them.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <functional>
+#include <set>
+#include <tuple>
+
+#include "ops.h"
+
+using namespace ck;
+
+namespace {
+
+int pow2ceil(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+struct Plan {
+  int no = 1, npad = 1, g1 = 1, g2 = 1;
+  std::vector<int> folds;
+};
+
+Plan bsgs_plan(int n_out, int n, int slots) {
+  Plan p;
+  p.no = pow2ceil(n_out);
+  p.npad = pow2ceil(std::max(n, p.no));
+  if (p.npad > slots) throw Error(CKKS_ERR_UNSUPPORTED, "matrix does not fit the slots");
+  int lg = 0;
+  while ((1 << lg) < p.no) lg++;
+  p.g1 = 1 << ((lg + 1) / 2);
+  p.g2 = p.no / p.g1;
+  for (int s = p.npad / 2; s >= p.no; s /= 2) p.folds.push_back(s);
+  return p;
+}
+
+// odd monomial coefficients of f_n(x) = sum_i 4^-i C(2i,i) x (1-x^2)^i
+std::vector<double> fn_coeffs(int n) {
+  auto C = [](int a, int b) {
+    int64_t r = 1;
+    for (int i = 1; i <= b; i++) r = r * (a - b + i) / i;
+    return r;
+  };
+  std::vector<double> c(n + 1);
+  for (int l = 0; l <= n; l++) {
+    int64_t num = 0;
+    for (int i = l; i <= n; i++) num += C(2 * i, i) * C(i, l) * ((int64_t)1 << (2 * (n - i)));
+    if (l & 1) num = -num;
+    c[l] = (double)num / (double)((int64_t)1 << (2 * n));
+  }
+  return c;
+}
+
+struct Layer {
+  int n_in, n_out, G, k;
+  double lo, hi, R, silu_lo, silu_hi;
+  std::vector<double> coef, w_s, w_b, cheb, knots, Wf;
+  std::vector<int> comp;
+  Plan plan_b, plan_s;
+  std::vector<double> diag_b, diag_s;  // [no][slots]
+};
+
+}  // namespace
+
+struct kan_model {
+  Ctx* ctx;
+  std::vector<Layer> layers;
+  std::map<std::tuple<int, int, int, int, uint64_t>, std::unique_ptr<DevBuf>> pts;
+};
+
+namespace {
+
+uint64_t dbits(double d) {
+  uint64_t u;
+  memcpy(&u, &d, 8);
+  return u;
+}
+
+// cached plaintext of make() at (layer, tag, sub, level, scale)
+template <class F>
+const uint64_t* cached_pt(kan_model& M, int layer, int tag, int sub, int level, double scale,
+                          F&& make) {
+  auto key = std::make_tuple(layer * 1000 + tag, sub, level, 0, dbits(scale));
+  auto it = M.pts.find(key);
+  if (it != M.pts.end()) return it->second->u64();
+  std::vector<double> v = make();
+  auto b = std::make_unique<DevBuf>(encode_vec(*M.ctx, v.data(), v.size(), level, scale));
+  const uint64_t* p = b->u64();
+  M.pts[key] = std::move(b);
+  return p;
+}
+
+std::vector<double> coltile(const Layer& L, int l, int r) {
+  // G matrix rows are identical knot vectors (uniform grid); columns l..r-1, 1-indexed
+  std::vector<double> out;
+  for (int c = l; c < r; c++)
+    for (int i = 0; i < L.n_in; i++) out.push_back(L.knots[c - 1]);
+  return out;
+}
+
+std::vector<double> diagonals(const std::vector<double>& M, int n_out, int n, const Plan& p,
+                              int slots) {
+  std::vector<double> Mp((size_t)p.no * p.npad, 0.0);
+  for (int o = 0; o < n_out; o++)
+    for (int i = 0; i < n; i++) Mp[(size_t)o * p.npad + i] = M[(size_t)o * n + i];
+  std::vector<double> D((size_t)p.no * slots, 0.0);
+  for (int t = 0; t < p.no; t++)
+    for (int s = 0; s < p.npad; s++)
+      D[(size_t)t * slots + s] = Mp[(size_t)(s % p.no) * p.npad + (s + t) % p.npad];
+  return D;
+}
+
+enum Tag { T_SILU_MUL = 1, T_SILU_ADD, T_MASK_R, T_G1, T_G2, T_U1M, T_U1A, T_U2M, T_U2A, T_DIAG_B, T_DIAG_S };
+
+Ct bsgs_matvec(kan_model& M, int li, bool spline, const ckks_keys& keys, const ckks_ct& v) {
+  Ctx& c = *M.ctx;
+  Layer& L = M.layers[li];
+  const Plan& p = spline ? L.plan_s : L.plan_b;
+  const std::vector<double>& D = spline ? L.diag_s : L.diag_b;
+  const int S = (int)(c.N / 2);
+  std::vector<int64_t> bs;
+  for (int j = 0; j < p.g1; j++) bs.push_back(j);
+  std::vector<Ct> baby = op_rotate_many(c, keys, v, bs);
+  const int lv = v.level;
+  const size_t rows = v.B * 2 * (lv + 1);
+  Ct z;
+  for (int i = 0; i < p.g2; i++) {
+    const double Spt = plain_scale(c, v.scale, lv);
+    Ct acc = ct_alloc(c, v.B, lv, v.scale * Spt);
+    Ct prod = ct_alloc(c, v.B, lv, v.scale * Spt);
+    for (int j = 0; j < p.g1; j++) {
+      const int t = p.g1 * i + j;
+      const uint64_t* pt = cached_pt(M, li, spline ? T_DIAG_S : T_DIAG_B, t, lv, Spt, [&] {
+        std::vector<double> d(S);
+        const int sh = p.g1 * i;
+        for (int s = 0; s < S; s++) d[s] = D[(size_t)t * S + ((s - sh) % S + S) % S];
+        return d;
+      });
+      k_mul_pt(c, baby[j]->d.u64(), pt, j == 0 ? acc->d.u64() : prod->d.u64(), rows, lv + 1);
+      if (j > 0) k_add(c, acc->d.u64(), prod->d.u64(), acc->d.u64(), rows, lv + 1, false);
+    }
+    Ct inner = op_rescale(c, *acc);
+    if (i > 0) inner = op_rotate(c, keys, *inner, (int64_t)p.g1 * i);
+    z = z ? op_add(c, *z, *inner, false) : std::move(inner);
+  }
+  for (int s : p.folds) {
+    Ct r = op_rotate(c, keys, *z, s);
+    z = op_add(c, *z, *r, false);
+  }
+  return z;
+}
+
+Ct eval_odd(Ctx& c, const ckks_keys& keys, const ckks_ct& u, const std::vector<double>& cf,
+            double cst) {
+  std::map<int, Ct> pw;
+  int need = 0;
+  for (size_t l = 0; l < cf.size(); l++)
+    if (cf[l] != 0.0) need = std::max(need, (int)(2 * l));
+  for (int b = 2; b <= need; b *= 2) {
+    const ckks_ct& h = b == 2 ? u : *pw[b / 2];
+    pw[b] = op_mul(c, keys, h, h);
+  }
+  std::vector<Ct> terms;
+  for (size_t l = 0; l < cf.size(); l++) {
+    if (cf[l] == 0.0) continue;
+    Ct T = op_mul_const(c, u, cf[l]);
+    int e = 2 * (int)l, b = 2;
+    while (e) {
+      if (e & b) {
+        T = op_mul(c, keys, *T, *pw[b]);
+        e ^= b;
+      }
+      b *= 2;
+    }
+    terms.push_back(std::move(T));
+  }
+  int lv = terms[0]->level;
+  for (auto& t : terms) lv = std::min(lv, t->level);
+  Ct out;
+  for (auto& t : terms) {
+    Ct d = op_level_down(c, *t, lv);
+    out = out ? op_add(c, *out, *d, false) : std::move(d);
+  }
+  if (cst != 0.0) out = op_add_const(c, *out, cst);
+  return out;
+}
+
+Ct polycomp0(Ctx& c, const ckks_keys& keys, const ckks_ct& a, const std::vector<int>& stages) {
+  Ct u;
+  const ckks_ct* cur = &a;
+  for (size_t s = 0; s < stages.size(); s++) {
+    std::vector<double> cf = fn_coeffs(stages[s]);
+    if (s + 1 == stages.size()) {
+      for (auto& x : cf) x = 0.5 * x;
+      u = eval_odd(c, keys, *cur, cf, 0.5);
+    } else {
+      u = eval_odd(c, keys, *cur, cf, 0.0);
+    }
+    cur = u.get();
+  }
+  return u;
+}
+
+Ct eval_cheb(Ctx& c, const ckks_keys& keys, const ckks_ct& y, const std::vector<double>& a) {
+  const int d = (int)a.size() - 1;
+  const int m = pow2ceil((int)ceil(sqrt((double)(d + 1))));
+  std::map<int, Ct> T;
+  T[1] = ct_copy(c, y);
+  for (int i = 2; i <= m; i++) {
+    if ((i & (i - 1)) == 0) {
+      Ct sq = op_mul(c, keys, *T[i / 2], *T[i / 2]);
+      T[i] = op_add_const(c, *op_mul_int(c, *sq, 2), -1.0);
+    } else {
+      int hb = 1;
+      while (hb * 2 <= i) hb *= 2;
+      const int lo = i - hb;
+      Ct pr = op_mul_int(c, *op_mul(c, keys, *T[hb], *T[lo]), 2);
+      if (hb - lo == 0)
+        T[i] = op_add_const(c, *pr, -1.0);
+      else
+        T[i] = op_add(c, *pr, *op_level_down(c, *T[hb - lo], pr->level), true);
+    }
+  }
+  std::map<int, Ct> Gs;
+  Gs[m] = ct_copy(c, *T[m]);
+  int D = m;
+  while (2 * D <= d) {
+    Ct sq = op_mul(c, keys, *Gs[D], *Gs[D]);
+    Gs[2 * D] = op_add_const(c, *op_mul_int(c, *sq, 2), -1.0);
+    D *= 2;
+  }
+  struct R {
+    Ct ct;
+    double v;
+  };
+  std::function<R(const std::vector<double>&)> rec = [&](const std::vector<double>& cf) -> R {
+    const int deg = (int)cf.size() - 1;
+    if (deg < m) {
+      if (deg == 0) return R{nullptr, cf[0]};
+      std::vector<const ckks_ct*> in;
+      std::vector<double> k;
+      for (int i = 1; i <= deg; i++) {
+        in.push_back(T[i].get());
+        k.push_back(cf[i]);
+      }
+      return R{op_lincomb(c, in, k, cf[0], -1), 0.0};
+    }
+    int Dd = m;
+    while (2 * Dd <= deg) Dd *= 2;
+    std::vector<double> q;
+    q.push_back(cf[Dd]);
+    for (int i = 1; i <= deg - Dd; i++) q.push_back(2.0 * cf[Dd + i]);
+    std::vector<double> r(cf.begin(), cf.begin() + Dd);
+    for (int i = 1; i <= deg - Dd; i++) r[Dd - i] -= cf[Dd + i];
+    R Q = rec(q);
+    R Rr = rec(r);
+    Ct P;
+    if (!Q.ct)
+      P = op_lincomb(c, {Gs[Dd].get()}, {Q.v}, 0.0, -1);
+    else
+      P = op_mul(c, keys, *Q.ct, *Gs[Dd]);
+    if (!Rr.ct) return R{op_add_const(c, *P, Rr.v), 0.0};
+    const int lv = std::min(P->level, Rr.ct->level);
+    return R{op_add(c, *op_level_down(c, *P, lv), *op_level_down(c, *Rr.ct, lv), false), 0.0};
+  };
+  R out = rec(a);
+  if (!out.ct) throw Error(CKKS_ERR_INVALID_ARG, "SiLU polynomial of degree 0");
+  return std::move(out.ct);
+}
+
+Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
+  Ctx& c = *M.ctx;
+  Layer& L = M.layers[li];
+  const int S = (int)(c.N / 2);
+  const int n_i = L.n_in, G = L.G, k = L.k;
+  const double R = L.R;
+  int J = 0;
+  while ((1 << J) < G + 2 * k) J++;
+  if ((int64_t)n_i << J > S) throw Error(CKKS_ERR_UNSUPPORTED, "n_i * 2^ceil(log2(g+2k)) > N/2");
+  if (x.level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+
+  // SiLU branch
+  const double sa = 2.0 / (L.silu_hi - L.silu_lo), sb = -(L.silu_hi + L.silu_lo) / (L.silu_hi - L.silu_lo);
+  const double S1 = plain_scale(c, x.scale, x.level);
+  const uint64_t* p_sm = cached_pt(M, li, T_SILU_MUL, 0, x.level, S1,
+                                   [&] { return std::vector<double>(n_i, sa * 1.0); });
+  Ct y0 = op_mul_pt(c, x, p_sm, S1);
+  const uint64_t* p_sa = cached_pt(M, li, T_SILU_ADD, 0, y0->level, y0->scale,
+                                   [&] { return std::vector<double>(n_i, sb * 1.0); });
+  Ct y = op_add_pt(c, *y0, p_sa);
+  if (L.plan_b.npad < S) y = op_add(c, *y, *op_rotate(c, keys, *y, -L.plan_b.npad), false);
+  Ct v = eval_cheb(c, keys, *y, L.cheb);
+  Ct yb = bsgs_matvec(M, li, false, keys, *v);
+
+  // Algorithm 1
+  const uint64_t* p_mr = cached_pt(M, li, T_MASK_R, 0, x.level, S1,
+                                   [&] { return std::vector<double>(n_i, 1.0 / (2.0 * R)); });
+  Ct xr = op_mul_pt(c, x, p_mr, S1);
+  for (int j = 1; j <= J; j++)
+    xr = op_add(c, *xr, *op_rotate(c, keys, *xr, -(int64_t)n_i * (1 << (j - 1))), false);
+
+  // Algorithm 2
+  const int r = G + 2 * k + 1;
+  const uint64_t* p_g1 = cached_pt(M, li, T_G1, 0, xr->level, xr->scale, [&] {
+    std::vector<double> g1 = coltile(L, 1, r);
+    for (auto& t : g1) t = -t / (2.0 * R);
+    return g1;
+  });
+  Ct a1 = op_add_pt(c, *xr, p_g1);
+  const uint64_t* p_g2 = cached_pt(M, li, T_G2, 0, xr->level, xr->scale, [&] {
+    std::vector<double> g2 = coltile(L, 2, r + 1);
+    for (auto& t : g2) t = t / (2.0 * R);
+    return g2;
+  });
+  Ct a2 = op_add_pt(c, *op_mul_int(c, *xr, -1), p_g2);
+  Ct s1 = polycomp0(c, keys, *a1, L.comp);
+  Ct s2 = polycomp0(c, keys, *a2, L.comp);
+  Ct b = op_mul(c, keys, *s1, *s2);
+  for (int j = 1; j <= k; j++) {
+    const std::vector<double> t1 = coltile(L, 1, r - j), t2 = coltile(L, j + 1, r);
+    const std::vector<double> t3 = coltile(L, j + 2, r + 1), t4 = coltile(L, 2, r - j + 1);
+    std::vector<double> A1(t1.size()), A2(t3.size());
+    for (size_t i = 0; i < t1.size(); i++) A1[i] = 1.0 / (t2[i] - t1[i]);
+    for (size_t i = 0; i < t3.size(); i++) A2[i] = 1.0 / (t3[i] - t4[i]);
+    const int lb = b->level;
+    Ct xd = op_mod_drop(c, *xr, lb + 1);
+    const double Su = plain_scale(c, xd->scale, xd->level);
+    const uint64_t* p1m = cached_pt(M, li, T_U1M, j, xd->level, Su, [&] {
+      std::vector<double> v2(A1.size());
+      for (size_t i = 0; i < A1.size(); i++) v2[i] = 2.0 * R * A1[i];
+      return v2;
+    });
+    Ct u1 = op_mul_pt(c, *xd, p1m, Su);
+    const uint64_t* p1a = cached_pt(M, li, T_U1A, j, u1->level, u1->scale, [&] {
+      std::vector<double> v2(A1.size());
+      for (size_t i = 0; i < A1.size(); i++) v2[i] = -t1[i] * A1[i];
+      return v2;
+    });
+    u1 = op_add_pt(c, *u1, p1a);
+    const uint64_t* p2m = cached_pt(M, li, T_U2M, j, xd->level, Su, [&] {
+      std::vector<double> v2(A2.size());
+      for (size_t i = 0; i < A2.size(); i++) v2[i] = -2.0 * R * A2[i];
+      return v2;
+    });
+    Ct u2 = op_mul_pt(c, *xd, p2m, Su);
+    const uint64_t* p2a = cached_pt(M, li, T_U2A, j, u2->level, u2->scale, [&] {
+      std::vector<double> v2(A2.size());
+      for (size_t i = 0; i < A2.size(); i++) v2[i] = t3[i] * A2[i];
+      return v2;
+    });
+    u2 = op_add_pt(c, *u2, p2a);
+    Ct rb = op_rotate(c, keys, *b, n_i);
+    b = op_mul_sum(c, keys, {{u1.get(), b.get()}, {u2.get(), rb.get()}});
+  }
+
+  // fused linear layer (Eq. 13)
+  if (L.plan_s.npad < S) b = op_add(c, *b, *op_rotate(c, keys, *b, -L.plan_s.npad), false);
+  Ct ys = bsgs_matvec(M, li, true, keys, *b);
+  const int lv = std::min(ys->level, yb->level);
+  return op_add(c, *op_level_down(c, *ys, lv), *op_level_down(c, *yb, lv), false);
+}
+
+int cheb_depth(int d) {
+  const int m = pow2ceil((int)ceil(sqrt((double)(d + 1))));
+  std::map<int, int> T;
+  T[1] = 0;
+  for (int i = 2; i <= m; i++) {
+    if ((i & (i - 1)) == 0) {
+      T[i] = T[i / 2] + 1;
+    } else {
+      int hb = 1;
+      while (hb * 2 <= i) hb *= 2;
+      T[i] = std::max(T[hb], T[i - hb]) + 1;
+    }
+  }
+  std::map<int, int> Gs;
+  Gs[m] = T[m];
+  for (int D = m; 2 * D <= d; D *= 2) Gs[2 * D] = Gs[D] + 1;
+  std::function<int(int)> rec = [&](int deg) -> int {  // -1 = constant
+    if (deg < m) {
+      if (deg == 0) return -1;
+      int mx = 0;
+      for (int i = 1; i <= deg; i++) mx = std::max(mx, T[i]);
+      return mx + 1;
+    }
+    int D = m;
+    while (2 * D <= deg) D *= 2;
+    const int q = rec(deg - D), r = rec(D - 1);
+    const int P = q < 0 ? Gs[D] + 1 : std::max(q, Gs[D]) + 1;
+    return r < 0 ? P : std::max(P, r);
+  };
+  return rec(d);
+}
+
+int layer_depth(const Layer& L) {
+  int dc = 0;
+  for (int n : L.comp) {
+    int lg = 0;
+    while ((2 << lg) <= 2 * n) lg++;
+    dc += 1 + lg;
+  }
+  const int spline = 3 + dc + L.k;
+  const int silu = 2 + cheb_depth((int)L.cheb.size() - 1);
+  return std::max(spline, silu);
+}
+
+std::vector<int> layer_rotations(const Layer& L, int slots) {
+  std::set<int> s;
+  int J = 0;
+  while ((1 << J) < L.G + 2 * L.k) J++;
+  for (int j = 1; j <= J; j++) s.insert(-L.n_in * (1 << (j - 1)));
+  s.insert(L.n_in);
+  for (int n : {L.n_in * (L.G + L.k), L.n_in}) {
+    Plan p = bsgs_plan(L.n_out, n, slots);
+    if (p.npad < slots) s.insert(-p.npad);
+    for (int j = 1; j < p.g1; j++) s.insert(j);
+    for (int i = 1; i < p.g2; i++) s.insert(p.g1 * i);
+    for (int f : p.folds) s.insert(f);
+  }
+  s.erase(0);
+  return std::vector<int>(s.begin(), s.end());
+}
+
+}  // namespace
+
+extern "C" {
+
+int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layers,
+                     kan_model** out) {
+  try {
+    if (!ctx || !layers || !out || n_layers == 0) return CKKS_ERR_INVALID_ARG;
+    auto M = std::make_unique<kan_model>();
+    M->ctx = &ctx->c;
+    const int S = (int)(ctx->c.N / 2);
+    for (size_t li = 0; li < n_layers; li++) {
+      const kan_layer_desc& d = layers[li];
+      if (d.n_in < 1 || d.n_out < 1 || d.G < 1 || d.k < 0 || !d.coef || !d.w_s || !d.w_b ||
+          !d.silu_cheb || d.silu_degree < 1 || !d.comp || d.n_comp < 1 || !(d.R > 0) ||
+          !(d.silu_hi > d.silu_lo) || !(d.grid_hi > d.grid_lo))
+        return CKKS_ERR_INVALID_ARG;
+      for (int i = 0; i < d.n_comp; i++)
+        if (d.comp[i] < 1 || d.comp[i] > 8) return CKKS_ERR_INVALID_ARG;
+      Layer L;
+      L.n_in = d.n_in;
+      L.n_out = d.n_out;
+      L.G = d.G;
+      L.k = d.k;
+      L.lo = d.grid_lo;
+      L.hi = d.grid_hi;
+      L.R = d.R;
+      L.silu_lo = d.silu_lo;
+      L.silu_hi = d.silu_hi;
+      const size_t nb = (size_t)d.G + d.k;
+      L.coef.assign(d.coef, d.coef + (size_t)d.n_out * d.n_in * nb);
+      L.w_s.assign(d.w_s, d.w_s + (size_t)d.n_out * d.n_in);
+      L.w_b.assign(d.w_b, d.w_b + (size_t)d.n_out * d.n_in);
+      L.cheb.assign(d.silu_cheb, d.silu_cheb + d.silu_degree + 1);
+      L.comp.assign(d.comp, d.comp + d.n_comp);
+      const double h = (L.hi - L.lo) / L.G;
+      for (int m = 0; m <= L.G + 2 * L.k; m++) L.knots.push_back(L.lo + (double)(m - L.k) * h);
+      // W_f[o][m n_i + i] = w_s[o][i] c[o][i][m]  (W' P, Algorithm 3 / Eq. 13)
+      const int n_s = d.n_in * (int)nb;
+      L.Wf.assign((size_t)d.n_out * n_s, 0.0);
+      for (int o = 0; o < d.n_out; o++)
+        for (int i = 0; i < d.n_in; i++)
+          for (size_t m = 0; m < nb; m++)
+            L.Wf[(size_t)o * n_s + m * d.n_in + i] =
+                L.w_s[(size_t)o * d.n_in + i] * L.coef[((size_t)o * d.n_in + i) * nb + m];
+      L.plan_b = bsgs_plan(d.n_out, d.n_in, S);
+      L.plan_s = bsgs_plan(d.n_out, n_s, S);
+      L.diag_b = diagonals(L.w_b, d.n_out, d.n_in, L.plan_b, S);
+      L.diag_s = diagonals(L.Wf, d.n_out, n_s, L.plan_s, S);
+      int J = 0;
+      while ((1 << J) < L.G + 2 * L.k) J++;
+      if ((int64_t)L.n_in << J > S) return CKKS_ERR_UNSUPPORTED;
+      M->layers.push_back(std::move(L));
+    }
+    *out = M.release();
+    return CKKS_OK;
+  } catch (const Error& e) {
+    return e.code;
+  } catch (...) {
+    return CKKS_ERR_CUDA;
+  }
+}
+
+int kan_model_destroy(kan_model* model) {
+  delete model;
+  return CKKS_OK;
+}
+
+int kan_model_rotations(const kan_model* model, int32_t* steps, size_t cap, size_t* n) {
+  if (!model || !n) return CKKS_ERR_INVALID_ARG;
+  std::set<int> s;
+  for (const Layer& L : model->layers)
+    for (int t : layer_rotations(L, (int)(model->ctx->N / 2))) s.insert(t);
+  *n = s.size();
+  size_t i = 0;
+  for (int t : s) {
+    if (i >= cap) break;
+    if (steps) steps[i] = t;
+    i++;
+  }
+  return CKKS_OK;
+}
+
+int kan_model_layer_depth(const kan_model* model, int layer, int* depth) {
+  if (!model || !depth || layer < 0 || layer >= (int)model->layers.size()) return CKKS_ERR_INVALID_ARG;
+  *depth = layer_depth(model->layers[layer]);
+  return CKKS_OK;
+}
+
+int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int layer,
+                   const ckks_ct* in, ckks_ct** out) {
+  try {
+    if (!ctx || !keys || !model || !in || !out || layer < 0 || layer >= (int)model->layers.size())
+      return CKKS_ERR_INVALID_ARG;
+    *out = layer_eval(*model, layer, *keys, *in).release();
+    return CKKS_OK;
+  } catch (const Error& e) {
+    return e.code;
+  } catch (...) {
+    return CKKS_ERR_CUDA;
+  }
+}
+
+int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, const ckks_ct* const* in,
+              size_t n_in, ckks_ct** out) {
+  try {
+    if (!ctx || !keys || !model || !in || !out || n_in == 0) return CKKS_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    int lv = in[0]->level;
+    for (size_t i = 0; i < n_in; i++) lv = std::min(lv, in[i]->level);
+    std::vector<Ct> aligned;
+    std::vector<const ckks_ct*> parts;
+    for (size_t i = 0; i < n_in; i++) {
+      if (in[i]->level != lv) {
+        aligned.push_back(op_level_down(c, *in[i], lv));
+        parts.push_back(aligned.back().get());
+      } else {
+        parts.push_back(in[i]);
+      }
+    }
+    Ct h = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
+    aligned.clear();
+    for (size_t li = 0; li < model->layers.size(); li++) h = layer_eval(*model, (int)li, *keys, *h);
+    *out = h.release();
+    return CKKS_OK;
+  } catch (const Error& e) {
+    return e.code;
+  } catch (...) {
+    return CKKS_ERR_CUDA;
+  }
+}
+
+}  // extern "C"

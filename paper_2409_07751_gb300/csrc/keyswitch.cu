@@ -1,0 +1,175 @@
+// Hybrid key switching: ModUp (fast basis conversion per digit), key inner
+// product over the extended basis QP (with the Galois automorphism of a
+// hoisted rotation fused into its loads), and ModDown.
+//
+// ModUp of digit j (Q primes D_j = [j*alpha, min((j+1)*alpha, l))):
+//   rows in D_j copy the NTT-form input;
+//   other rows t: sum_{i in D_j} [x_i Dhat_i^{-1}]_{q_i} (Dhat_i mod m_t) mod m_t,
+//   then NTT.
+// ModDown: out_i = (acc_i - Conv_{P->Q}([acc]_P)_i) * P^{-1} mod q_i.
+#include "modarith.cuh"
+
+namespace ck {
+
+namespace {
+
+constexpr int TPB = 256;
+inline unsigned grid_for(size_t total) {
+  size_t g = (total + TPB - 1) / TPB;
+  const size_t cap = 152 * 32;
+  return (unsigned)(g < cap ? (g ? g : 1) : cap);
+}
+#define GRID_LOOP(idx, total) \
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (total); idx += (size_t)gridDim.x * blockDim.x)
+
+constexpr int MAX_ALPHA = 16;
+
+// thread per (b, j, n); xc: [B][l][N] coefficient form; d: NTT form
+__global__ void modup_kernel(const uint64_t* xc, const uint64_t* d, uint64_t* ext, size_t B,
+                             int log_n, int l, int alpha, int beta, int rows, int L,
+                             const Mod* mods, const uint64_t* dhinv, const uint64_t* dhinvs,
+                             const uint64_t* dh, const uint64_t* dhs) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(idx, B * (size_t)beta * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bj = idx >> log_n;
+    const int j = (int)(bj % beta);
+    const size_t b = bj / beta;
+    const int lo = j * alpha;
+    const int hi = min((j + 1) * alpha, l);
+    uint64_t v[MAX_ALPHA];
+    for (int a = 0; a < hi - lo; a++) {
+      const int i = lo + a;
+      const uint64_t x = xc[(b * l + i) * N + n];
+      v[a] = mul_shoup(x, dhinv[j * alpha + a], dhinvs[j * alpha + a], mods[i].q);
+    }
+    uint64_t* out = ext + ((b * beta + j) * rows) * N + n;
+    for (int r = 0; r < rows; r++) {
+      if (r >= lo && r < hi) {
+        out[(size_t)r * N] = d[(b * l + r) * N + n];
+        continue;
+      }
+      const int mi = r < l ? r : L + 1 + (r - l);
+      const uint64_t m = mods[mi].q;
+      uint64_t acc = 0;
+      for (int a = 0; a < hi - lo; a++) {
+        const size_t ti = ((size_t)(j * alpha + a)) * rows + r;
+        acc = add_mod(acc, mul_shoup(v[a], dh[ti], dhs[ti], m), m);
+      }
+      out[(size_t)r * N] = acc;
+    }
+  }
+}
+
+// thread per (r, n); loops over the batch so each key word is read once.
+// ext: [B][beta][rows][N]; key: [beta_max][2][n_qp][N]; acc: [B][2][rows][N]
+__global__ void inner_product_kernel(const uint64_t* ext, const uint64_t* key, uint64_t* acc,
+                                     size_t B, int log_n, int l, int beta, int rows, int L,
+                                     int n_qp, const Mod* mods, const uint32_t* perm) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(idx, (size_t)rows * N) {
+    const size_t n = idx & (N - 1);
+    const int r = (int)(idx >> log_n);
+    const int mi = r < l ? r : L + 1 + (r - l);
+    const Mod m = mods[mi];
+    const size_t src = perm ? perm[n] : n;
+    uint64_t kb[32], ka[32];
+    for (int j = 0; j < beta; j++) {
+      kb[j] = key[(((size_t)j * 2 + 0) * n_qp + mi) * N + n];
+      ka[j] = key[(((size_t)j * 2 + 1) * n_qp + mi) * N + n];
+    }
+    for (size_t b = 0; b < B; b++) {
+      uint64_t a0 = 0, a1 = 0;
+      for (int j = 0; j < beta; j++) {
+        const uint64_t e = ext[((b * beta + j) * rows + r) * N + src];
+        a0 = add_mod(a0, mul_mod(e, kb[j], m), m.q);
+        a1 = add_mod(a1, mul_mod(e, ka[j], m), m.q);
+      }
+      acc[((b * 2 + 0) * rows + r) * N + n] = a0;
+      acc[((b * 2 + 1) * rows + r) * N + n] = a1;
+    }
+  }
+}
+
+// thread per (bk, n): y_a = [acc_P[a] Phat_a^{-1}]_{p_a}; conv_i = sum_a y_a Phat_a mod q_i
+__global__ void moddown_conv_kernel(const uint64_t* acc, uint64_t* conv, size_t BK, int log_n,
+                                    int l, int alpha, int rows, int L, const Mod* mods,
+                                    const uint64_t* yinv, const uint64_t* yinvs,
+                                    const uint64_t* ph, const uint64_t* phs) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(idx, BK * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bk = idx >> log_n;
+    uint64_t y[MAX_ALPHA];
+    for (int a = 0; a < alpha; a++) {
+      const uint64_t x = acc[(bk * rows + l + a) * N + n];
+      y[a] = mul_shoup(x, yinv[a], yinvs[a], mods[L + 1 + a].q);
+    }
+    for (int i = 0; i < l; i++) {
+      const uint64_t q = mods[i].q;
+      uint64_t s = 0;
+      for (int a = 0; a < alpha; a++) {
+        const size_t ti = (size_t)a * (L + 1) + i;
+        s = add_mod(s, mul_shoup(y[a], ph[ti], phs[ti], q), q);
+      }
+      conv[(bk * l + i) * N + n] = s;
+    }
+  }
+}
+
+__global__ void moddown_finish_kernel(const uint64_t* acc, const uint64_t* conv, uint64_t* out,
+                                      size_t BK, int log_n, int l, int rows, const Mod* mods,
+                                      const uint64_t* pinv, const uint64_t* pinvs) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(idx, BK * l * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bi = idx >> log_n;
+    const int i = (int)(bi % l);
+    const size_t bk = bi / l;
+    const uint64_t q = mods[i].q;
+    const uint64_t a = acc[(bk * rows + i) * N + n];
+    out[idx] = mul_shoup(sub_mod(a, conv[idx], q), pinv[i], pinvs[i], q);
+  }
+}
+
+}  // namespace
+
+void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext) {
+  ConvTables& T = c.tables(level);
+  const int l = T.l;
+  if (c.alpha > MAX_ALPHA) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
+  DevBuf xc(&c, B * l * c.N * 8);
+  CK_CUDA(cudaMemcpyAsync(xc.p, d, xc.bytes, cudaMemcpyDeviceToDevice, c.stream));
+  ntt_inverse(c, xc.u64(), B * l, c.iota(), l);
+  modup_kernel<<<grid_for(B * T.beta * c.N), TPB, 0, c.stream>>>(
+      xc.u64(), d, ext, B, c.log_n, l, c.alpha, T.beta, T.rows, c.L, c.dmod(), T.dhinv.u64(),
+      T.dhinv_s.u64(), T.dh.u64(), T.dh_s.u64());
+  CK_CUDA(cudaGetLastError());
+  ntt_forward(c, ext, B * T.beta * T.rows, static_cast<const int16_t*>(T.ext_pattern.p),
+              T.beta * T.rows);
+}
+
+void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
+                   uint64_t galois, uint64_t* out) {
+  ConvTables& T = c.tables(level);
+  const int l = T.l, rows = T.rows;
+  if (T.beta > 32) throw Error(CKKS_ERR_UNSUPPORTED, "more than 32 digits");
+  const uint32_t* perm = galois ? c.perm(galois) : nullptr;
+  DevBuf acc(&c, B * 2 * rows * c.N * 8);
+  inner_product_kernel<<<grid_for((size_t)rows * c.N), TPB, 0, c.stream>>>(
+      ext, key, acc.u64(), B, c.log_n, l, T.beta, rows, c.L, c.n_qp, c.dmod(), perm);
+  CK_CUDA(cudaGetLastError());
+  ntt_inverse(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows);
+  DevBuf conv(&c, B * 2 * l * c.N * 8);
+  moddown_conv_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+      acc.u64(), conv.u64(), B * 2, c.log_n, l, c.alpha, rows, c.L, c.dmod(), c.d_md_yinv.u64(),
+      c.d_md_yinv_s.u64(), c.d_md_ph.u64(), c.d_md_ph_s.u64());
+  CK_CUDA(cudaGetLastError());
+  ntt_forward(c, conv.u64(), B * 2 * l, c.iota(), l);
+  moddown_finish_kernel<<<grid_for(B * 2 * l * c.N), TPB, 0, c.stream>>>(
+      acc.u64(), conv.u64(), out, B * 2, c.log_n, l, rows, c.dmod(), T.md_pinv.u64(),
+      T.md_pinv_s.u64());
+  CK_CUDA(cudaGetLastError());
+}
+
+}  // namespace ck

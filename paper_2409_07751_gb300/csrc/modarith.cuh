@@ -1,0 +1,50 @@
+// Device modular arithmetic on uint64 residues (q < 2^62).
+//
+// Products of two variable residues use Barrett reduction with the
+// bit-length-dependent shift of the classical algorithm (Menezes et al.,
+// Handbook of Applied Cryptography, Alg. 14.42): for x < 2^(2s),
+// qhat = ((x >> (s-1)) * mu) >> (s+1), mu = floor(2^(2s)/q), and
+// x - qhat*q < 3q. Products by a fixed operand w use Shoup's method with the
+// precomputed w' = floor(w * 2^64 / q): a*w - hi(a*w')*q lies in [0, 2q).
+#pragma once
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace ck {
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+  uint64_t s = a + b;
+  return s >= q ? s - q : s;
+}
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+  return a >= b ? a - b : a + (q - b);
+}
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const Mod& m) {
+  const uint64_t lo = a * b;
+  const uint64_t hi = __umul64hi(a, b);
+  const uint32_t s = m.s;
+  const uint64_t x1 = (lo >> (s - 1)) | (hi << (65 - s));
+  const uint64_t ql = x1 * m.mu;
+  const uint64_t qh = __umul64hi(x1, m.mu);
+  const uint64_t qhat = (ql >> (s + 1)) | (qh << (63 - s));
+  uint64_t r = lo - qhat * m.q;
+  if (r >= m.q) r -= m.q;
+  if (r >= m.q) r -= m.q;
+  return r;
+}
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+  const uint64_t t = __umul64hi(a, ws);
+  uint64_t r = a * w - t * q;
+  return r >= q ? r - q : r;
+}
+// reduction of an arbitrary 64-bit value (rarely used; plain division)
+__device__ __forceinline__ uint64_t reduce64(uint64_t a, uint64_t q) { return a % q; }
+// signed value -> residue
+__device__ __forceinline__ uint64_t smod64(int64_t v, uint64_t q) {
+  if (v >= 0) return (uint64_t)v % q;
+  const uint64_t m = ((uint64_t)(-(v + 1)) + 1) % q;
+  return m ? q - m : 0;
+}
+
+}  // namespace ck

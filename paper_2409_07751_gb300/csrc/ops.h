@@ -1,0 +1,66 @@
+// Ciphertext operations with level and scale bookkeeping.
+//
+// Scale rule: a ciphertext at level l carries the canonical scale Delta_l
+// (Delta_{l-1} = Delta_l^2 / q_l). Plaintext operands of a product are
+// encoded at the scale that lands the rescaled product on Delta_{l-1};
+// moving to a lower level multiplies by an integer constant and rescales;
+// a rescaled scale within 2^-30 of the canonical one is snapped to it.
+#pragma once
+#include <utility>
+
+#include "internal.h"
+
+namespace ck {
+
+using Ct = std::unique_ptr<ckks_ct>;
+
+constexpr double SNAP = 1.0 / 1073741824.0;  // 2^-30
+
+Ct ct_alloc(Ctx& c, size_t B, int level, double scale);
+Ct ct_copy(Ctx& c, const ckks_ct& a);
+void check_pair(const ckks_ct& a, const ckks_ct& b);
+
+int64_t round_const(double v, double scale);
+double plain_scale(const Ctx& c, double ct_scale, int level);
+
+// plaintext [l][N] (device) of a real vector at `level` and `scale`
+DevBuf encode_vec(Ctx& c, const double* host, size_t n, int level, double scale);
+
+Ct op_add(Ctx& c, const ckks_ct& a, const ckks_ct& b, bool sub);
+Ct op_mul_int(Ctx& c, const ckks_ct& a, int64_t k);
+Ct op_add_const(Ctx& c, const ckks_ct& a, double v);
+Ct op_add_pt(Ctx& c, const ckks_ct& a, const uint64_t* pt);
+Ct op_mod_drop(Ctx& c, const ckks_ct& a, int level);
+Ct op_rescale(Ctx& c, const ckks_ct& a);
+// a (x) pt then rescale; pt must be encoded at plain_scale(a.scale, a.level)
+Ct op_mul_pt(Ctx& c, const ckks_ct& a, const uint64_t* pt, double pt_scale);
+Ct op_mul_const(Ctx& c, const ckks_ct& a, double v);
+Ct op_level_down(Ctx& c, const ckks_ct& a, int level);
+Ct op_lincomb(Ctx& c, const std::vector<const ckks_ct*>& in, const std::vector<double>& k,
+              double cst, int level);
+Ct op_mul_relin(Ctx& c, const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
+Ct op_mul(Ctx& c, const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
+Ct op_mul_sum(Ctx& c, const ckks_keys& keys,
+              const std::vector<std::pair<const ckks_ct*, const ckks_ct*>>& pairs);
+std::vector<Ct> op_rotate_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
+                               const std::vector<int64_t>& steps);
+Ct op_rotate(Ctx& c, const ckks_keys& keys, const ckks_ct& a, int64_t step);
+Ct op_concat(Ctx& c, const std::vector<const ckks_ct*>& in);
+
+// keys.cu
+std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps);
+Ct encrypt(Ctx& c, const ckks_keys& keys, const double* values, size_t B, size_t n, int level,
+           uint64_t seed, uint64_t first_index);
+void decrypt(Ctx& c, const ckks_keys& keys, const ckks_ct& ct, double* out, size_t n);
+
+// elementwise.cu (extra entry points)
+void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows, int l);
+void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l);
+void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::vector<int64_t>& k,
+                   uint64_t* out, size_t rows, int l);
+void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
+                     uint64_t* out, size_t B, int l);
+void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,
+                      int level, const uint64_t* inv, const uint64_t* invs);
+
+}  // namespace ck

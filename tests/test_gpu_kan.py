@@ -1,0 +1,83 @@
+"""GPU parity of the encrypted KAN layer and network: the CUDA schedule's
+ciphertexts must equal the oracle's word for word (same seeded keys,
+inputs and model), and decryptions must match the HE-friendly FP64 KAN
+within CKKS noise. Sizes: a tiny model at N = 2^7 (several BSGS tiles, ragged
+n_i), and the [4,8,4,1] G=5 k=3 network with the full 36-level chain at
+N = 2^11, batched at uneven levels."""
+import numpy as np
+import pytest
+
+from oracle import calibrate, ckks as O, kan_he, kan_plain
+from paper_2409_07751_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2409_07751_gb300 import build, ckks
+    build.build()
+    return ckks
+
+
+def _setup(G, log_n, L, alpha, model):
+    gctx = G.Context(log_n, L, alpha)
+    octx = O.Ctx(O.Params(log_n, L, alpha))
+    gm = G.Model(gctx, model)
+    rots = kan_he.model_rotations(model, octx.slots)
+    assert gm.rotations() == rots
+    gk = G.Keys(gctx, W.SEED_KEYS, rots)
+    ok = O.Keys(octx, W.SEED_KEYS, rots)
+    return gctx, octx, gm, gk, ok
+
+
+def test_tiny_layer_and_network_bit_exact(G):
+    model = W.make_model("t", widths=[3, 5, 2], G=3, k=2)
+    X = W.uniform_inputs(64, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    gctx, octx, gm, gk, ok = _setup(G, 7, 17, 2, m)
+    for li in range(len(m)):
+        assert gm.layer_depth(li) == 7
+    x = X[:2]
+    oc = O.encrypt(octx, ok, x[0], octx.L, W.SEED_ENC, 0)
+    gc = G.Ciphertext.import_(gctx, oc.data, oc.level, oc.scale)
+    # one layer
+    o1 = kan_he.layer_eval(octx, ok, oc, m[0])
+    g1 = G.kan_layer_eval(gctx, gk, gm, 0, gc)
+    assert g1.level == o1.level and g1.scale == o1.scale
+    assert (g1.export()[0] == o1.data).all()
+    # whole network through the client path (GPU encryption)
+    gin = G.encrypt(gctx, gk, x, octx.L, W.SEED_ENC, 0)
+    gout = G.kan_infer(gctx, gk, gm, [gin])
+    for b in range(2):
+        oc = O.encrypt(octx, ok, x[b], octx.L, W.SEED_ENC, b)
+        oo = kan_he.infer(octx, ok, oc, m)
+        assert (gout.export()[b] == oo.data).all()
+    dec = G.decrypt(gctx, gk, gout, 2)
+    hef = kan_plain.forward(m, x, "poly", "poly")
+    assert np.abs(dec - hef).max() < 1e-6
+
+
+def test_kan_4_8_4_1_batched_uneven_levels(G):
+    model = W.make_model("kan_4_8_4_1")
+    X = W.uniform_inputs(256, 4)
+    m = calibrate.calibrate(model, X, 27, [3])
+    gctx, octx, gm, gk, ok = _setup(G, 11, 36, 4, m)
+    depth = sum(gm.layer_depth(i) for i in range(3))
+    assert depth <= 36
+    slack = 36 - depth
+    x = X[:3]
+    levels = [36, 36 - slack, 36 - min(1, slack)]
+    gins = [G.encrypt(gctx, gk, x[b], levels[b], W.SEED_ENC, b) for b in range(3)]
+    gout = G.kan_infer(gctx, gk, gm, gins)
+    assert gout.batch == 3
+    data = gout.export()
+    lv = min(levels)
+    for b in (0, 1):
+        oc = O.encrypt(octx, ok, x[b], levels[b], W.SEED_ENC, b)
+        oc = O.level_down(octx, oc, lv)
+        oo = kan_he.infer(octx, ok, oc, m)
+        assert (data[b] == oo.data).all(), b
+    dec = G.decrypt(gctx, gk, gout, 1)
+    hef = kan_plain.forward(m, x, "poly", "poly")
+    assert np.abs(dec - hef).max() < 1e-4
