@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: encrypted KAN inferences/s on GB300.
+
+Workload (one step): the encrypted KAN [4,8,4,1] (grid G=5 on [-1,1], k=3,
+SiLU degree 27 on data-fitted ranges) evaluated on a batch of 64 encrypted
+inputs (uniform [-1,1]^4) at uneven levels, CKKS N=2^16 with 36 rescaling
+levels, one kan_infer call (all 64 inputs in one batched launch sequence).
+Inputs stay resident in HBM between steps; one step reads ~2 GB of
+ciphertexts plus ~5 GB of switching keys, far above the 129 MB L2.
+
+Reported beside the headline: the per-step p50/p99 latency, HMult/s and
+HRot/s at N=2^16 with 37 limbs, the live roofline of the dominant kernel
+kind (CUDA events around every launch during the timed region), an
+end-to-end figure through the C ABI with pinned host buffers (ciphertexts in,
+ciphertexts out, copies inside the timed region), the oracle timed on a
+bounded sample on the host cores, and the SM clocks sampled while timing.
+
+Multi-GPU (torchrun): requests shard across ranks (each rank its own batch
+and a replica of the keys); no data-path collective, weak scaling.
+`--impl reference` times the CPU oracle instead (bounded sample per step).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted KAN inferences/s"
+UNIT = "inferences/s"
+WORKLOAD = "encrypted KAN [4,8,4,1] G=5 k=3, CKKS N=2^16, 36 levels, batch 64 at uneven levels"
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=64)
+    p.add_argument("--log-n", type=int, default=16)
+    p.add_argument("--levels", type=int, default=36)
+    p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-micro", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def config(a):
+    return {"workload": WORKLOAD, "model": "kan_4_8_4_1", "n_poly": 1 << a.log_n,
+            "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": 27, "comparison": "f_3",
+            "input_levels": "uniform over [L - slack, L]", "parallelism": "replicas (request sharding)",
+            "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)"}
+
+
+def model_and_inputs(a, rank):
+    from paper_2409_07751_gb300 import workloads as W
+    model = W.make_model("kan_4_8_4_1")
+    Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
+    X = W.uniform_inputs(a.batch, 4, seed=W.SEED_INPUTS + rank)
+    return model, Xcal, X
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle sample
+def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
+    """Time the oracle (plain single-threaded CPU code) on the same workload.
+
+    The oracle needs minutes to hours per inference at N=2^16, so each sample
+    runs one inference from the start and stops after `budget_s` seconds at a
+    key-switch boundary; the fraction done is the number of key switches
+    completed over the inference's total (counted on the same schedule at
+    N=2^11, where the rotation plans are identical). Keys and the input are
+    random residues of the right shapes (timing does not depend on them).
+    """
+    import numpy as np
+    from oracle import ckks as O, kan_he
+
+    class _Stop(Exception):
+        pass
+
+    real_ks, real_modup = O._ks, O._modup
+
+    # total key switches of one inference (same schedule, small ring, no arithmetic)
+    counter = {"n": 0}
+
+    def count_ks(ctx, ext, level, key, g):
+        counter["n"] += 1
+        return np.zeros((2, level + 1, ctx.N), np.uint64)
+
+    def skip_modup(ctx, poly, level):
+        return None
+
+    small = O.Ctx(O.Params(11, a.levels, 4))
+
+    class Fake:
+        pass
+
+    fk = Fake()
+    fk.relin = None
+    fk.galois = {small.galois(t): None for t in kan_he.model_rotations(model_he, small.slots)}
+    x = O.Ct(np.zeros((2, a.levels + 1, small.N), np.uint64), a.levels, small.delta[a.levels])
+    O._ks, O._modup = count_ks, skip_modup
+    try:
+        kan_he.infer(small, fk, x, model_he)
+    finally:
+        O._ks, O._modup = real_ks, real_modup
+    total = counter["n"]
+
+    ctx = O.Ctx(O.Params(a.log_n, a.levels, 4))
+    Z = np.zeros((ctx.beta_max, 2, ctx.n_qp, ctx.N), np.uint64)
+    keys = Fake()
+    keys.relin = Z
+    keys.galois = {ctx.galois(t): Z for t in kan_he.model_rotations(model_he, ctx.slots)}
+    rng = np.random.default_rng(0)
+    data = np.stack([np.stack([rng.integers(0, ctx.q[t], ctx.N, dtype=np.uint64)
+                               for t in range(a.levels + 1)]) for _ in range(2)])
+    ct = O.Ct(data, a.levels, ctx.delta[a.levels])
+    rates = []
+    for it in range(warmup + steps):
+        done = {"n": 0}
+        t0 = time.perf_counter()
+
+        def timed_ks(ctx_, ext, level, key, g):
+            r = real_ks(ctx_, ext, level, key, g)
+            done["n"] += 1
+            if time.perf_counter() - t0 > budget_s:
+                raise _Stop()
+            return r
+
+        O._ks = timed_ks
+        try:
+            kan_he.infer(ctx, keys, ct, model_he)
+        except _Stop:
+            pass
+        finally:
+            O._ks = real_ks
+        el = time.perf_counter() - t0
+        if it >= warmup:
+            rates.append((done["n"] / total) / el)
+    sample = ("first %d of %d key switches of one inference (N=2^%d, %d levels), single thread, "
+              "random keys and input, %.0f s budget per sample" % (done["n"], total, a.log_n, a.levels,
+                                                                    budget_s))
+    return statistics.mean(rates), sample, total
+
+
+def reference_arm(a):
+    """--impl reference: the CPU oracle as it stands, bounded samples."""
+    from paper_2409_07751_gb300 import workloads as W
+    from oracle import calibrate as OC
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    model, Xcal, _ = model_and_inputs(a, 0)
+    m = OC.calibrate(model, Xcal, 27, [3])
+    per_step = max(5.0, min(a.cpu_budget, 150.0 / max(1, a.steps + a.warmup)))
+    t0 = time.perf_counter()
+    v, sample, _ = oracle_sample(m, a, per_step, steps=a.steps, warmup=a.warmup)
+    el = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * el / (a.steps + a.warmup),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": config(a),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    a = args_()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        from paper_2409_07751_gb300 import build
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2409_07751_gb300 import ckks as G
+    from paper_2409_07751_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    ctx = G.Context(a.log_n, a.levels, 4, device=local)
+    ctx.set_stream(stream.cuda_stream)
+    model, Xcal, X = model_and_inputs(a, rank)
+    m = G.calibrate(model, Xcal, 27, [3])
+    gm = G.Model(ctx, m)
+    depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
+    slack = a.levels - depth
+    levels = W.uneven_levels(a.batch, a.levels, slack, seed=W.SEED_INPUTS + 1 + rank)
+    keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+    cts = []
+    for lv in sorted(set(int(x) for x in levels)):
+        sel = np.nonzero(levels == lv)[0]
+        cts.append(G.encrypt(ctx, keys, X[sel], lv, W.SEED_ENC, first_index=int(sel[0]) + rank * a.batch))
+
+    def step():
+        out = G.kan_infer(ctx, keys, gm, cts)
+        out.close()
+        return out
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- timed region
+    before = ctx.launch_counts()
+    ctx.profile(True)
+    clk = Clocks(local)
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    ev[0].record(stream)
+    for i in range(a.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    prof = ctx.profile_collect()
+    ctx.profile(False)
+    after = ctx.launch_counts()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
+    elapsed = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    launches = sum(after[k] - before[k] for k in after if k != "copy")
+    value = world * a.batch * a.steps / (elapsed / 1000.0)
+
+    # roofline of the dominant kernel kind
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    kinds = {k: v for k, v in prof.items() if k != "copy"}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms, by, n = kinds[dom]
+    achieved = by / (ms / 1000.0) / 1e9
+    total_ms = sum(v[0] for v in kinds.values())
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
+                "share_of_kernel_time": ms / total_ms,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])}
+
+    # ---------------- micro: HMult / HRot per second at N=2^16, 37 limbs
+    micro = None
+    if not a.no_micro:
+        micro = {}
+        for B in (1, 8):
+            x = G.encrypt(ctx, keys, X[:B], a.levels, 9, 0)
+            for name, fn in (("hmult", lambda: G.mul(ctx, keys, x, x)),
+                             ("hrot", lambda: G.rotate(ctx, keys, x, 1))):
+                fn().close()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 3
+                e0.record(stream)
+                for _ in range(reps):
+                    fn().close()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                micro["%s_per_s_batch%d" % (name, B)] = B * reps / (e0.elapsed_time(e1) / 1000.0)
+            x.close()
+        micro["limbs"] = a.levels + 1
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        hin = []
+        for c in cts:
+            buf = torch.empty(c.words(), dtype=torch.int64, pin_memory=True)
+            c.export_to(buf.data_ptr(), c.words())
+            hin.append((buf, c.batch, c.level, c.scale))
+        probe = G.kan_infer(ctx, keys, gm, cts)
+        out_words = probe.words()
+        probe.close()
+        hout = torch.empty(out_words, dtype=torch.int64, pin_memory=True)
+        h2d = sum(b.numel() * 8 for b, _, _, _ in hin)
+
+        def e2e_step():
+            ins = [G.Ciphertext.import_from(ctx, b.data_ptr(), B, lv, sc) for b, B, lv, sc in hin]
+            out = G.kan_infer(ctx, keys, gm, ins)
+            out.export_to(hout.data_ptr(), out_words)
+            for c in ins:
+                c.close()
+            out.close()
+
+        e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        el = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * a.batch * a.steps / (el / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_words * 8,
+               "path": "ckks_ct_import -> kan_infer -> ckks_ct_export"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": elapsed / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": config(a),
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": float(np.percentile(step_ms, 99)), "per": "batch of %d" % a.batch},
+            "roofline": roofline, "kernel_time_shares": shares, "gpu_launches": launches,
+            "clocks": clocks, "e2e": e2e, "micro": micro, "depth": depth, "slack": slack}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        from oracle import calibrate as OC
+        mo = OC.calibrate(model, Xcal, 27, [3])
+        v, sample, _ = oracle_sample(mo, a, a.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -79,6 +79,20 @@ int ckks_synchronize(ckks_ctx* ctx);
  * the first x^((q-1)/2N), x = 2,3,..., with psi^N = -1. Inputs must be < q. */
 int ckks_ntt(ckks_ctx* ctx, uint64_t* d_rows, size_t n_rows, int limbs, int inverse);
 
+/* ------------------------------------------------------------ launch accounting
+ * Every kernel launch is counted per kind (names from ckks_kernel_kind_name,
+ * kinds 0 .. ckks_kernel_kind_count()-1; the last kind counts device copies,
+ * not kernels). With profiling on, each launch is also bracketed by CUDA
+ * events on the context's stream; ckks_profile_collect synchronizes, then
+ * writes per kind the summed event time (ms), the summed algorithmic bytes
+ * (the minimum HBM traffic of the launch: inputs read once, outputs written
+ * once) and the number of timed launches, and clears the records. */
+int ckks_kernel_kind_count(void);
+const char* ckks_kernel_kind_name(int kind);
+int ckks_launch_counts(const ckks_ctx* ctx, uint64_t* counts, int cap);
+int ckks_profile_enable(ckks_ctx* ctx, int on);
+int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* launches, int cap);
+
 /* ------------------------------------------------------------ keys
  * Secret-key generation from `seed` (ternary secret, ChaCha20 stream), the
  * relinearisation key, and one Galois key per rotation step in rot_steps
@@ -168,6 +182,22 @@ typedef struct {
   const int* comp;
   int n_comp;
 } kan_layer_desc;
+
+/* Host-only model preparation (no device work).
+ * kan_silu_fit: Chebyshev coefficients cheb[0..degree] of the weighted
+ * least-squares SiLU fit of Eq. 12 on [lo, hi] (n_samples evenly spaced
+ * points, weight 10 within mu +- 3 sigma, 1 outside), solved by Householder QR.
+ * kan_calibrate: for each layer (only n_in, n_out, G, k, grid, coef, w_s,
+ * w_b of `layers` are read), the statistics of the layer's inputs over the
+ * n calibration vectors X[n][n_in] under the exact FP64 KAN (Eqs. 1-5), the
+ * SiLU range of Eq. 11 (or fixed_range[0..1] if not NULL) and its fit, and
+ * the comparison bound R = 1.1 (max|x| + max|knot|) / 2 of Algorithm 2.
+ * Outputs per layer: R[l], silu_lo[l], silu_hi[l], cheb[l*(degree+1) ..]. */
+int kan_silu_fit(double lo, double hi, double mu, double sigma, int degree, int n_samples,
+                 double* cheb);
+int kan_calibrate(const kan_layer_desc* layers, size_t n_layers, const double* X, size_t n,
+                  int silu_degree, const double* fixed_range, int n_fit_samples, double* R,
+                  double* silu_lo, double* silu_hi, double* cheb);
 
 int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layers,
                      kan_model** out);

@@ -37,6 +37,11 @@ SIGNATURES = {
     "ckks_set_stream": (c_i32, [c_vp, c_vp]),
     "ckks_synchronize": (c_i32, [c_vp]),
     "ckks_ntt": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_i32]),
+    "ckks_kernel_kind_count": (c_i32, []),
+    "ckks_kernel_kind_name": (ctypes.c_char_p, [c_i32]),
+    "ckks_launch_counts": (c_i32, [c_vp, c_vp, c_i32]),
+    "ckks_profile_enable": (c_i32, [c_vp, c_i32]),
+    "ckks_profile_collect": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32]),
     "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
@@ -61,6 +66,8 @@ SIGNATURES = {
     "ckks_level_down": (c_i32, [c_vp, c_vp, c_i32, PP]),
     "ckks_rotate": (c_i32, [c_vp, c_vp, c_vp, ctypes.c_int32, PP]),
     "ckks_rotate_hoisted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "kan_silu_fit": (c_i32, [c_dbl, c_dbl, c_dbl, c_dbl, c_i32, c_i32, c_vp]),
+    "kan_calibrate": (c_i32, [c_vp, c_sz, c_vp, c_sz, c_i32, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "kan_model_create": (c_i32, [c_vp, c_vp, c_sz, PP]),
     "kan_model_destroy": (c_i32, [c_vp]),
     "kan_model_rotations": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
@@ -132,6 +139,28 @@ class Context:
     def ntt(self, dev_ptr, n_rows, limbs, inverse=False):
         check(lib().ckks_ntt(self.h, dev_ptr, n_rows, limbs, 1 if inverse else 0))
 
+    @staticmethod
+    def kernel_kinds():
+        n = lib().ckks_kernel_kind_count()
+        return [lib().ckks_kernel_kind_name(k).decode() for k in range(n)]
+
+    def launch_counts(self):
+        names = self.kernel_kinds()
+        out = np.zeros(len(names), np.uint64)
+        check(lib().ckks_launch_counts(self.h, _p(out), len(names)))
+        return dict(zip(names, (int(x) for x in out)))
+
+    def profile(self, on):
+        check(lib().ckks_profile_enable(self.h, 1 if on else 0))
+
+    def profile_collect(self):
+        """{kind: (ms, algorithmic bytes, launches)} since the last collect."""
+        names = self.kernel_kinds()
+        ms, by = np.zeros(len(names)), np.zeros(len(names))
+        ln = np.zeros(len(names), np.uint64)
+        check(lib().ckks_profile_collect(self.h, _p(ms), _p(by), _p(ln), len(names)))
+        return {n: (float(a), float(b), int(c)) for n, a, b, c in zip(names, ms, by, ln) if c}
+
 
 class Keys:
     def __init__(self, ctx, seed, rot_steps=()):
@@ -195,6 +224,19 @@ class Ciphertext:
             data = data[None]
         h = c_vp()
         check(lib().ckks_ct_import(ctx.h, _p(data), data.shape[0], level, scale, ctypes.byref(h)))
+        return Ciphertext(ctx, h)
+
+    def words(self):
+        return self.batch * 2 * (self.level + 1) * self.ctx.N
+
+    def export_to(self, host_ptr, cap_words):
+        """Copy to caller-owned host memory (e.g. a pinned buffer)."""
+        check(lib().ckks_ct_export(self.h, host_ptr, cap_words))
+
+    @staticmethod
+    def import_from(ctx, host_ptr, batch, level, scale):
+        h = c_vp()
+        check(lib().ckks_ct_import(ctx.h, host_ptr, batch, level, scale, ctypes.byref(h)))
         return Ciphertext(ctx, h)
 
     def slice(self, first, count):
@@ -277,6 +319,49 @@ def rotate_hoisted(ctx, keys, a, steps):
     return [Ciphertext(ctx, c_vp(h)) for h in hs]
 
 
+def _descs(layers, keep):
+    descs = (KanLayerDesc * len(layers))()
+    for d, L in zip(descs, layers):
+        arrs = [np.ascontiguousarray(L[k], dtype=np.float64) for k in ("coef", "w_s", "w_b")]
+        cheb = np.ascontiguousarray(L.get("silu_cheb", [0.0, 0.0]), dtype=np.float64)
+        comp = np.ascontiguousarray(L.get("comp", [1]), dtype=np.int32)
+        keep += arrs + [cheb, comp]
+        d.n_in, d.n_out, d.G, d.k = L["n_in"], L["n_out"], L["G"], L["k"]
+        d.grid_lo, d.grid_hi = L["lo"], L["hi"]
+        d.coef, d.w_s, d.w_b = _p(arrs[0]), _p(arrs[1]), _p(arrs[2])
+        d.R, d.silu_lo, d.silu_hi = L.get("R", 1.0), L.get("silu_lo", -1.0), L.get("silu_hi", 1.0)
+        d.silu_cheb, d.silu_degree = _p(cheb), len(cheb) - 1
+        d.comp, d.n_comp = _p(comp), len(comp)
+    return descs
+
+
+def silu_fit(lo, hi, mu, sigma, degree, n_samples=10000):
+    out = np.zeros(degree + 1)
+    check(lib().kan_silu_fit(lo, hi, mu, sigma, degree, n_samples, _p(out)))
+    return out
+
+
+def calibrate(layers, X, silu_degree, comp, fixed_range=None, n_fit_samples=10000):
+    """Per-layer R, SiLU range and fit (Eqs. 11-12) computed by the library;
+    returns copies of the layer dicts with the HE keys filled in."""
+    keep = []
+    descs = _descs(layers, keep)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = len(layers)
+    R, lo, hi = np.zeros(n), np.zeros(n), np.zeros(n)
+    cheb = np.zeros((n, silu_degree + 1))
+    fr = None if fixed_range is None else np.ascontiguousarray(fixed_range, dtype=np.float64)
+    check(lib().kan_calibrate(descs, n, _p(X), X.shape[0], silu_degree, _p(fr), n_fit_samples,
+                              _p(R), _p(lo), _p(hi), _p(cheb)))
+    out = []
+    for i, L in enumerate(layers):
+        L = dict(L)
+        L.update(R=float(R[i]), silu_lo=float(lo[i]), silu_hi=float(hi[i]), silu_cheb=cheb[i].copy(),
+                 comp=list(comp))
+        out.append(L)
+    return out
+
+
 class Model:
     """kan_model handle; `layers` are dicts as produced for the plaintext KAN
     plus the HE keys R, silu_lo, silu_hi, silu_cheb and comp."""
@@ -284,17 +369,7 @@ class Model:
     def __init__(self, ctx, layers):
         self.ctx = ctx
         self._keep = []
-        descs = (KanLayerDesc * len(layers))()
-        for d, L in zip(descs, layers):
-            arrs = [np.ascontiguousarray(L[k], dtype=np.float64) for k in ("coef", "w_s", "w_b", "silu_cheb")]
-            comp = np.ascontiguousarray(L["comp"], dtype=np.int32)
-            self._keep += arrs + [comp]
-            d.n_in, d.n_out, d.G, d.k = L["n_in"], L["n_out"], L["G"], L["k"]
-            d.grid_lo, d.grid_hi = L["lo"], L["hi"]
-            d.coef, d.w_s, d.w_b = _p(arrs[0]), _p(arrs[1]), _p(arrs[2])
-            d.R, d.silu_lo, d.silu_hi = L["R"], L["silu_lo"], L["silu_hi"]
-            d.silu_cheb, d.silu_degree = _p(arrs[3]), len(arrs[3]) - 1
-            d.comp, d.n_comp = _p(comp), len(comp)
+        descs = _descs(layers, self._keep)
         h = c_vp()
         check(lib().kan_model_create(ctx.h, descs, len(layers), ctypes.byref(h)))
         self.h = h

@@ -97,6 +97,49 @@ int ckks_synchronize(ckks_ctx* ctx) {
   });
 }
 
+int ckks_kernel_kind_count(void) { return K_KIND_COUNT; }
+
+const char* ckks_kernel_kind_name(int kind) { return kernel_kind_name(kind); }
+
+int ckks_launch_counts(const ckks_ctx* ctx, uint64_t* counts, int cap) {
+  return guard([&] {
+    need(ctx && counts, "NULL argument");
+    for (int k = 0; k < K_KIND_COUNT && k < cap; k++) counts[k] = ctx->c.launches[k];
+  });
+}
+
+int ckks_profile_enable(ckks_ctx* ctx, int on) {
+  return guard([&] {
+    need(ctx != nullptr, "ctx is NULL");
+    ctx->c.prof = on != 0;
+  });
+}
+
+int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* launches, int cap) {
+  return guard([&] {
+    need(ctx != nullptr, "ctx is NULL");
+    Ctx& c = ctx->c;
+    CK_CUDA(cudaStreamSynchronize(c.stream));
+    for (int k = 0; k < cap; k++) {
+      if (ms) ms[k] = 0;
+      if (bytes) bytes[k] = 0;
+      if (launches) launches[k] = 0;
+    }
+    for (auto& r : c.prof_recs) {
+      float t = 0;
+      CK_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      if (r.kind < cap) {
+        if (ms) ms[r.kind] += t;
+        if (bytes) bytes[r.kind] += r.bytes;
+        if (launches) launches[r.kind] += 1;
+      }
+      c.ev_pool.push_back(r.a);
+      c.ev_pool.push_back(r.b);
+    }
+    c.prof_recs.clear();
+  });
+}
+
 int ckks_ntt(ckks_ctx* ctx, uint64_t* d_rows, size_t n_rows, int limbs, int inverse) {
   return guard([&] {
     need(ctx && d_rows, "NULL argument");

@@ -38,6 +38,39 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
   return *this;
 }
 
+const char* kernel_kind_name(int k) {
+  static const char* names[K_KIND_COUNT] = {
+      "ntt_small", "ntt_fwd_columns", "ntt_fwd_chunks", "ntt_inv_chunks", "ntt_inv_columns",
+      "modup", "key_inner_product", "moddown_conv", "moddown_finish", "tensor", "mul_plain",
+      "add", "mul_int", "lincomb", "rotate_finish", "automorphism", "rescale_spread",
+      "rescale_finish", "int_to_rns", "encode_fft", "sample", "crypt", "copy"};
+  return (k >= 0 && k < K_KIND_COUNT) ? names[k] : "?";
+}
+
+cudaEvent_t Ctx::take_event() {
+  if (!ev_pool.empty()) {
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+Launch::Launch(Ctx& cx, int k, double algorithmic_bytes) : c(cx), kind(k), bytes(algorithmic_bytes) {
+  c.launches[k]++;
+  if (c.prof) {
+    cudaEvent_t a = c.take_event();
+    b = c.take_event();
+    CK_CUDA(cudaEventRecord(a, c.stream));
+    c.prof_recs.push_back(ProfRec{k, bytes, a, b});
+  }
+}
+Launch::~Launch() {
+  if (b) cudaEventRecord(b, c.stream);
+}
+
 // ------------------------------------------------------------------ host math
 uint64_t mulmod_h(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)(((u128)a * b) % q); }
 uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t q) {
@@ -267,6 +300,11 @@ void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p
 
 Ctx::~Ctx() {
   if (stream) cudaStreamSynchronize(stream);
+  for (auto& r : prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ev_pool) cudaEventDestroy(e);
   conv.clear();
   perms.clear();
   d_mod.reset();

@@ -189,28 +189,33 @@ __global__ void int_to_rns_kernel(const int64_t* v, uint64_t* out, size_t polys,
 void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,
            bool sub) {
   const size_t total = rows * c.N;
+  Launch L_(c, K_ADD, 3.0 * total * 8);
   add_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, b, out, total, c.log_n, l, c.dmod(), sub);
   CK_CUDA(cudaGetLastError());
 }
 
 void k_mul_pt(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t rows, int l) {
   const size_t total = rows * c.N;
+  Launch L_(c, K_MUL_PT, 2.0 * total * 8);
   mul_pt_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, out, total, c.log_n, l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows, int l) {
   const size_t total = rows * c.N;
+  Launch L_(c, K_MUL_INT, 2.0 * total * 8);
   mul_int_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, k, out, total, c.log_n, l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l) {
+  Launch L_(c, K_ADD, 2.0 * B * l * c.N * 8);
   add_int_c0_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, k, B, c.log_n, l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_add_pt_c0(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t B, int l) {
+  Launch L_(c, K_ADD, 5.0 * B * l * c.N * 8);
   add_pt_c0_kernel<<<grid_for(B * 2 * l * c.N), TPB, 0, c.stream>>>(a, pt, out, B, c.log_n, l,
                                                                      c.dmod());
   CK_CUDA(cudaGetLastError());
@@ -218,6 +223,7 @@ void k_add_pt_c0(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, s
 
 void k_tensor(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t B, int l,
               bool accumulate) {
+  Launch L_(c, K_TENSOR, (accumulate ? 10.0 : 7.0) * B * l * c.N * 8);
   tensor_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, b, out, B, c.log_n, l, c.dmod(),
                                                              accumulate);
   CK_CUDA(cudaGetLastError());
@@ -234,6 +240,7 @@ void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::ve
     C.c[j] = k[j];
   }
   const size_t total = rows * c.N;
+  Launch L_(c, K_LINCOMB, (in.size() + 1.0) * total * 8);
   lincomb_kernel<<<grid_for(total), TPB, 0, c.stream>>>(P, C, (int)in.size(), out, total, c.log_n,
                                                         l, c.dmod());
   CK_CUDA(cudaGetLastError());
@@ -241,24 +248,28 @@ void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::ve
 
 void k_copy_limbs(Ctx& c, const uint64_t* in, int l_in, uint64_t* out, int l_out, size_t polys) {
   const size_t w = (size_t)l_out * c.N * 8;
+  Launch L_(c, K_COPY, 2.0 * w * polys);
   CK_CUDA(cudaMemcpy2DAsync(out, w, in, (size_t)l_in * c.N * 8, w, polys, cudaMemcpyDeviceToDevice,
                             c.stream));
 }
 
 void k_automorphism(Ctx& c, const uint64_t* in, uint64_t* out, size_t rows, const uint32_t* perm) {
   const size_t total = rows * c.N;
+  Launch L_(c, K_AUTO, 2.0 * total * 8);
   automorphism_kernel<<<grid_for(total), TPB, 0, c.stream>>>(in, out, total, c.log_n, perm);
   CK_CUDA(cudaGetLastError());
 }
 
 void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
                      uint64_t* out, size_t B, int l) {
+  Launch L_(c, K_ROT_FINISH, 5.0 * B * l * c.N * 8);
   rotate_finish_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, ks, perm, out, B, c.log_n,
                                                                     l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_rescale_spread(Ctx& c, const uint64_t* last, uint64_t* out, size_t polys, int level) {
+  Launch L_(c, K_RS_SPREAD, (1.0 + level) * polys * c.N * 8);
   rescale_spread_kernel<<<grid_for(polys * level * c.N), TPB, 0, c.stream>>>(last, out, polys,
                                                                             c.log_n, level, c.dmod());
   CK_CUDA(cudaGetLastError());
@@ -266,6 +277,7 @@ void k_rescale_spread(Ctx& c, const uint64_t* last, uint64_t* out, size_t polys,
 
 void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,
                       int level, const uint64_t* inv, const uint64_t* invs) {
+  Launch L_(c, K_RS_FINISH, 3.0 * level * polys * c.N * 8);
   rescale_finish_kernel<<<grid_for(polys * level * c.N), TPB, 0, c.stream>>>(
       in, r, out, polys, c.log_n, level, c.dmod(), inv, invs);
   CK_CUDA(cudaGetLastError());
@@ -273,6 +285,7 @@ void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* o
 
 void k_int_to_rns(Ctx& c, const int64_t* v, uint64_t* out, size_t polys, int rows,
                   const int16_t* pattern) {
+  Launch L_(c, K_INT_RNS, (1.0 + rows) * polys * c.N * 8);
   int_to_rns_kernel<<<grid_for(polys * rows * c.N), TPB, 0, c.stream>>>(v, out, polys, rows,
                                                                        c.log_n, pattern, c.dmod());
   CK_CUDA(cudaGetLastError());

@@ -113,9 +113,11 @@ __global__ void gather_kernel(const double* xr, double* out, size_t B, size_t nv
 
 void run_stages(Ctx& c, double* xr, double* xi, size_t B, int sign) {
   const size_t n = c.N / 2;
-  for (uint32_t len = 2; len <= n; len <<= 1)
+  for (uint32_t len = 2; len <= n; len <<= 1) {
+    Launch L_(c, K_ENCODE, 8.0 * B * n * 8);
     stage_kernel<<<grid_for(B * (n / 2)), TPB, 0, c.stream>>>(
         xr, xi, B, c.log_n, len, static_cast<const double*>(c.d_fft.p), sign);
+  }
   CK_CUDA(cudaGetLastError());
 }
 
@@ -128,15 +130,20 @@ int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double sca
   CK_CUDA(cudaMemsetAsync(xr.p, 0, xr.bytes, c.stream));
   CK_CUDA(cudaMemsetAsync(xi.p, 0, xi.bytes, c.stream));
   CK_CUDA(cudaMemsetAsync(c.d_flag.p, 0, 4, c.stream));
-  if (nv)
+  if (nv) {
+    Launch L_(c, K_ENCODE, 2.0 * B * nv * 8);
     place_kernel<<<grid_for(B * nv), TPB, 0, c.stream>>>(d_v, nv, static_cast<double*>(xr.p), B,
                                                          c.log_n, static_cast<const uint32_t*>(c.d_slot.p));
+  }
   run_stages(c, static_cast<double*>(xr.p), static_cast<double*>(xi.p), B, -1);
   const double f = scale / (double)n;
+  {
+  Launch L_(c, K_ENCODE, 4.0 * B * n * 8);
   untwist_round_kernel<<<grid_for(B * n), TPB, 0, c.stream>>>(
       static_cast<double*>(xr.p), static_cast<double*>(xi.p), static_cast<int64_t*>(coef.p), B,
       c.log_n, static_cast<const double*>(c.d_fft.p), f, static_cast<int*>(c.d_flag.p));
   CK_CUDA(cudaGetLastError());
+  }
   const int l = level + 1;
   k_int_to_rns(c, static_cast<int64_t*>(coef.p), pt, B, l, c.iota());
   ntt_forward(c, pt, B * l, c.iota(), l);
@@ -149,12 +156,16 @@ int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double sca
 void decode_limb0(Ctx& c, const uint64_t* m, size_t B, double scale, double* d_out, size_t nv) {
   const size_t n = c.N / 2;
   DevBuf xr(&c, B * n * 8), xi(&c, B * n * 8);
+  {
+  Launch L_(c, K_ENCODE, 4.0 * B * n * 8);
   twist_kernel<<<grid_for(B * n), TPB, 0, c.stream>>>(m, static_cast<double*>(xr.p),
                                                       static_cast<double*>(xi.p), B, c.log_n,
                                                       c.mod[0], scale,
                                                       static_cast<const double*>(c.d_fft.p));
   CK_CUDA(cudaGetLastError());
+  }
   run_stages(c, static_cast<double*>(xr.p), static_cast<double*>(xi.p), B, +1);
+  Launch L_(c, K_ENCODE, 2.0 * B * nv * 8);
   gather_kernel<<<grid_for(B * nv), TPB, 0, c.stream>>>(static_cast<double*>(xr.p), d_out, B, nv,
                                                         c.log_n,
                                                         static_cast<const uint32_t*>(c.d_slot.p));

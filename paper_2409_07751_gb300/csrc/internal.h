@@ -60,6 +60,21 @@ struct ConvTables {
   DevBuf md_pinv, md_pinv_s;  // [l]: P^-1 mod q_i
 };
 
+// Kernel kinds timed by the optional per-launch CUDA-event profiler.
+enum KernelKind {
+  K_NTT_SMALL, K_NTT_FWD_COL, K_NTT_FWD_CHUNK, K_NTT_INV_CHUNK, K_NTT_INV_COL,
+  K_MODUP, K_INNER, K_MD_CONV, K_MD_FINISH, K_TENSOR, K_MUL_PT, K_ADD, K_MUL_INT,
+  K_LINCOMB, K_ROT_FINISH, K_AUTO, K_RS_SPREAD, K_RS_FINISH, K_INT_RNS, K_ENCODE,
+  K_SAMPLE, K_CRYPT, K_COPY, K_KIND_COUNT
+};
+const char* kernel_kind_name(int k);
+
+struct ProfRec {
+  int kind;
+  double bytes;
+  cudaEvent_t a, b;
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -84,6 +99,13 @@ struct Ctx {
   DevBuf d_flag;            // int32 device status word (encoding overflow)
   DevBuf d_rs_inv, d_rs_invs;     // [(L+1)][(L+1)]: q_l^-1 mod q_t at [l][t]
   DevBuf d_pmod;                  // [L+1]: P mod q_t
+
+  // launch accounting and optional per-launch event timing
+  uint64_t launches[K_KIND_COUNT] = {};
+  bool prof = false;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> ev_pool;
+  cudaEvent_t take_event();
 
   ~Ctx();
   const Mod* dmod() const { return static_cast<const Mod*>(d_mod.p); }
@@ -118,6 +140,17 @@ struct ckks_ct {
 
 namespace ck {
 
+// RAII marker around one launch (or copy): counts it and, when profiling is
+// on, brackets it with events on the context's stream.
+struct Launch {
+  Ctx& c;
+  int kind;
+  double bytes;
+  cudaEvent_t b = nullptr;
+  Launch(Ctx& cx, int k, double algorithmic_bytes);
+  ~Launch();
+};
+
 // ---- host helpers (context.cu)
 uint64_t mulmod_h(uint64_t a, uint64_t b, uint64_t q);
 uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t q);
@@ -132,8 +165,11 @@ void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p
 
 // ---- NTT (ntt.cu): rows r at base + r*N use modulus pattern[r % P]; a
 // negative pattern entry skips the row.
-void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P);
-void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P);
+// `active` = rows actually transformed (for traffic accounting).
+void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
+                 size_t active = SIZE_MAX);
+void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
+                 size_t active = SIZE_MAX);
 
 // ---- elementwise (elementwise.cu). Ciphertext batches are [B][polys][l][N].
 void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,

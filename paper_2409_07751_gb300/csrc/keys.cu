@@ -92,10 +92,13 @@ std::unique_ptr<DevBuf> switch_key(Ctx& c, const ckks_keys& k, uint64_t seed, ui
   CK_CUDA(cudaMemcpy2DAsync(key->u64() + (size_t)n_qp * N, 2 * (size_t)n_qp * N * 8, a.p,
                             (size_t)n_qp * N * 8, (size_t)n_qp * N * 8, beta,
                             cudaMemcpyDeviceToDevice, c.stream));
+  {
+  Launch L_(c, K_CRYPT, 5.0 * beta * n_qp * N * 8);
   keygen_b_kernel<<<grid_for((size_t)beta * n_qp * N), TPB, 0, c.stream>>>(
       key->u64(), er.u64(), k.s.u64(), sp.u64(), c.d_pmod.u64(), beta, n_qp, c.L, c.alpha, c.log_n,
       c.dmod());
   CK_CUDA(cudaGetLastError());
+  }
   return key;
 }
 
@@ -141,10 +144,13 @@ Ct encrypt(Ctx& c, const ckks_keys& keys, const double* values, size_t B, size_t
   ntt_forward(c, er.u64(), B * l, c.iota(), l);
   sample_uniform(c, seed, d_ids.u64(), B, l, c.iota(), a.u64());
   Ct ct = ct_alloc(c, B, level, c.delta[level]);
+  {
+  Launch L_(c, K_CRYPT, 6.0 * B * l * N * 8);
   encrypt_kernel<<<grid_for(B * l * N), TPB, 0, c.stream>>>(ct->d.u64(), m.u64(), a.u64(),
                                                              er.u64(), keys.s.u64(), B, l, c.log_n,
                                                              c.dmod());
   CK_CUDA(cudaGetLastError());
+  }
   CK_CUDA(cudaStreamSynchronize(c.stream));  // host ids vector goes out of scope
   return ct;
 }
@@ -153,9 +159,12 @@ void decrypt(Ctx& c, const ckks_keys& keys, const ckks_ct& ct, double* out, size
   if (n > c.N / 2) throw Error(CKKS_ERR_INVALID_ARG, "more values than slots");
   const size_t N = c.N;
   DevBuf x(&c, ct.B * N * 8);
+  {
+  Launch L_(c, K_CRYPT, 4.0 * ct.B * N * 8);
   decrypt_limb0_kernel<<<grid_for(ct.B * N), TPB, 0, c.stream>>>(
       ct.d.u64(), keys.s.u64(), x.u64(), ct.B, ct.level + 1, c.log_n, c.dmod());
   CK_CUDA(cudaGetLastError());
+  }
   ntt_inverse(c, x.u64(), ct.B, c.iota(), 1);
   DevBuf o(&c, std::max<size_t>(ct.B * n, 1) * 8);
   if (n) decode_limb0(c, x.u64(), ct.B, ct.scale, static_cast<double*>(o.p), n);

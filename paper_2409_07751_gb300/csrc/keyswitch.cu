@@ -141,12 +141,16 @@ void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext) {
   DevBuf xc(&c, B * l * c.N * 8);
   CK_CUDA(cudaMemcpyAsync(xc.p, d, xc.bytes, cudaMemcpyDeviceToDevice, c.stream));
   ntt_inverse(c, xc.u64(), B * l, c.iota(), l);
+  const double W8 = (double)c.N * 8.0;
+  {
+  Launch L_(c, K_MODUP, W8 * (double)B * (2.0 * l + (double)T.beta * T.rows));
   modup_kernel<<<grid_for(B * T.beta * c.N), TPB, 0, c.stream>>>(
       xc.u64(), d, ext, B, c.log_n, l, c.alpha, T.beta, T.rows, c.L, c.dmod(), T.dhinv.u64(),
       T.dhinv_s.u64(), T.dh.u64(), T.dh_s.u64());
   CK_CUDA(cudaGetLastError());
+  }
   ntt_forward(c, ext, B * T.beta * T.rows, static_cast<const int16_t*>(T.ext_pattern.p),
-              T.beta * T.rows);
+              T.beta * T.rows, B * ((size_t)T.beta * T.rows - l));
 }
 
 void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
@@ -156,16 +160,25 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
   if (T.beta > 32) throw Error(CKKS_ERR_UNSUPPORTED, "more than 32 digits");
   const uint32_t* perm = galois ? c.perm(galois) : nullptr;
   DevBuf acc(&c, B * 2 * rows * c.N * 8);
+  const double W8 = (double)c.N * 8.0;
+  {
+  Launch L_(c, K_INNER, W8 * rows * ((double)B * T.beta + 2.0 * T.beta + 2.0 * B));
   inner_product_kernel<<<grid_for((size_t)rows * c.N), TPB, 0, c.stream>>>(
       ext, key, acc.u64(), B, c.log_n, l, T.beta, rows, c.L, c.n_qp, c.dmod(), perm);
   CK_CUDA(cudaGetLastError());
-  ntt_inverse(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows);
+  }
+  ntt_inverse(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows,
+              B * 2 * (size_t)c.alpha);
   DevBuf conv(&c, B * 2 * l * c.N * 8);
+  {
+  Launch L_(c, K_MD_CONV, W8 * B * 2.0 * (c.alpha + l));
   moddown_conv_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
       acc.u64(), conv.u64(), B * 2, c.log_n, l, c.alpha, rows, c.L, c.dmod(), c.d_md_yinv.u64(),
       c.d_md_yinv_s.u64(), c.d_md_ph.u64(), c.d_md_ph_s.u64());
   CK_CUDA(cudaGetLastError());
+  }
   ntt_forward(c, conv.u64(), B * 2 * l, c.iota(), l);
+  Launch L2_(c, K_MD_FINISH, W8 * B * 2.0 * 3.0 * l);
   moddown_finish_kernel<<<grid_for(B * 2 * l * c.N), TPB, 0, c.stream>>>(
       acc.u64(), conv.u64(), out, B * 2, c.log_n, l, rows, c.dmod(), T.md_pinv.u64(),
       T.md_pinv_s.u64());

@@ -13,6 +13,8 @@
 // remaining log2(N2) stages stay inside contiguous chunks of N2 elements,
 // which one CTA transforms in shared memory. The inverse runs the same two
 // phases in the opposite order.
+#include <algorithm>
+
 #include "modarith.cuh"
 
 namespace ck {
@@ -187,8 +189,9 @@ void launch_columns(int N1, dim3 g, cudaStream_t s, uint64_t* base, int log_n,
 }
 
 template <bool INV>
-void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P) {
+void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P, size_t active) {
   if (n_rows == 0) return;
+  const double bytes = 2.0 * (double)std::min(active, n_rows) * (double)c.N * 8.0;
   const Mod* mods = c.dmod();
   const uint64_t* tw = static_cast<const uint64_t*>(INV ? c.d_itw.p : c.d_tw.p);
   const uint64_t* tws = static_cast<const uint64_t*>(INV ? c.d_itws.p : c.d_tws.p);
@@ -196,6 +199,7 @@ void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int 
   const uint64_t* nis = static_cast<const uint64_t*>(c.d_ninvs.p);
   if (c.log_n <= CHUNK_LOG) {
     const int threads = std::min<int>(256, (int)(c.N / 2));
+    Launch L_(c, K_NTT_SMALL, bytes);
     ntt_small<INV><<<(unsigned)n_rows, threads, c.N * 8, c.stream>>>(base, c.log_n, pattern, P,
                                                                      mods, tw, tws, ni, nis);
   } else {
@@ -203,10 +207,18 @@ void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int 
     const dim3 gcol((unsigned)(n_rows * (CHUNK / 256)));
     const dim3 gchk((unsigned)(n_rows * N1));
     if (!INV) {
-      launch_columns<false>(N1, gcol, c.stream, base, c.log_n, pattern, P, mods, tw, tws, ni, nis);
+      {
+        Launch L_(c, K_NTT_FWD_COL, bytes);
+        launch_columns<false>(N1, gcol, c.stream, base, c.log_n, pattern, P, mods, tw, tws, ni, nis);
+      }
+      Launch L_(c, K_NTT_FWD_CHUNK, bytes);
       ntt_chunks<false><<<gchk, CHUNK_THREADS, 0, c.stream>>>(base, c.log_n, pattern, P, mods, tw, tws);
     } else {
-      ntt_chunks<true><<<gchk, CHUNK_THREADS, 0, c.stream>>>(base, c.log_n, pattern, P, mods, tw, tws);
+      {
+        Launch L_(c, K_NTT_INV_CHUNK, bytes);
+        ntt_chunks<true><<<gchk, CHUNK_THREADS, 0, c.stream>>>(base, c.log_n, pattern, P, mods, tw, tws);
+      }
+      Launch L_(c, K_NTT_INV_COL, bytes);
       launch_columns<true>(N1, gcol, c.stream, base, c.log_n, pattern, P, mods, tw, tws, ni, nis);
     }
   }
@@ -215,11 +227,13 @@ void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int 
 
 }  // namespace
 
-void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P) {
-  ntt_run<false>(c, base, n_rows, pattern, P);
+void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
+                 size_t active) {
+  ntt_run<false>(c, base, n_rows, pattern, P, active);
 }
-void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P) {
-  ntt_run<true>(c, base, n_rows, pattern, P);
+void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
+                 size_t active) {
+  ntt_run<true>(c, base, n_rows, pattern, P, active);
 }
 
 }  // namespace ck

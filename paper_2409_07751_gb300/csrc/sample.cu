@@ -110,17 +110,20 @@ __global__ void uniform_kernel(uint64_t seed, const uint64_t* ids, size_t count,
 
 void sample_ternary(Ctx& c, uint64_t seed, int64_t* out) {
   if (c.N < 16) throw Error(CKKS_ERR_UNSUPPORTED, "N < 16");
+  Launch L_(c, K_SAMPLE, c.N * 8.0);
   ternary_kernel<<<grid_for(c.N / 16), TPB, 0, c.stream>>>(seed, out, c.N);
   CK_CUDA(cudaGetLastError());
 }
 
 void sample_cbd(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int64_t* out) {
+  Launch L_(c, K_SAMPLE, count * c.N * 8.0);
   cbd_kernel<<<grid_for(count * c.N / 8), TPB, 0, c.stream>>>(seed, ids, count, out, c.N);
   CK_CUDA(cudaGetLastError());
 }
 
 void sample_uniform(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int rows,
                     const int16_t* pattern, uint64_t* out) {
+  Launch L_(c, K_SAMPLE, count * rows * c.N * 8.0);
   uniform_kernel<<<grid_for(count * rows * c.N / 4), TPB, 0, c.stream>>>(
       seed, ids, count, rows, pattern, c.dmod(), out, c.N);
   CK_CUDA(cudaGetLastError());
