@@ -240,7 +240,9 @@ def main():
     from paper_2409_07751_gb300 import ckks as G
     from paper_2409_07751_gb300 import workloads as W
 
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream shared by the library and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = G.Context(a.log_n, a.levels, 4, device=local)
     ctx.set_stream(stream.cuda_stream)
     model, Xcal, X = model_and_inputs(a, rank)
