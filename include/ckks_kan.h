@@ -139,6 +139,22 @@ int ckks_mul_relin(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const
                    ckks_ct** out);
 /* Divide by the top prime q_l with centred rounding; level - 1. */
 int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct** out);
+/* The same rescale for callers that cannot allocate device memory (for
+ * example while a stream is being captured, or under a fixed memory budget);
+ * the paper has no counterpart. Computes exactly what ckks_rescale computes,
+ * on raw device buffers: d_in holds `batch` ciphertexts [batch][2][level+1][N]
+ * in NTT form at `level` (>= 1), d_out receives [batch][2][level][N]; the
+ * output scale is the input scale / q_level (the caller keeps the scale).
+ * Both buffers are caller-owned device memory on the context's device; work
+ * is queued on the context's stream. No allocation happens: the working
+ * memory is a fixed 64 MiB device array inside the library (8 Mi words, held
+ * by every GPU that loads the library until exit); sizes needing more than
+ * 2 * batch * N * (level + 1) <= 8 Mi words are rejected with
+ * CKKS_ERR_INVALID_ARG. The first call on a device looks the array up (do it
+ * before any stream capture). All calls share the array: calls that overlap
+ * on the GPU race, so serialize them. */
+int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, size_t batch, int level,
+                         uint64_t* d_out);
 /* Eq. 8 complete: bring both to the lower level, multiply, relinearise, rescale. */
 int ckks_mul(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const ckks_ct* b,
              ckks_ct** out);

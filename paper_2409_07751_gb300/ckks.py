@@ -59,6 +59,7 @@ SIGNATURES = {
     "ckks_mul_relin": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
     "ckks_rescale": (c_i32, [c_vp, c_vp, PP]),
     "ckks_mul": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
+    "ckks_rescale_noalloc": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_vp]),
     "ckks_mul_plain": (c_i32, [c_vp, c_vp, c_vp, c_sz, PP]),
     "ckks_add_plain": (c_i32, [c_vp, c_vp, c_vp, c_sz, PP]),
     "ckks_mul_const": (c_i32, [c_vp, c_vp, c_dbl, PP]),
@@ -280,6 +281,11 @@ def mul_relin(ctx, keys, a, b):
 
 def rescale(ctx, a):
     return _out(ctx, lib().ckks_rescale, ctx.h, a.h)
+
+
+def rescale_noalloc(ctx, d_in, batch, level, d_out):
+    """Rescale raw device buffers without any device allocation (see the header)."""
+    check(lib().ckks_rescale_noalloc(ctx.h, d_in, batch, level, d_out))
 
 
 def mul(ctx, keys, a, b):
