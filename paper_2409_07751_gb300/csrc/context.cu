@@ -40,7 +40,7 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
 
 const char* kernel_kind_name(int k) {
   static const char* names[K_KIND_COUNT] = {
-      "ntt_small", "ntt_fwd_columns", "ntt_fwd_chunks", "ntt_inv_chunks", "ntt_inv_columns",
+      "ntt_small", "ntt_fwd", "ntt_inv",
       "modup", "key_inner_product", "moddown_conv", "moddown_finish", "tensor", "mul_plain",
       "add", "mul_int", "lincomb", "rotate_finish", "automorphism", "rescale_spread",
       "rescale_finish", "int_to_rns", "encode_fft", "sample", "crypt", "copy"};

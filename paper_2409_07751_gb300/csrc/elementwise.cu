@@ -36,20 +36,21 @@ __global__ void mul_pt_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* o
   }
 }
 
-struct Consts {
-  int64_t c[32];
+constexpr int LC_TERMS = 16;
+struct LincombRes {
+  uint64_t v[LC_TERMS][MAX_LIMBS];
 };
 
-__global__ void mul_int_kernel(const uint64_t* a, int64_t k, uint64_t* out, size_t total,
+__global__ void mul_int_kernel(const uint64_t* a, LimbRes k, uint64_t* out, size_t total,
                                int log_n, int l, const Mod* mods) {
   GRID_LOOP(i, total) {
     const int t = (int)((i >> log_n) % l);
-    out[i] = mul_mod(a[i], smod64(k, mods[t].q), mods[t]);
+    out[i] = mul_mod(a[i], k.v[t], mods[t]);
   }
 }
 
 // poly 0 of each batch element += k (a constant polynomial is constant in NTT form)
-__global__ void add_int_c0_kernel(uint64_t* a, int64_t k, size_t B, int log_n, int l,
+__global__ void add_int_c0_kernel(uint64_t* a, LimbRes k, size_t B, int log_n, int l,
                                   const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
   const size_t per = (size_t)l * N;
@@ -57,7 +58,7 @@ __global__ void add_int_c0_kernel(uint64_t* a, int64_t k, size_t B, int log_n, i
     const size_t b = i / per, r = i % per;
     const int t = (int)(r >> log_n);
     uint64_t* p = a + b * 2 * per + r;
-    *p = add_mod(*p, smod64(k, mods[t].q), mods[t].q);
+    *p = add_mod(*p, k.v[t], mods[t].q);
   }
 }
 
@@ -105,16 +106,16 @@ __global__ void tensor_kernel(const uint64_t* a, const uint64_t* b, uint64_t* ou
 }
 
 struct Ptrs {
-  const uint64_t* p[32];
+  const uint64_t* p[LC_TERMS];
 };
 
-__global__ void lincomb_kernel(Ptrs in, Consts k, int K, uint64_t* out, size_t total, int log_n,
-                               int l, const Mod* mods) {
+__global__ void lincomb_kernel(Ptrs in, LincombRes k, int K, uint64_t* out, size_t total,
+                               int log_n, int l, const Mod* mods) {
   GRID_LOOP(i, total) {
     const int t = (int)((i >> log_n) % l);
     const Mod m = mods[t];
     uint64_t acc = 0;
-    for (int j = 0; j < K; j++) acc = add_mod(acc, mul_mod(in.p[j][i], smod64(k.c[j], m.q), m), m.q);
+    for (int j = 0; j < K; j++) acc = add_mod(acc, mul_mod(in.p[j][i], k.v[j][t], m), m.q);
     out[i] = acc;
   }
 }
@@ -184,6 +185,21 @@ __global__ void int_to_rns_kernel(const int64_t* v, uint64_t* out, size_t polys,
   }
 }
 
+LimbRes limb_res(const Ctx& c, int64_t k, int l) {
+  if (l > MAX_LIMBS) throw Error(CKKS_ERR_UNSUPPORTED, "more than 64 limbs");
+  LimbRes r{};
+  for (int t = 0; t < l; t++) {
+    const uint64_t q = c.mod[t];
+    if (k >= 0) {
+      r.v[t] = (uint64_t)k % q;
+    } else {
+      const uint64_t m = ((uint64_t)(-(k + 1)) + 1) % q;
+      r.v[t] = m ? q - m : 0;
+    }
+  }
+  return r;
+}
+
 }  // namespace
 
 void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,
@@ -204,13 +220,15 @@ void k_mul_pt(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size
 void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows, int l) {
   const size_t total = rows * c.N;
   Launch L_(c, K_MUL_INT, 2.0 * total * 8);
-  mul_int_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, k, out, total, c.log_n, l, c.dmod());
+  mul_int_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, limb_res(c, k, l), out, total, c.log_n,
+                                                        l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l) {
   Launch L_(c, K_ADD, 2.0 * B * l * c.N * 8);
-  add_int_c0_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, k, B, c.log_n, l, c.dmod());
+  add_int_c0_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, limb_res(c, k, l), B, c.log_n,
+                                                                 l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
@@ -231,13 +249,15 @@ void k_tensor(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_
 
 void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::vector<int64_t>& k,
                    uint64_t* out, size_t rows, int l) {
-  if (in.size() > 32 || in.size() != k.size() || in.empty())
-    throw Error(CKKS_ERR_INVALID_ARG, "lincomb: 1..32 terms");
+  if (in.size() > (size_t)LC_TERMS || in.size() != k.size() || in.empty())
+    throw Error(CKKS_ERR_INVALID_ARG, "lincomb: 1..16 terms");
+  if (l > MAX_LIMBS) throw Error(CKKS_ERR_UNSUPPORTED, "more than 64 limbs");
   Ptrs P{};
-  Consts C{};
+  LincombRes C;  // by-value kernel argument (8 KiB)
   for (size_t j = 0; j < in.size(); j++) {
     P.p[j] = in[j];
-    C.c[j] = k[j];
+    const LimbRes r = limb_res(c, k[j], l);
+    for (int t = 0; t < l; t++) C.v[j][t] = r.v[t];
   }
   const size_t total = rows * c.N;
   Launch L_(c, K_LINCOMB, (in.size() + 1.0) * total * 8);

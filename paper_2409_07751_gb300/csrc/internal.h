@@ -62,7 +62,7 @@ struct ConvTables {
 
 // Kernel kinds timed by the optional per-launch CUDA-event profiler.
 enum KernelKind {
-  K_NTT_SMALL, K_NTT_FWD_COL, K_NTT_FWD_CHUNK, K_NTT_INV_CHUNK, K_NTT_INV_COL,
+  K_NTT_SMALL, K_NTT_FWD, K_NTT_INV,
   K_MODUP, K_INNER, K_MD_CONV, K_MD_FINISH, K_TENSOR, K_MUL_PT, K_ADD, K_MUL_INT,
   K_LINCOMB, K_ROT_FINISH, K_AUTO, K_RS_SPREAD, K_RS_FINISH, K_INT_RNS, K_ENCODE,
   K_SAMPLE, K_CRYPT, K_COPY, K_KIND_COUNT

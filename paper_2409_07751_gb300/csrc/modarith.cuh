@@ -40,11 +40,21 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
 }
 // reduction of an arbitrary 64-bit value (rarely used; plain division)
 __device__ __forceinline__ uint64_t reduce64(uint64_t a, uint64_t q) { return a % q; }
-// signed value -> residue
+// signed value -> residue (the division only runs when |v| >= q)
 __device__ __forceinline__ uint64_t smod64(int64_t v, uint64_t q) {
-  if (v >= 0) return (uint64_t)v % q;
-  const uint64_t m = ((uint64_t)(-(v + 1)) + 1) % q;
+  if (v >= 0) {
+    const uint64_t u = (uint64_t)v;
+    return u < q ? u : u % q;
+  }
+  uint64_t m = (uint64_t)(-(v + 1)) + 1;
+  m = m < q ? m : m % q;
   return m ? q - m : 0;
 }
+
+// per-limb residues of host constants, passed by value to kernels
+constexpr int MAX_LIMBS = 64;
+struct LimbRes {
+  uint64_t v[MAX_LIMBS];
+};
 
 }  // namespace ck

@@ -155,9 +155,9 @@ Ct op_lincomb(Ctx& c, const std::vector<const ckks_ct*>& in, const std::vector<d
   if (ptrs.empty()) {
     CK_CUDA(cudaMemsetAsync(acc->d.p, 0, acc->d.bytes, c.stream));
   } else {
-    // at most 32 terms per pass
-    for (size_t s = 0; s < ptrs.size(); s += 32) {
-      const size_t e = std::min(ptrs.size(), s + 32);
+    // at most 16 terms per pass
+    for (size_t s = 0; s < ptrs.size(); s += 16) {
+      const size_t e = std::min(ptrs.size(), s + 16);
       std::vector<const uint64_t*> pp(ptrs.begin() + s, ptrs.begin() + e);
       std::vector<int64_t> kk(ks.begin() + s, ks.begin() + e);
       if (s == 0) {
