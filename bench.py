@@ -49,7 +49,44 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-micro", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--kernel", default=None, choices=["ntt", "intt"],
+                   help="time one kernel kind alone (NTT limbs/s) instead of the network")
+    p.add_argument("--rows", type=int, default=592, help="limbs per launch for --kernel")
     return p.parse_args()
+
+
+def kernel_arm(a):
+    """--kernel ntt|intt: forward or inverse NTT of `rows` random limbs of
+    N = 2^log_n (moduli cycling through the 37 Q primes) per launch."""
+    import numpy as np
+    import torch
+    from paper_2409_07751_gb300 import build
+    build.build()
+    from paper_2409_07751_gb300 import ckks as G
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = G.Context(a.log_n, a.levels, 4)
+    ctx.set_stream(stream.cuda_stream)
+    limbs = a.levels + 1
+    N = 1 << a.log_n
+    rng = np.random.default_rng(0)
+    h = np.stack([rng.integers(0, int(ctx.moduli[r % limbs]), N, dtype=np.uint64) for r in range(a.rows)])
+    d = torch.from_numpy(h.view(np.int64)).cuda()
+    inv = a.kernel == "intt"
+    for _ in range(a.warmup):
+        ctx.ntt(d.data_ptr(), a.rows, limbs, inv)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        ctx.ntt(d.data_ptr(), a.rows, limbs, inv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    by = 2.0 * a.rows * N * 8
+    print(json.dumps({"kernel": a.kernel, "rows": a.rows, "n_poly": N, "ms_per_launch": ms,
+                      "limbs_per_s": a.rows / (ms / 1000.0), "algorithmic_GBps": by / (ms / 1000.0) / 1e9}),
+          flush=True)
 
 
 def config(a):
@@ -59,11 +96,29 @@ def config(a):
             "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)"}
 
 
+def shard_plan(rank, batch):
+    """Request sharding across ranks: rank r serves its own batch (its own
+    input and level seeds, object ids r*batch ..), with no exchange."""
+    from paper_2409_07751_gb300 import workloads as W
+    return {"input_seed": W.SEED_INPUTS + rank, "level_seed": W.SEED_INPUTS + 1 + rank,
+            "first_index": rank * batch}
+
+
+def reduce_max(value, dist, device):
+    """Max of a per-rank scalar over all ranks (the slowest rank sets the time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def model_and_inputs(a, rank):
     from paper_2409_07751_gb300 import workloads as W
     model = W.make_model("kan_4_8_4_1")
     Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
-    X = W.uniform_inputs(a.batch, 4, seed=W.SEED_INPUTS + rank)
+    X = W.uniform_inputs(a.batch, 4, seed=shard_plan(rank, a.batch)["input_seed"])
     return model, Xcal, X
 
 
@@ -222,6 +277,8 @@ def main():
     a = args_()
     if a.impl == "reference":
         return reference_arm(a)
+    if a.kernel:
+        return kernel_arm(a)
     import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -250,12 +307,13 @@ def main():
     gm = G.Model(ctx, m)
     depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
     slack = a.levels - depth
-    levels = W.uneven_levels(a.batch, a.levels, slack, seed=W.SEED_INPUTS + 1 + rank)
+    plan = shard_plan(rank, a.batch)
+    levels = W.uneven_levels(a.batch, a.levels, slack, seed=plan["level_seed"])
     keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
     cts = []
     for lv in sorted(set(int(x) for x in levels)):
         sel = np.nonzero(levels == lv)[0]
-        cts.append(G.encrypt(ctx, keys, X[sel], lv, W.SEED_ENC, first_index=int(sel[0]) + rank * a.batch))
+        cts.append(G.encrypt(ctx, keys, X[sel], lv, W.SEED_ENC, first_index=int(sel[0]) + plan["first_index"]))
 
     def step():
         out = G.kan_infer(ctx, keys, gm, cts)
@@ -288,11 +346,7 @@ def main():
     ctx.profile(False)
     after = ctx.launch_counts()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
-    elapsed = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = reduce_max(ev[0].elapsed_time(ev[-1]), dist, "cuda")
     launches = sum(after[k] - before[k] for k in after if k != "copy")
     value = world * a.batch * a.steps / (elapsed / 1000.0)
 
@@ -367,11 +421,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        el = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = reduce_max(e0.elapsed_time(e1), dist, "cuda")
         e2e = {"value": world * a.batch * a.steps / (el / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_words * 8,
                "path": "ckks_ct_import -> kan_infer -> ckks_ct_export"}

@@ -40,7 +40,7 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
 
 const char* kernel_kind_name(int k) {
   static const char* names[K_KIND_COUNT] = {
-      "ntt_small", "ntt_fwd", "ntt_inv",
+      "ntt_small", "ntt_fwd", "ntt_inv", "modup_ntt", "moddown_ntt", "rescale_ntt",
       "modup", "key_inner_product", "moddown_conv", "moddown_finish", "tensor", "mul_plain",
       "add", "mul_int", "lincomb", "rotate_finish", "automorphism", "rescale_spread",
       "rescale_finish", "int_to_rns", "encode_fft", "sample", "crypt", "copy"};
@@ -90,6 +90,7 @@ Mod make_mod(uint64_t q) {
   m.s = 64 - __builtin_clzll(q);
   m.mu = (uint64_t)(((u128)1 << (2 * m.s)) / q);
   m.pad = 0;
+  m.t64 = (uint64_t)((((u128)1) << 64) % q);
   return m;
 }
 
@@ -381,6 +382,25 @@ ConvTables& Ctx::tables(int level) {
   T->pq_pattern = upload(this, pq);
   T->md_pinv = upload(this, pinv);
   T->md_pinv_s = upload(this, pinvs);
+  std::vector<uint64_t> xp(l), xps(l), mp(rows, 0), mps(rows, 0);
+  for (int j = 0; j < beta; j++)
+    for (int i = j * A; i < std::min((j + 1) * A, l); i++) {
+      const uint64_t ninv = invmod_h(N % mod[i], mod[i]);
+      xp[i] = mulmod_h(ninv, dhinv[(size_t)j * A + (i - j * A)], mod[i]);
+      xps[i] = shoup_h(xp[i], mod[i]);
+    }
+  for (int a = 0; a < A; a++) {
+    const uint64_t pa = mod[L + 1 + a];
+    uint64_t h = 1;
+    for (int b = 0; b < A; b++)
+      if (b != a) h = mulmod_h(h, mod[L + 1 + b] % pa, pa);
+    mp[l + a] = mulmod_h(invmod_h(N % pa, pa), invmod_h(h, pa), pa);
+    mps[l + a] = shoup_h(mp[l + a], pa);
+  }
+  T->xs_post = upload(this, xp);
+  T->xs_post_s = upload(this, xps);
+  T->md_post = upload(this, mp);
+  T->md_post_s = upload(this, mps);
   auto& ref = *T;
   conv[level] = std::move(T);
   return ref;

@@ -17,9 +17,10 @@ namespace ck {
 // Per-modulus constants visible to kernels.
 struct Mod {
   uint64_t q;
-  uint64_t mu;  // floor(2^(2s) / q), Barrett
-  uint32_t s;   // bit length of q
+  uint64_t mu;   // floor(2^(2s) / q), Barrett
+  uint32_t s;    // bit length of q
   uint32_t pad;
+  uint64_t t64;  // 2^64 mod q
 };
 
 struct Error : std::runtime_error {
@@ -58,11 +59,13 @@ struct ConvTables {
   DevBuf ext_pattern;      // int16 [beta*rows]: modulus index of the row, -1 = digit row
   DevBuf pq_pattern;       // int16 [rows]: -1 for Q rows, special modulus for P rows
   DevBuf md_pinv, md_pinv_s;  // [l]: P^-1 mod q_i
+  DevBuf xs_post, xs_post_s;  // [l]: N^-1 Dhat_i^-1 mod q_i (fused ModUp)
+  DevBuf md_post, md_post_s;  // [rows]: N^-1 Phat_a^-1 mod p_a on P rows (fused ModDown)
 };
 
 // Kernel kinds timed by the optional per-launch CUDA-event profiler.
 enum KernelKind {
-  K_NTT_SMALL, K_NTT_FWD, K_NTT_INV,
+  K_NTT_SMALL, K_NTT_FWD, K_NTT_INV, K_MODUP_NTT, K_MODDOWN_NTT, K_RESCALE_NTT,
   K_MODUP, K_INNER, K_MD_CONV, K_MD_FINISH, K_TENSOR, K_MUL_PT, K_ADD, K_MUL_INT,
   K_LINCOMB, K_ROT_FINISH, K_AUTO, K_RS_SPREAD, K_RS_FINISH, K_INT_RNS, K_ENCODE,
   K_SAMPLE, K_CRYPT, K_COPY, K_KIND_COUNT
@@ -170,6 +173,17 @@ void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, 
                  size_t active = SIZE_MAX);
 void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
                  size_t active = SIZE_MAX);
+
+// Fused row kernels (N >= 8192): ModUp conversion in the forward NTT's
+// loads; ModDown / rescale subtract-and-scale in its stores.
+bool ntt_fused_available(const Ctx& c);
+void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
+                      const uint64_t* post, const uint64_t* posts, size_t active = SIZE_MAX);
+void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, int level,
+                     uint64_t* ext);
+void ntt_moddown_fused(Ctx& c, const uint64_t* acc, size_t BK, int level, uint64_t* out);
+void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t polys, int level,
+                       uint64_t* out);
 
 // ---- elementwise (elementwise.cu). Ciphertext batches are [B][polys][l][N].
 void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,

@@ -7,6 +7,8 @@
 //   other rows t: sum_{i in D_j} [x_i Dhat_i^{-1}]_{q_i} (Dhat_i mod m_t) mod m_t,
 //   then NTT.
 // ModDown: out_i = (acc_i - Conv_{P->Q}([acc]_P)_i) * P^{-1} mod q_i.
+#include <algorithm>
+
 #include "modarith.cuh"
 
 namespace ck {
@@ -61,32 +63,57 @@ __global__ void modup_kernel(const uint64_t* xc, const uint64_t* d, uint64_t* ex
   }
 }
 
-// thread per (r, n); loops over the batch so each key word is read once.
+constexpr int IP_THREADS = 128;
+
+// thread per (r, n); loops over the batch so each key word is read from HBM
+// once per launch. The thread's 2*beta key words sit in shared memory (a
+// private slice per thread, so no synchronization); products are summed as
+// 128-bit values and reduced once per output (moduli of >= 33 bits).
 // ext: [B][beta][rows][N]; key: [beta_max][2][n_qp][N]; acc: [B][2][rows][N]
-__global__ void inner_product_kernel(const uint64_t* ext, const uint64_t* key, uint64_t* acc,
-                                     size_t B, int log_n, int l, int beta, int rows, int L,
-                                     int n_qp, const Mod* mods, const uint32_t* perm) {
+__global__ void __launch_bounds__(IP_THREADS)
+    inner_product_kernel(const uint64_t* ext, const uint64_t* key, uint64_t* acc, size_t B,
+                         int log_n, int l, int beta, int rows, int L, int n_qp, const Mod* mods,
+                         const uint32_t* perm) {
+  extern __shared__ uint64_t kw[];  // [2*beta][IP_THREADS]
   const size_t N = (size_t)1 << log_n;
+  const uint32_t tid = threadIdx.x;
   GRID_LOOP(idx, (size_t)rows * N) {
     const size_t n = idx & (N - 1);
     const int r = (int)(idx >> log_n);
     const int mi = r < l ? r : L + 1 + (r - l);
     const Mod m = mods[mi];
     const size_t src = perm ? perm[n] : n;
-    uint64_t kb[32], ka[32];
     for (int j = 0; j < beta; j++) {
-      kb[j] = key[(((size_t)j * 2 + 0) * n_qp + mi) * N + n];
-      ka[j] = key[(((size_t)j * 2 + 1) * n_qp + mi) * N + n];
+      kw[(2 * j) * IP_THREADS + tid] = key[(((size_t)j * 2 + 0) * n_qp + mi) * N + n];
+      kw[(2 * j + 1) * IP_THREADS + tid] = key[(((size_t)j * 2 + 1) * n_qp + mi) * N + n];
     }
+    const bool lazy = m.s >= 33;
     for (size_t b = 0; b < B; b++) {
-      uint64_t a0 = 0, a1 = 0;
-      for (int j = 0; j < beta; j++) {
-        const uint64_t e = ext[((b * beta + j) * rows + r) * N + src];
-        a0 = add_mod(a0, mul_mod(e, kb[j], m), m.q);
-        a1 = add_mod(a1, mul_mod(e, ka[j], m), m.q);
+      const uint64_t* e0 = ext + ((b * beta) * rows + r) * N + src;
+      if (lazy) {
+        uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+        for (int j = 0; j < beta; j++) {
+          const uint64_t e = e0[(size_t)j * rows * N];
+          const uint64_t k0 = kw[(2 * j) * IP_THREADS + tid], k1 = kw[(2 * j + 1) * IP_THREADS + tid];
+          uint64_t p = e * k0;
+          h0 += __umul64hi(e, k0) + ((l0 + p) < l0 ? 1 : 0);
+          l0 += p;
+          p = e * k1;
+          h1 += __umul64hi(e, k1) + ((l1 + p) < l1 ? 1 : 0);
+          l1 += p;
+        }
+        acc[((b * 2 + 0) * rows + r) * N + n] = reduce_wide(l0, h0, m);
+        acc[((b * 2 + 1) * rows + r) * N + n] = reduce_wide(l1, h1, m);
+      } else {
+        uint64_t a0 = 0, a1 = 0;
+        for (int j = 0; j < beta; j++) {
+          const uint64_t e = e0[(size_t)j * rows * N];
+          a0 = add_mod(a0, mul_mod(e, kw[(2 * j) * IP_THREADS + tid], m), m.q);
+          a1 = add_mod(a1, mul_mod(e, kw[(2 * j + 1) * IP_THREADS + tid], m), m.q);
+        }
+        acc[((b * 2 + 0) * rows + r) * N + n] = a0;
+        acc[((b * 2 + 1) * rows + r) * N + n] = a1;
       }
-      acc[((b * 2 + 0) * rows + r) * N + n] = a0;
-      acc[((b * 2 + 1) * rows + r) * N + n] = a1;
     }
   }
 }
@@ -140,6 +167,11 @@ void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext) {
   if (c.alpha > MAX_ALPHA) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
   DevBuf xc(&c, B * l * c.N * 8);
   CK_CUDA(cudaMemcpyAsync(xc.p, d, xc.bytes, cudaMemcpyDeviceToDevice, c.stream));
+  if (ntt_fused_available(c)) {
+    ntt_inverse_post(c, xc.u64(), B * l, c.iota(), l, T.xs_post.u64(), T.xs_post_s.u64());
+    ntt_modup_fused(c, xc.u64(), d, B, level, ext);
+    return;
+  }
   ntt_inverse(c, xc.u64(), B * l, c.iota(), l);
   const double W8 = (double)c.N * 8.0;
   {
@@ -163,9 +195,17 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
   const double W8 = (double)c.N * 8.0;
   {
   Launch L_(c, K_INNER, W8 * rows * ((double)B * T.beta + 2.0 * T.beta + 2.0 * B));
-  inner_product_kernel<<<grid_for((size_t)rows * c.N), TPB, 0, c.stream>>>(
+  const size_t ip_total = (size_t)rows * c.N;
+  const size_t ip_blocks = std::min<size_t>((ip_total + IP_THREADS - 1) / IP_THREADS, 152 * 64);
+  inner_product_kernel<<<(unsigned)ip_blocks, IP_THREADS, 2 * T.beta * IP_THREADS * 8, c.stream>>>(
       ext, key, acc.u64(), B, c.log_n, l, T.beta, rows, c.L, c.n_qp, c.dmod(), perm);
   CK_CUDA(cudaGetLastError());
+  }
+  if (ntt_fused_available(c)) {
+    ntt_inverse_post(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows,
+                     T.md_post.u64(), T.md_post_s.u64(), B * 2 * (size_t)c.alpha);
+    ntt_moddown_fused(c, acc.u64(), B * 2, level, out);
+    return;
   }
   ntt_inverse(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows,
               B * 2 * (size_t)c.alpha);

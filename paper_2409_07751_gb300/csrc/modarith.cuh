@@ -20,6 +20,25 @@ __device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) 
 __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
   return a >= b ? a - b : a + (q - b);
 }
+// (hi:lo) mod q for (hi:lo) < 2^(2s)
+__device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi, const Mod& m) {
+  const uint32_t s = m.s;
+  const uint64_t x1 = (lo >> (s - 1)) | (hi << (65 - s));
+  const uint64_t ql = x1 * m.mu;
+  const uint64_t qh = __umul64hi(x1, m.mu);
+  const uint64_t qhat = (ql >> (s + 1)) | (qh << (63 - s));
+  uint64_t r = lo - qhat * m.q;
+  if (r >= m.q) r -= m.q;
+  if (r >= m.q) r -= m.q;
+  return r;
+}
+// any 128-bit (hi:lo) mod q, for q of at least 33 bits
+__device__ __forceinline__ uint64_t reduce_wide(uint64_t lo, uint64_t hi, const Mod& m) {
+  const uint64_t h = reduce128(hi, 0, m), l = reduce128(lo, 0, m);
+  const uint64_t plo = h * m.t64, phi = __umul64hi(h, m.t64);
+  const uint64_t slo = plo + l;
+  return reduce128(slo, phi + (slo < plo ? 1 : 0), m);
+}
 __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const Mod& m) {
   const uint64_t lo = a * b;
   const uint64_t hi = __umul64hi(a, b);

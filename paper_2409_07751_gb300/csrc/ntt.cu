@@ -17,6 +17,7 @@
 // Butterflies are Harvey's lazy forms: values live in [0, 4q) (forward) or
 // [0, 2q) (inverse) and are fully reduced only on the final store.
 #include <algorithm>
+#include <type_traits>
 
 #include "modarith.cuh"
 
@@ -105,6 +106,15 @@ __global__ void ntt_small(uint64_t* base, int log_n, const int16_t* pattern, int
   }
 }
 
+// Shared-memory swizzle within each 16-element block: with it, every access
+// pattern of the radix-8 rounds and of the chunk loads touches 16 distinct
+// 8-byte banks per half-warp (without it the distance-1 round is 8-way
+// conflicted).
+__device__ __forceinline__ uint32_t swz(uint32_t i) {
+  const uint32_t x = i >> 4;
+  return i ^ ((x & 7) | ((x & 4) << 1));
+}
+
 // ---------------------------------------------------------------- radix-8 rounds
 // Group g (0..511) of a chunk: elements base + k*s (k < 8), base = blk8*8s + r.
 // B8 = global index of the 8s-block. Forward: distances 4s, 2s, s (stage
@@ -119,7 +129,7 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
   const uint32_t m4 = 1u << (log_n - ls - 3);
   uint64_t x[8];
 #pragma unroll
-  for (int k = 0; k < 8; k++) x[k] = sm[base + ((uint32_t)k << ls)];
+  for (int k = 0; k < 8; k++) x[k] = sm[swz(base + ((uint32_t)k << ls))];
   if (!INV) {
     {
       const uint32_t i = m4 + B8;
@@ -162,50 +172,236 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
     }
   }
 #pragma unroll
-  for (int k = 0; k < 8; k++) sm[base + ((uint32_t)k << ls)] = x[k];
+  for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
 }
 
 // column transform of N1 elements (stride CHUNK) in registers
-template <int N1, bool INV>
-__device__ __forceinline__ void column(uint64_t* a, const uint64_t* w, const uint64_t* ws,
-                                       uint64_t q, uint64_t q2, uint64_t ni, uint64_t nis) {
+// forward: x[s] = ld(c + s*CHUNK) -> stages -> mid[c + s*CHUNK] (lazy, [0,4q))
+template <int N1, class D, class R>
+__device__ __forceinline__ void column_fwd(const D& d, const R& r, uint32_t c, const uint64_t* w,
+                                           const uint64_t* ws, uint64_t q, uint64_t q2,
+                                           const uint64_t* kc) {
+  uint64_t x[N1];
+#pragma unroll
+  for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc);
+#pragma unroll
+  for (int m = 1; m < N1; m <<= 1) {
+    const int t1 = N1 / (2 * m);
+#pragma unroll
+    for (int i = 0; i < m; i++) {
+      const uint64_t wv = w[m + i], wsv = ws[m + i];
+#pragma unroll
+      for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < N1; s++) r.mid[c + (size_t)s * CHUNK] = x[s];
+}
+
+template <int N1>
+__device__ __forceinline__ void column_inv(uint64_t* a, const uint64_t* w, const uint64_t* ws,
+                                           uint64_t q, uint64_t q2, uint64_t post, uint64_t posts) {
   uint64_t x[N1];
 #pragma unroll
   for (int s = 0; s < N1; s++) x[s] = a[(size_t)s * CHUNK];
-  if (!INV) {
 #pragma unroll
-    for (int m = 1; m < N1; m <<= 1) {
-      const int t1 = N1 / (2 * m);
+  for (int m = N1 / 2; m >= 1; m >>= 1) {
+    const int t1 = N1 / (2 * m);
 #pragma unroll
-      for (int i = 0; i < m; i++) {
-        const uint64_t wv = w[m + i], wsv = ws[m + i];
+    for (int i = 0; i < m; i++) {
+      const uint64_t wv = w[m + i], wsv = ws[m + i];
 #pragma unroll
-        for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
-      }
+      for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
     }
+  }
 #pragma unroll
-    for (int s = 0; s < N1; s++) a[(size_t)s * CHUNK] = x[s];
-  } else {
-#pragma unroll
-    for (int m = N1 / 2; m >= 1; m >>= 1) {
-      const int t1 = N1 / (2 * m);
-#pragma unroll
-      for (int i = 0; i < m; i++) {
-        const uint64_t wv = w[m + i], wsv = ws[m + i];
-#pragma unroll
-        for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
-      }
+  for (int s = 0; s < N1; s++) a[(size_t)s * CHUNK] = mul_shoup(x[s], post, posts, q);
+}
+
+// Per-CTA row description produced by a descriptor's setup().
+struct Row {
+  int mi;            // modulus index
+  uint64_t* mid;     // row used for the intermediate (and the output unless stored elsewhere)
+  const uint64_t* src;   // prologue source rows
+  const uint64_t* src2;  // epilogue source row
+  int n_src;
+  uint64_t k, ks;    // epilogue constant
+  uint64_t aux;      // rescale: q of the dropped prime
+};
+
+constexpr int MAX_SRC = 16;
+
+// plain forward NTT of pattern-selected rows
+struct DescPlain {
+  uint64_t* base;
+  const int16_t* pattern;
+  int P;
+  size_t N;
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t*) const {
+    r.mi = pattern[blk % P];
+    if (r.mi < 0) return false;
+    r.mid = base + (size_t)blk * N;
+    return true;
+  }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*) const { return r.mid[i]; }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
+    r.mid[i] = v;
+  }
+};
+
+// ModUp target row: sum_a xs[a][i] * [Dhat_a]_{m} mod m, then NTT; digit rows copy d.
+struct DescModUp {
+  const uint64_t* xs;  // [B][l][N] coefficients already scaled by N^-1 Dhat^-1 (the iNTT post factor)
+  const uint64_t* d;   // [B][l][N] NTT form
+  uint64_t* ext;       // [B][beta][rows][N]
+  const uint64_t* dh;  // [beta][alpha][rows]
+  const uint64_t* dhs;
+  int l, beta, rows, alpha, L;
+  size_t N;
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc) const {
+    const int rr = (int)(blk % rows);
+    const int j = (int)((blk / rows) % beta);
+    const size_t b = blk / ((size_t)rows * beta);
+    const int lo = j * alpha, hi = min((j + 1) * alpha, l);
+    uint64_t* out = ext + (((size_t)b * beta + j) * rows + rr) * N;
+    if (rr >= lo && rr < hi) {
+      const uint64_t* src = d + ((size_t)b * l + rr) * N;
+      for (size_t i = threadIdx.x; i < N; i += blockDim.x) out[i] = src[i];
+      return false;
     }
+    r.mi = rr < l ? rr : L + 1 + (rr - l);
+    r.mid = out;
+    r.src = xs + ((size_t)b * l + lo) * N;
+    r.n_src = hi - lo;
+    if (threadIdx.x < (unsigned)r.n_src) {
+      const size_t ti = ((size_t)(j * alpha) + threadIdx.x) * rows + rr;
+      kc[threadIdx.x] = dh[ti];
+      kc[MAX_SRC + threadIdx.x] = dhs[ti];
+    }
+    return true;
+  }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc) const {
+    const uint64_t m = r.aux;
+    uint64_t acc = 0;
+    for (int a = 0; a < r.n_src; a++)
+      acc = add_mod(acc, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
+    return acc;
+  }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
+    r.mid[i] = v;
+  }
+};
+
+// ModDown output row i of (b,k): (acc_i - NTT(sum_a y_a [Phat_a]_{q_i})) * P^-1
+struct DescModDown {
+  const uint64_t* acc;  // [BK][rows][N]; P rows already inverse-transformed and scaled
+  uint64_t* out;        // [BK][l][N]
+  const uint64_t* ph;   // [alpha][L+1]
+  const uint64_t* phs;
+  const uint64_t* pinv;  // [l]
+  const uint64_t* pinvs;
+  int l, rows, alpha, L;
+  size_t N;
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc) const {
+    const int i = (int)(blk % l);
+    const size_t bk = blk / l;
+    r.mi = i;
+    r.mid = out + (bk * l + i) * N;
+    r.src = acc + (bk * rows + l) * N;
+    r.src2 = acc + (bk * rows + i) * N;
+    r.n_src = alpha;
+    r.k = pinv[i];
+    r.ks = pinvs[i];
+    if (threadIdx.x < (unsigned)alpha) {
+      kc[threadIdx.x] = ph[(size_t)threadIdx.x * (L + 1) + i];
+      kc[MAX_SRC + threadIdx.x] = phs[(size_t)threadIdx.x * (L + 1) + i];
+    }
+    return true;
+  }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc) const {
+    const uint64_t m = r.aux;
+    uint64_t s = 0;
+    for (int a = 0; a < r.n_src; a++)
+      s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
+    return s;
+  }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
+    r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+  }
+};
+
+// Rescale output row t of poly p: (c_t - NTT(centred(last) mod q_t)) * q_level^-1
+struct DescRescale {
+  const uint64_t* in;    // [polys][level+1][N]
+  const uint64_t* last;  // [polys][N] coefficient form of limb `level`
+  uint64_t* out;         // [polys][level][N]
+  const uint64_t* inv;   // [level]: q_level^-1 mod q_t
+  const uint64_t* invs;
+  uint64_t ql;
+  int level;
+  size_t N;
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t*) const {
+    const int t = (int)(blk % level);
+    const size_t p = blk / level;
+    r.mi = t;
+    r.mid = out + (p * level + t) * N;
+    r.src = last + p * N;
+    r.src2 = in + (p * (level + 1) + t) * N;
+    r.k = inv[t];
+    r.ks = invs[t];
+    return true;
+  }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*) const {
+    const uint64_t x = r.src[i];
+    const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
+    return smod64(v, r.aux);
+  }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
+    r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+  }
+};
+
+// Forward NTT, one CTA per output row: columns (prologue loads) then chunks
+// (epilogue stores).
+template <int N1, class D>
+__global__ void __launch_bounds__(ROW_THREADS, 1)
+    ntt_fwd_row(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws) {
+  __shared__ uint64_t s[CHUNK];
+  __shared__ uint64_t kc[2 * MAX_SRC];
+  Row r;
+  r.n_src = 0;
+  if (!d.setup(blockIdx.x, r, kc)) return;
+  __syncthreads();
+  const size_t N = (size_t)N1 * CHUNK;
+  const uint64_t q = mods[r.mi].q, q2 = 2 * q;
+  r.aux = q;
+  const uint64_t* w = tw + (size_t)r.mi * N;
+  const uint64_t* ws = tws + (size_t)r.mi * N;
+  const uint32_t g = threadIdx.x;
+  for (uint32_t c = g; c < CHUNK; c += ROW_THREADS) column_fwd<N1>(d, r, c, w, ws, q, q2, kc);
+  __syncthreads();
+  for (uint32_t chunk = 0; chunk < (uint32_t)N1; chunk++) {
+    const uint64_t* ac = r.mid + (size_t)chunk * CHUNK;
+    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) s[swz(i)] = ac[i];
+    __syncthreads();
 #pragma unroll
-    for (int s = 0; s < N1; s++) a[(size_t)s * CHUNK] = mul_shoup(x[s], ni, nis, q);
+    for (int ls = 9; ls >= 0; ls -= 3) {
+      round8<false>(s, g, ls, chunk, log_n, w, ws, q, q2);
+      __syncthreads();
+    }
+    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS)
+      d.store(r, chunk * CHUNK + i, reduce4(s[swz(i)], q, q2), q, kc);
+    __syncthreads();
   }
 }
 
-// One CTA per row: forward = columns then chunks; inverse = chunks then columns.
-template <int N1, bool INV>
+// Inverse NTT of pattern-selected rows; the final scaling is post[row % P]
+// (default N^-1).
+template <int N1>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
-    ntt_row(uint64_t* base, int log_n, const int16_t* pattern, int P, const Mod* mods,
-            const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv, const uint64_t* ninvs) {
+    ntt_inv_row(uint64_t* base, int log_n, const int16_t* pattern, int P, const Mod* mods,
+                const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
+                const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts) {
   __shared__ uint64_t s[CHUNK];
   const size_t row = blockIdx.x;
   const int mi = pattern[row % P];
@@ -215,42 +411,61 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
   const uint64_t* w = tw + (size_t)mi * N;
   const uint64_t* ws = tws + (size_t)mi * N;
   uint64_t* a = base + row * N;
-  const uint64_t ni = ninv[mi], nis = ninvs[mi];
+  const uint64_t pv = post ? post[row % P] : ninv[mi];
+  const uint64_t pvs = post ? posts[row % P] : ninvs[mi];
   const uint32_t g = threadIdx.x;
-  if (!INV) {
-    for (uint32_t c = g; c < CHUNK; c += ROW_THREADS) column<N1, false>(a + c, w, ws, q, q2, ni, nis);
-    __syncthreads();
-  }
   for (uint32_t chunk = 0; chunk < (uint32_t)N1; chunk++) {
     uint64_t* ac = a + (size_t)chunk * CHUNK;
-    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) s[i] = ac[i];
+    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) s[swz(i)] = ac[i];
     __syncthreads();
-    if (!INV) {
 #pragma unroll
-      for (int ls = 9; ls >= 0; ls -= 3) {
-        round8<false>(s, g, ls, chunk, log_n, w, ws, q, q2);
-        __syncthreads();
-      }
-      for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) ac[i] = reduce4(s[i], q, q2);
-    } else {
-#pragma unroll
-      for (int ls = 0; ls <= 9; ls += 3) {
-        round8<true>(s, g, ls, chunk, log_n, w, ws, q, q2);
-        __syncthreads();
-      }
-      for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) ac[i] = s[i];
+    for (int ls = 0; ls <= 9; ls += 3) {
+      round8<true>(s, g, ls, chunk, log_n, w, ws, q, q2);
+      __syncthreads();
     }
+    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) ac[i] = s[swz(i)];
     __syncthreads();
   }
-  if (INV)
-    for (uint32_t c = g; c < CHUNK; c += ROW_THREADS) column<N1, true>(a + c, w, ws, q, q2, ni, nis);
+  for (uint32_t c = g; c < CHUNK; c += ROW_THREADS) column_inv<N1>(a + c, w, ws, q, q2, pv, pvs);
 }
 
-template <int N1, bool INV>
-void launch_row(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, int P) {
-  ntt_row<N1, INV><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(
-      base, c.log_n, pattern, P, c.dmod(), static_cast<const uint64_t*>(INV ? c.d_itw.p : c.d_tw.p),
-      static_cast<const uint64_t*>(INV ? c.d_itws.p : c.d_tws.p), c.d_ninv.u64(), c.d_ninvs.u64());
+template <class D>
+void launch_fwd(Ctx& c, size_t n_rows, const D& d) {
+  if (n_rows == 0) return;
+  const uint64_t* tw = c.d_tw.u64();
+  const uint64_t* tws = c.d_tws.u64();
+  switch (c.log_n - CHUNK_LOG) {
+    case 1: ntt_fwd_row<2, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
+    case 2: ntt_fwd_row<4, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
+    case 3: ntt_fwd_row<8, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
+    case 4: ntt_fwd_row<16, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
+    default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
+  }
+  CK_CUDA(cudaGetLastError());
+}
+
+void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, int P,
+                const uint64_t* post, const uint64_t* posts) {
+  if (n_rows == 0) return;
+  const uint64_t* tw = c.d_itw.u64();
+  const uint64_t* tws = c.d_itws.u64();
+  const uint64_t* ni = c.d_ninv.u64();
+  const uint64_t* nis = c.d_ninvs.u64();
+#define INV_CASE(K, N1)                                                                      \
+  case K:                                                                                    \
+    ntt_inv_row<N1><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(base, c.log_n, pattern, \
+                                                                     P, c.dmod(), tw, tws,  \
+                                                                     ni, nis, post, posts); \
+    break;
+  switch (c.log_n - CHUNK_LOG) {
+    INV_CASE(1, 2)
+    INV_CASE(2, 4)
+    INV_CASE(3, 8)
+    INV_CASE(4, 16)
+    default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
+  }
+#undef INV_CASE
+  CK_CUDA(cudaGetLastError());
 }
 
 template <bool INV>
@@ -264,17 +479,14 @@ void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int 
         base, c.log_n, pattern, P, c.dmod(),
         static_cast<const uint64_t*>(INV ? c.d_itw.p : c.d_tw.p),
         static_cast<const uint64_t*>(INV ? c.d_itws.p : c.d_tws.p), c.d_ninv.u64(), c.d_ninvs.u64());
+    CK_CUDA(cudaGetLastError());
+  } else if (!INV) {
+    Launch L_(c, K_NTT_FWD, bytes);
+    launch_fwd(c, n_rows, DescPlain{base, pattern, P, c.N});
   } else {
-    Launch L_(c, INV ? K_NTT_INV : K_NTT_FWD, bytes);
-    switch (c.log_n - CHUNK_LOG) {
-      case 1: launch_row<2, INV>(c, n_rows, base, pattern, P); break;
-      case 2: launch_row<4, INV>(c, n_rows, base, pattern, P); break;
-      case 3: launch_row<8, INV>(c, n_rows, base, pattern, P); break;
-      case 4: launch_row<16, INV>(c, n_rows, base, pattern, P); break;
-      default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
-    }
+    Launch L_(c, K_NTT_INV, bytes);
+    launch_inv(c, n_rows, base, pattern, P, nullptr, nullptr);
   }
-  CK_CUDA(cudaGetLastError());
 }
 
 }  // namespace
@@ -286,6 +498,44 @@ void ntt_forward(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, 
 void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
                  size_t active) {
   ntt_run<true>(c, base, n_rows, pattern, P, active);
+}
+
+bool ntt_fused_available(const Ctx& c) { return c.log_n > CHUNK_LOG && c.log_n <= CHUNK_LOG + 4; }
+
+void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
+                      const uint64_t* post, const uint64_t* posts, size_t active) {
+  Launch L_(c, K_NTT_INV, 2.0 * (double)std::min(active, n_rows) * (double)c.N * 8.0);
+  launch_inv(c, n_rows, base, pattern, P, post, posts);
+}
+
+void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, int level,
+                     uint64_t* ext) {
+  ConvTables& T = c.tables(level);
+  if (c.alpha > MAX_SRC) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
+  const double W8 = (double)c.N * 8.0;
+  // reads: alpha scaled source rows per target row (L2-resident per digit) and
+  // the digit rows once; writes every extended row once
+  Launch L_(c, K_MODUP_NTT, W8 * (double)B * (2.0 * T.l + (double)T.beta * T.rows));
+  DescModUp dsc{xs, d, ext, T.dh.u64(), T.dh_s.u64(), T.l, T.beta, T.rows, c.alpha, c.L, c.N};
+  launch_fwd(c, B * T.beta * T.rows, dsc);
+}
+
+void ntt_moddown_fused(Ctx& c, const uint64_t* acc, size_t BK, int level, uint64_t* out) {
+  ConvTables& T = c.tables(level);
+  const double W8 = (double)c.N * 8.0;
+  Launch L_(c, K_MODDOWN_NTT, W8 * (double)BK * (c.alpha + 2.0 * T.l));
+  DescModDown dsc{acc, out, c.d_md_ph.u64(), c.d_md_ph_s.u64(), T.md_pinv.u64(), T.md_pinv_s.u64(),
+                  T.l, T.rows, c.alpha, c.L, c.N};
+  launch_fwd(c, BK * T.l, dsc);
+}
+
+void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t polys, int level,
+                       uint64_t* out) {
+  const double W8 = (double)c.N * 8.0;
+  Launch L_(c, K_RESCALE_NTT, W8 * (double)polys * (1.0 + 2.0 * level));
+  DescRescale dsc{in, last, out, c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
+                  c.d_rs_invs.u64() + (size_t)level * (c.L + 1), c.mod[level], level, c.N};
+  launch_fwd(c, polys * level, dsc);
 }
 
 }  // namespace ck

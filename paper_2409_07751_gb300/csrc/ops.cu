@@ -86,12 +86,17 @@ Ct op_rescale(Ctx& c, const ckks_ct& a) {
                             (size_t)(lv + 1) * c.N * 8, c.N * 8, polys, cudaMemcpyDeviceToDevice,
                             c.stream));
   ntt_inverse(c, last.u64(), polys, c.iota() + lv, 1);
-  DevBuf R(&c, polys * lv * c.N * 8);
-  k_rescale_spread(c, last.u64(), R.u64(), polys, lv);
-  ntt_forward(c, R.u64(), polys * lv, c.iota(), lv);
   double s = a.scale / (double)c.mod[lv];
   const double d = c.delta[lv - 1];
   if (fabs(s / d - 1.0) < SNAP) s = d;
+  if (ntt_fused_available(c)) {
+    Ct r = ct_alloc(c, a.B, lv - 1, s);
+    ntt_rescale_fused(c, a.d.u64(), last.u64(), polys, lv, r->d.u64());
+    return r;
+  }
+  DevBuf R(&c, polys * lv * c.N * 8);
+  k_rescale_spread(c, last.u64(), R.u64(), polys, lv);
+  ntt_forward(c, R.u64(), polys * lv, c.iota(), lv);
   Ct r = ct_alloc(c, a.B, lv - 1, s);
   k_rescale_finish(c, a.d.u64(), R.u64(), r->d.u64(), polys, lv,
                    c.d_rs_inv.u64() + (size_t)lv * (c.L + 1),
