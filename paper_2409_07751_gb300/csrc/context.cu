@@ -230,6 +230,32 @@ void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p
     ninv[t] = invmod_h(N % q, q);
     ninvs[t] = shoup_h(ninv[t], q);
   }
+  if (log_n > 12) {
+    // rounds with base distance s = 2^ls, ls = 9, 6, 3, 0: nodes m4 + B8,
+    // m4 = N / (8 s), B8 < m4, stored consecutively round after round
+    size_t nodes = 0;
+    for (int ls = 9; ls >= 0; ls -= 3) nodes += N >> (ls + 3);
+    c.tw8_nodes = nodes;
+    std::vector<uint64_t> t8((size_t)c.n_qp * nodes * 14), it8((size_t)c.n_qp * nodes * 14);
+    for (int t = 0; t < c.n_qp; t++) {
+      size_t node = (size_t)t * nodes;
+      for (int ls = 9; ls >= 0; ls -= 3) {
+        const uint64_t m4 = N >> (ls + 3);
+        for (uint64_t B8 = 0; B8 < m4; B8++, node++) {
+          const uint64_t idx[7] = {m4 + B8, 2 * m4 + 2 * B8, 2 * m4 + 2 * B8 + 1, 4 * m4 + 4 * B8,
+                                   4 * m4 + 4 * B8 + 1, 4 * m4 + 4 * B8 + 2, 4 * m4 + 4 * B8 + 3};
+          for (int k = 0; k < 7; k++) {
+            t8[node * 14 + 2 * k] = tw[t * N + idx[k]];
+            t8[node * 14 + 2 * k + 1] = tws[t * N + idx[k]];
+            it8[node * 14 + 2 * k] = itw[t * N + idx[k]];
+            it8[node * 14 + 2 * k + 1] = itws[t * N + idx[k]];
+          }
+        }
+      }
+    }
+    c.d_tw8 = upload(&c, t8);
+    c.d_itw8 = upload(&c, it8);
+  }
   c.d_mod = upload(&c, mods);
   c.d_tw = upload(&c, tw);
   c.d_tws = upload(&c, tws);
@@ -313,6 +339,8 @@ Ctx::~Ctx() {
   d_tws.reset();
   d_itw.reset();
   d_itws.reset();
+  d_tw8.reset();
+  d_itw8.reset();
   d_ninv.reset();
   d_ninvs.reset();
   d_iota.reset();

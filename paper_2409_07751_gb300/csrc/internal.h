@@ -92,6 +92,10 @@ struct Ctx {
   DevBuf d_tw, d_tws;       // [n_qp][N] psi^brv(k) and Shoup companions
   DevBuf d_itw, d_itws;     // inverse
   DevBuf d_ninv, d_ninvs;   // [n_qp]
+  // radix-8 round twiddles (N >= 8192): per modulus, per round node k of the
+  // stage tree, 7 (twiddle, Shoup) pairs: node, its 2 children, 4 grandchildren
+  DevBuf d_tw8, d_itw8;
+  size_t tw8_nodes = 0;     // nodes per modulus
   DevBuf d_iota;            // int16 [n_qp]: 0..n_qp-1
   DevBuf d_fft;             // double [2N][2]: cos, sin of 2 pi k / 2N
   DevBuf d_slot;            // uint32 [N/2]: k_j = (5^j mod 2N - 1) / 4

@@ -19,9 +19,13 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "modarith.cuh"
 
 namespace ck {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -119,57 +123,45 @@ __device__ __forceinline__ uint32_t swz(uint32_t i) {
 // Group g (0..511) of a chunk: elements base + k*s (k < 8), base = blk8*8s + r.
 // B8 = global index of the 8s-block. Forward: distances 4s, 2s, s (stage
 // indices m4 = N/(8s), 2 m4, 4 m4). Inverse: distances s, 2s, 4s.
+// t8: this modulus' packed round twiddles (7 (w, w') pairs per node).
+__device__ __forceinline__ uint32_t node_base(uint32_t ls, int log_n) {
+  // nodes of earlier rounds (base distances 512, 64, 8 before 64, 8, 1)
+  uint32_t off = 0;
+  for (int r = 9; r > (int)ls; r -= 3) off += 1u << (log_n - r - 3);
+  return off;
+}
+
 template <bool INV>
 __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
-                                       int log_n, const uint64_t* w, const uint64_t* ws,
-                                       uint64_t q, uint64_t q2) {
+                                       int log_n, const ulonglong2* t8, uint64_t q, uint64_t q2) {
   const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
   const uint32_t base = (blk8 << (ls + 3)) + r;
   const uint32_t B8 = (chunk << (CHUNK_LOG - ls - 3)) + blk8;
-  const uint32_t m4 = 1u << (log_n - ls - 3);
+  const ulonglong2* T = t8 + (size_t)(node_base(ls, log_n) + B8) * 7;
   uint64_t x[8];
 #pragma unroll
   for (int k = 0; k < 8; k++) x[k] = sm[swz(base + ((uint32_t)k << ls))];
+  ulonglong2 tt[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) tt[k] = T[k];
   if (!INV) {
-    {
-      const uint32_t i = m4 + B8;
-      const uint64_t a = w[i], as = ws[i];
 #pragma unroll
-      for (int k = 0; k < 4; k++) ct_lazy(x[k], x[k + 4], a, as, q, q2);
-    }
-    {
-      const uint32_t i = 2 * m4 + 2 * B8;
-      const uint64_t a = w[i], as = ws[i], b = w[i + 1], bs = ws[i + 1];
-      ct_lazy(x[0], x[2], a, as, q, q2);
-      ct_lazy(x[1], x[3], a, as, q, q2);
-      ct_lazy(x[4], x[6], b, bs, q, q2);
-      ct_lazy(x[5], x[7], b, bs, q, q2);
-    }
-    {
-      const uint32_t i = 4 * m4 + 4 * B8;
+    for (int k = 0; k < 4; k++) ct_lazy(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
+    ct_lazy(x[0], x[2], tt[1].x, tt[1].y, q, q2);
+    ct_lazy(x[1], x[3], tt[1].x, tt[1].y, q, q2);
+    ct_lazy(x[4], x[6], tt[2].x, tt[2].y, q, q2);
+    ct_lazy(x[5], x[7], tt[2].x, tt[2].y, q, q2);
 #pragma unroll
-      for (int k = 0; k < 4; k++) ct_lazy(x[2 * k], x[2 * k + 1], w[i + k], ws[i + k], q, q2);
-    }
+    for (int k = 0; k < 4; k++) ct_lazy(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
   } else {
-    {
-      const uint32_t i = 4 * m4 + 4 * B8;
 #pragma unroll
-      for (int k = 0; k < 4; k++) gs_lazy(x[2 * k], x[2 * k + 1], w[i + k], ws[i + k], q, q2);
-    }
-    {
-      const uint32_t i = 2 * m4 + 2 * B8;
-      const uint64_t a = w[i], as = ws[i], b = w[i + 1], bs = ws[i + 1];
-      gs_lazy(x[0], x[2], a, as, q, q2);
-      gs_lazy(x[1], x[3], a, as, q, q2);
-      gs_lazy(x[4], x[6], b, bs, q, q2);
-      gs_lazy(x[5], x[7], b, bs, q, q2);
-    }
-    {
-      const uint32_t i = m4 + B8;
-      const uint64_t a = w[i], as = ws[i];
+    for (int k = 0; k < 4; k++) gs_lazy(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
+    gs_lazy(x[0], x[2], tt[1].x, tt[1].y, q, q2);
+    gs_lazy(x[1], x[3], tt[1].x, tt[1].y, q, q2);
+    gs_lazy(x[4], x[6], tt[2].x, tt[2].y, q, q2);
+    gs_lazy(x[5], x[7], tt[2].x, tt[2].y, q, q2);
 #pragma unroll
-      for (int k = 0; k < 4; k++) gs_lazy(x[k], x[k + 4], a, as, q, q2);
-    }
+    for (int k = 0; k < 4; k++) gs_lazy(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
   }
 #pragma unroll
   for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
@@ -237,7 +229,7 @@ struct DescPlain {
   const int16_t* pattern;
   int P;
   size_t N;
-  __device__ bool setup(uint32_t blk, Row& r, uint64_t*) const {
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t*, uint32_t, uint32_t) const {
     r.mi = pattern[blk % P];
     if (r.mi < 0) return false;
     r.mid = base + (size_t)blk * N;
@@ -258,7 +250,7 @@ struct DescModUp {
   const uint64_t* dhs;
   int l, beta, rows, alpha, L;
   size_t N;
-  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc) const {
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
     const int rr = (int)(blk % rows);
     const int j = (int)((blk / rows) % beta);
     const size_t b = blk / ((size_t)rows * beta);
@@ -266,7 +258,8 @@ struct DescModUp {
     uint64_t* out = ext + (((size_t)b * beta + j) * rows + rr) * N;
     if (rr >= lo && rr < hi) {
       const uint64_t* src = d + ((size_t)b * l + rr) * N;
-      for (size_t i = threadIdx.x; i < N; i += blockDim.x) out[i] = src[i];
+      const size_t per = N / nparts;
+      for (size_t i = part * per + threadIdx.x; i < (part + 1) * per; i += blockDim.x) out[i] = src[i];
       return false;
     }
     r.mi = rr < l ? rr : L + 1 + (rr - l);
@@ -302,7 +295,7 @@ struct DescModDown {
   const uint64_t* pinvs;
   int l, rows, alpha, L;
   size_t N;
-  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc) const {
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
     const int i = (int)(blk % l);
     const size_t bk = blk / l;
     r.mi = i;
@@ -340,7 +333,7 @@ struct DescRescale {
   uint64_t ql;
   int level;
   size_t N;
-  __device__ bool setup(uint32_t blk, Row& r, uint64_t*) const {
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t*, uint32_t, uint32_t) const {
     const int t = (int)(blk % level);
     const size_t p = blk / level;
     r.mi = t;
@@ -361,72 +354,170 @@ struct DescRescale {
   }
 };
 
-// Forward NTT, one CTA per output row: columns (prologue loads) then chunks
-// (epilogue stores).
+// Forward NTT of one row per cluster of CS CTAs (CS = N1/4, or 1 for N1 <= 4).
+// CTA `rank` owns chunks [rank*CPC, (rank+1)*CPC) of the row in shared memory.
+// Column phase: the CTA transforms columns [rank*CHUNK/CS, ...) from the
+// prologue loads and writes element s of each column into the shared memory
+// of the CTA owning chunk s (distributed shared memory). After a cluster
+// barrier each CTA runs the radix-8 rounds on its own chunks in place and
+// writes the results through the epilogue. The row never round-trips
+// through global memory.
 template <int N1, class D>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
-    ntt_fwd_row(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws) {
-  __shared__ uint64_t s[CHUNK];
+    ntt_fwd_cl(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws,
+               const ulonglong2* tw8, size_t nodes) {
+  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  constexpr int CPC = N1 / CS;
+  extern __shared__ uint64_t sm[];  // CPC chunks
   __shared__ uint64_t kc[2 * MAX_SRC];
+  const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
+  const uint32_t row = blockIdx.x / CS;
   Row r;
   r.n_src = 0;
-  if (!d.setup(blockIdx.x, r, kc)) return;
+  if (!d.setup(row, r, kc, rank, CS)) return;  // same decision on every CTA of the cluster
   __syncthreads();
   const size_t N = (size_t)N1 * CHUNK;
   const uint64_t q = mods[r.mi].q, q2 = 2 * q;
   r.aux = q;
   const uint64_t* w = tw + (size_t)r.mi * N;
   const uint64_t* ws = tws + (size_t)r.mi * N;
+  const ulonglong2* t8 = tw8 + (size_t)r.mi * nodes * 7;
   const uint32_t g = threadIdx.x;
-  for (uint32_t c = g; c < CHUNK; c += ROW_THREADS) column_fwd<N1>(d, r, c, w, ws, q, q2, kc);
-  __syncthreads();
-  for (uint32_t chunk = 0; chunk < (uint32_t)N1; chunk++) {
-    const uint64_t* ac = r.mid + (size_t)chunk * CHUNK;
-    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) s[swz(i)] = ac[i];
+  uint64_t* own[CS];
+  if constexpr (CS > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+    for (int k = 0; k < CS; k++) own[k] = cl.map_shared_rank(sm, k);
+  } else {
+    own[0] = sm;
+  }
+  constexpr uint32_t COLS = CHUNK / CS;
+  for (uint32_t c = rank * COLS + g; c < (rank + 1) * COLS; c += ROW_THREADS) {
+    uint64_t x[N1];
+#pragma unroll
+    for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc);
+#pragma unroll
+    for (int m = 1; m < N1; m <<= 1) {
+      const int t1 = N1 / (2 * m);
+#pragma unroll
+      for (int i = 0; i < m; i++) {
+        const uint64_t wv = w[m + i], wsv = ws[m + i];
+#pragma unroll
+        for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < N1; s++) own[s / CPC][(s % CPC) * CHUNK + swz(c)] = x[s];
+  }
+  if constexpr (CS > 1)
+    cg::this_cluster().sync();
+  else
     __syncthreads();
+  for (int lc = 0; lc < CPC; lc++) {
+    const uint32_t chunk = rank * CPC + lc;
+    uint64_t* s = sm + lc * CHUNK;
 #pragma unroll
     for (int ls = 9; ls >= 0; ls -= 3) {
-      round8<false>(s, g, ls, chunk, log_n, w, ws, q, q2);
+      round8<false>(s, g, ls, chunk, log_n, t8, q, q2);
       __syncthreads();
     }
     for (uint32_t i = g; i < CHUNK; i += ROW_THREADS)
       d.store(r, chunk * CHUNK + i, reduce4(s[swz(i)], q, q2), q, kc);
-    __syncthreads();
   }
 }
 
-// Inverse NTT of pattern-selected rows; the final scaling is post[row % P]
-// (default N^-1).
+// Inverse NTT of pattern-selected rows, one row per cluster: each CTA loads
+// and transforms its own chunks, then (after a cluster barrier) transforms
+// its share of the columns, reading the elements from the owners' shared
+// memory, and writes the row scaled by post[row % P] (default N^-1).
 template <int N1>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
-    ntt_inv_row(uint64_t* base, int log_n, const int16_t* pattern, int P, const Mod* mods,
-                const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
-                const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts) {
-  __shared__ uint64_t s[CHUNK];
-  const size_t row = blockIdx.x;
+    ntt_inv_cl(uint64_t* base, int log_n, const int16_t* pattern, int P, const Mod* mods,
+               const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
+               const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts,
+               const ulonglong2* tw8, size_t nodes) {
+  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  constexpr int CPC = N1 / CS;
+  extern __shared__ uint64_t sm[];
+  const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
+  const size_t row = blockIdx.x / CS;
   const int mi = pattern[row % P];
-  if (mi < 0) return;
+  if (mi < 0) return;  // same decision on every CTA of the cluster
   const size_t N = (size_t)N1 * CHUNK;
   const uint64_t q = mods[mi].q, q2 = 2 * q;
   const uint64_t* w = tw + (size_t)mi * N;
   const uint64_t* ws = tws + (size_t)mi * N;
+  const ulonglong2* t8 = tw8 + (size_t)mi * nodes * 7;
   uint64_t* a = base + row * N;
   const uint64_t pv = post ? post[row % P] : ninv[mi];
   const uint64_t pvs = post ? posts[row % P] : ninvs[mi];
   const uint32_t g = threadIdx.x;
-  for (uint32_t chunk = 0; chunk < (uint32_t)N1; chunk++) {
-    uint64_t* ac = a + (size_t)chunk * CHUNK;
+  for (int lc = 0; lc < CPC; lc++) {
+    const uint32_t chunk = rank * CPC + lc;
+    uint64_t* s = sm + lc * CHUNK;
+    const uint64_t* ac = a + (size_t)chunk * CHUNK;
     for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) s[swz(i)] = ac[i];
     __syncthreads();
 #pragma unroll
     for (int ls = 0; ls <= 9; ls += 3) {
-      round8<true>(s, g, ls, chunk, log_n, w, ws, q, q2);
+      round8<true>(s, g, ls, chunk, log_n, t8, q, q2);
       __syncthreads();
     }
-    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) ac[i] = s[swz(i)];
-    __syncthreads();
   }
-  for (uint32_t c = g; c < CHUNK; c += ROW_THREADS) column_inv<N1>(a + c, w, ws, q, q2, pv, pvs);
+  const uint64_t* own[CS];
+  if constexpr (CS > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+#pragma unroll
+    for (int k = 0; k < CS; k++) own[k] = cl.map_shared_rank(sm, k);
+  } else {
+    own[0] = sm;
+  }
+  constexpr uint32_t COLS = CHUNK / CS;
+  for (uint32_t c = rank * COLS + g; c < (rank + 1) * COLS; c += ROW_THREADS) {
+    uint64_t x[N1];
+#pragma unroll
+    for (int s = 0; s < N1; s++) x[s] = own[s / CPC][(s % CPC) * CHUNK + swz(c)];
+#pragma unroll
+    for (int m = N1 / 2; m >= 1; m >>= 1) {
+      const int t1 = N1 / (2 * m);
+#pragma unroll
+      for (int i = 0; i < m; i++) {
+        const uint64_t wv = w[m + i], wsv = ws[m + i];
+#pragma unroll
+        for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < N1; s++) a[c + (size_t)s * CHUNK] = mul_shoup(x[s], pv, pvs, q);
+  }
+  if constexpr (CS > 1) cg::this_cluster().sync();  // peers may still read this CTA's chunks
+}
+
+template <int N1, class K, class... Args>
+void launch_cl(Ctx& c, K kernel, size_t n_rows, Args... args) {
+  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  constexpr int CPC = N1 / CS;
+  const size_t smem = (size_t)CPC * CHUNK * 8;
+  static bool attr[64] = {};
+  if (!attr[c.device & 63]) {
+    CK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (CS > 1) CK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
+    attr[c.device & 63] = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_rows * CS));
+  cfg.blockDim = dim3(ROW_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CK_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
 }
 
 template <class D>
@@ -434,14 +525,17 @@ void launch_fwd(Ctx& c, size_t n_rows, const D& d) {
   if (n_rows == 0) return;
   const uint64_t* tw = c.d_tw.u64();
   const uint64_t* tws = c.d_tws.u64();
+  const ulonglong2* t8 = static_cast<const ulonglong2*>(c.d_tw8.p);
+  const size_t nd = c.tw8_nodes;
+  const int ln = c.log_n;
+  const Mod* md = c.dmod();
   switch (c.log_n - CHUNK_LOG) {
-    case 1: ntt_fwd_row<2, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
-    case 2: ntt_fwd_row<4, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
-    case 3: ntt_fwd_row<8, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
-    case 4: ntt_fwd_row<16, D><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(d, c.log_n, c.dmod(), tw, tws); break;
+    case 1: launch_cl<2>(c, ntt_fwd_cl<2, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 2: launch_cl<4>(c, ntt_fwd_cl<4, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 3: launch_cl<8>(c, ntt_fwd_cl<8, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 4: launch_cl<16>(c, ntt_fwd_cl<16, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
-  CK_CUDA(cudaGetLastError());
 }
 
 void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, int P,
@@ -451,21 +545,17 @@ void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, i
   const uint64_t* tws = c.d_itws.u64();
   const uint64_t* ni = c.d_ninv.u64();
   const uint64_t* nis = c.d_ninvs.u64();
-#define INV_CASE(K, N1)                                                                      \
-  case K:                                                                                    \
-    ntt_inv_row<N1><<<(unsigned)n_rows, ROW_THREADS, 0, c.stream>>>(base, c.log_n, pattern, \
-                                                                     P, c.dmod(), tw, tws,  \
-                                                                     ni, nis, post, posts); \
-    break;
+  const ulonglong2* t8 = static_cast<const ulonglong2*>(c.d_itw8.p);
+  const size_t nd = c.tw8_nodes;
+  const int ln = c.log_n;
+  const Mod* md = c.dmod();
   switch (c.log_n - CHUNK_LOG) {
-    INV_CASE(1, 2)
-    INV_CASE(2, 4)
-    INV_CASE(3, 8)
-    INV_CASE(4, 16)
+    case 1: launch_cl<2>(c, ntt_inv_cl<2>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 2: launch_cl<4>(c, ntt_inv_cl<4>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 3: launch_cl<8>(c, ntt_inv_cl<8>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 4: launch_cl<16>(c, ntt_inv_cl<16>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
-#undef INV_CASE
-  CK_CUDA(cudaGetLastError());
 }
 
 template <bool INV>

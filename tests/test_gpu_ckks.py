@@ -16,6 +16,8 @@ PARAMS = {
     "n32": dict(log_n=5, n_scale=5, n_special=2),
     "n4k": dict(log_n=12, n_scale=4, n_special=3),
     "n8k": dict(log_n=13, n_scale=3, n_special=1),
+    "n16k": dict(log_n=14, n_scale=3, n_special=2),
+    "n32k": dict(log_n=15, n_scale=4, n_special=1),
     "n64k": dict(log_n=16, n_scale=3, n_special=2),
 }
 
@@ -113,7 +115,7 @@ def _same(gc, oc):
     assert (gc.export()[0] == oc.data).all()
 
 
-@pytest.mark.parametrize("name", ["n32", "n4k", "n8k"])
+@pytest.mark.parametrize("name", ["n32", "n4k", "n8k", "n16k", "n32k", "n64k"])
 def test_ops_bit_exact(G, name):
     gctx, octx, gk, ok = pair(G, name)
     L = gctx.L
