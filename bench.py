@@ -31,6 +31,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Instructions a lazy (Harvey) 64-bit modular multiply-and-butterfly needs on
+# 32-bit integer lanes: 10 multiply-adds for the three 64x64 partial-product
+# sets (low of y*w, high of y*w', low of t*q) and 10 adds, compares and selects
+# for the 64-bit lazy corrections.
+ALU_INSTR_PER_MODMUL = 20
+
 METRIC = "encrypted KAN inferences/s"
 UNIT = "inferences/s"
 WORKLOAD = "encrypted KAN [4,8,4,1] G=5 k=3, CKKS N=2^16, 36 levels, batch 64 at uneven levels"
@@ -359,14 +365,25 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6800.0))
     kinds = {k: v for k, v in prof.items() if k != "copy"}
     dom = max(kinds, key=lambda k: kinds[k][0])
-    ms, by, n = kinds[dom]
+    ms, by, n, mm = kinds[dom]
     achieved = by / (ms / 1000.0) / 1e9
     total_ms = sum(v[0] for v in kinds.values())
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
-                "share_of_kernel_time": ms / total_ms,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    if mm > 0:
+        # integer-issue roofline: SMs x 4 schedulers x 32 lanes x max SM clock,
+        # at ALU_INSTR_PER_MODMUL instructions per lazy 64-bit modular multiply
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        alu_peak = sms * 4 * 32 * clk / ALU_INSTR_PER_MODMUL / 1e9
+        alu = mm / (ms / 1000.0) / 1e9
+        roofline = {"kernel": dom, "bound": "alu", "achieved": alu, "peak": alu_peak,
+                    "unit": "Gmodmul/s", "frac": alu / alu_peak, "traffic": None, "hbm": hbm,
+                    "modmul_per_launch": mm / n}
+    else:
+        roofline = dict({"kernel": dom, "bound": "hbm", "traffic": None}, **hbm)
+    roofline.update({"algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
+                     "share_of_kernel_time": ms / total_ms})
     shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])}
 
     # ---------------- micro: HMult / HRot per second at N=2^16, 37 limbs

@@ -92,6 +92,11 @@ const char* ckks_kernel_kind_name(int kind);
 int ckks_launch_counts(const ckks_ctx* ctx, uint64_t* counts, int cap);
 int ckks_profile_enable(ckks_ctx* ctx, int on);
 int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* launches, int cap);
+/* Same, plus per kind the summed algorithmic count of 64-bit modular
+ * multiplications (NTT butterflies, basis-conversion and scaling products,
+ * key inner-product products); modmuls may be NULL. */
+int ckks_profile_collect2(ckks_ctx* ctx, double* ms, double* bytes, double* modmuls,
+                          uint64_t* launches, int cap);
 
 /* ------------------------------------------------------------ keys
  * Secret-key generation from `seed` (ternary secret, ChaCha20 stream), the
@@ -233,6 +238,31 @@ int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int l
  * to the lowest level, concatenated into one batch and evaluated together. */
 int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model,
               const ckks_ct* const* in, size_t n_in, ckks_ct** out);
+
+/* ------------------------------------------------------------ serving
+ * Continuous batching of encrypted inference requests (the serving pattern
+ * of the build; the paper itself times single inputs). Requests are admitted
+ * first-come first-served while the sum of their device-memory footprints
+ * (32 x the input ciphertext's bytes) stays within hbm_budget_bytes. Each
+ * kan_server_step evaluates one layer for every active request, batching
+ * requests of the same model, layer and level into one evaluation; requests
+ * submitted meanwhile join at the next step. Results are word-for-word those
+ * of evaluating each request alone. kan_server_take returns CKKS_PENDING
+ * while a request is still queued or running. The server does not own the
+ * models or keys, which must outlive it. */
+#define CKKS_PENDING 1
+typedef struct kan_server kan_server;
+int kan_server_create(ckks_ctx* ctx, size_t hbm_budget_bytes, kan_server** out);
+int kan_server_destroy(kan_server* server);
+int kan_server_add_model(kan_server* server, kan_model* model, const ckks_keys* keys,
+                         int* model_id);
+/* `in` holds one request (batch 1 ciphertext, copied); errors: LEVEL if its
+ * level is below the model's depth, OUT_OF_MEMORY if it alone exceeds the budget. */
+int kan_server_submit(kan_server* server, int model_id, const ckks_ct* in, uint64_t* request_id);
+int kan_server_step(kan_server* server, size_t* completed);
+int kan_server_take(kan_server* server, uint64_t request_id, ckks_ct** out);
+int kan_server_status(const kan_server* server, size_t* waiting, size_t* active,
+                      size_t* finished, size_t* hbm_in_use, size_t* hbm_peak);
 
 #ifdef __cplusplus
 }

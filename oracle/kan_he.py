@@ -230,7 +230,9 @@ def eval_cheb(ctx, keys, y, a):
 # ------------------------------------------------------------------ layer
 def layer_rotations(layer, slots):
     """Every rotation step the layer schedule uses."""
-    n_i, n_o, G, k = layer["n_in"], layer["n_out"], layer["G"], layer["k"]
+    K, n_c = chunking(layer, slots)
+    n_o, G, k = layer["n_out"], layer["G"], layer["k"]
+    n_i = n_c
     J = math.ceil(math.log2(G + 2 * k))
     steps = {-n_i * 2 ** (j - 1) for j in range(1, J + 1)}
     steps.add(n_i)
@@ -304,10 +306,55 @@ def layer_eval(ctx, keys, x, layer):
     return ckks.add(ctx, ckks.level_down(ctx, ys, lv), ckks.level_down(ctx, yb, lv))
 
 
+def chunking(layer, slots):
+    """(K, n_c): a layer whose repeat-packed input n_i 2^ceil(log2(g+2k))
+    exceeds the slots takes K input ciphertexts of n_c = slots / 2^J inputs
+    each (the last one zero-padded); otherwise (1, n_i)."""
+    J = math.ceil(math.log2(layer["G"] + 2 * layer["k"]))
+    cap = slots >> J
+    n_i = layer["n_in"]
+    if n_i <= cap:
+        return 1, n_i
+    return -(-n_i // cap), cap
+
+
+def chunk_layer(layer, c, n_c):
+    """The layer restricted to inputs [c n_c, (c+1) n_c), zero-padded."""
+    n_i, n_o, nb = layer["n_in"], layer["n_out"], layer["G"] + layer["k"]
+    sub = dict(layer)
+    sub["n_in"] = n_c
+    coef = np.zeros((n_o, n_c, nb))
+    ws = np.zeros((n_o, n_c))
+    wb = np.zeros((n_o, n_c))
+    hi = min(n_i, (c + 1) * n_c)
+    coef[:, : hi - c * n_c] = layer["coef"][:, c * n_c: hi]
+    ws[:, : hi - c * n_c] = layer["w_s"][:, c * n_c: hi]
+    wb[:, : hi - c * n_c] = layer["w_b"][:, c * n_c: hi]
+    sub["coef"], sub["w_s"], sub["w_b"] = coef, ws, wb
+    return sub
+
+
+def layer_eval_chunked(ctx, keys, xs, layer):
+    """Wide layer: chunk c (ciphertext xs[c]) goes through the layer with the
+    column blocks of chunk c; the partial outputs are summed in chunk order."""
+    K, n_c = chunking(layer, ctx.slots)
+    if len(xs) != K:
+        raise ValueError("layer needs %d input ciphertexts" % K)
+    out = None
+    for c in range(K):
+        y = layer_eval(ctx, keys, xs[c], chunk_layer(layer, c, n_c))
+        out = y if out is None else ckks.add(ctx, out, y)
+    return out
+
+
 def infer(ctx, keys, x, model):
+    """x: one ciphertext, or the list of K chunk ciphertexts of a wide first layer."""
     h = x
     for layer in model:
-        h = layer_eval(ctx, keys, h, layer)
+        if isinstance(h, (list, tuple)):
+            h = layer_eval_chunked(ctx, keys, list(h), layer)
+        else:
+            h = layer_eval(ctx, keys, h, layer)
     return h
 
 

@@ -42,6 +42,7 @@ SIGNATURES = {
     "ckks_launch_counts": (c_i32, [c_vp, c_vp, c_i32]),
     "ckks_profile_enable": (c_i32, [c_vp, c_i32]),
     "ckks_profile_collect": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32]),
+    "ckks_profile_collect2": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32]),
     "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
@@ -75,7 +76,16 @@ SIGNATURES = {
     "kan_model_layer_depth": (c_i32, [c_vp, c_i32, c_vp]),
     "kan_layer_eval": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, PP]),
     "kan_infer": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, PP]),
+    "kan_server_create": (c_i32, [c_vp, c_sz, PP]),
+    "kan_server_destroy": (c_i32, [c_vp]),
+    "kan_server_add_model": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "kan_server_submit": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
+    "kan_server_step": (c_i32, [c_vp, c_vp]),
+    "kan_server_take": (c_i32, [c_vp, c_u64, PP]),
+    "kan_server_status": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
+
+PENDING = 1
 
 
 def lib():
@@ -155,12 +165,14 @@ class Context:
         check(lib().ckks_profile_enable(self.h, 1 if on else 0))
 
     def profile_collect(self):
-        """{kind: (ms, algorithmic bytes, launches)} since the last collect."""
+        """{kind: (ms, algorithmic bytes, launches, modular multiplications)}
+        since the last collect."""
         names = self.kernel_kinds()
-        ms, by = np.zeros(len(names)), np.zeros(len(names))
+        ms, by, mm = np.zeros(len(names)), np.zeros(len(names)), np.zeros(len(names))
         ln = np.zeros(len(names), np.uint64)
-        check(lib().ckks_profile_collect(self.h, _p(ms), _p(by), _p(ln), len(names)))
-        return {n: (float(a), float(b), int(c)) for n, a, b, c in zip(names, ms, by, ln) if c}
+        check(lib().ckks_profile_collect2(self.h, _p(ms), _p(by), _p(mm), _p(ln), len(names)))
+        return {n: (float(a), float(b), int(c), float(d))
+                for n, a, b, c, d in zip(names, ms, by, ln, mm) if c}
 
 
 class Keys:
@@ -412,3 +424,54 @@ def kan_layer_eval(ctx, keys, model, layer, ct):
 def kan_infer(ctx, keys, model, cts):
     hs = (c_vp * len(cts))(*[c.h.value if isinstance(c.h, c_vp) else c.h for c in cts])
     return _out(ctx, lib().kan_infer, ctx.h, keys.h, model.h, hs, len(cts))
+
+
+class Server:
+    """kan_server handle: continuous batching of encrypted KAN requests."""
+
+    def __init__(self, ctx, hbm_budget_bytes):
+        h = c_vp()
+        check(lib().kan_server_create(ctx.h, int(hbm_budget_bytes), ctypes.byref(h)))
+        self.h, self.ctx = h, ctx
+        self._models = []
+
+    def close(self):
+        if self.h:
+            lib().kan_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_model(self, model, keys):
+        mid = ctypes.c_int()
+        check(lib().kan_server_add_model(self.h, model.h, keys.h, ctypes.byref(mid)))
+        self._models.append((model, keys))
+        return mid.value
+
+    def submit(self, model_id, ct):
+        rid = c_u64()
+        check(lib().kan_server_submit(self.h, int(model_id), ct.h, ctypes.byref(rid)))
+        return rid.value
+
+    def step(self):
+        n = c_sz()
+        check(lib().kan_server_step(self.h, ctypes.byref(n)))
+        return n.value
+
+    def take(self, request_id):
+        """The finished ciphertext, or None while the request is pending."""
+        h = c_vp()
+        rc = lib().kan_server_take(self.h, int(request_id), ctypes.byref(h))
+        if rc == PENDING:
+            return None
+        check(rc)
+        return Ciphertext(self.ctx, h)
+
+    def status(self):
+        v = [c_sz() for _ in range(5)]
+        check(lib().kan_server_status(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("waiting", "active", "finished", "hbm_in_use", "hbm_peak"), (x.value for x in v)))

@@ -116,6 +116,11 @@ int ckks_profile_enable(ckks_ctx* ctx, int on) {
 }
 
 int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* launches, int cap) {
+  return ckks_profile_collect2(ctx, ms, bytes, nullptr, launches, cap);
+}
+
+int ckks_profile_collect2(ckks_ctx* ctx, double* ms, double* bytes, double* modmuls,
+                          uint64_t* launches, int cap) {
   return guard([&] {
     need(ctx != nullptr, "ctx is NULL");
     Ctx& c = ctx->c;
@@ -123,6 +128,7 @@ int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* lau
     for (int k = 0; k < cap; k++) {
       if (ms) ms[k] = 0;
       if (bytes) bytes[k] = 0;
+      if (modmuls) modmuls[k] = 0;
       if (launches) launches[k] = 0;
     }
     for (auto& r : c.prof_recs) {
@@ -131,6 +137,7 @@ int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* lau
       if (r.kind < cap) {
         if (ms) ms[r.kind] += t;
         if (bytes) bytes[r.kind] += r.bytes;
+        if (modmuls) modmuls[r.kind] += r.ops;
         if (launches) launches[r.kind] += 1;
       }
       c.ev_pool.push_back(r.a);

@@ -58,13 +58,14 @@ cudaEvent_t Ctx::take_event() {
   return e;
 }
 
-Launch::Launch(Ctx& cx, int k, double algorithmic_bytes) : c(cx), kind(k), bytes(algorithmic_bytes) {
+Launch::Launch(Ctx& cx, int k, double algorithmic_bytes, double modmuls)
+    : c(cx), kind(k), bytes(algorithmic_bytes) {
   c.launches[k]++;
   if (c.prof) {
     cudaEvent_t a = c.take_event();
     b = c.take_event();
     CK_CUDA(cudaEventRecord(a, c.stream));
-    c.prof_recs.push_back(ProfRec{k, bytes, a, b});
+    c.prof_recs.push_back(ProfRec{k, bytes, modmuls, a, b});
   }
 }
 Launch::~Launch() {

@@ -75,6 +75,7 @@ const char* kernel_kind_name(int k);
 struct ProfRec {
   int kind;
   double bytes;
+  double ops;  // algorithmic 64-bit modular multiplications
   cudaEvent_t a, b;
 };
 
@@ -154,7 +155,7 @@ struct Launch {
   int kind;
   double bytes;
   cudaEvent_t b = nullptr;
-  Launch(Ctx& cx, int k, double algorithmic_bytes);
+  Launch(Ctx& cx, int k, double algorithmic_bytes, double modmuls = 0.0);
   ~Launch();
 };
 

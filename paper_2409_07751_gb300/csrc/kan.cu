@@ -438,6 +438,19 @@ std::vector<int> layer_rotations(const Layer& L, int slots) {
 
 }  // namespace
 
+// internal entry points for the serving scheduler
+namespace ck {
+Ct kan_eval_layer(kan_model& M, int layer, const ckks_keys& keys, const ckks_ct& x) {
+  return layer_eval(M, layer, keys, x);
+}
+int kan_num_layers(const kan_model& M) { return (int)M.layers.size(); }
+int kan_total_depth(const kan_model& M) {
+  int d = 0;
+  for (const Layer& L : M.layers) d += layer_depth(L);
+  return d;
+}
+}  // namespace ck
+
 extern "C" {
 
 int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layers,

@@ -194,7 +194,8 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
   DevBuf acc(&c, B * 2 * rows * c.N * 8);
   const double W8 = (double)c.N * 8.0;
   {
-  Launch L_(c, K_INNER, W8 * rows * ((double)B * T.beta + 2.0 * T.beta + 2.0 * B));
+  Launch L_(c, K_INNER, W8 * rows * ((double)B * T.beta + 2.0 * T.beta + 2.0 * B),
+            2.0 * (double)B * T.beta * rows * (double)c.N);
   const size_t ip_total = (size_t)rows * c.N;
   const size_t ip_blocks = std::min<size_t>((ip_total + IP_THREADS - 1) / IP_THREADS, 152 * 64);
   inner_product_kernel<<<(unsigned)ip_blocks, IP_THREADS, 2 * T.beta * IP_THREADS * 8, c.stream>>>(

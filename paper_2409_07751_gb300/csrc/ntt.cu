@@ -31,7 +31,7 @@ namespace {
 
 constexpr int CHUNK_LOG = 12;
 constexpr int CHUNK = 1 << CHUNK_LOG;  // N2
-constexpr int ROW_THREADS = 512;       // one radix-8 group per thread per round
+constexpr int ROW_THREADS = 512;       // one radix-8 group of each of two chunks per thread
 
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
   return a * w - __umul64hi(a, ws) * q;  // in [0, 2q) for any a < 2^64
@@ -165,6 +165,68 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
   }
 #pragma unroll
   for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
+}
+
+// The same round on group g of two chunks at once (chunk and chunk + 1, in
+// shared memory at sm and sm + CHUNK): two independent dependency chains per
+// thread, interleaved by the compiler.
+template <bool INV>
+__device__ __forceinline__ void round8x2(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
+                                         int log_n, const ulonglong2* t8, uint64_t q,
+                                         uint64_t q2) {
+  const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
+  const uint32_t base = (blk8 << (ls + 3)) + r;
+  const uint32_t per = CHUNK >> (ls + 3);
+  const uint32_t nb = node_base(ls, log_n);
+  uint64_t x[2][8];
+  ulonglong2 tt[2][7];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const ulonglong2* T = t8 + (size_t)(nb + (chunk + h) * per + blk8) * 7;
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[h][k] = sm[h * CHUNK + swz(base + ((uint32_t)k << ls))];
+#pragma unroll
+    for (int k = 0; k < 7; k++) tt[h][k] = T[k];
+  }
+  if (!INV) {
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) ct_lazy(x[h][k], x[h][k + 4], tt[h][0].x, tt[h][0].y, q, q2);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      ct_lazy(x[h][0], x[h][2], tt[h][1].x, tt[h][1].y, q, q2);
+      ct_lazy(x[h][1], x[h][3], tt[h][1].x, tt[h][1].y, q, q2);
+      ct_lazy(x[h][4], x[h][6], tt[h][2].x, tt[h][2].y, q, q2);
+      ct_lazy(x[h][5], x[h][7], tt[h][2].x, tt[h][2].y, q, q2);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        ct_lazy(x[h][2 * k], x[h][2 * k + 1], tt[h][3 + k].x, tt[h][3 + k].y, q, q2);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        gs_lazy(x[h][2 * k], x[h][2 * k + 1], tt[h][3 + k].x, tt[h][3 + k].y, q, q2);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      gs_lazy(x[h][0], x[h][2], tt[h][1].x, tt[h][1].y, q, q2);
+      gs_lazy(x[h][1], x[h][3], tt[h][1].x, tt[h][1].y, q, q2);
+      gs_lazy(x[h][4], x[h][6], tt[h][2].x, tt[h][2].y, q, q2);
+      gs_lazy(x[h][5], x[h][7], tt[h][2].x, tt[h][2].y, q, q2);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) gs_lazy(x[h][k], x[h][k + 4], tt[h][0].x, tt[h][0].y, q, q2);
+  }
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+#pragma unroll
+    for (int k = 0; k < 8; k++) sm[h * CHUNK + swz(base + ((uint32_t)k << ls))] = x[h][k];
 }
 
 // column transform of N1 elements (stride CHUNK) in registers
@@ -370,19 +432,19 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
   constexpr int CPC = N1 / CS;
   extern __shared__ uint64_t sm[];  // CPC chunks
   __shared__ uint64_t kc[2 * MAX_SRC];
+  __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
   const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
   const uint32_t row = blockIdx.x / CS;
   Row r;
   r.n_src = 0;
   if (!d.setup(row, r, kc, rank, CS)) return;  // same decision on every CTA of the cluster
-  __syncthreads();
   const size_t N = (size_t)N1 * CHUNK;
   const uint64_t q = mods[r.mi].q, q2 = 2 * q;
   r.aux = q;
-  const uint64_t* w = tw + (size_t)r.mi * N;
-  const uint64_t* ws = tws + (size_t)r.mi * N;
   const ulonglong2* t8 = tw8 + (size_t)r.mi * nodes * 7;
   const uint32_t g = threadIdx.x;
+  if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)r.mi * N + g], tws[(size_t)r.mi * N + g]);
+  __syncthreads();
   uint64_t* own[CS];
   if constexpr (CS > 1) {
     cg::cluster_group cl = cg::this_cluster();
@@ -401,9 +463,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
       const int t1 = N1 / (2 * m);
 #pragma unroll
       for (int i = 0; i < m; i++) {
-        const uint64_t wv = w[m + i], wsv = ws[m + i];
+        const ulonglong2 tv = ctw[m + i];
 #pragma unroll
-        for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
+        for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
       }
     }
 #pragma unroll
@@ -413,16 +475,17 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     cg::this_cluster().sync();
   else
     __syncthreads();
-  for (int lc = 0; lc < CPC; lc++) {
+  // chunks in pairs (CPC is even): one group of each chunk per thread
+  for (int lc = 0; lc < CPC; lc += 2) {
     const uint32_t chunk = rank * CPC + lc;
     uint64_t* s = sm + lc * CHUNK;
 #pragma unroll
     for (int ls = 9; ls >= 0; ls -= 3) {
-      round8<false>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8x2<false>(s, g, ls, chunk, log_n, t8, q, q2);
       __syncthreads();
     }
-    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS)
-      d.store(r, chunk * CHUNK + i, reduce4(s[swz(i)], q, q2), q, kc);
+    for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS)
+      d.store(r, chunk * CHUNK + i, reduce4(s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))], q, q2), q, kc);
   }
 }
 
@@ -439,28 +502,30 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
   constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
   constexpr int CPC = N1 / CS;
   extern __shared__ uint64_t sm[];
+  __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
   const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
   const size_t row = blockIdx.x / CS;
   const int mi = pattern[row % P];
   if (mi < 0) return;  // same decision on every CTA of the cluster
   const size_t N = (size_t)N1 * CHUNK;
   const uint64_t q = mods[mi].q, q2 = 2 * q;
-  const uint64_t* w = tw + (size_t)mi * N;
-  const uint64_t* ws = tws + (size_t)mi * N;
   const ulonglong2* t8 = tw8 + (size_t)mi * nodes * 7;
   uint64_t* a = base + row * N;
   const uint64_t pv = post ? post[row % P] : ninv[mi];
   const uint64_t pvs = post ? posts[row % P] : ninvs[mi];
   const uint32_t g = threadIdx.x;
-  for (int lc = 0; lc < CPC; lc++) {
+  if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)mi * N + g], tws[(size_t)mi * N + g]);
+  // chunks in pairs (CPC is even): one group of each chunk per thread
+  for (int lc = 0; lc < CPC; lc += 2) {
     const uint32_t chunk = rank * CPC + lc;
     uint64_t* s = sm + lc * CHUNK;
     const uint64_t* ac = a + (size_t)chunk * CHUNK;
-    for (uint32_t i = g; i < CHUNK; i += ROW_THREADS) s[swz(i)] = ac[i];
+    for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS)
+      s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))] = ac[i];
     __syncthreads();
 #pragma unroll
     for (int ls = 0; ls <= 9; ls += 3) {
-      round8<true>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8x2<true>(s, g, ls, chunk, log_n, t8, q, q2);
       __syncthreads();
     }
   }
@@ -483,9 +548,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
       const int t1 = N1 / (2 * m);
 #pragma unroll
       for (int i = 0; i < m; i++) {
-        const uint64_t wv = w[m + i], wsv = ws[m + i];
+        const ulonglong2 tv = ctw[m + i];
 #pragma unroll
-        for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
+        for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
       }
     }
 #pragma unroll
@@ -562,19 +627,20 @@ template <bool INV>
 void ntt_run(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P, size_t active) {
   if (n_rows == 0) return;
   const double bytes = 2.0 * (double)std::min(active, n_rows) * (double)c.N * 8.0;
+  const double bf = (double)std::min(active, n_rows) * (double)(c.N / 2) * c.log_n;  // butterflies
   if (c.log_n <= CHUNK_LOG) {
     const int threads = std::min<int>(256, (int)(c.N / 2));
-    Launch L_(c, K_NTT_SMALL, bytes);
+    Launch L_(c, K_NTT_SMALL, bytes, bf);
     ntt_small<INV><<<(unsigned)n_rows, threads, c.N * 8, c.stream>>>(
         base, c.log_n, pattern, P, c.dmod(),
         static_cast<const uint64_t*>(INV ? c.d_itw.p : c.d_tw.p),
         static_cast<const uint64_t*>(INV ? c.d_itws.p : c.d_tws.p), c.d_ninv.u64(), c.d_ninvs.u64());
     CK_CUDA(cudaGetLastError());
   } else if (!INV) {
-    Launch L_(c, K_NTT_FWD, bytes);
+    Launch L_(c, K_NTT_FWD, bytes, bf);
     launch_fwd(c, n_rows, DescPlain{base, pattern, P, c.N});
   } else {
-    Launch L_(c, K_NTT_INV, bytes);
+    Launch L_(c, K_NTT_INV, bytes, bf + (double)std::min(active, n_rows) * c.N);
     launch_inv(c, n_rows, base, pattern, P, nullptr, nullptr);
   }
 }
@@ -594,7 +660,8 @@ bool ntt_fused_available(const Ctx& c) { return c.log_n > CHUNK_LOG && c.log_n <
 
 void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
                       const uint64_t* post, const uint64_t* posts, size_t active) {
-  Launch L_(c, K_NTT_INV, 2.0 * (double)std::min(active, n_rows) * (double)c.N * 8.0);
+  const double rws = (double)std::min(active, n_rows);
+  Launch L_(c, K_NTT_INV, 2.0 * rws * (double)c.N * 8.0, rws * ((double)(c.N / 2) * c.log_n + c.N));
   launch_inv(c, n_rows, base, pattern, P, post, posts);
 }
 
@@ -605,7 +672,9 @@ void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, in
   const double W8 = (double)c.N * 8.0;
   // reads: alpha scaled source rows per target row (L2-resident per digit) and
   // the digit rows once; writes every extended row once
-  Launch L_(c, K_MODUP_NTT, W8 * (double)B * (2.0 * T.l + (double)T.beta * T.rows));
+  const double out_rows = (double)B * ((double)T.beta * T.rows - T.l);
+  Launch L_(c, K_MODUP_NTT, W8 * (double)B * (2.0 * T.l + (double)T.beta * T.rows),
+            out_rows * ((double)(c.N / 2) * c.log_n + (double)c.alpha * c.N));
   DescModUp dsc{xs, d, ext, T.dh.u64(), T.dh_s.u64(), T.l, T.beta, T.rows, c.alpha, c.L, c.N};
   launch_fwd(c, B * T.beta * T.rows, dsc);
 }
@@ -613,7 +682,8 @@ void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, in
 void ntt_moddown_fused(Ctx& c, const uint64_t* acc, size_t BK, int level, uint64_t* out) {
   ConvTables& T = c.tables(level);
   const double W8 = (double)c.N * 8.0;
-  Launch L_(c, K_MODDOWN_NTT, W8 * (double)BK * (c.alpha + 2.0 * T.l));
+  Launch L_(c, K_MODDOWN_NTT, W8 * (double)BK * (c.alpha + 2.0 * T.l),
+            (double)BK * T.l * ((double)(c.N / 2) * c.log_n + (c.alpha + 1.0) * c.N));
   DescModDown dsc{acc, out, c.d_md_ph.u64(), c.d_md_ph_s.u64(), T.md_pinv.u64(), T.md_pinv_s.u64(),
                   T.l, T.rows, c.alpha, c.L, c.N};
   launch_fwd(c, BK * T.l, dsc);
@@ -622,7 +692,8 @@ void ntt_moddown_fused(Ctx& c, const uint64_t* acc, size_t BK, int level, uint64
 void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t polys, int level,
                        uint64_t* out) {
   const double W8 = (double)c.N * 8.0;
-  Launch L_(c, K_RESCALE_NTT, W8 * (double)polys * (1.0 + 2.0 * level));
+  Launch L_(c, K_RESCALE_NTT, W8 * (double)polys * (1.0 + 2.0 * level),
+            (double)polys * level * ((double)(c.N / 2) * c.log_n + c.N));
   DescRescale dsc{in, last, out, c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
                   c.d_rs_invs.u64() + (size_t)level * (c.L + 1), c.mod[level], level, c.N};
   launch_fwd(c, polys * level, dsc);

@@ -33,6 +33,7 @@ int64_t round_const(double v, double scale) {
 }
 
 double plain_scale(const Ctx& c, double ct_scale, int level) {
+  if (level < 1 || level > c.L) throw Error(CKKS_ERR_LEVEL, "level exhausted");
   return (c.delta[level - 1] * (double)c.mod[level]) / ct_scale;
 }
 

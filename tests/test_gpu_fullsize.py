@@ -1,0 +1,72 @@
+"""Full-size checks of the configurations (N = 2^15 / 2^16, full prime
+chains): the oracle needs tens of minutes per inference at these sizes, so
+these tests check properties that hold at any size — decrypt(GPU inference)
+equals the FP64 HE-friendly KAN (same SiLU polynomial, same comparison
+composite, same recursion) within CKKS noise — and report the error split
+against the exact KAN (SiLU error, comparison error, CKKS noise)."""
+import numpy as np
+import pytest
+
+from oracle import kan_plain
+from paper_2409_07751_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2409_07751_gb300 import build, ckks
+    build.build()
+    return ckks
+
+
+def _split(m, x, dec):
+    ex = kan_plain.forward(m, x)
+    hef = kan_plain.forward(m, x, "poly", "poly")
+    silu = np.abs(kan_plain.forward(m, x, "poly", "exact") - ex).max()
+    comp = np.abs(kan_plain.forward(m, x, "exact", "poly") - ex).max()
+    noise = np.abs(dec - hef).max()
+    print("error split: silu %.3g comparison %.3g ckks-noise %.3g total-vs-exact %.3g"
+          % (silu, comp, noise, np.abs(dec - ex).max()))
+    return noise
+
+
+def _run(G, log_n, L, alpha, model, X, levels, degree, comp, fixed=None, tol=1e-4):
+    Xcal = X[len(levels):]
+    m = G.calibrate(model, Xcal, degree, comp, fixed_range=fixed)
+    ctx = G.Context(log_n, L, alpha)
+    gm = G.Model(ctx, m)
+    depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
+    assert depth <= min(levels)
+    keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+    x = X[: len(levels)]
+    cts = [G.encrypt(ctx, keys, x[b], int(levels[b]), W.SEED_ENC, b) for b in range(len(levels))]
+    out = G.kan_infer(ctx, keys, gm, cts)
+    assert out.level == min(levels) - depth
+    dec = G.decrypt(ctx, keys, out, m[-1]["n_out"])
+    assert _split(m, x, dec) < tol
+
+
+def test_c1_kan_2_5_1_n32k(G):
+    """[2,5,1], G=5, k=3, SiLU degree 15 on [-4,4], N=2^15, q0 + 18 x 40-bit,
+    one special prime."""
+    model = W.make_model("kan_2_5_1")
+    X = W.uniform_inputs(300, 2)
+    _run(G, 15, 18, 1, model, X, [18, 18, 17], 15, [1], fixed=(-4.0, 4.0))
+
+
+def test_c2_kan_4_8_4_1_n64k_uneven(G):
+    """[4,8,4,1], G=5, k=3, SiLU degree 27 on data-fitted ranges, N=2^16,
+    36 levels, inputs at uneven levels (the bench workload's launch shape)."""
+    model = W.make_model("kan_4_8_4_1")
+    X = W.uniform_inputs(260, 4)
+    lv = W.uneven_levels(4, 36, 9)
+    _run(G, 16, 36, 4, model, X, lv, 27, [3])
+
+
+def test_c3_kan_784_64_10_images(G):
+    """[784,64,10], G=5, k=3 on synthetic 28x28 blob images, N=2^16,
+    36 levels; 784 * 16 copies repeat-packed into 2^15 slots."""
+    model = W.make_model("kan_784_64_10")
+    X = W.blob_images(66)
+    _run(G, 16, 36, 4, model, X, [36, 36], 15, [3], tol=1e-3)

@@ -58,6 +58,34 @@ def test_tiny_layer_and_network_bit_exact(G):
     assert np.abs(dec - hef).max() < 1e-6
 
 
+@pytest.mark.parametrize("G_,k_", [(1, 0), (2, 1), (4, 0)])
+def test_degenerate_grids_bit_exact(G, G_, k_):
+    """Order-0 splines (no recursion), a single interval, linear splines."""
+    model = W.make_model("t", widths=[3, 2], G=G_, k=k_)
+    X = W.uniform_inputs(64, 3)
+    m = calibrate.calibrate(model, X, 5, [1])
+    gctx, octx, gm, gk, ok = _setup(G, 7, 12, 2, m)
+    oc = O.encrypt(octx, ok, X[0], octx.L, W.SEED_ENC, 0)
+    gc = G.Ciphertext.import_(gctx, oc.data, oc.level, oc.scale)
+    oo = kan_he.infer(octx, ok, oc, m)
+    go = G.kan_infer(gctx, gk, gm, [gc])
+    assert (go.export()[0] == oo.data).all()
+
+
+def test_level_exhausted_is_an_error(G):
+    model = W.make_model("t", widths=[3, 2], G=3, k=2)
+    m = calibrate.calibrate(model, W.uniform_inputs(64, 3), 7, [1])
+    gctx = G.Context(7, 17, 2)
+    gm = G.Model(gctx, m)
+    gk = G.Keys(gctx, 1, gm.rotations())
+    c = G.encrypt(gctx, gk, [0.1, 0.2, 0.3], 4, seed=1)  # below the layer depth
+    with pytest.raises(G.CkksError) as e:
+        G.kan_infer(gctx, gk, gm, [c])
+    assert e.value.code == -2
+    with pytest.raises(G.CkksError):
+        G.kan_infer(gctx, gk, gm, [])
+
+
 def test_kan_4_8_4_1_batched_uneven_levels(G):
     model = W.make_model("kan_4_8_4_1")
     X = W.uniform_inputs(256, 4)
