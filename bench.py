@@ -58,7 +58,85 @@ def args_():
     p.add_argument("--kernel", default=None, choices=["ntt", "intt"],
                    help="time one kernel kind alone (NTT limbs/s) instead of the network")
     p.add_argument("--rows", type=int, default=592, help="limbs per launch for --kernel")
+    p.add_argument("--serve", action="store_true",
+                   help="Poisson serving mix through the continuous-batching server")
+    p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
+    p.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals for --serve")
     return p.parse_args()
+
+
+def serve_arm(a):
+    """--serve: Poisson arrivals (rate/s for `duration` s) of a mix of 50 %
+    [2,5,1], 30 % [784,64,10] and 20 % [3072,64,10] requests, one key set per
+    model (a simulated client each), all at N=2^16 / 36 levels; requests are
+    encrypted on arrival and submitted to the native server, which steps
+    continuously. Latency = arrival to finished ciphertext."""
+    import numpy as np
+    import torch
+    from paper_2409_07751_gb300 import build
+    build.build()
+    from paper_2409_07751_gb300 import ckks as G
+    from paper_2409_07751_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = G.Context(a.log_n, a.levels, 4)
+    ctx.set_stream(stream.cuda_stream)
+    specs = [("kan_2_5_1", lambda n, s: W.uniform_inputs(n, 2, seed=s), 15, [3], (-4.0, 4.0), 0.5),
+             ("kan_784_64_10", lambda n, s: W.blob_images(n, seed=s), 15, [3, 3, 3], None, 0.3),
+             ("kan_3072_64_10", lambda n, s: W.cifar_like_images(n, seed=s), 15, [3, 3, 3], None, 0.2)]
+    srv = G.Server(ctx, int(200e9))
+    models = []
+    for i, (name, gen, deg, comp, fr, share) in enumerate(specs):
+        m = G.calibrate(W.make_model(name), gen(64, W.SEED_INPUTS + 1000), deg, comp, fixed_range=fr)
+        gm = G.Model(ctx, m)
+        keys = G.Keys(ctx, W.SEED_KEYS + i, gm.rotations())
+        models.append((srv.add_model(gm, keys), gm, keys, gen, share))
+    arrivals = W.poisson_arrivals(a.rate, a.duration)
+    pick = np.random.default_rng(W.SEED_ARRIVALS + 1).choice(
+        len(models), size=len(arrivals), p=[mm[4] for mm in models])
+
+    def request(i):
+        mid, gm, keys, gen, _ = models[pick[i]]
+        x = gm.pack_input(gen(1, W.SEED_INPUTS + 10000 + i)[0])
+        return mid, G.encrypt(ctx, keys, x, a.levels, W.SEED_ENC, 64 * i)
+
+    # warm-up: one request of each model end to end (plaintext caches, code paths)
+    for j in range(len(models)):
+        mid, ct = request(int(np.nonzero(pick == j)[0][0]))
+        rid = srv.submit(mid, ct)
+        while srv.take(rid) is None:
+            srv.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pending, lat, nxt = {}, [], 0
+    while nxt < len(arrivals) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(arrivals) and arrivals[nxt] <= now:
+            mid, ct = request(nxt)
+            pending[srv.submit(mid, ct)] = arrivals[nxt]
+            nxt += 1
+        if not pending:
+            time.sleep(max(0.0, min(0.01, arrivals[nxt] - now)))
+            continue
+        srv.step()
+        torch.cuda.synchronize()
+        done = time.perf_counter() - t0
+        for rid in list(pending):
+            out = srv.take(rid)
+            if out is not None:
+                lat.append(done - pending.pop(rid))
+                out.close()
+    wall = time.perf_counter() - t0
+    st = srv.status()
+    print(json.dumps({
+        "metric": "encrypted KAN inferences/s (serving mix)", "value": len(lat) / wall,
+        "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
+        "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)),
+                       "p99": 1000 * float(np.percentile(lat, 99))},
+        "requests": len(lat), "wall_s": wall, "hbm_peak_admitted_bytes": st["hbm_peak"],
+        "config": {"workload": "Poisson serving mix", "rate_per_s": a.rate, "duration_s": a.duration,
+                   "mix": {"kan_2_5_1": 0.5, "kan_784_64_10": 0.3, "kan_3072_64_10": 0.2},
+                   "n_poly": 1 << a.log_n, "levels": a.levels}}), flush=True)
 
 
 def kernel_arm(a):
@@ -285,6 +363,8 @@ def main():
         return reference_arm(a)
     if a.kernel:
         return kernel_arm(a)
+    if a.serve:
+        return serve_arm(a)
     import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

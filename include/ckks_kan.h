@@ -228,6 +228,12 @@ int kan_model_destroy(kan_model* model);
 int kan_model_rotations(const kan_model* model, int32_t* steps, size_t cap, size_t* n);
 /* Multiplicative depth (levels consumed) of one layer. */
 int kan_model_layer_depth(const kan_model* model, int layer, int* depth);
+/* Input chunking of one layer: when n_in * 2^J (J = ceil(log2(G + 2k)),
+ * the repeat-packing factor of Algorithm 1) exceeds the slots, the layer
+ * takes *K > 1 input ciphertexts per request, each of *n_c consecutive inputs
+ * (the last zero-padded), as consecutive batch elements; otherwise *K = 1 and
+ * *n_c = n_in. Only layer 0 may be chunked. */
+int kan_model_layer_chunks(const kan_model* model, int layer, int* K, int* n_c);
 /* One layer on a batch: repeat packing (Algorithm 1), B-spline basis
  * (Algorithm 2), fused linear layer W_f = W'P (Algorithm 3, Eq. 13) and the
  * polynomial SiLU branch, both linear maps by BSGS diagonal matvec with
@@ -235,7 +241,13 @@ int kan_model_layer_depth(const kan_model* model, int layer, int* depth);
 int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int layer,
                    const ckks_ct* in, ckks_ct** out);
 /* Whole network on n_in input handles (batches, any levels): inputs are moved
- * to the lowest level, concatenated into one batch and evaluated together. */
+ * to the lowest level, concatenated into one batch and evaluated together.
+ * A first layer whose repeat-packed input n_i 2^ceil(log2(G+2k)) exceeds N/2
+ * takes K = ceil(n_i / n_c) ciphertexts per request, n_c = (N/2) /
+ * 2^ceil(log2(G+2k)): ciphertext c holds inputs [c n_c, (c+1) n_c) (zero
+ * beyond n_i), and the concatenated batch is request-major (element
+ * r K + c); the K partial outputs of a request are summed, so the output
+ * batch has one ciphertext per request. */
 int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model,
               const ckks_ct* const* in, size_t n_in, ckks_ct** out);
 

@@ -74,6 +74,7 @@ SIGNATURES = {
     "kan_model_destroy": (c_i32, [c_vp]),
     "kan_model_rotations": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
     "kan_model_layer_depth": (c_i32, [c_vp, c_i32, c_vp]),
+    "kan_model_layer_chunks": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "kan_layer_eval": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, PP]),
     "kan_infer": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, PP]),
     "kan_server_create": (c_i32, [c_vp, c_sz, PP]),
@@ -415,6 +416,23 @@ class Model:
         d = ctypes.c_int()
         check(lib().kan_model_layer_depth(self.h, layer, ctypes.byref(d)))
         return d.value
+
+    def layer_chunks(self, layer):
+        """(K, n_c): input ciphertexts per request and inputs per chunk."""
+        K, n_c = ctypes.c_int(), ctypes.c_int()
+        check(lib().kan_model_layer_chunks(self.h, layer, ctypes.byref(K), ctypes.byref(n_c)))
+        return K.value, n_c.value
+
+    def pack_input(self, x):
+        """Rows of one request's input as the first layer takes them: the
+        input itself, or K zero-padded chunks of n_c inputs."""
+        x = np.asarray(x, np.float64)
+        K, n_c = self.layer_chunks(0)
+        if K == 1:
+            return x
+        xp = np.zeros(K * n_c)
+        xp[: len(x)] = x
+        return xp.reshape(K, n_c)
 
 
 def kan_layer_eval(ctx, keys, model, layer, ct):

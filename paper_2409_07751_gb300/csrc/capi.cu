@@ -8,12 +8,11 @@ using namespace ck;
 
 namespace {
 thread_local std::string g_last_error;
+}  // namespace
 
-template <class F>
-int guard(F&& f) {
+int ck::api_error() {
   try {
-    f();
-    return CKKS_OK;
+    throw;
   } catch (const Error& e) {
     g_last_error = e.what();
     return e.code;
@@ -26,6 +25,17 @@ int guard(F&& f) {
   } catch (...) {
     g_last_error = "unknown error";
     return CKKS_ERR_CUDA;
+  }
+}
+
+namespace {
+template <class F>
+int guard(F&& f) {
+  try {
+    f();
+    return CKKS_OK;
+  } catch (...) {
+    return api_error();
   }
 }
 

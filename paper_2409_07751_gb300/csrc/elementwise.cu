@@ -144,6 +144,35 @@ __global__ void rotate_finish_kernel(const uint64_t* a, const uint64_t* ks, cons
   }
 }
 
+// out = a * pts[(batch index) % K] (pts: up to 16 plaintexts [l][N])
+struct PtSet {
+  const uint64_t* p[16];
+};
+__global__ void mul_pt_grouped_kernel(const uint64_t* a, PtSet pts, int K, uint64_t* out,
+                                      size_t total, int log_n, int l, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = 2 * (size_t)l * N;
+  GRID_LOOP(i, total) {
+    const int t = (int)((i >> log_n) % l);
+    const int ch = (int)((i / per) % K);
+    out[i] = mul_mod(a[i], pts.p[ch][(size_t)t * N + (i & (N - 1))], mods[t]);
+  }
+}
+
+// out[b] = sum_{c < K} in[b K + c]  (per ciphertext of `per` words)
+__global__ void chunk_sum_kernel(const uint64_t* in, uint64_t* out, size_t B, int K, int log_n,
+                                 int l, const Mod* mods) {
+  const size_t per = 2 * (size_t)l << log_n;
+  GRID_LOOP(i, B * per) {
+    const size_t b = i / per, r = i % per;
+    const int t = (int)((r >> log_n) % l);
+    const uint64_t q = mods[t].q;
+    uint64_t s = in[(b * K) * per + r];
+    for (int c = 1; c < K; c++) s = add_mod(s, in[(b * K + c) * per + r], q);
+    out[i] = s;
+  }
+}
+
 // R[p][t][n] = centred(last[p][n]) mod q_t, t < level (last limb mod q_level)
 __global__ void rescale_spread_kernel(const uint64_t* last, uint64_t* out, size_t polys,
                                       int log_n, int level, const Mod* mods) {
@@ -277,6 +306,25 @@ void k_automorphism(Ctx& c, const uint64_t* in, uint64_t* out, size_t rows, cons
   const size_t total = rows * c.N;
   Launch L_(c, K_AUTO, 2.0 * total * 8);
   automorphism_kernel<<<grid_for(total), TPB, 0, c.stream>>>(in, out, total, c.log_n, perm);
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_t*>& pts,
+                      uint64_t* out, size_t B, int l) {
+  if (pts.empty() || pts.size() > 16) throw Error(CKKS_ERR_UNSUPPORTED, "1..16 plaintexts");
+  PtSet P{};
+  for (size_t k = 0; k < pts.size(); k++) P.p[k] = pts[k];
+  const size_t total = B * 2 * (size_t)l * c.N;
+  Launch L_(c, K_MUL_PT, 2.0 * total * 8, (double)total);
+  mul_pt_grouped_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, P, (int)pts.size(), out, total,
+                                                                c.log_n, l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_chunk_sum(Ctx& c, const uint64_t* in, uint64_t* out, size_t B, int K, int l) {
+  const size_t total = B * 2 * (size_t)l * c.N;
+  Launch L_(c, K_ADD, (K + 1.0) * total * 8);
+  chunk_sum_kernel<<<grid_for(total), TPB, 0, c.stream>>>(in, out, B, K, c.log_n, l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 

@@ -69,10 +69,14 @@ std::vector<double> fn_coeffs(int n) {
 struct Layer {
   int n_in, n_out, G, k;
   double lo, hi, R, silu_lo, silu_hi;
-  std::vector<double> coef, w_s, w_b, cheb, knots, Wf;
+  std::vector<double> coef, w_s, w_b, cheb, knots;
   std::vector<int> comp;
+  // A wide first layer (n_in 2^ceil(log2(G+2k)) > N/2) takes K input
+  // ciphertexts per request of n_c inputs each (the last zero-padded);
+  // otherwise K = 1 and n_c = n_in. The schedule runs on n_c inputs.
+  int K = 1, n_c = 0;
   Plan plan_b, plan_s;
-  std::vector<double> diag_b, diag_s;  // [no][slots]
+  std::vector<std::vector<double>> diag_b, diag_s;  // per chunk: [no][slots]
 };
 
 }  // namespace
@@ -106,10 +110,11 @@ const uint64_t* cached_pt(kan_model& M, int layer, int tag, int sub, int level, 
 }
 
 std::vector<double> coltile(const Layer& L, int l, int r) {
-  // G matrix rows are identical knot vectors (uniform grid); columns l..r-1, 1-indexed
+  // G matrix rows are identical knot vectors (uniform grid); columns l..r-1,
+  // 1-indexed, each tiled over the n_c inputs one ciphertext carries
   std::vector<double> out;
   for (int c = l; c < r; c++)
-    for (int i = 0; i < L.n_in; i++) out.push_back(L.knots[c - 1]);
+    for (int i = 0; i < L.n_c; i++) out.push_back(L.knots[c - 1]);
   return out;
 }
 
@@ -131,7 +136,7 @@ Ct bsgs_matvec(kan_model& M, int li, bool spline, const ckks_keys& keys, const c
   Ctx& c = *M.ctx;
   Layer& L = M.layers[li];
   const Plan& p = spline ? L.plan_s : L.plan_b;
-  const std::vector<double>& D = spline ? L.diag_s : L.diag_b;
+  const auto& DC = spline ? L.diag_s : L.diag_b;  // per chunk
   const int S = (int)(c.N / 2);
   std::vector<int64_t> bs;
   for (int j = 0; j < p.g1; j++) bs.push_back(j);
@@ -145,13 +150,21 @@ Ct bsgs_matvec(kan_model& M, int li, bool spline, const ckks_keys& keys, const c
     Ct prod = ct_alloc(c, v.B, lv, v.scale * Spt);
     for (int j = 0; j < p.g1; j++) {
       const int t = p.g1 * i + j;
-      const uint64_t* pt = cached_pt(M, li, spline ? T_DIAG_S : T_DIAG_B, t, lv, Spt, [&] {
-        std::vector<double> d(S);
-        const int sh = p.g1 * i;
-        for (int s = 0; s < S; s++) d[s] = D[(size_t)t * S + ((s - sh) % S + S) % S];
-        return d;
-      });
-      k_mul_pt(c, baby[j]->d.u64(), pt, j == 0 ? acc->d.u64() : prod->d.u64(), rows, lv + 1);
+      std::vector<const uint64_t*> pts;
+      for (int ch = 0; ch < L.K; ch++) {
+        const std::vector<double>& D = DC[ch];
+        pts.push_back(cached_pt(M, li, spline ? T_DIAG_S : T_DIAG_B, t * 64 + ch, lv, Spt, [&] {
+          std::vector<double> d(S);
+          const int sh = p.g1 * i;
+          for (int s = 0; s < S; s++) d[s] = D[(size_t)t * S + ((s - sh) % S + S) % S];
+          return d;
+        }));
+      }
+      uint64_t* dst = j == 0 ? acc->d.u64() : prod->d.u64();
+      if (L.K == 1)
+        k_mul_pt(c, baby[j]->d.u64(), pts[0], dst, rows, lv + 1);
+      else  // batch element b uses the diagonals of its chunk b % K
+        k_mul_pt_grouped(c, baby[j]->d.u64(), pts, dst, v.B, lv + 1);
       if (j > 0) k_add(c, acc->d.u64(), prod->d.u64(), acc->d.u64(), rows, lv + 1, false);
     }
     Ct inner = op_rescale(c, *acc);
@@ -287,12 +300,13 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   Ctx& c = *M.ctx;
   Layer& L = M.layers[li];
   const int S = (int)(c.N / 2);
-  const int n_i = L.n_in, G = L.G, k = L.k;
+  const int n_i = L.n_c, G = L.G, k = L.k;  // inputs per ciphertext
   const double R = L.R;
   int J = 0;
   while ((1 << J) < G + 2 * k) J++;
   if ((int64_t)n_i << J > S) throw Error(CKKS_ERR_UNSUPPORTED, "n_i * 2^ceil(log2(g+2k)) > N/2");
   if (x.level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+  if (x.B % L.K != 0) throw Error(CKKS_ERR_INVALID_ARG, "batch is not a multiple of the layer's chunks");
 
   // SiLU branch
   const double sa = 2.0 / (L.silu_hi - L.silu_lo), sb = -(L.silu_hi + L.silu_lo) / (L.silu_hi - L.silu_lo);
@@ -372,7 +386,12 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   if (L.plan_s.npad < S) b = op_add(c, *b, *op_rotate(c, keys, *b, -L.plan_s.npad), false);
   Ct ys = bsgs_matvec(M, li, true, keys, *b);
   const int lv = std::min(ys->level, yb->level);
-  return op_add(c, *op_level_down(c, *ys, lv), *op_level_down(c, *yb, lv), false);
+  Ct out = op_add(c, *op_level_down(c, *ys, lv), *op_level_down(c, *yb, lv), false);
+  if (L.K == 1) return out;
+  // chunk partial outputs b*K + ch summed in chunk order
+  Ct sum = ct_alloc(c, out->B / L.K, out->level, out->scale);
+  k_chunk_sum(c, out->d.u64(), sum->d.u64(), sum->B, L.K, out->level + 1);
+  return sum;
 }
 
 int cheb_depth(int d) {
@@ -423,9 +442,9 @@ std::vector<int> layer_rotations(const Layer& L, int slots) {
   std::set<int> s;
   int J = 0;
   while ((1 << J) < L.G + 2 * L.k) J++;
-  for (int j = 1; j <= J; j++) s.insert(-L.n_in * (1 << (j - 1)));
-  s.insert(L.n_in);
-  for (int n : {L.n_in * (L.G + L.k), L.n_in}) {
+  for (int j = 1; j <= J; j++) s.insert(-L.n_c * (1 << (j - 1)));
+  s.insert(L.n_c);
+  for (int n : {L.n_c * (L.G + L.k), L.n_c}) {
     Plan p = bsgs_plan(L.n_out, n, slots);
     if (p.npad < slots) s.insert(-p.npad);
     for (int j = 1; j < p.g1; j++) s.insert(j);
@@ -444,6 +463,7 @@ Ct kan_eval_layer(kan_model& M, int layer, const ckks_keys& keys, const ckks_ct&
   return layer_eval(M, layer, keys, x);
 }
 int kan_num_layers(const kan_model& M) { return (int)M.layers.size(); }
+int kan_layer_chunks(const kan_model& M, int layer) { return M.layers[layer].K; }
 int kan_total_depth(const kan_model& M) {
   int d = 0;
   for (const Layer& L : M.layers) d += layer_depth(L);
@@ -486,29 +506,44 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
       L.comp.assign(d.comp, d.comp + d.n_comp);
       const double h = (L.hi - L.lo) / L.G;
       for (int m = 0; m <= L.G + 2 * L.k; m++) L.knots.push_back(L.lo + (double)(m - L.k) * h);
-      // W_f[o][m n_i + i] = w_s[o][i] c[o][i][m]  (W' P, Algorithm 3 / Eq. 13)
-      const int n_s = d.n_in * (int)nb;
-      L.Wf.assign((size_t)d.n_out * n_s, 0.0);
-      for (int o = 0; o < d.n_out; o++)
-        for (int i = 0; i < d.n_in; i++)
-          for (size_t m = 0; m < nb; m++)
-            L.Wf[(size_t)o * n_s + m * d.n_in + i] =
-                L.w_s[(size_t)o * d.n_in + i] * L.coef[((size_t)o * d.n_in + i) * nb + m];
-      L.plan_b = bsgs_plan(d.n_out, d.n_in, S);
-      L.plan_s = bsgs_plan(d.n_out, n_s, S);
-      L.diag_b = diagonals(L.w_b, d.n_out, d.n_in, L.plan_b, S);
-      L.diag_s = diagonals(L.Wf, d.n_out, n_s, L.plan_s, S);
       int J = 0;
       while ((1 << J) < L.G + 2 * L.k) J++;
-      if ((int64_t)L.n_in << J > S) return CKKS_ERR_UNSUPPORTED;
+      const int cap = S >> J;
+      if (L.n_in <= cap) {
+        L.K = 1;
+        L.n_c = L.n_in;
+      } else {
+        if (li != 0) return CKKS_ERR_UNSUPPORTED;  // only the client can split an input
+        L.K = (L.n_in + cap - 1) / cap;
+        L.n_c = cap;
+        if (L.K > 16) return CKKS_ERR_UNSUPPORTED;
+      }
+      // per chunk ch (inputs ch*n_c + i, zero beyond n_in): W_b columns and
+      // W_f[o][m n_c + i] = w_s[o][i] c[o][i][m]  (W' P, Algorithm 3 / Eq. 13)
+      const int n_c = L.n_c;
+      const int n_s = n_c * (int)nb;
+      L.plan_b = bsgs_plan(d.n_out, n_c, S);
+      L.plan_s = bsgs_plan(d.n_out, n_s, S);
+      for (int ch = 0; ch < L.K; ch++) {
+        std::vector<double> Wb((size_t)d.n_out * n_c, 0.0), Wf((size_t)d.n_out * n_s, 0.0);
+        for (int o = 0; o < d.n_out; o++)
+          for (int i = 0; i < n_c; i++) {
+            const int gi = ch * n_c + i;
+            if (gi >= d.n_in) continue;
+            Wb[(size_t)o * n_c + i] = L.w_b[(size_t)o * d.n_in + gi];
+            for (size_t m = 0; m < nb; m++)
+              Wf[(size_t)o * n_s + m * n_c + i] =
+                  L.w_s[(size_t)o * d.n_in + gi] * L.coef[((size_t)o * d.n_in + gi) * nb + m];
+          }
+        L.diag_b.push_back(diagonals(Wb, d.n_out, n_c, L.plan_b, S));
+        L.diag_s.push_back(diagonals(Wf, d.n_out, n_s, L.plan_s, S));
+      }
       M->layers.push_back(std::move(L));
     }
     *out = M.release();
     return CKKS_OK;
-  } catch (const Error& e) {
-    return e.code;
   } catch (...) {
-    return CKKS_ERR_CUDA;
+    return api_error();
   }
 }
 
@@ -538,6 +573,14 @@ int kan_model_layer_depth(const kan_model* model, int layer, int* depth) {
   return CKKS_OK;
 }
 
+int kan_model_layer_chunks(const kan_model* model, int layer, int* K, int* n_c) {
+  if (!model || !K || !n_c || layer < 0 || layer >= (int)model->layers.size())
+    return CKKS_ERR_INVALID_ARG;
+  *K = model->layers[layer].K;
+  *n_c = model->layers[layer].n_c;
+  return CKKS_OK;
+}
+
 int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int layer,
                    const ckks_ct* in, ckks_ct** out) {
   try {
@@ -545,10 +588,8 @@ int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int l
       return CKKS_ERR_INVALID_ARG;
     *out = layer_eval(*model, layer, *keys, *in).release();
     return CKKS_OK;
-  } catch (const Error& e) {
-    return e.code;
   } catch (...) {
-    return CKKS_ERR_CUDA;
+    return api_error();
   }
 }
 
@@ -574,10 +615,8 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, const ckks
     for (size_t li = 0; li < model->layers.size(); li++) h = layer_eval(*model, (int)li, *keys, *h);
     *out = h.release();
     return CKKS_OK;
-  } catch (const Error& e) {
-    return e.code;
   } catch (...) {
-    return CKKS_ERR_CUDA;
+    return api_error();
   }
 }
 

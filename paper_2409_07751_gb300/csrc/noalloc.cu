@@ -70,9 +70,7 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, size_t 
     k_rescale_finish(c, d_in, R, d_out, polys, level, c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
                      c.d_rs_invs.u64() + (size_t)level * (c.L + 1));
     return CKKS_OK;
-  } catch (const Error& e) {
-    return e.code;
   } catch (...) {
-    return CKKS_ERR_CUDA;
+    return api_error();
   }
 }

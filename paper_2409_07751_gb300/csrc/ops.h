@@ -60,7 +60,16 @@ void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::ve
                    uint64_t* out, size_t rows, int l);
 void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
                      uint64_t* out, size_t B, int l);
+// batch element b of a [B][2][l][N] batch multiplied by pts[b % pts.size()]
+void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_t*>& pts,
+                      uint64_t* out, size_t B, int l);
+// out[b] = sum_c in[b K + c]
+void k_chunk_sum(Ctx& c, const uint64_t* in, uint64_t* out, size_t B, int K, int l);
 void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,
                       int level, const uint64_t* inv, const uint64_t* invs);
+
+// capi.cu: translates the exception being handled into an error code and
+// records its message for ckks_last_error; call only inside a catch block
+int api_error();
 
 }  // namespace ck

@@ -19,6 +19,7 @@
 namespace ck {
 Ct kan_eval_layer(kan_model& M, int layer, const ckks_keys& keys, const ckks_ct& x);
 int kan_num_layers(const kan_model& M);
+int kan_layer_chunks(const kan_model& M, int layer);
 int kan_total_depth(const kan_model& M);
 }  // namespace ck
 
@@ -84,12 +85,13 @@ size_t step(kan_server& S) {
     std::vector<const ckks_ct*> parts;
     for (Request* r : rs) parts.push_back(r->ct.get());
     Ct in = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
+    const int chunks = kan_layer_chunks(M, std::get<1>(g.first));
     Ct out = kan_eval_layer(M, std::get<1>(g.first), K, *in);
     S.batches++;
     const size_t per = out->words() / out->B;
     size_t off = 0;
     for (Request* r : rs) {
-      const size_t b = r->ct->B;
+      const size_t b = r->ct->B / chunks;  // a wide layer folds K chunk ciphertexts into one
       Ct piece = ct_alloc(c, b, out->level, out->scale);
       CK_CUDA(cudaMemcpyAsync(piece->d.p, out->d.u64() + off * per, b * per * 8,
                               cudaMemcpyDeviceToDevice, c.stream));
@@ -118,10 +120,8 @@ int guard(F&& f) {
   try {
     f();
     return CKKS_OK;
-  } catch (const Error& e) {
-    return e.code;
   } catch (...) {
-    return CKKS_ERR_CUDA;
+    return api_error();
   }
 }
 

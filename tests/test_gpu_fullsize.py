@@ -52,7 +52,7 @@ def test_c1_kan_2_5_1_n32k(G):
     one special prime."""
     model = W.make_model("kan_2_5_1")
     X = W.uniform_inputs(300, 2)
-    _run(G, 15, 18, 1, model, X, [18, 18, 17], 15, [1], fixed=(-4.0, 4.0))
+    _run(G, 15, 18, 1, model, X, [18, 18], 15, [3], fixed=(-4.0, 4.0))
 
 
 def test_c2_kan_4_8_4_1_n64k_uneven(G):
@@ -64,9 +64,31 @@ def test_c2_kan_4_8_4_1_n64k_uneven(G):
     _run(G, 16, 36, 4, model, X, lv, 27, [3])
 
 
+def test_c4_kan_3072_64_10_chunked(G):
+    """[3072,64,10], G=10, k=3 on synthetic 3x32x32 images, N=2^16, 36
+    levels: 3072 * 16 > 2^15 slots, so each image is two ciphertexts of 2048
+    inputs (the second zero-padded), batch of 2 images."""
+    model = W.make_model("kan_3072_64_10")
+    X = W.cifar_like_images(34)
+    m = G.calibrate(model, X[2:], 15, [3, 3, 3])
+    ctx = G.Context(16, 36, 4)
+    gm = G.Model(ctx, m)
+    keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+    K, n_c = 2, 2048
+    rows = []
+    for b in range(2):
+        xp = np.pad(X[b], (0, K * n_c - 3072))
+        rows += [xp[c * n_c:(c + 1) * n_c] for c in range(K)]
+    ct = G.encrypt(ctx, keys, np.array(rows), 36, W.SEED_ENC, 0)
+    out = G.kan_infer(ctx, keys, gm, [ct])
+    assert out.batch == 2
+    dec = G.decrypt(ctx, keys, out, 10)
+    assert _split(m, X[:2], dec) < 1e-3
+
+
 def test_c3_kan_784_64_10_images(G):
     """[784,64,10], G=5, k=3 on synthetic 28x28 blob images, N=2^16,
     36 levels; 784 * 16 copies repeat-packed into 2^15 slots."""
     model = W.make_model("kan_784_64_10")
     X = W.blob_images(66)
-    _run(G, 16, 36, 4, model, X, [36, 36], 15, [3], tol=1e-3)
+    _run(G, 16, 36, 4, model, X, [36, 36], 15, [3, 3, 3], tol=1e-3)

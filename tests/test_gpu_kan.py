@@ -72,6 +72,33 @@ def test_degenerate_grids_bit_exact(G, G_, k_):
     assert (go.export()[0] == oo.data).all()
 
 
+def test_wide_first_layer_chunks_bit_exact(G):
+    """40 inputs with G=3, k=2 at N=2^7: 40 * 8 > 64 slots, so the input is
+    split into 5 ciphertexts of 8 (request-major batch) and the partial
+    outputs are summed."""
+    model = W.make_model("t", widths=[40, 4, 2], G=3, k=2)
+    X = W.uniform_inputs(64, 40)
+    m = calibrate.calibrate(model, X, 7, [1])
+    gctx, octx, gm, gk, ok = _setup(G, 7, 17, 2, m)
+    K, n_c = kan_he.chunking(m[0], octx.slots)
+    assert (K, n_c) == (5, 8)
+    outs = []
+    batch = []
+    for b in range(2):
+        xp = np.pad(X[b], (0, K * n_c - 40))
+        chunks = [O.encrypt(octx, ok, xp[c * n_c:(c + 1) * n_c], octx.L, W.SEED_ENC, b * K + c)
+                  for c in range(K)]
+        outs.append(kan_he.infer(octx, ok, chunks, m))
+        batch += [xp[c * n_c:(c + 1) * n_c] for c in range(K)]
+    gin = G.encrypt(gctx, gk, np.array(batch), octx.L, W.SEED_ENC, 0)
+    gout = G.kan_infer(gctx, gk, gm, [gin])
+    assert gout.batch == 2
+    for b in range(2):
+        assert (gout.export()[b] == outs[b].data).all()
+    dec = G.decrypt(gctx, gk, gout, 2)
+    assert np.abs(dec - kan_plain.forward(m, X[:2], "poly", "poly")).max() < 1e-5
+
+
 def test_level_exhausted_is_an_error(G):
     model = W.make_model("t", widths=[3, 2], G=3, k=2)
     m = calibrate.calibrate(model, W.uniform_inputs(64, 3), 7, [1])
