@@ -281,6 +281,10 @@ def layer_eval(ctx, keys, x, layer):
     s1 = polycomp0(ctx, keys, a1, layer["comp"])
     s2 = polycomp0(ctx, keys, a2, layer["comp"])
     b = ckks.mul(ctx, keys, s1, s2)
+    if k == 0:
+        # order-0 basis: outside its n_i g valid slots b holds PolyComp(0)^2 =
+        # 1/4, which the matvec's replication would fold in; zero it (1 level)
+        b = ckks.mul_plain(ctx, b, np.ones(n_i * G))
     for j in range(1, k + 1):
         t1 = coltile(Gm, 1, r - j)
         t2 = coltile(Gm, j + 1, r)

@@ -130,7 +130,8 @@ std::vector<double> diagonals(const std::vector<double>& M, int n_out, int n, co
   return D;
 }
 
-enum Tag { T_SILU_MUL = 1, T_SILU_ADD, T_MASK_R, T_G1, T_G2, T_U1M, T_U1A, T_U2M, T_U2A, T_DIAG_B, T_DIAG_S };
+enum Tag { T_SILU_MUL = 1, T_SILU_ADD, T_MASK_R, T_G1, T_G2, T_U1M, T_U1A, T_U2M, T_U2A, T_DIAG_B, T_DIAG_S,
+           T_MASK_B0, T_DIAG_P, T_DIAG_W };
 
 Ct bsgs_matvec(kan_model& M, int li, bool spline, const ckks_keys& keys, const ckks_ct& v) {
   Ctx& c = *M.ctx;
@@ -345,6 +346,14 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   Ct s1 = polycomp0(c, keys, *a1, L.comp);
   Ct s2 = polycomp0(c, keys, *a2, L.comp);
   Ct b = op_mul(c, keys, *s1, *s2);
+  if (k == 0) {
+    // order-0 basis: outside its n_i g valid slots b holds PolyComp(0)^2 =
+    // 1/4, which the matvec's replication would fold in; zero it (1 level)
+    const double Sb = plain_scale(c, b->scale, b->level);
+    const uint64_t* p_b0 = cached_pt(M, li, T_MASK_B0, 0, b->level, Sb,
+                                     [&] { return std::vector<double>((size_t)n_i * G, 1.0); });
+    b = op_mul_pt(c, *b, p_b0, Sb);
+  }
   for (int j = 1; j <= k; j++) {
     const std::vector<double> t1 = coltile(L, 1, r - j), t2 = coltile(L, j + 1, r);
     const std::vector<double> t3 = coltile(L, j + 2, r + 1), t4 = coltile(L, 2, r - j + 1);
@@ -433,7 +442,7 @@ int layer_depth(const Layer& L) {
     while ((2 << lg) <= 2 * n) lg++;
     dc += 1 + lg;
   }
-  const int spline = 3 + dc + L.k;
+  const int spline = 3 + dc + std::max(L.k, 1);  // k = 0 masks its basis instead
   const int silu = 2 + cheb_depth((int)L.cheb.size() - 1);
   return std::max(spline, silu);
 }

@@ -143,6 +143,26 @@ def test_ops_bit_exact(G, name):
     assert np.abs(dec - x * y).max() < 1e-6
 
 
+@pytest.mark.parametrize("name", ["n16k", "n64k"])
+def test_unfused_form_matches_oracle(G, name):
+    """With kernel fusion off (separate conversion, transform and pointwise
+    launches) every op still equals the oracle word for word."""
+    gctx, octx, gk, ok = pair(G, name)
+    gctx.set_fusion(False)
+    try:
+        L = gctx.L
+        x, ox, gx = _both(G, gctx, octx, gk, ok, L, 1, 0)
+        y, oy, gy = _both(G, gctx, octx, gk, ok, L, 2, 1)
+        _same(G.mul(gctx, gk, gx, gy), O.mul(octx, ok, ox, oy))
+        _same(G.rescale(gctx, gx), O.rescale(octx, ox))
+        _same(G.level_down(gctx, gx, 1), O.level_down(octx, ox, 1))
+        _same(G.rotate(gctx, gk, gx, 3), O.rotate(octx, ok, ox, 3))
+        for h, t in zip(G.rotate_hoisted(gctx, gk, gx, [1, -5]), [1, -5]):
+            _same(h, O.rotate(octx, ok, ox, t))
+    finally:
+        gctx.set_fusion(True)
+
+
 def test_batched_ops_match_single(G):
     gctx, octx, gk, ok = pair(G, "n4k")
     rng = np.random.default_rng(11)

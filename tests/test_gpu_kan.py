@@ -70,6 +70,8 @@ def test_degenerate_grids_bit_exact(G, G_, k_):
     oo = kan_he.infer(octx, ok, oc, m)
     go = G.kan_infer(gctx, gk, gm, [gc])
     assert (go.export()[0] == oo.data).all()
+    hef = kan_plain.forward(m, X[:1], "poly", "poly")
+    assert np.abs(G.decrypt(gctx, gk, go, 2) - hef).max() < 1e-5
 
 
 def test_wide_first_layer_chunks_bit_exact(G):

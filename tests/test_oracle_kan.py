@@ -192,3 +192,20 @@ def test_he_kan_matches_hef(he_small):
         dec = ckks.decrypt(ctx, keys, out, 2)
         hef = kan_plain.forward(m, X[b:b + 1], "poly", "poly")[0]
         assert np.abs(dec - hef).max() < 1e-5
+
+
+@pytest.mark.parametrize("G_,k_", [(1, 0), (4, 0), (2, 1)])
+def test_he_kan_degenerate_grids_match_hef(he_small, G_, k_):
+    """Order-0 splines and a single interval: the encrypted layer still
+    equals the HE-friendly KAN (for k = 0 the basis must be zero outside its
+    n_i g slots before the matvec replicates it)."""
+    ctx = he_small
+    model = W.make_model("t", widths=[3, 2], G=G_, k=k_)
+    X = W.uniform_inputs(64, 3)
+    m = calibrate.calibrate(model, X, 5, [1])
+    keys = ckks.Keys(ctx, 1, rot_steps=kan_he.model_rotations(m, ctx.slots))
+    c = ckks.encrypt(ctx, keys, X[0], ctx.L, 2, 0)
+    out = kan_he.infer(ctx, keys, c, m)
+    dec = ckks.decrypt(ctx, keys, out, 2)
+    hef = kan_plain.forward(m, X[:1], "poly", "poly")[0]
+    assert np.abs(dec - hef).max() < 1e-5
