@@ -55,14 +55,75 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-micro", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--kernel", default=None, choices=["ntt", "intt"],
+    p.add_argument("--kernel", default=None, choices=["ntt", "intt", "hmult"],
                    help="time one kernel kind alone (NTT limbs/s) instead of the network")
     p.add_argument("--rows", type=int, default=592, help="limbs per launch for --kernel")
     p.add_argument("--serve", action="store_true",
                    help="Poisson serving mix through the continuous-batching server")
+    p.add_argument("--no-graphs", action="store_true",
+                   help="run the layer schedules eagerly instead of replaying CUDA graphs")
+    p.add_argument("--table3", action="store_true",
+                   help="one KAN layer per (n_i, g, k) shape: lazy combination vs the naive method")
     p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
     p.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals for --serve")
     return p.parse_args()
+
+
+TABLE3_SHAPES = [(64, 3, 2), (128, 5, 3), (256, 5, 3), (256, 10, 3), (256, 10, 5)]
+
+
+def table3_arm(a):
+    """--table3: the B-spline layer shapes (n_i, g, k) of the paper's Table 3,
+    each as one KAN layer [n_i, 64] (SiLU degree 15, comparison f_3) on one
+    encrypted input at N=2^16 with 14 levels: kan_layer_eval with lazy
+    combination (W_f = W'P, Eq. 13) against the naive method (HE permutation
+    by P, then W'). Reports GPU ms per layer and the plaintext-multiply and
+    rotation launches of each schedule."""
+    import numpy as np
+    import torch
+    from paper_2409_07751_gb300 import build
+    build.build()
+    from paper_2409_07751_gb300 import ckks as G
+    from paper_2409_07751_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = G.Context(a.log_n, 14, 4)
+    ctx.set_stream(stream.cuda_stream)
+    rows = []
+    for n_i, g, k in TABLE3_SHAPES:
+        model = W.make_model("t", widths=[n_i, 64], G=g, k=k)
+        X = W.uniform_inputs(65, n_i)
+        m = G.calibrate(model, X[1:], 15, [3])
+        row = {"n_i": n_i, "g": g, "k": k, "n_out": 64}
+        for naive in (False, True):
+            gm = G.Model(ctx, [dict(L, naive=naive) for L in m])
+            keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+            x = G.encrypt(ctx, keys, X[:1], 14, W.SEED_ENC, 0)
+            G.kan_layer_eval(ctx, keys, gm, 0, x).close()  # plaintext cache
+            torch.cuda.synchronize()
+            before = ctx.launch_counts()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                G.kan_layer_eval(ctx, keys, gm, 0, x).close()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            after = ctx.launch_counts()
+            tag = "naive" if naive else "lazy"
+            row[tag + "_ms"] = e0.elapsed_time(e1) / reps
+            row[tag + "_mul_plain"] = (after["mul_plain"] - before["mul_plain"]) // reps
+            row[tag + "_rotations"] = (after["rotate_finish"] - before["rotate_finish"]) // reps
+            row[tag + "_depth"] = gm.layer_depth(0)
+            x.close()
+            keys.close()
+            gm.close()
+        row["speedup"] = row["naive_ms"] / row["lazy_ms"]
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"metric": "KAN layer latency, lazy combination vs naive (Table 3 shapes)",
+                      "unit": "ms", "n_poly": 1 << a.log_n, "levels": 14, "batch": 1,
+                      "rows": rows}), flush=True)
 
 
 def serve_arm(a):
@@ -141,7 +202,9 @@ def serve_arm(a):
 
 def kernel_arm(a):
     """--kernel ntt|intt: forward or inverse NTT of `rows` random limbs of
-    N = 2^log_n (moduli cycling through the 37 Q primes) per launch."""
+    N = 2^log_n (moduli cycling through the Q primes) per launch;
+    --kernel hmult: HMult with relinearisation and rescale of `batch`
+    ciphertexts at the top level."""
     import numpy as np
     import torch
     from paper_2409_07751_gb300 import build
@@ -153,6 +216,25 @@ def kernel_arm(a):
     ctx.set_stream(stream.cuda_stream)
     limbs = a.levels + 1
     N = 1 << a.log_n
+    if a.kernel == "hmult":
+        # HMult (tensor, ModUp, key inner product, ModDown, rescale) on a
+        # batch of `batch` ciphertexts at the top level
+        keys = G.Keys(ctx, 1, [])
+        x = G.encrypt(ctx, keys, np.random.default_rng(0).uniform(-1, 1, (a.batch, ctx.slots)),
+                      a.levels, 2, 0)
+        for _ in range(a.warmup):
+            G.mul(ctx, keys, x, x).close()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            G.mul(ctx, keys, x, x).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        print(json.dumps({"kernel": "hmult", "batch": a.batch, "limbs": limbs, "n_poly": N,
+                          "ms_per_call": ms, "hmult_per_s": a.batch / (ms / 1000.0)}), flush=True)
+        return
     rng = np.random.default_rng(0)
     h = np.stack([rng.integers(0, int(ctx.moduli[r % limbs]), N, dtype=np.uint64) for r in range(a.rows)])
     d = torch.from_numpy(h.view(np.int64)).cuda()
@@ -177,7 +259,8 @@ def config(a):
     return {"workload": WORKLOAD, "model": "kan_4_8_4_1", "n_poly": 1 << a.log_n,
             "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": 27, "comparison": "f_3",
             "input_levels": "uniform over [L - slack, L]", "parallelism": "replicas (request sharding)",
-            "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)"}
+            "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)",
+            "schedule": "eager" if getattr(a, "no_graphs", False) else "CUDA graph per layer"}
 
 
 def shard_plan(rank, batch):
@@ -365,6 +448,8 @@ def main():
         return kernel_arm(a)
     if a.serve:
         return serve_arm(a)
+    if a.table3:
+        return table3_arm(a)
     import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -391,6 +476,7 @@ def main():
     model, Xcal, X = model_and_inputs(a, rank)
     m = G.calibrate(model, Xcal, 27, [3])
     gm = G.Model(ctx, m)
+    gm.set_graphs(not a.no_graphs)
     depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
     slack = a.levels - depth
     plan = shard_plan(rank, a.batch)
@@ -463,29 +549,58 @@ def main():
     else:
         roofline = dict({"kernel": dom, "bound": "hbm", "traffic": None}, **hbm)
     roofline.update({"algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
-                     "share_of_kernel_time": ms / total_ms})
+                     "share_of_kernel_time": ms / total_ms,
+                     "kernel_ms_per_step": total_ms / a.steps})
     shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])}
 
-    # ---------------- micro: HMult / HRot per second at N=2^16, 37 limbs
+    def timed(fn, reps):
+        def run():
+            r = fn()
+            if r is not None:
+                r.close()
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0 / reps
+
+    # ---------------- the plain form: one request at a time, fusion off
+    plain = None
+    if not a.no_micro:
+        one = G.encrypt(ctx, keys, X[:1], a.levels, 9, 0)
+        gm.set_graphs(False)
+        plain = {}
+        for fused in (False, True):
+            ctx.set_fusion(fused)
+            s = timed(lambda: G.kan_infer(ctx, keys, gm, [one]), 2)
+            plain["fused" if fused else "unfused"] = {"value": 1.0 / s, "unit": UNIT, "batch": 1}
+        ctx.set_fusion(True)
+        gm.set_graphs(not a.no_graphs)
+        one.close()
+        plain["batched_over_plain"] = value / world / plain["unfused"]["value"]
+
+    # ---------------- micro: HMult / HRot per second at N=2^16, l in {37, 19, 2}
     micro = None
     if not a.no_micro:
         micro = {}
-        for B in (1, 8):
-            x = G.encrypt(ctx, keys, X[:B], a.levels, 9, 0)
-            for name, fn in (("hmult", lambda: G.mul(ctx, keys, x, x)),
-                             ("hrot", lambda: G.rotate(ctx, keys, x, 1))):
-                fn().close()
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                reps = 3
-                e0.record(stream)
-                for _ in range(reps):
-                    fn().close()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                micro["%s_per_s_batch%d" % (name, B)] = B * reps / (e0.elapsed_time(e1) / 1000.0)
-            x.close()
-        micro["limbs"] = a.levels + 1
+        for lv in (a.levels, a.levels // 2, 1):
+            for B in (1, 8, 64):
+                x = G.encrypt(ctx, keys, X[:B], lv, 9, 0)
+                for name, fn in (("hmult", lambda: G.mul(ctx, keys, x, x)),
+                                 ("hrot", lambda: G.rotate(ctx, keys, x, 1))):
+                    s = timed(fn, 3 if B < 64 else 2)
+                    micro["%s_per_s_l%d_b%d" % (name, lv + 1, B)] = B / s
+                x.close()
+        rows = 2 * (a.levels + 1) * 8
+        buf = torch.zeros(rows * ctx.N, dtype=torch.int64, device="cuda")
+        for inv in (False, True):
+            s = timed(lambda: ctx.ntt(buf.data_ptr(), rows, a.levels + 1, inv), 5)
+            micro["%s_limbs_per_s" % ("intt" if inv else "ntt")] = rows / s
+        del buf
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -530,7 +645,8 @@ def main():
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": float(np.percentile(step_ms, 99)), "per": "batch of %d" % a.batch},
             "roofline": roofline, "kernel_time_shares": shares, "gpu_launches": launches,
-            "clocks": clocks, "e2e": e2e, "micro": micro, "depth": depth, "slack": slack}
+            "clocks": clocks, "e2e": e2e, "plain_form": plain, "micro": micro, "depth": depth,
+            "slack": slack}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import calibrate as OC
         mo = OC.calibrate(model, Xcal, 27, [3])

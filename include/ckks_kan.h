@@ -70,6 +70,12 @@ int ckks_context_destroy(ckks_ctx* ctx);
 int ckks_context_info(const ckks_ctx* ctx, uint64_t* moduli, double* delta, int* n_qp);
 /* Queue work on `stream` (a cudaStream_t) instead of the library's own stream. */
 int ckks_set_stream(ckks_ctx* ctx, void* stream);
+/* Kernel fusion on (default, enabled != 0) or off. On: ModUp's basis
+ * conversion, ModDown's and rescale's subtract-and-scale run inside the
+ * NTT kernels' loads and stores (N = 2^13 .. 2^16). Off: separate
+ * conversion, transform and pointwise launches, the plain form. Results are
+ * identical word for word either way; only speed changes. */
+int ckks_set_fusion(ckks_ctx* ctx, int enabled);
 int ckks_synchronize(ckks_ctx* ctx);
 
 /* ------------------------------------------------------------ raw kernels
@@ -202,6 +208,11 @@ typedef struct {
   int silu_degree;
   const int* comp;
   int n_comp;
+  /* 0: lazy combination, the fused W_f = W'P of Eq. 13 on the ColTile basis.
+   * 1: the naive method the paper compares against (Table 3): an HE matvec by
+   * the permutation P of Algorithm 3 (n_i(g+k) diagonals, one more level),
+   * then W' on the row-major basis. */
+  int naive;
 } kan_layer_desc;
 
 /* Host-only model preparation (no device work).
@@ -234,6 +245,15 @@ int kan_model_layer_depth(const kan_model* model, int layer, int* depth);
  * (the last zero-padded), as consecutive batch elements; otherwise *K = 1 and
  * *n_c = n_in. Only layer 0 may be chunked. */
 int kan_model_layer_chunks(const kan_model* model, int layer, int* K, int* n_c);
+/* CUDA-graph replay of layer schedules on (enabled != 0) or off (default;
+ * turning it off frees the captured graphs). With graphs on, kan_layer_eval,
+ * kan_infer and the server run each layer, per input shape (batch, level,
+ * scale) and key set, eagerly on the first call, capture the schedule into a
+ * graph on the second and replay it afterwards; every temporary is
+ * allocated inside the graph, the input and result pass through two
+ * graph-owned buffers. Results are identical word for word to the eager
+ * schedule. */
+int kan_model_set_graphs(kan_model* model, int enabled);
 /* One layer on a batch: repeat packing (Algorithm 1), B-spline basis
  * (Algorithm 2), fused linear layer W_f = W'P (Algorithm 3, Eq. 13) and the
  * polynomial SiLU branch, both linear maps by BSGS diagonal matvec with

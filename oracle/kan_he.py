@@ -236,8 +236,11 @@ def layer_rotations(layer, slots):
     J = math.ceil(math.log2(G + 2 * k))
     steps = {-n_i * 2 ** (j - 1) for j in range(1, J + 1)}
     steps.add(n_i)
-    for n in (n_i * (G + k), n_i):
-        p = bsgs_plan(n_o, n, slots)
+    plans = [(n_o, n_i * (G + k)), (n_o, n_i)]
+    if layer.get("naive"):
+        plans.append((n_i * (G + k), n_i * (G + k)))
+    for n_out, n in plans:
+        p = bsgs_plan(n_out, n, slots)
         if p["npad"] < slots:
             steps.add(-p["npad"])
         steps.update(range(1, p["g1"]))
@@ -299,12 +302,23 @@ def layer_eval(ctx, keys, x, layer):
         rb = ckks.rotate(ctx, keys, b, n_i)
         b = ckks.mul_sum(ctx, keys, [(u1, b), (u2, rb)])
 
-    # fused linear layer (Eq. 13) by BSGS
-    Wf = fused_weights(layer)
     plan_s = bsgs_plan(n_o, n_i * (G + k), S)
+    if layer.get("naive"):
+        # the naive method the paper compares against (Table 3): reorder the
+        # ColTile basis to row-major by an HE matvec with the permutation P of
+        # Algorithm 3, then multiply by W' (one more level, n_i(g+k) diagonals)
+        n = n_i * (G + k)
+        plan_p = bsgs_plan(n, n, S)
+        if plan_p["npad"] < S:
+            b = ckks.add(ctx, b, ckks.rotate(ctx, keys, b, -plan_p["npad"]))
+        b = bsgs_matvec(ctx, keys, b, permutation_matrix(n_i, G + k), plan_p)
+        Ws = lazy_weights(layer)
+    else:
+        # fused linear layer (Eq. 13)
+        Ws = fused_weights(layer)
     if plan_s["npad"] < S:
         b = ckks.add(ctx, b, ckks.rotate(ctx, keys, b, -plan_s["npad"]))
-    ys = bsgs_matvec(ctx, keys, b, Wf, plan_s)
+    ys = bsgs_matvec(ctx, keys, b, Ws, plan_s)
 
     lv = min(ys.level, yb.level)
     return ckks.add(ctx, ckks.level_down(ctx, ys, lv), ckks.level_down(ctx, yb, lv))

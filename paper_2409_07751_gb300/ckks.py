@@ -25,7 +25,7 @@ class KanLayerDesc(ctypes.Structure):
                 ("coef", c_vp), ("w_s", c_vp), ("w_b", c_vp),
                 ("R", c_dbl), ("silu_lo", c_dbl), ("silu_hi", c_dbl),
                 ("silu_cheb", c_vp), ("silu_degree", c_i32),
-                ("comp", c_vp), ("n_comp", c_i32)]
+                ("comp", c_vp), ("n_comp", c_i32), ("naive", c_i32)]
 
 
 SIGNATURES = {
@@ -35,6 +35,7 @@ SIGNATURES = {
     "ckks_context_destroy": (c_i32, [c_vp]),
     "ckks_context_info": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "ckks_set_stream": (c_i32, [c_vp, c_vp]),
+    "ckks_set_fusion": (c_i32, [c_vp, c_i32]),
     "ckks_synchronize": (c_i32, [c_vp]),
     "ckks_ntt": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_i32]),
     "ckks_kernel_kind_count": (c_i32, []),
@@ -75,6 +76,7 @@ SIGNATURES = {
     "kan_model_rotations": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
     "kan_model_layer_depth": (c_i32, [c_vp, c_i32, c_vp]),
     "kan_model_layer_chunks": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
+    "kan_model_set_graphs": (c_i32, [c_vp, c_i32]),
     "kan_layer_eval": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp, PP]),
     "kan_infer": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, PP]),
     "kan_server_create": (c_i32, [c_vp, c_sz, PP]),
@@ -144,6 +146,9 @@ class Context:
 
     def set_stream(self, stream_ptr):
         check(lib().ckks_set_stream(self.h, stream_ptr))
+
+    def set_fusion(self, enabled):
+        check(lib().ckks_set_fusion(self.h, 1 if enabled else 0))
 
     def galois(self, step):
         return int(lib().ckks_galois_element(self.h, int(step)))
@@ -351,6 +356,7 @@ def _descs(layers, keep):
         d.R, d.silu_lo, d.silu_hi = L.get("R", 1.0), L.get("silu_lo", -1.0), L.get("silu_hi", 1.0)
         d.silu_cheb, d.silu_degree = _p(cheb), len(cheb) - 1
         d.comp, d.n_comp = _p(comp), len(comp)
+        d.naive = 1 if L.get("naive") else 0
     return descs
 
 
@@ -416,6 +422,9 @@ class Model:
         d = ctypes.c_int()
         check(lib().kan_model_layer_depth(self.h, layer, ctypes.byref(d)))
         return d.value
+
+    def set_graphs(self, enabled):
+        check(lib().kan_model_set_graphs(self.h, 1 if enabled else 0))
 
     def layer_chunks(self, layer):
         """(K, n_c): input ciphertexts per request and inputs per chunk."""

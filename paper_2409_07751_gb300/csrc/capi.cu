@@ -100,6 +100,13 @@ int ckks_set_stream(ckks_ctx* ctx, void* stream) {
   });
 }
 
+int ckks_set_fusion(ckks_ctx* ctx, int enabled) {
+  return guard([&] {
+    need(ctx != nullptr, "ctx is NULL");
+    ctx->c.fused = enabled != 0;
+  });
+}
+
 int ckks_synchronize(ckks_ctx* ctx) {
   return guard([&] {
     need(ctx != nullptr, "ctx is NULL");
@@ -154,6 +161,13 @@ int ckks_profile_collect2(ckks_ctx* ctx, double* ms, double* bytes, double* modm
       c.ev_pool.push_back(r.b);
     }
     c.prof_recs.clear();
+    for (int k = 0; k < K_KIND_COUNT && k < cap; k++) {
+      if (ms) ms[k] += c.prof_acc[k][0];
+      if (bytes) bytes[k] += c.prof_acc[k][1];
+      if (modmuls) modmuls[k] += c.prof_acc[k][2];
+      if (launches) launches[k] += (uint64_t)c.prof_acc[k][3];
+    }
+    memset(c.prof_acc, 0, sizeof(c.prof_acc));
   });
 }
 

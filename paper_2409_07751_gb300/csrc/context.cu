@@ -64,12 +64,19 @@ Launch::Launch(Ctx& cx, int k, double algorithmic_bytes, double modmuls)
   if (c.prof) {
     cudaEvent_t a = c.take_event();
     b = c.take_event();
-    CK_CUDA(cudaEventRecord(a, c.stream));
-    c.prof_recs.push_back(ProfRec{k, bytes, modmuls, a, b});
+    // inside a graph capture the records become event-record nodes
+    CK_CUDA(c.prof_sink ? cudaEventRecordWithFlags(a, c.stream, cudaEventRecordExternal)
+                        : cudaEventRecord(a, c.stream));
+    (c.prof_sink ? *c.prof_sink : c.prof_recs).push_back(ProfRec{k, bytes, modmuls, a, b});
   }
 }
 Launch::~Launch() {
-  if (b) cudaEventRecord(b, c.stream);
+  if (b) {
+    if (c.prof_sink)
+      cudaEventRecordWithFlags(b, c.stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(b, c.stream);
+  }
 }
 
 // ------------------------------------------------------------------ host math

@@ -86,6 +86,9 @@ struct Ctx {
   int log_n = 0;
   uint64_t N = 0;
   int L = 0, alpha = 0, n_qp = 0, beta_max = 0;
+  // fused NTT kernels (basis conversion / rescale inside the transforms'
+  // loads and stores); off = separate conversion and transform launches
+  bool fused = true;
   std::vector<uint64_t> mod, psi;
   std::vector<double> delta;
   // device tables
@@ -112,6 +115,11 @@ struct Ctx {
   uint64_t launches[K_KIND_COUNT] = {};
   bool prof = false;
   std::vector<ProfRec> prof_recs;
+  // while a schedule is captured into a CUDA graph, its launch records go
+  // to the graph's own list (its events become event-record nodes)
+  std::vector<ProfRec>* prof_sink = nullptr;
+  // per kind, from replayed graphs: ms, algorithmic bytes, modmuls, launches
+  double prof_acc[K_KIND_COUNT][4] = {};
   std::vector<cudaEvent_t> ev_pool;
   cudaEvent_t take_event();
 

@@ -75,16 +75,47 @@ struct Layer {
   // ciphertexts per request of n_c inputs each (the last zero-padded);
   // otherwise K = 1 and n_c = n_in. The schedule runs on n_c inputs.
   int K = 1, n_c = 0;
-  Plan plan_b, plan_s;
+  // naive: the spline branch reorders the ColTile basis by an HE matvec
+  // with the permutation P (plan_p) and diag_s then holds W' instead of W_f
+  bool naive = false;
+  Plan plan_b, plan_s, plan_p;
   std::vector<std::vector<double>> diag_b, diag_s;  // per chunk: [no][slots]
 };
 
+}  // namespace
+
+namespace {
+// One layer schedule captured into a CUDA graph for one input shape. The
+// graph reads its input from `in` and writes its result to `out`; every
+// temporary is allocated and freed inside the graph.
+struct GraphEntry {
+  int uses = 0;
+  uint64_t eager_launches = 0;
+  cudaGraphExec_t exec = nullptr;
+  Ct in, out;
+  uint64_t launches[K_KIND_COUNT] = {};
+  std::vector<ProfRec> prof;  // event pairs recorded by the graph (profiled capture)
+  GraphEntry() = default;
+  GraphEntry(const GraphEntry&) = delete;
+  GraphEntry& operator=(const GraphEntry&) = delete;
+  ~GraphEntry() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto& r : prof) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+};
+// (layer, batch, level, scale bits, key set, profiled)
+using GraphKey = std::tuple<int, size_t, int, uint64_t, const ckks_keys*, bool>;
 }  // namespace
 
 struct kan_model {
   Ctx* ctx;
   std::vector<Layer> layers;
   std::map<std::tuple<int, int, int, int, uint64_t>, std::unique_ptr<DevBuf>> pts;
+  bool graphs = false;
+  std::map<GraphKey, std::unique_ptr<GraphEntry>> graph_cache;  // destroyed before pts
 };
 
 namespace {
@@ -133,11 +164,17 @@ std::vector<double> diagonals(const std::vector<double>& M, int n_out, int n, co
 enum Tag { T_SILU_MUL = 1, T_SILU_ADD, T_MASK_R, T_G1, T_G2, T_U1M, T_U1A, T_U2M, T_U2A, T_DIAG_B, T_DIAG_S,
            T_MASK_B0, T_DIAG_P, T_DIAG_W };
 
-Ct bsgs_matvec(kan_model& M, int li, bool spline, const ckks_keys& keys, const ckks_ct& v) {
+// accessor of diagonals precomputed per chunk as [no][slots]
+auto stored_diag(const std::vector<std::vector<double>>& DC, int S) {
+  return [&DC, S](int ch, int t, int s) { return DC[ch][(size_t)t * S + s]; };
+}
+
+// y = M v by baby-step giant-step over the extended diagonals dval(ch, t, s)
+// (chunk ch, diagonal t, slot s); batch element b uses chunk b % nch
+template <class DV>
+Ct bsgs_matvec(kan_model& M, int li, int tag, const Plan& p, int nch, DV&& dval,
+               const ckks_keys& keys, const ckks_ct& v) {
   Ctx& c = *M.ctx;
-  Layer& L = M.layers[li];
-  const Plan& p = spline ? L.plan_s : L.plan_b;
-  const auto& DC = spline ? L.diag_s : L.diag_b;  // per chunk
   const int S = (int)(c.N / 2);
   std::vector<int64_t> bs;
   for (int j = 0; j < p.g1; j++) bs.push_back(j);
@@ -152,17 +189,16 @@ Ct bsgs_matvec(kan_model& M, int li, bool spline, const ckks_keys& keys, const c
     for (int j = 0; j < p.g1; j++) {
       const int t = p.g1 * i + j;
       std::vector<const uint64_t*> pts;
-      for (int ch = 0; ch < L.K; ch++) {
-        const std::vector<double>& D = DC[ch];
-        pts.push_back(cached_pt(M, li, spline ? T_DIAG_S : T_DIAG_B, t * 64 + ch, lv, Spt, [&] {
+      for (int ch = 0; ch < nch; ch++) {
+        pts.push_back(cached_pt(M, li, tag, t * 64 + ch, lv, Spt, [&] {
           std::vector<double> d(S);
           const int sh = p.g1 * i;
-          for (int s = 0; s < S; s++) d[s] = D[(size_t)t * S + ((s - sh) % S + S) % S];
+          for (int s = 0; s < S; s++) d[s] = dval(ch, t, ((s - sh) % S + S) % S);
           return d;
         }));
       }
       uint64_t* dst = j == 0 ? acc->d.u64() : prod->d.u64();
-      if (L.K == 1)
+      if (nch == 1)
         k_mul_pt(c, baby[j]->d.u64(), pts[0], dst, rows, lv + 1);
       else  // batch element b uses the diagonals of its chunk b % K
         k_mul_pt_grouped(c, baby[j]->d.u64(), pts, dst, v.B, lv + 1);
@@ -320,7 +356,7 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   Ct y = op_add_pt(c, *y0, p_sa);
   if (L.plan_b.npad < S) y = op_add(c, *y, *op_rotate(c, keys, *y, -L.plan_b.npad), false);
   Ct v = eval_cheb(c, keys, *y, L.cheb);
-  Ct yb = bsgs_matvec(M, li, false, keys, *v);
+  Ct yb = bsgs_matvec(M, li, T_DIAG_B, L.plan_b, L.K, stored_diag(L.diag_b, S), keys, *v);
 
   // Algorithm 1
   const uint64_t* p_mr = cached_pt(M, li, T_MASK_R, 0, x.level, S1,
@@ -391,9 +427,23 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
     b = op_mul_sum(c, keys, {{u1.get(), b.get()}, {u2.get(), rb.get()}});
   }
 
-  // fused linear layer (Eq. 13)
+  if (L.naive) {
+    // the naive method: reorder the ColTile basis to row-major by an HE
+    // matvec with the permutation P of Algorithm 3, shared by every chunk
+    if (L.plan_p.npad < S) b = op_add(c, *b, *op_rotate(c, keys, *b, -L.plan_p.npad), false);
+    const int nb = G + k, n = n_i * nb, npad = L.plan_p.npad, no = L.plan_p.no;
+    auto perm = [=](int, int t, int s) -> double {
+      if (s >= npad) return 0.0;
+      const int r = s % no, col = (s + t) % npad;  // P[r][col]
+      if (r >= n || col >= n) return 0.0;
+      return col == (r % nb) * n_i + r / nb ? 1.0 : 0.0;
+    };
+    b = bsgs_matvec(M, li, T_DIAG_P, L.plan_p, 1, perm, keys, *b);
+  }
+  // fused linear layer W_f (Eq. 13), or W' after the naive permutation
   if (L.plan_s.npad < S) b = op_add(c, *b, *op_rotate(c, keys, *b, -L.plan_s.npad), false);
-  Ct ys = bsgs_matvec(M, li, true, keys, *b);
+  Ct ys = bsgs_matvec(M, li, L.naive ? T_DIAG_W : T_DIAG_S, L.plan_s, L.K, stored_diag(L.diag_s, S),
+                      keys, *b);
   const int lv = std::min(ys->level, yb->level);
   Ct out = op_add(c, *op_level_down(c, *ys, lv), *op_level_down(c, *yb, lv), false);
   if (L.K == 1) return out;
@@ -401,6 +451,95 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   Ct sum = ct_alloc(c, out->B / L.K, out->level, out->scale);
   k_chunk_sum(c, out->d.u64(), sum->d.u64(), sum->B, L.K, out->level + 1);
   return sum;
+}
+
+// Capture layer li's schedule on input shape x into g (the plaintext cache
+// and the conversion tables are already filled by an eager run).
+void capture_layer(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x, GraphEntry& g) {
+  Ctx& c = *M.ctx;
+  g.in = ct_alloc(c, x.B, x.level, x.scale);
+  if (c.prof) {  // events for the record nodes, created before the capture
+    std::vector<cudaEvent_t> ev;
+    for (uint64_t i = 0; i < 2 * g.eager_launches; i++) ev.push_back(c.take_event());
+    for (cudaEvent_t e : ev) c.ev_pool.push_back(e);
+  }
+  uint64_t before[K_KIND_COUNT];
+  memcpy(before, c.launches, sizeof(before));
+  std::vector<ProfRec> recs;
+  c.prof_sink = &recs;
+  cudaGraph_t graph = nullptr;
+  CK_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    Ct y = layer_eval(M, li, keys, *g.in);
+    if (y->B != g.out->B || y->level != g.out->level || y->scale != g.out->scale)
+      throw Error(CKKS_ERR_CUDA, "layer output shape differs between runs");
+    CK_CUDA(cudaMemcpyAsync(g.out->d.p, y->d.p, y->d.bytes, cudaMemcpyDeviceToDevice, c.stream));
+    y.reset();
+    CK_CUDA(cudaStreamEndCapture(c.stream, &graph));
+  } catch (...) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(c.stream, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    cudaGetLastError();
+    c.prof_sink = nullptr;
+    memcpy(c.launches, before, sizeof(before));
+    for (auto& r : recs) {
+      c.ev_pool.push_back(r.a);
+      c.ev_pool.push_back(r.b);
+    }
+    throw;
+  }
+  c.prof_sink = nullptr;
+  for (int k = 0; k < K_KIND_COUNT; k++) {
+    g.launches[k] = c.launches[k] - before[k];
+    c.launches[k] = before[k];
+  }
+  g.prof = std::move(recs);
+  const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK_CUDA(e);
+}
+
+// Layer li on x: eager, or with graphs on, replayed from the graph captured
+// for x's shape (first call of a shape eager, second captures). Replays
+// compute exactly what the eager schedule computes.
+Ct layer_run(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
+  if (!M.graphs) return layer_eval(M, li, keys, x);
+  Ctx& c = *M.ctx;
+  auto& slot = M.graph_cache[GraphKey(li, x.B, x.level, dbits(x.scale), &keys, c.prof)];
+  if (!slot) slot = std::make_unique<GraphEntry>();
+  GraphEntry& g = *slot;
+  if (g.uses++ == 0) {
+    uint64_t n0 = 0, n1 = 0;
+    for (int k = 0; k < K_KIND_COUNT; k++) n0 += c.launches[k];
+    Ct y = layer_eval(M, li, keys, x);
+    for (int k = 0; k < K_KIND_COUNT; k++) n1 += c.launches[k];
+    g.eager_launches = n1 - n0;
+    g.out = ct_alloc(c, y->B, y->level, y->scale);
+    return y;
+  }
+  if (!g.exec) capture_layer(M, li, keys, x, g);
+  {
+    Launch L_(c, K_COPY, 2.0 * (double)x.d.bytes);
+    CK_CUDA(cudaMemcpyAsync(g.in->d.p, x.d.p, x.d.bytes, cudaMemcpyDeviceToDevice, c.stream));
+  }
+  CK_CUDA(cudaGraphLaunch(g.exec, c.stream));
+  for (int k = 0; k < K_KIND_COUNT; k++) c.launches[k] += g.launches[k];
+  if (c.prof && !g.prof.empty()) {
+    CK_CUDA(cudaStreamSynchronize(c.stream));
+    for (const ProfRec& r : g.prof) {
+      float t = 0;
+      CK_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      c.prof_acc[r.kind][0] += t;
+      c.prof_acc[r.kind][1] += r.bytes;
+      c.prof_acc[r.kind][2] += r.ops;
+      c.prof_acc[r.kind][3] += 1;
+    }
+  }
+  Ct r = ct_alloc(c, g.out->B, g.out->level, g.out->scale);
+  Launch L_(c, K_COPY, 2.0 * (double)r->d.bytes);
+  CK_CUDA(cudaMemcpyAsync(r->d.p, g.out->d.p, r->d.bytes, cudaMemcpyDeviceToDevice, c.stream));
+  return r;
 }
 
 int cheb_depth(int d) {
@@ -442,7 +581,8 @@ int layer_depth(const Layer& L) {
     while ((2 << lg) <= 2 * n) lg++;
     dc += 1 + lg;
   }
-  const int spline = 3 + dc + std::max(L.k, 1);  // k = 0 masks its basis instead
+  // k = 0 masks its basis instead of a recursion step; naive adds the P matvec
+  const int spline = 3 + dc + std::max(L.k, 1) + (L.naive ? 1 : 0);
   const int silu = 2 + cheb_depth((int)L.cheb.size() - 1);
   return std::max(spline, silu);
 }
@@ -453,8 +593,11 @@ std::vector<int> layer_rotations(const Layer& L, int slots) {
   while ((1 << J) < L.G + 2 * L.k) J++;
   for (int j = 1; j <= J; j++) s.insert(-L.n_c * (1 << (j - 1)));
   s.insert(L.n_c);
-  for (int n : {L.n_c * (L.G + L.k), L.n_c}) {
-    Plan p = bsgs_plan(L.n_out, n, slots);
+  const int n_s = L.n_c * (L.G + L.k);
+  std::vector<std::pair<int, int>> shapes = {{L.n_out, n_s}, {L.n_out, L.n_c}};
+  if (L.naive) shapes.push_back({n_s, n_s});
+  for (auto sh : shapes) {
+    Plan p = bsgs_plan(sh.first, sh.second, slots);
     if (p.npad < slots) s.insert(-p.npad);
     for (int j = 1; j < p.g1; j++) s.insert(j);
     for (int i = 1; i < p.g2; i++) s.insert(p.g1 * i);
@@ -469,7 +612,7 @@ std::vector<int> layer_rotations(const Layer& L, int slots) {
 // internal entry points for the serving scheduler
 namespace ck {
 Ct kan_eval_layer(kan_model& M, int layer, const ckks_keys& keys, const ckks_ct& x) {
-  return layer_eval(M, layer, keys, x);
+  return layer_run(M, layer, keys, x);
 }
 int kan_num_layers(const kan_model& M) { return (int)M.layers.size(); }
 int kan_layer_chunks(const kan_model& M, int layer) { return M.layers[layer].K; }
@@ -531,8 +674,10 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
       // W_f[o][m n_c + i] = w_s[o][i] c[o][i][m]  (W' P, Algorithm 3 / Eq. 13)
       const int n_c = L.n_c;
       const int n_s = n_c * (int)nb;
+      L.naive = d.naive != 0;
       L.plan_b = bsgs_plan(d.n_out, n_c, S);
       L.plan_s = bsgs_plan(d.n_out, n_s, S);
+      if (L.naive) L.plan_p = bsgs_plan(n_s, n_s, S);
       for (int ch = 0; ch < L.K; ch++) {
         std::vector<double> Wb((size_t)d.n_out * n_c, 0.0), Wf((size_t)d.n_out * n_s, 0.0);
         for (int o = 0; o < d.n_out; o++)
@@ -540,8 +685,8 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
             const int gi = ch * n_c + i;
             if (gi >= d.n_in) continue;
             Wb[(size_t)o * n_c + i] = L.w_b[(size_t)o * d.n_in + gi];
-            for (size_t m = 0; m < nb; m++)
-              Wf[(size_t)o * n_s + m * n_c + i] =
+            for (size_t m = 0; m < nb; m++)  // W' is row-major in (i, m), W_f ColTile
+              Wf[(size_t)o * n_s + (L.naive ? i * nb + m : m * n_c + i)] =
                   L.w_s[(size_t)o * d.n_in + gi] * L.coef[((size_t)o * d.n_in + gi) * nb + m];
           }
         L.diag_b.push_back(diagonals(Wb, d.n_out, n_c, L.plan_b, S));
@@ -582,6 +727,18 @@ int kan_model_layer_depth(const kan_model* model, int layer, int* depth) {
   return CKKS_OK;
 }
 
+int kan_model_set_graphs(kan_model* model, int enabled) {
+  try {
+    if (!model) return CKKS_ERR_INVALID_ARG;
+    CK_CUDA(cudaStreamSynchronize(model->ctx->stream));
+    model->graphs = enabled != 0;
+    if (!model->graphs) model->graph_cache.clear();
+    return CKKS_OK;
+  } catch (...) {
+    return api_error();
+  }
+}
+
 int kan_model_layer_chunks(const kan_model* model, int layer, int* K, int* n_c) {
   if (!model || !K || !n_c || layer < 0 || layer >= (int)model->layers.size())
     return CKKS_ERR_INVALID_ARG;
@@ -595,7 +752,7 @@ int kan_layer_eval(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, int l
   try {
     if (!ctx || !keys || !model || !in || !out || layer < 0 || layer >= (int)model->layers.size())
       return CKKS_ERR_INVALID_ARG;
-    *out = layer_eval(*model, layer, *keys, *in).release();
+    *out = layer_run(*model, layer, *keys, *in).release();
     return CKKS_OK;
   } catch (...) {
     return api_error();
@@ -621,7 +778,7 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, const ckks
     }
     Ct h = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
     aligned.clear();
-    for (size_t li = 0; li < model->layers.size(); li++) h = layer_eval(*model, (int)li, *keys, *h);
+    for (size_t li = 0; li < model->layers.size(); li++) h = layer_run(*model, (int)li, *keys, *h);
     *out = h.release();
     return CKKS_OK;
   } catch (...) {

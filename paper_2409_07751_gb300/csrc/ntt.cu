@@ -52,6 +52,29 @@ __device__ __forceinline__ void gs_lazy(uint64_t& x, uint64_t& y, uint64_t w, ui
   x = s >= q2 ? s - q2 : s;
   y = shoup_lazy(u - v + q2, w, ws, q);
 }
+// Forward butterfly without the reduction of x, for moduli q < 2^44: both
+// outputs grow by less than 2q per stage, so 16 stages from inputs below 4q
+// stay below 36q < 2^50 (the Shoup product accepts any input below 2^64).
+__device__ __forceinline__ void ct_grow(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
+                                        uint64_t q, uint64_t q2) {
+  const uint64_t u = x;
+  const uint64_t t = shoup_lazy(y, w, ws, q);
+  x = u + t;
+  y = u - t + q2;
+}
+template <bool GROW>
+__device__ __forceinline__ void ct_step(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
+                                        uint64_t q, uint64_t q2) {
+  if (GROW)
+    ct_grow(x, y, w, ws, q, q2);
+  else
+    ct_lazy(x, y, w, ws, q, q2);
+}
+// x < 2^64 -> x mod q, with w1s = floor(2^64 / q) (Shoup's product by 1)
+__device__ __forceinline__ uint64_t reduce_full(uint64_t x, uint64_t q, uint64_t w1s) {
+  const uint64_t t = x - __umul64hi(x, w1s) * q;
+  return t >= q ? t - q : t;
+}
 __device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q, uint64_t q2) {
   x = x >= q2 ? x - q2 : x;
   return x >= q ? x - q : x;
@@ -170,7 +193,7 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
 // The same round on group g of two chunks at once (chunk and chunk + 1, in
 // shared memory at sm and sm + CHUNK): two independent dependency chains per
 // thread, interleaved by the compiler.
-template <bool INV>
+template <bool INV, bool GROW = false>
 __device__ __forceinline__ void round8x2(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
                                          int log_n, const ulonglong2* t8, uint64_t q,
                                          uint64_t q2) {
@@ -192,19 +215,19 @@ __device__ __forceinline__ void round8x2(uint64_t* sm, uint32_t g, uint32_t ls, 
 #pragma unroll
     for (int k = 0; k < 4; k++)
 #pragma unroll
-      for (int h = 0; h < 2; h++) ct_lazy(x[h][k], x[h][k + 4], tt[h][0].x, tt[h][0].y, q, q2);
+      for (int h = 0; h < 2; h++) ct_step<GROW>(x[h][k], x[h][k + 4], tt[h][0].x, tt[h][0].y, q, q2);
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-      ct_lazy(x[h][0], x[h][2], tt[h][1].x, tt[h][1].y, q, q2);
-      ct_lazy(x[h][1], x[h][3], tt[h][1].x, tt[h][1].y, q, q2);
-      ct_lazy(x[h][4], x[h][6], tt[h][2].x, tt[h][2].y, q, q2);
-      ct_lazy(x[h][5], x[h][7], tt[h][2].x, tt[h][2].y, q, q2);
+      ct_step<GROW>(x[h][0], x[h][2], tt[h][1].x, tt[h][1].y, q, q2);
+      ct_step<GROW>(x[h][1], x[h][3], tt[h][1].x, tt[h][1].y, q, q2);
+      ct_step<GROW>(x[h][4], x[h][6], tt[h][2].x, tt[h][2].y, q, q2);
+      ct_step<GROW>(x[h][5], x[h][7], tt[h][2].x, tt[h][2].y, q, q2);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++)
 #pragma unroll
       for (int h = 0; h < 2; h++)
-        ct_lazy(x[h][2 * k], x[h][2 * k + 1], tt[h][3 + k].x, tt[h][3 + k].y, q, q2);
+        ct_step<GROW>(x[h][2 * k], x[h][2 * k + 1], tt[h][3 + k].x, tt[h][3 + k].y, q, q2);
   } else {
 #pragma unroll
     for (int k = 0; k < 4; k++)
@@ -416,35 +439,17 @@ struct DescRescale {
   }
 };
 
-// Forward NTT of one row per cluster of CS CTAs (CS = N1/4, or 1 for N1 <= 4).
-// CTA `rank` owns chunks [rank*CPC, (rank+1)*CPC) of the row in shared memory.
-// Column phase: the CTA transforms columns [rank*CHUNK/CS, ...) from the
-// prologue loads and writes element s of each column into the shared memory
-// of the CTA owning chunk s (distributed shared memory). After a cluster
-// barrier each CTA runs the radix-8 rounds on its own chunks in place and
-// writes the results through the epilogue. The row never round-trips
-// through global memory.
-template <int N1, class D>
-__global__ void __launch_bounds__(ROW_THREADS, 1)
-    ntt_fwd_cl(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws,
-               const ulonglong2* tw8, size_t nodes) {
+// Column and chunk phases of the forward cluster NTT (see ntt_fwd_cl).
+template <int N1, class D, bool GROW>
+__device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ulonglong2* t8,
+                                         uint64_t q, const uint64_t* kc, const ulonglong2* ctw,
+                                         uint64_t* sm) {
   constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
   constexpr int CPC = N1 / CS;
-  extern __shared__ uint64_t sm[];  // CPC chunks
-  __shared__ uint64_t kc[2 * MAX_SRC];
-  __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
+  const uint64_t q2 = 2 * q;
+  const uint64_t w1s = GROW ? ~0ull / q : 0;  // floor(2^64 / q) for odd q
   const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
-  const uint32_t row = blockIdx.x / CS;
-  Row r;
-  r.n_src = 0;
-  if (!d.setup(row, r, kc, rank, CS)) return;  // same decision on every CTA of the cluster
-  const size_t N = (size_t)N1 * CHUNK;
-  const uint64_t q = mods[r.mi].q, q2 = 2 * q;
-  r.aux = q;
-  const ulonglong2* t8 = tw8 + (size_t)r.mi * nodes * 7;
   const uint32_t g = threadIdx.x;
-  if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)r.mi * N + g], tws[(size_t)r.mi * N + g]);
-  __syncthreads();
   uint64_t* own[CS];
   if constexpr (CS > 1) {
     cg::cluster_group cl = cg::this_cluster();
@@ -465,7 +470,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
       for (int i = 0; i < m; i++) {
         const ulonglong2 tv = ctw[m + i];
 #pragma unroll
-        for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
+        for (int jj = 0; jj < t1; jj++)
+          ct_step<GROW>(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
       }
     }
 #pragma unroll
@@ -481,12 +487,49 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint64_t* s = sm + lc * CHUNK;
 #pragma unroll
     for (int ls = 9; ls >= 0; ls -= 3) {
-      round8x2<false>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8x2<false, GROW>(s, g, ls, chunk, log_n, t8, q, q2);
       __syncthreads();
     }
-    for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS)
-      d.store(r, chunk * CHUNK + i, reduce4(s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))], q, q2), q, kc);
+    for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS) {
+      const uint64_t v = s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))];
+      d.store(r, chunk * CHUNK + i, GROW ? reduce_full(v, q, w1s) : reduce4(v, q, q2), q, kc);
+    }
   }
+}
+
+// Forward NTT of one row per cluster of CS CTAs (CS = N1/4, or 1 for N1 <= 4).
+// CTA `rank` owns chunks [rank*CPC, (rank+1)*CPC) of the row in shared memory.
+// Column phase: the CTA transforms columns [rank*CHUNK/CS, ...) from the
+// prologue loads and writes element s of each column into the shared memory
+// of the CTA owning chunk s (distributed shared memory). After a cluster
+// barrier each CTA runs the radix-8 rounds on its own chunks in place and
+// writes the results through the epilogue. The row never round-trips
+// through global memory.
+template <int N1, class D>
+__global__ void __launch_bounds__(ROW_THREADS, 1)
+    ntt_fwd_cl(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws,
+               const ulonglong2* tw8, size_t nodes) {
+  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  extern __shared__ uint64_t sm[];  // CPC = N1 / CS chunks
+  __shared__ uint64_t kc[2 * MAX_SRC];
+  __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
+  const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
+  const uint32_t row = blockIdx.x / CS;
+  Row r;
+  r.n_src = 0;
+  if (!d.setup(row, r, kc, rank, CS)) return;  // same decision on every CTA of the cluster
+  const size_t N = (size_t)N1 * CHUNK;
+  const uint64_t q = mods[r.mi].q;
+  r.aux = q;
+  const ulonglong2* t8 = tw8 + (size_t)r.mi * nodes * 7;
+  const uint32_t g = threadIdx.x;
+  if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)r.mi * N + g], tws[(size_t)r.mi * N + g]);
+  __syncthreads();
+  // every CTA of a cluster works on the same row, so the branch is uniform
+  if (q < (1ull << 44))
+    fwd_rows<N1, D, true>(d, r, log_n, t8, q, kc, ctw, sm);
+  else
+    fwd_rows<N1, D, false>(d, r, log_n, t8, q, kc, ctw, sm);
 }
 
 // Inverse NTT of pattern-selected rows, one row per cluster: each CTA loads
@@ -656,7 +699,9 @@ void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, 
   ntt_run<true>(c, base, n_rows, pattern, P, active);
 }
 
-bool ntt_fused_available(const Ctx& c) { return c.log_n > CHUNK_LOG && c.log_n <= CHUNK_LOG + 4; }
+bool ntt_fused_available(const Ctx& c) {
+  return c.fused && c.log_n > CHUNK_LOG && c.log_n <= CHUNK_LOG + 4;
+}
 
 void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
                       const uint64_t* post, const uint64_t* posts, size_t active) {

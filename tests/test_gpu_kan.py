@@ -101,6 +101,67 @@ def test_wide_first_layer_chunks_bit_exact(G):
     assert np.abs(dec - kan_plain.forward(m, X[:2], "poly", "poly")).max() < 1e-5
 
 
+def test_naive_permutation_method_bit_exact(G):
+    """The naive method (HE permutation of the basis by P, then W'), on a
+    network and on a chunked wide first layer, equals the oracle word for
+    word and is one level deeper per layer than lazy combination."""
+    model = W.make_model("t", widths=[40, 4, 2], G=3, k=2)
+    X = W.uniform_inputs(64, 40)
+    m = calibrate.calibrate(model, X, 7, [1])
+    naive = [dict(L, naive=True) for L in m]
+    gctx, octx, gm, gk, ok = _setup(G, 7, 19, 2, naive)
+    lazy = G.Model(gctx, m)
+    for li in range(2):
+        assert gm.layer_depth(li) == lazy.layer_depth(li) + 1
+    K, n_c = kan_he.chunking(m[0], octx.slots)
+    xp = np.pad(X[0], (0, K * n_c - 40))
+    rows = [xp[c * n_c:(c + 1) * n_c] for c in range(K)]
+    chunks = [O.encrypt(octx, ok, r, octx.L, W.SEED_ENC, c) for c, r in enumerate(rows)]
+    oo = kan_he.infer(octx, ok, chunks, naive)
+    gin = G.encrypt(gctx, gk, np.array(rows), octx.L, W.SEED_ENC, 0)
+    go = G.kan_infer(gctx, gk, gm, [gin])
+    assert (go.export()[0] == oo.data).all()
+    hef = kan_plain.forward(m, X[:1], "poly", "poly")
+    assert np.abs(G.decrypt(gctx, gk, go, 2) - hef).max() < 1e-5
+
+
+@pytest.mark.parametrize("log_n", [7, 13])
+def test_graph_replay_matches_eager(G, log_n):
+    """With graphs on, the first call of a shape runs eagerly, the second
+    captures, the third replays: every result equals the eager schedule's
+    word for word, and the replay counts the same kernel launches."""
+    model = W.make_model("kan_4_8_4_1")
+    X = W.uniform_inputs(256, 4)
+    m = calibrate.calibrate(model, X, 27, [3])
+    ctx = G.Context(log_n, 36, 4)
+    gm = G.Model(ctx, m)
+    keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+    x = G.encrypt(ctx, keys, X[:3], 36, W.SEED_ENC, 0)
+    ref = G.kan_infer(ctx, keys, gm, [x]).export()
+    c0 = ctx.launch_counts()
+    G.kan_infer(ctx, keys, gm, [x]).close()
+    c1 = ctx.launch_counts()
+    eager = {k: c1[k] - c0[k] for k in c1 if k != "copy"}
+    gm.set_graphs(True)
+    for prof in (False, True):  # a profiled capture records its events as graph nodes
+        ctx.profile(prof)
+        for call in range(3):
+            if call == 2:
+                ctx.profile_collect()  # keep the replay's records only
+            a = ctx.launch_counts()
+            out = G.kan_infer(ctx, keys, gm, [x])
+            b = ctx.launch_counts()
+            assert (out.export() == ref).all(), (prof, call)
+            assert {k: b[k] - a[k] for k in b if k != "copy"} == eager, (prof, call)
+        if prof:
+            p = ctx.profile_collect()
+            assert {k: v[2] for k, v in p.items() if k != "copy"} == {k: v for k, v in eager.items() if v}
+            assert all(v[0] > 0 for k, v in p.items())
+    ctx.profile(False)
+    gm.set_graphs(False)
+    assert (G.kan_infer(ctx, keys, gm, [x]).export() == ref).all()
+
+
 def test_level_exhausted_is_an_error(G):
     model = W.make_model("t", widths=[3, 2], G=3, k=2)
     m = calibrate.calibrate(model, W.uniform_inputs(64, 3), 7, [1])

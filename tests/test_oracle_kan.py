@@ -209,3 +209,46 @@ def test_he_kan_degenerate_grids_match_hef(he_small, G_, k_):
     dec = ckks.decrypt(ctx, keys, out, 2)
     hef = kan_plain.forward(m, X[:1], "poly", "poly")[0]
     assert np.abs(dec - hef).max() < 1e-5
+
+
+def test_he_naive_permutation_method_matches_hef(he_small):
+    """The naive method (HE permutation by P of Algorithm 3, then W') gives
+    the same network values as lazy combination, one level deeper."""
+    ctx = he_small
+    model = W.make_model("t", widths=[3, 4, 2], G=3, k=2)
+    X = W.uniform_inputs(100, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    naive = [dict(L, naive=True) for L in m]
+    keys = ckks.Keys(ctx, 1, rot_steps=kan_he.model_rotations(naive, ctx.slots))
+    c = ckks.encrypt(ctx, keys, X[0], ctx.L, 2, 0)
+    lazy = kan_he.layer_eval(ctx, keys, c, m[0])
+    out = kan_he.layer_eval(ctx, keys, c, naive[0])
+    assert out.level == lazy.level - 1
+    full = kan_he.infer(ctx, keys, c, naive)
+    hef = kan_plain.forward(m, X[:1], "poly", "poly")[0]
+    assert np.abs(ckks.decrypt(ctx, keys, full, 2) - hef).max() < 1e-5
+
+
+def test_permutation_bsgs_reorders_coltile_to_row_major():
+    """The naive method's P matvec on the BSGS diagonal algebra (plaintext
+    slots): ColTile order m n_i + i in, row-major i (g+k) + m out."""
+    S, n_i, nb = 256, 5, 6
+    n = n_i * nb
+    P = kan_he.permutation_matrix(n_i, nb)
+    plan = kan_he.bsgs_plan(n, n, S)
+    D = kan_he.diagonals(P, plan, S)
+    rng = np.random.default_rng(8)
+    B = rng.normal(size=(n_i, nb))  # B[i, m]
+    v = np.zeros(S)
+    v[:n] = B.T.reshape(-1)  # ColTile
+    v = v + np.roll(v, plan["npad"])  # replicate to [0, 2 npad)
+
+    def rot(a, t):
+        return np.roll(a, -t)
+
+    z = np.zeros(S)
+    for i in range(plan["g2"]):
+        inner = sum(np.roll(D[plan["g1"] * i + j], plan["g1"] * i) * rot(v, j) for j in range(plan["g1"]))
+        z += rot(inner, plan["g1"] * i)
+    assert np.allclose(z[:n], B.reshape(-1))
+    assert np.allclose(z[n:], 0.0)
