@@ -216,20 +216,27 @@ typedef struct {
 } kan_layer_desc;
 
 /* Host-only model preparation (no device work).
- * kan_silu_fit: Chebyshev coefficients cheb[0..degree] of the weighted
- * least-squares SiLU fit of Eq. 12 on [lo, hi] (n_samples evenly spaced
- * points, weight 10 within mu +- 3 sigma, 1 outside), solved by Householder QR.
+ * kan_silu_fit: Chebyshev coefficients cheb[0..degree] (basis of [lo, hi]
+ * mapped to [-1, 1]) of the SiLU fit on n_samples evenly spaced points of
+ * [lo, hi]: method KAN_FIT_WLS is Eq. 12 (weight 10 within mu +- 3 sigma, 1
+ * outside), KAN_FIT_OLS unit weights (both by Householder QR), KAN_FIT_REMEZ
+ * the minimax polynomial over the points by the Remez exchange.
  * kan_calibrate: for each layer (only n_in, n_out, G, k, grid, coef, w_s,
  * w_b of `layers` are read), the statistics of the layer's inputs over the
  * n calibration vectors X[n][n_in] under the exact FP64 KAN (Eqs. 1-5), the
  * SiLU range of Eq. 11 (or fixed_range[0..1] if not NULL) and its fit, and
  * the comparison bound R = 1.1 (max|x| + max|knot|) / 2 of Algorithm 2.
  * Outputs per layer: R[l], silu_lo[l], silu_hi[l], cheb[l*(degree+1) ..]. */
+enum {
+  KAN_FIT_WLS = 0,   /* Eq. 12: weight 10 within mu +- 3 sigma, 1 outside */
+  KAN_FIT_OLS = 1,   /* least squares, unit weights (Table 5 comparison) */
+  KAN_FIT_REMEZ = 2  /* minimax on [lo, hi] by the Remez exchange (Table 5) */
+};
 int kan_silu_fit(double lo, double hi, double mu, double sigma, int degree, int n_samples,
-                 double* cheb);
+                 int method, double* cheb);
 int kan_calibrate(const kan_layer_desc* layers, size_t n_layers, const double* X, size_t n,
-                  int silu_degree, const double* fixed_range, int n_fit_samples, double* R,
-                  double* silu_lo, double* silu_hi, double* cheb);
+                  int silu_degree, const double* fixed_range, int n_fit_samples, int fit_method,
+                  double* R, double* silu_lo, double* silu_hi, double* cheb);
 
 int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layers,
                      kan_model** out);

@@ -12,7 +12,7 @@ from .kan_plain import forward, knots
 from .silu_fit import fit_silu, layer_stats, silu_range
 
 
-def calibrate(model, X, silu_degree, comp, fixed_range=None, n_samples=10000):
+def calibrate(model, X, silu_degree, comp, fixed_range=None, n_samples=10000, method="wls"):
     _, acts = forward(model, X, collect=True)
     out = []
     for layer, a in zip(model, acts):
@@ -20,7 +20,7 @@ def calibrate(model, X, silu_degree, comp, fixed_range=None, n_samples=10000):
         lo, hi = fixed_range if fixed_range is not None else silu_range(mu, sigma, mn, mx)
         L = dict(layer)
         L["silu_lo"], L["silu_hi"] = float(lo), float(hi)
-        L["silu_cheb"] = fit_silu(lo, hi, mu, sigma, silu_degree, n_samples)
+        L["silu_cheb"] = fit_silu(lo, hi, mu, sigma, silu_degree, n_samples, method)
         L["silu_stats"] = (mu, sigma, mn, mx)
         t = knots(layer)
         L["R"] = 1.1 * (np.abs(a).max() + np.abs(t).max()) / 2.0

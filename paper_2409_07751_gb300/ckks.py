@@ -69,8 +69,9 @@ SIGNATURES = {
     "ckks_level_down": (c_i32, [c_vp, c_vp, c_i32, PP]),
     "ckks_rotate": (c_i32, [c_vp, c_vp, c_vp, ctypes.c_int32, PP]),
     "ckks_rotate_hoisted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
-    "kan_silu_fit": (c_i32, [c_dbl, c_dbl, c_dbl, c_dbl, c_i32, c_i32, c_vp]),
-    "kan_calibrate": (c_i32, [c_vp, c_sz, c_vp, c_sz, c_i32, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "kan_silu_fit": (c_i32, [c_dbl, c_dbl, c_dbl, c_dbl, c_i32, c_i32, c_i32, c_vp]),
+    "kan_calibrate": (c_i32, [c_vp, c_sz, c_vp, c_sz, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp,
+                              c_vp]),
     "kan_model_create": (c_i32, [c_vp, c_vp, c_sz, PP]),
     "kan_model_destroy": (c_i32, [c_vp]),
     "kan_model_rotations": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
@@ -360,13 +361,16 @@ def _descs(layers, keep):
     return descs
 
 
-def silu_fit(lo, hi, mu, sigma, degree, n_samples=10000):
+FIT_METHODS = {"wls": 0, "ols": 1, "remez": 2}
+
+
+def silu_fit(lo, hi, mu, sigma, degree, n_samples=10000, method="wls"):
     out = np.zeros(degree + 1)
-    check(lib().kan_silu_fit(lo, hi, mu, sigma, degree, n_samples, _p(out)))
+    check(lib().kan_silu_fit(lo, hi, mu, sigma, degree, n_samples, FIT_METHODS[method], _p(out)))
     return out
 
 
-def calibrate(layers, X, silu_degree, comp, fixed_range=None, n_fit_samples=10000):
+def calibrate(layers, X, silu_degree, comp, fixed_range=None, n_fit_samples=10000, method="wls"):
     """Per-layer R, SiLU range and fit (Eqs. 11-12) computed by the library;
     returns copies of the layer dicts with the HE keys filled in."""
     keep = []
@@ -377,7 +381,7 @@ def calibrate(layers, X, silu_degree, comp, fixed_range=None, n_fit_samples=1000
     cheb = np.zeros((n, silu_degree + 1))
     fr = None if fixed_range is None else np.ascontiguousarray(fixed_range, dtype=np.float64)
     check(lib().kan_calibrate(descs, n, _p(X), X.shape[0], silu_degree, _p(fr), n_fit_samples,
-                              _p(R), _p(lo), _p(hi), _p(cheb)))
+                              FIT_METHODS[method], _p(R), _p(lo), _p(hi), _p(cheb)))
     out = []
     for i, L in enumerate(layers):
         L = dict(L)

@@ -2,7 +2,9 @@
 // paper (Eq. 11: range [max(mu - 5 sigma, x_min), min(mu + 5 sigma, x_max)]
 // from the layer's input statistics under the plaintext KAN; Eq. 12:
 // weighted least squares with weight 10 inside mu +- 3 sigma and 1 outside)
-// and the comparison bound R of Algorithm 2.
+// and the comparison bound R of Algorithm 2. The SiLU fits the paper compares
+// against (Table 5) on the same range and degree: OLS (unit weights) and the
+// minimax polynomial by the Remez exchange.
 //
 // Readings: samples are n evenly spaced points including both ends; the
 // polynomial is in the Chebyshev basis of the range mapped to [-1, 1]; the
@@ -95,19 +97,114 @@ std::vector<double> lstsq_qr(std::vector<double> A, std::vector<double> r, int m
   return a;
 }
 
+// sum_j c_j T_j(y) by Clenshaw's recurrence
+double cheb_val(const std::vector<double>& c, double y) {
+  double b1 = 0, b2 = 0;
+  for (int j = (int)c.size() - 1; j >= 1; j--) {
+    const double b = 2.0 * y * b1 - b2 + c[j];
+    b2 = b1;
+    b1 = b;
+  }
+  return y * b1 - b2 + c[0];
+}
+
+// Minimax Chebyshev coefficients of silu on [lo, hi] (mapped to [-1, 1]) by
+// the Remez exchange over the n_samples grid: a reference of d + 2 points,
+// first the Chebyshev extrema; solve p(y_i) + (-1)^i E = f(y_i); move the
+// reference to the alternating extrema of the error (one per run of equal
+// sign, the smaller end run dropped while there are more than d + 2); stop
+// when the reference repeats.
+std::vector<double> remez_fit(double lo, double hi, int d, int n_samples) {
+  const int n = d + 2;
+  auto fx = [&](double y) { return silu(0.5 * (hi - lo) * y + 0.5 * (hi + lo)); };
+  std::vector<double> grid(n_samples);
+  for (int s = 0; s < n_samples; s++) {
+    const double x = lo + (hi - lo) * (double)s / (double)(n_samples - 1);
+    grid[s] = (2.0 * x - (lo + hi)) / (hi - lo);
+  }
+  std::vector<double> ref(n), c(d + 1, 0.0);
+  for (int i = 0; i < n; i++) ref[i] = -cos(M_PI * i / (n - 1));
+  std::vector<int> prev;
+  for (int it = 0; it < 60; it++) {
+    std::vector<double> A((size_t)n * n), r(n);
+    for (int i = 0; i < n; i++) {
+      double t0 = 1.0, t1 = ref[i];
+      for (int j = 0; j <= d; j++) {
+        double tj;
+        if (j == 0) tj = 1.0;
+        else if (j == 1) tj = ref[i];
+        else {
+          tj = 2.0 * ref[i] * t1 - t0;
+          t0 = t1;
+          t1 = tj;
+        }
+        A[(size_t)i * n + j] = tj;
+      }
+      A[(size_t)i * n + d + 1] = (i & 1) ? -1.0 : 1.0;
+      r[i] = fx(ref[i]);
+    }
+    const std::vector<double> sol = lstsq_qr(A, r, n, n);
+    c.assign(sol.begin(), sol.begin() + d + 1);
+    // runs of equal error sign and their extremum
+    std::vector<std::pair<int, double>> runs;
+    int st = 0;
+    double prev_sign = 0;
+    std::vector<double> e(n_samples);
+    for (int s = 0; s < n_samples; s++) e[s] = fx(grid[s]) - cheb_val(c, grid[s]);
+    for (int s = 0; s <= n_samples; s++) {
+      double sg = 0;
+      if (s < n_samples) {
+        sg = e[s] > 0 ? 1.0 : (e[s] < 0 ? -1.0 : 0.0);
+        if (sg == 0) sg = prev_sign;
+      }
+      if (s == 0) {
+        prev_sign = sg;
+        continue;
+      }
+      if (s == n_samples || sg != prev_sign) {
+        int best = st;
+        for (int k = st; k < s; k++)
+          if (fabs(e[k]) > fabs(e[best])) best = k;
+        runs.push_back({best, fabs(e[best])});
+        st = s;
+      }
+      prev_sign = sg;
+    }
+    if ((int)runs.size() < n) break;
+    while ((int)runs.size() > n) {
+      if (runs.front().second < runs.back().second)
+        runs.erase(runs.begin());
+      else
+        runs.pop_back();
+    }
+    std::vector<int> idx;
+    for (auto& rr : runs) idx.push_back(rr.first);
+    if (idx == prev) break;
+    prev = idx;
+    for (int i = 0; i < n; i++) ref[i] = grid[idx[i]];
+  }
+  return c;
+}
+
 }  // namespace
 
 extern "C" {
 
 int kan_silu_fit(double lo, double hi, double mu, double sigma, int degree, int n_samples,
-                 double* cheb) {
-  if (!(hi > lo) || degree < 1 || n_samples <= degree || !cheb) return CKKS_ERR_INVALID_ARG;
+                 int method, double* cheb) {
+  if (!(hi > lo) || degree < 1 || n_samples <= degree + 1 || !cheb || method < 0 || method > 2)
+    return CKKS_ERR_INVALID_ARG;
   const int n = degree + 1;
+  if (method == KAN_FIT_REMEZ) {
+    const std::vector<double> c = remez_fit(lo, hi, degree, n_samples);
+    for (int j = 0; j < n; j++) cheb[j] = c[j];
+    return CKKS_OK;
+  }
   std::vector<double> A((size_t)n_samples * n), r(n_samples);
   for (int s = 0; s < n_samples; s++) {
     const double x = lo + (hi - lo) * (double)s / (double)(n_samples - 1);
     const double y = (2.0 * x - (lo + hi)) / (hi - lo);
-    const double sw = sqrt(fabs(x - mu) <= 3.0 * sigma ? 10.0 : 1.0);
+    const double sw = method == KAN_FIT_OLS ? 1.0 : sqrt(fabs(x - mu) <= 3.0 * sigma ? 10.0 : 1.0);
     double t0 = 1.0, t1 = y;
     for (int j = 0; j < n; j++) {
       double tj;
@@ -128,8 +225,8 @@ int kan_silu_fit(double lo, double hi, double mu, double sigma, int degree, int 
 }
 
 int kan_calibrate(const kan_layer_desc* layers, size_t n_layers, const double* X, size_t n,
-                  int silu_degree, const double* fixed_range, int n_fit_samples, double* R,
-                  double* silu_lo, double* silu_hi, double* cheb) {
+                  int silu_degree, const double* fixed_range, int n_fit_samples, int fit_method,
+                  double* R, double* silu_lo, double* silu_hi, double* cheb) {
   if (!layers || !X || n == 0 || !R || !silu_lo || !silu_hi || !cheb) return CKKS_ERR_INVALID_ARG;
   std::vector<double> h(X, X + n * layers[0].n_in), y;
   for (size_t li = 0; li < n_layers; li++) {
@@ -155,7 +252,7 @@ int kan_calibrate(const kan_layer_desc* layers, size_t n_layers, const double* X
     }
     silu_lo[li] = lo;
     silu_hi[li] = hi;
-    const int rc = kan_silu_fit(lo, hi, mu, sigma, silu_degree, n_fit_samples,
+    const int rc = kan_silu_fit(lo, hi, mu, sigma, silu_degree, n_fit_samples, fit_method,
                                 cheb + li * (size_t)(silu_degree + 1));
     if (rc != CKKS_OK) return rc;
     double tmax = 0;

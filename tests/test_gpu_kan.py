@@ -125,7 +125,7 @@ def test_naive_permutation_method_bit_exact(G):
     assert np.abs(G.decrypt(gctx, gk, go, 2) - hef).max() < 1e-5
 
 
-@pytest.mark.parametrize("log_n", [7, 13])
+@pytest.mark.parametrize("log_n", [8, 13])
 def test_graph_replay_matches_eager(G, log_n):
     """With graphs on, the first call of a shape runs eagerly, the second
     captures, the third replays: every result equals the eager schedule's

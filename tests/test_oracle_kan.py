@@ -252,3 +252,29 @@ def test_permutation_bsgs_reorders_coltile_to_row_major():
         z += rot(inner, plan["g1"] * i)
     assert np.allclose(z[:n], B.reshape(-1))
     assert np.allclose(z[n:], 0.0)
+
+
+def test_remez_closed_forms_and_equioscillation():
+    """Remez pins: the minimax cubic of x^4 on [-1, 1] is x^4 - T_4/8 and the
+    minimax quadratic of |x| is x^2 + 1/8 (Chebyshev alternation); the SiLU
+    minimax error equioscillates at d + 2 points."""
+    c = silu_fit.fit_silu(-1, 1, 0, 1, 3, 20001, "remez", f=lambda x: x ** 4)
+    assert np.abs(c - [3 / 8, 0, 1 / 2, 0]).max() < 1e-9
+    c = silu_fit.fit_silu(-1, 1, 0, 1, 2, 20001, "remez", f=np.abs)
+    assert np.abs(c - [5 / 8, 0, 1 / 2]).max() < 1e-6
+    lo, hi, d = -12.4, 14.74, 10
+    c = silu_fit.fit_silu(lo, hi, 0, 1, d, 10000, "remez")
+    x = np.linspace(lo, hi, 10000)
+    e = kan_plain.silu(x) - np.polynomial.chebyshev.chebval((2 * x - (lo + hi)) / (hi - lo), c)
+    ext = [a + int(np.argmax(np.abs(e[a:b]))) for a, b in silu_fit._runs(e)]
+    assert len(ext) >= d + 2
+    mags = np.abs(e[ext])
+    assert mags.max() - np.sort(mags)[-(d + 2)] < 1e-6 * mags.max()
+
+
+def test_ols_matches_numpy_chebfit():
+    lo, hi = -9.77, 11.01
+    a = silu_fit.fit_silu(lo, hi, 0.0, 1.0, 10, 3000, "ols")
+    x = np.linspace(lo, hi, 3000)
+    ref = np.polynomial.chebyshev.chebfit((2 * x - (lo + hi)) / (hi - lo), kan_plain.silu(x), 10)
+    assert np.abs(a - ref).max() < 1e-9
