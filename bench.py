@@ -60,8 +60,12 @@ def args_():
     p.add_argument("--rows", type=int, default=592, help="limbs per launch for --kernel")
     p.add_argument("--serve", action="store_true",
                    help="Poisson serving mix through the continuous-batching server")
-    p.add_argument("--no-graphs", action="store_true",
-                   help="run the layer schedules eagerly instead of replaying CUDA graphs")
+    p.add_argument("--graphs", action="store_true",
+                   help="time CUDA-graph replays of the layer schedules instead of eager launches")
+    p.add_argument("--alpha", type=int, default=0,
+                   help="key-switching digit size (special primes); 0 = autotune within --max-qp-bits")
+    p.add_argument("--max-qp-bits", type=int, default=1740,
+                   help="bound on log2(QP) for the digit-layout autotuner (128-bit budget)")
     p.add_argument("--table3", action="store_true",
                    help="one KAN layer per (n_i, g, k) shape: lazy combination vs the naive method")
     p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
@@ -260,7 +264,9 @@ def config(a):
             "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": 27, "comparison": "f_3",
             "input_levels": "uniform over [L - slack, L]", "parallelism": "replicas (request sharding)",
             "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)",
-            "schedule": "eager" if getattr(a, "no_graphs", False) else "CUDA graph per layer"}
+            "schedule": "CUDA graph per layer" if getattr(a, "graphs", False) else "eager",
+            "alpha": getattr(a, "alpha", 4), "p_bits": getattr(a, "p_bits", 60),
+            "log_qp": 60 + 40 * a.levels + getattr(a, "alpha", 4) * getattr(a, "p_bits", 60)}
 
 
 def shard_plan(rank, batch):
@@ -352,7 +358,7 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
     class _Stop(Exception):
         pass
 
-    real_ks, real_modup = O._ks, O._modup
+    real_ks, real_ksr, real_modup = O._ks, O._ks_rescale, O._modup
 
     # total key switches of one inference (same schedule, small ring, no arithmetic)
     counter = {"n": 0}
@@ -360,6 +366,10 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
     def count_ks(ctx, ext, level, key, g):
         counter["n"] += 1
         return np.zeros((2, level + 1, ctx.N), np.uint64)
+
+    def count_ksr(ctx, d, ext, level, key):
+        counter["n"] += 1
+        return np.zeros((2, level, ctx.N), np.uint64)
 
     def skip_modup(ctx, poly, level):
         return None
@@ -373,14 +383,14 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
     fk.relin = None
     fk.galois = {small.galois(t): None for t in kan_he.model_rotations(model_he, small.slots)}
     x = O.Ct(np.zeros((2, a.levels + 1, small.N), np.uint64), a.levels, small.delta[a.levels])
-    O._ks, O._modup = count_ks, skip_modup
+    O._ks, O._ks_rescale, O._modup = count_ks, count_ksr, skip_modup
     try:
         kan_he.infer(small, fk, x, model_he)
     finally:
-        O._ks, O._modup = real_ks, real_modup
+        O._ks, O._ks_rescale, O._modup = real_ks, real_ksr, real_modup
     total = counter["n"]
 
-    ctx = O.Ctx(O.Params(a.log_n, a.levels, 4))
+    ctx = O.Ctx(O.Params(a.log_n, a.levels, getattr(a, "alpha", 0) or 4, p_bits=getattr(a, "p_bits", 60)))
     Z = np.zeros((ctx.beta_max, 2, ctx.n_qp, ctx.N), np.uint64)
     keys = Fake()
     keys.relin = Z
@@ -394,20 +404,28 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
         done = {"n": 0}
         t0 = time.perf_counter()
 
-        def timed_ks(ctx_, ext, level, key, g):
-            r = real_ks(ctx_, ext, level, key, g)
+        def tick():
             done["n"] += 1
             if time.perf_counter() - t0 > budget_s:
                 raise _Stop()
+
+        def timed_ks(ctx_, ext, level, key, g):
+            r = real_ks(ctx_, ext, level, key, g)
+            tick()
             return r
 
-        O._ks = timed_ks
+        def timed_ksr(ctx_, d, ext, level, key):
+            r = real_ksr(ctx_, d, ext, level, key)
+            tick()
+            return r
+
+        O._ks, O._ks_rescale = timed_ks, timed_ksr
         try:
             kan_he.infer(ctx, keys, ct, model_he)
         except _Stop:
             pass
         finally:
-            O._ks = real_ks
+            O._ks, O._ks_rescale = real_ks, real_ksr
         el = time.perf_counter() - t0
         if it >= warmup:
             rates.append((done["n"] / total) / el)
@@ -471,12 +489,16 @@ def main():
     # a dedicated (non-default) stream shared by the library and the timing events
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = G.Context(a.log_n, a.levels, 4, device=local)
+    a.p_bits, tuned = 60, None
+    if a.alpha == 0:
+        a.alpha, a.p_bits, tuned = G.autotune_keyswitch(a.log_n, a.levels, a.max_qp_bits, batch=8,
+                                                        device=local)
+    ctx = G.Context(a.log_n, a.levels, a.alpha, p_bits=a.p_bits, device=local)
     ctx.set_stream(stream.cuda_stream)
     model, Xcal, X = model_and_inputs(a, rank)
     m = G.calibrate(model, Xcal, 27, [3])
     gm = G.Model(ctx, m)
-    gm.set_graphs(not a.no_graphs)
+    gm.set_graphs(a.graphs)
     depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
     slack = a.levels - depth
     plan = shard_plan(rank, a.batch)
@@ -550,7 +572,8 @@ def main():
         roofline = dict({"kernel": dom, "bound": "hbm", "traffic": None}, **hbm)
     roofline.update({"algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
                      "share_of_kernel_time": ms / total_ms,
-                     "kernel_ms_per_step": total_ms / a.steps})
+                     "kernel_ms_per_step": total_ms / a.steps,
+                     "copy_ms_per_step": prof.get("copy", (0.0,))[0] / a.steps})
     shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])}
 
     def timed(fn, reps):
@@ -579,9 +602,24 @@ def main():
             s = timed(lambda: G.kan_infer(ctx, keys, gm, [one]), 2)
             plain["fused" if fused else "unfused"] = {"value": 1.0 / s, "unit": UNIT, "batch": 1}
         ctx.set_fusion(True)
-        gm.set_graphs(not a.no_graphs)
+        plain["fused_graphs"] = None
+        gm.set_graphs(True)
+        s = timed(lambda: G.kan_infer(ctx, keys, gm, [one]), 3)  # eager, capture, replays
+        s = timed(lambda: G.kan_infer(ctx, keys, gm, [one]), 3)
+        plain["fused_graphs"] = {"value": 1.0 / s, "unit": UNIT, "batch": 1}
+        gm.set_graphs(a.graphs)
         one.close()
         plain["batched_over_plain"] = value / world / plain["unfused"]["value"]
+
+    # ---------------- the same batch replayed from CUDA graphs (no profiling)
+    graph_replay = None
+    if not a.no_micro and not a.graphs:
+        gm.set_graphs(True)
+        step()  # eager run of each layer shape
+        step()  # capture
+        s = timed(lambda: G.kan_infer(ctx, keys, gm, cts), 2)
+        graph_replay = {"value": world * a.batch / s, "unit": UNIT, "batch": a.batch}
+        gm.set_graphs(False)
 
     # ---------------- micro: HMult / HRot per second at N=2^16, l in {37, 19, 2}
     micro = None
@@ -645,7 +683,8 @@ def main():
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": float(np.percentile(step_ms, 99)), "per": "batch of %d" % a.batch},
             "roofline": roofline, "kernel_time_shares": shares, "gpu_launches": launches,
-            "clocks": clocks, "e2e": e2e, "plain_form": plain, "micro": micro, "depth": depth,
+            "clocks": clocks, "e2e": e2e, "plain_form": plain, "graph_replay": graph_replay,
+            "keyswitch_autotune_ms": tuned, "micro": micro, "depth": depth,
             "slack": slack}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import calibrate as OC

@@ -65,6 +65,20 @@ const char* ckks_last_error(void);
 int ckks_context_create(int log_n, int q0_bits, int scale_bits, int n_scale, int p_bits,
                         int n_special, int device, ckks_ctx** out);
 int ckks_context_destroy(ckks_ctx* ctx);
+/* Hybrid key-switching digit layout by measurement (no counterpart in the
+ * paper, which delegates key switching to SEAL). For the chain q0_bits +
+ * n_scale x scale_bits and a bound max_qp_bits on log2(QP) (the security
+ * budget), every alpha in {1, 2, 3, 4, 5, 6, 8, 10, 12} takes special primes
+ * of p_bits = min(60, floor((max_qp_bits - log2 Q) / alpha)) bits and is kept
+ * if p_bits >= 30 and alpha p_bits >= q0_bits + (alpha - 1) scale_bits (P
+ * covers the largest digit). Each kept layout builds a context on `device`,
+ * and times 3 x (HMult + HRot) of `batch` ciphertexts at the top level.
+ * Out: the fastest alpha and its p_bits; tried[i], ms[i] (ms per HMult+HRot)
+ * for the first `cap` layouts timed; *n_tried their count (all may be NULL
+ * but alpha and p_bits). UNSUPPORTED if no layout fits. */
+int ckks_autotune_keyswitch(int log_n, int q0_bits, int scale_bits, int n_scale, int max_qp_bits,
+                            int batch, int device, int* alpha, int* p_bits, int* tried,
+                            double* ms, int cap, int* n_tried);
 /* moduli: n_qp = n_scale + 1 + n_special words (q_0..q_L, p_0..); delta: n_scale + 1
  * canonical scales; either may be NULL. */
 int ckks_context_info(const ckks_ctx* ctx, uint64_t* moduli, double* delta, int* n_qp);

@@ -73,6 +73,7 @@ def lib():
         "or_rescale": (None, [vp, vp, i32, i32, vp]),
         "or_modup": (None, [vp, vp, i32, vp]),
         "or_keyswitch_ext": (None, [vp, vp, i32, vp, u64, vp]),
+        "or_relin_rescale": (None, [vp, vp, vp, i32, vp, vp]),
         "or_ext_rows": (u64, [vp, i32]),
         "or_galois_elt": (u64, [vp, i64]),
     }

@@ -11,6 +11,11 @@ Delta_{l-1} = Delta_l^2 / q_l. Products of two level-l ciphertexts rescale
 onto Delta_{l-1}; plaintext operands are encoded at the scale that lands the
 rescaled product on the canonical scale; moving a ciphertext to a lower level
 multiplies it by an integer constant and rescales.
+
+HMult (a reading; the paper delegates key switching to SEAL): the
+relinearisation's ModDown by P and the rescale by q_level are one division
+by P q_level with a fast basis conversion of the dropped limbs, so each
+product pays one set of forward transforms for both.
 """
 import numpy as np
 
@@ -297,16 +302,39 @@ def mul_relin(ctx, keys, a, b):
     return relinearise(ctx, keys, tensor(ctx, a, b), a.level, a.scale * b.scale)
 
 
+def _ks_rescale(ctx, d, ext, level, key):
+    """Key inner product of d2's ModUp, then (d0, d1) + KS(d2) divided by
+    P q_level in one basis conversion (relinearise and rescale together)."""
+    out = np.zeros((2, level, ctx.N), np.uint64)
+    ctx.L_.or_relin_rescale(ctx.h, ptr(np.ascontiguousarray(d[:2])), ptr(ext), level, ptr(key),
+                            ptr(out))
+    return out
+
+
+def relin_rescale(ctx, keys, d, level, scale):
+    """(d0, d1, d2) at `level` -> relinearised and rescaled to level - 1."""
+    if level < 1:
+        raise ValueError("level exhausted")
+    ext = _modup(ctx, d[2], level)
+    out = _ks_rescale(ctx, d, ext, level, keys.relin)
+    s = scale / ctx.q[level]
+    dl = ctx.delta[level - 1]
+    if abs(s / dl - 1.0) < SNAP:
+        s = dl
+    return Ct(out, level - 1, s)
+
+
 def mul(ctx, keys, a, b):
-    """Eq. 8: align both to the lower level, multiply, relinearise, rescale."""
+    """Eq. 8: align both to the lower level, multiply, relinearise and
+    rescale (one division by P q_level)."""
     lv = min(a.level, b.level)
     a = level_down(ctx, a, lv)
     b = level_down(ctx, b, lv)
-    return rescale(ctx, mul_relin(ctx, keys, a, b))
+    return relin_rescale(ctx, keys, tensor(ctx, a, b), lv, a.scale * b.scale)
 
 
 def mul_sum(ctx, keys, pairs):
-    """sum_k a_k (x) b_k with a single relinearisation, then rescale."""
+    """sum_k a_k (x) b_k with a single relinearisation and rescale."""
     lv = min(min(a.level, b.level) for a, b in pairs)
     acc = None
     scale = None
@@ -320,7 +348,7 @@ def mul_sum(ctx, keys, pairs):
             o = np.zeros_like(acc)
             ctx.L_.or_add(ctx.h, ptr(acc), ptr(d), 3, lv + 1, 0, ptr(o))
             acc = o
-    return rescale(ctx, relinearise(ctx, keys, acc, lv, scale))
+    return relin_rescale(ctx, keys, acc, lv, scale)
 
 
 def rotate_many(ctx, keys, a, steps):

@@ -852,19 +852,12 @@ void or_modup(const or_ctx* c, const uint64_t* d, int level, uint64_t* ext) {
   free(v);
 }
 
-/*
- * Key inner product + ModDown:
- *   acc_k[t] = sum_j ext[j][t] * key[j][k][t]   (k = 0,1; over QP_l)
- *   out_k[i] = (acc_k[i] - Conv_{P->Q}([acc_k]_P)_i) * P^{-1} mod q_i,
- *   Conv_{P->Q}(y)_i = sum_k [y_k * Phat_k^{-1}]_{p_k} * (Phat_k mod q_i).
- * `ext` rows follow or_modup; if g != 0 every ext row is first mapped by the
- * NTT-domain automorphism X -> X^g (hoisted rotation: automorphism after
- * ModUp). out: [2][l][N].
- */
-void or_keyswitch_ext(const or_ctx* c, const uint64_t* ext_in, int level, const uint64_t* key,
-                      uint64_t g, uint64_t* out) {
+/* acc_k[t] = sum_j ext[j][t] * key[j][k][t] over QP_l (k = 0, 1); ext rows
+ * follow or_modup, mapped first by X -> X^g when g != 0. acc: [2][rows][N] */
+static uint64_t* key_product(const or_ctx* c, const uint64_t* ext_in, int level,
+                             const uint64_t* key, uint64_t g) {
   const uint64_t N = c->N;
-  const int l = level + 1, rows = l + c->alpha, A = c->alpha;
+  const int l = level + 1, rows = l + c->alpha;
   const int beta = (l + c->alpha - 1) / c->alpha;
   uint64_t* ext = malloc((uint64_t)beta * rows * N * sizeof(uint64_t));
   if (g != 0)
@@ -883,9 +876,119 @@ void or_keyswitch_ext(const or_ctx* c, const uint64_t* ext_in, int level, const 
         for (uint64_t n = 0; n < N; n++) a[n] = addmod(a[n], mulmod(e[n], kk[n], m), m);
       }
     }
+  free(ext);
+  return acc;
+}
+
+/*
+ * Relinearisation and rescale as one division (HMult, Eq. 8). With d0, d1
+ * of the tensor product at level l (NTT form, [2][l+1][N]) and the key
+ * inner product acc_k over QP_l of d2's ModUp (relinearisation key), per k:
+ *   y = P d_k + acc_k over QP_l (on the special primes y = acc_k),
+ *   M = P q_l, D = {q_l, p_0 .. p_{alpha-1}} (the limbs dropped),
+ *   out_k[i] = (y_i - Conv_{D->Q}([y]_D)_i) * M^{-1} mod q_i, i < l,
+ *   Conv_{D->Q}(y)_i = sum_{m in D} v_m ((M/m) mod q_i) - u (M mod q_i),
+ *   v_m = [y_m (M/m)^{-1}]_m, u = floor(sum_m v_m / m + 1/2) in double
+ * precision (m in the order q_l, p_0, ..): the conversion of the centred
+ * representative of [y]_M, so out = y / M rounded to nearest. out: [2][l][N].
+ * This replaces ModDown by P followed by rescaling by q_l; the result
+ * differs from that sequence only in the rounding of the division.
+ */
+void or_relin_rescale(const or_ctx* c, const uint64_t* d01, const uint64_t* ext_in, int level,
+                      const uint64_t* key, uint64_t* out) {
+  const uint64_t N = c->N;
+  const int l = level + 1, rows = l + c->alpha, A = c->alpha;
+  uint64_t* acc = key_product(c, ext_in, level, key, 0);
+  /* the dropped moduli: D[0] = q_level, D[1 + a] = p_a */
+  uint64_t* Dm = malloc((uint64_t)(A + 1) * sizeof(uint64_t));
+  int* Dt = malloc((uint64_t)(A + 1) * sizeof(int));
+  Dt[0] = level;
+  for (int a = 0; a < A; a++) Dt[1 + a] = pidx(c, a);
+  for (int m = 0; m <= A; m++) Dm[m] = c->mod[Dt[m]];
+  uint64_t* y = malloc((uint64_t)(A + 1) * N * sizeof(uint64_t));
+  uint64_t* conv = malloc(N * sizeof(uint64_t));
+  uint64_t* uo = malloc(N * sizeof(uint64_t));
+  for (int k = 0; k < 2; k++) {
+    for (int m = 0; m <= A; m++) {
+      const uint64_t qm = Dm[m];
+      uint64_t* ym = y + (uint64_t)m * N;
+      const uint64_t* am = acc + ((uint64_t)k * rows + (m == 0 ? level : l + m - 1)) * N;
+      if (m == 0) { /* y = P d_k + acc_k on q_level */
+        uint64_t P = 1;
+        for (int a = 0; a < A; a++) P = mulmod(P, c->mod[pidx(c, a)] % qm, qm);
+        const uint64_t* dk = d01 + ((uint64_t)k * l + level) * N;
+        for (uint64_t n = 0; n < N; n++) ym[n] = addmod(mulmod(P, dk[n], qm), am[n], qm);
+      } else {
+        memcpy(ym, am, N * sizeof(uint64_t));
+      }
+      or_ntt_inverse(ym, c->log_n, qm, c->psi[Dt[m]]);
+      uint64_t h = 1; /* (M / D[m]) mod D[m] */
+      for (int o = 0; o <= A; o++)
+        if (o != m) h = mulmod(h, Dm[o] % qm, qm);
+      const uint64_t hi = invmod(h, qm);
+      for (uint64_t n = 0; n < N; n++) ym[n] = mulmod(ym[n], hi, qm);
+    }
+    for (uint64_t n = 0; n < N; n++) {
+      double sf = 0.0;
+      for (int m = 0; m <= A; m++) sf += (double)y[(uint64_t)m * N + n] * (1.0 / (double)Dm[m]);
+      uo[n] = (uint64_t)floor(sf + 0.5);
+    }
+    for (int i = 0; i < level; i++) {
+      const uint64_t q = c->mod[i];
+      uint64_t M = 1, P = 1;
+      for (int m = 0; m <= A; m++) M = mulmod(M, Dm[m] % q, q);
+      for (int a = 0; a < A; a++) P = mulmod(P, c->mod[pidx(c, a)] % q, q);
+      for (uint64_t n = 0; n < N; n++) {
+        uint64_t s = 0;
+        for (int m = 0; m <= A; m++) {
+          uint64_t h = 1;
+          for (int o = 0; o <= A; o++)
+            if (o != m) h = mulmod(h, Dm[o] % q, q);
+          s = addmod(s, mulmod(y[(uint64_t)m * N + n] % q, h, q), q);
+        }
+        conv[n] = submod(s, mulmod(uo[n] % q, M, q), q);
+      }
+      or_ntt_forward(conv, c->log_n, q, c->psi[i]);
+      const uint64_t Minv = invmod(M, q);
+      const uint64_t* ai = acc + ((uint64_t)k * rows + i) * N;
+      const uint64_t* di = d01 + ((uint64_t)k * l + i) * N;
+      uint64_t* o = out + ((uint64_t)k * level + i) * N;
+      for (uint64_t n = 0; n < N; n++) {
+        const uint64_t yi = addmod(mulmod(P, di[n], q), ai[n], q);
+        o[n] = mulmod(submod(yi, conv[n], q), Minv, q);
+      }
+    }
+  }
+  free(acc);
+  free(Dm);
+  free(Dt);
+  free(y);
+  free(conv);
+  free(uo);
+}
+
+/*
+ * Key inner product + ModDown:
+ *   acc_k[t] = sum_j ext[j][t] * key[j][k][t]   (k = 0,1; over QP_l)
+ *   out_k[i] = (acc_k[i] - Conv_{P->Q}([acc_k]_P)_i) * P^{-1} mod q_i,
+ *   Conv_{P->Q}(y)_i = sum_k v_k (Phat_k mod q_i) - u (P mod q_i),
+ *   v_k = [y_k * Phat_k^{-1}]_{p_k}, u = floor(sum_k v_k / p_k + 1/2)
+ * (the sum in double precision, k ascending): the conversion of the centred
+ * representative of [acc_k]_P (Halevi, Polyakov and Shoup 2019), so out is
+ * acc_k / P rounded to nearest, without the bias of the uncentred sum.
+ * `ext` rows follow or_modup; if g != 0 every ext row is first mapped by the
+ * NTT-domain automorphism X -> X^g (hoisted rotation: automorphism after
+ * ModUp). out: [2][l][N].
+ */
+void or_keyswitch_ext(const or_ctx* c, const uint64_t* ext_in, int level, const uint64_t* key,
+                      uint64_t g, uint64_t* out) {
+  const uint64_t N = c->N;
+  const int l = level + 1, rows = l + c->alpha, A = c->alpha;
+  uint64_t* acc = key_product(c, ext_in, level, key, g);
   /* ModDown */
   uint64_t* y = malloc((uint64_t)A * N * sizeof(uint64_t));
   uint64_t* conv = malloc(N * sizeof(uint64_t));
+  uint64_t* u = malloc(N * sizeof(uint64_t));
   for (int k = 0; k < 2; k++) {
     for (int a = 0; a < A; a++) {
       const int t = pidx(c, a);
@@ -899,8 +1002,15 @@ void or_keyswitch_ext(const or_ctx* c, const uint64_t* ext_in, int level, const 
       const uint64_t phi = invmod(ph, pa);
       for (uint64_t n = 0; n < N; n++) ya[n] = mulmod(ya[n], phi, pa);
     }
+    for (uint64_t n = 0; n < N; n++) {
+      double sf = 0.0;
+      for (int a = 0; a < A; a++) sf += (double)y[(uint64_t)a * N + n] * (1.0 / (double)c->mod[pidx(c, a)]);
+      u[n] = (uint64_t)floor(sf + 0.5);
+    }
     for (int i = 0; i < l; i++) {
       const uint64_t q = c->mod[i];
+      uint64_t P = 1;
+      for (int a = 0; a < A; a++) P = mulmod(P, c->mod[pidx(c, a)] % q, q);
       for (uint64_t n = 0; n < N; n++) {
         uint64_t s = 0;
         for (int a = 0; a < A; a++) {
@@ -909,21 +1019,19 @@ void or_keyswitch_ext(const or_ctx* c, const uint64_t* ext_in, int level, const 
             if (b != a) ph = mulmod(ph, c->mod[pidx(c, b)] % q, q);
           s = addmod(s, mulmod(y[(uint64_t)a * N + n] % q, ph, q), q);
         }
-        conv[n] = s;
+        conv[n] = submod(s, mulmod(u[n] % q, P, q), q);
       }
       or_ntt_forward(conv, c->log_n, q, c->psi[i]);
-      uint64_t P = 1;
-      for (int a = 0; a < A; a++) P = mulmod(P, c->mod[pidx(c, a)] % q, q);
       const uint64_t Pinv = invmod(P, q);
       const uint64_t* ai = acc + ((uint64_t)k * rows + i) * N;
       uint64_t* o = out + ((uint64_t)k * l + i) * N;
       for (uint64_t n = 0; n < N; n++) o[n] = mulmod(submod(ai[n], conv[n], q), Pinv, q);
     }
   }
-  free(ext);
   free(acc);
   free(y);
   free(conv);
+  free(u);
 }
 
 uint64_t or_ext_rows(const or_ctx* c, int level) {

@@ -33,6 +33,8 @@ SIGNATURES = {
     "ckks_last_error": (ctypes.c_char_p, []),
     "ckks_context_create": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, PP]),
     "ckks_context_destroy": (c_i32, [c_vp]),
+    "ckks_autotune_keyswitch": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp,
+                                        c_vp, c_vp, c_i32, c_vp]),
     "ckks_context_info": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "ckks_set_stream": (c_i32, [c_vp, c_vp]),
     "ckks_set_fusion": (c_i32, [c_vp, c_i32]),
@@ -119,6 +121,17 @@ def check(rc):
 
 def _p(a):
     return a.ctypes.data if a is not None else None
+
+
+def autotune_keyswitch(log_n, n_scale, max_qp_bits, batch=8, q0_bits=60, scale_bits=40, device=0):
+    """(alpha, p_bits, {alpha: ms per HMult+HRot}) of the fastest digit layout."""
+    a, p, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    tried = np.zeros(16, np.int32)
+    ms = np.zeros(16)
+    check(lib().ckks_autotune_keyswitch(log_n, q0_bits, scale_bits, n_scale, max_qp_bits, batch, device,
+                                        ctypes.byref(a), ctypes.byref(p), _p(tried), _p(ms), 16,
+                                        ctypes.byref(n)))
+    return a.value, p.value, {int(t): float(m) for t, m in zip(tried[:n.value], ms[:n.value])}
 
 
 class Context:

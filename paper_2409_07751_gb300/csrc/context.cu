@@ -43,7 +43,8 @@ const char* kernel_kind_name(int k) {
       "ntt_small", "ntt_fwd", "ntt_inv", "modup_ntt", "moddown_ntt", "rescale_ntt",
       "modup", "key_inner_product", "moddown_conv", "moddown_finish", "tensor", "mul_plain",
       "add", "mul_int", "lincomb", "rotate_finish", "automorphism", "rescale_spread",
-      "rescale_finish", "int_to_rns", "encode_fft", "sample", "crypt", "copy"};
+      "rescale_finish", "int_to_rns", "encode_fft", "sample", "crypt", "copy",
+      "relin_rescale_ntt", "relin_rescale_top", "conversion_overflow"};
   return (k >= 0 && k < K_KIND_COUNT) ? names[k] : "?";
 }
 
@@ -437,6 +438,75 @@ ConvTables& Ctx::tables(int level) {
   T->xs_post_s = upload(this, xps);
   T->md_post = upload(this, mp);
   T->md_post_s = upload(this, mps);
+  {
+    std::vector<double> inv(A);
+    for (int a = 0; a < A; a++) inv[a] = 1.0 / (double)mod[L + 1 + a];
+    std::vector<uint64_t> pq(l), pqs(l);
+    for (int i = 0; i < l; i++) {
+      uint64_t P = 1;
+      for (int a = 0; a < A; a++) P = mulmod_h(P, mod[L + 1 + a] % mod[i], mod[i]);
+      pq[i] = P;
+      pqs[i] = shoup_h(P, mod[i]);
+    }
+    T->md_inv = upload(this, inv);
+    T->md_pq = upload(this, pq);
+    T->md_pq_s = upload(this, pqs);
+  }
+  // merged relinearise + rescale (levels >= 1): D = {q_level, p_0 .. p_{A-1}}
+  if (level >= 1) {
+    std::vector<int> Dt = {level};
+    for (int a = 0; a < A; a++) Dt.push_back(L + 1 + a);
+    const int nD = A + 1;
+    std::vector<int16_t> rp(rows, -1);
+    std::vector<uint64_t> rpost(rows, 0), rposts(rows, 0), yinv(nD), yinvs(nD);
+    std::vector<uint64_t> mh((size_t)nD * l, 0), mhs((size_t)nD * l, 0), minv(l), minvs(l);
+    for (int m = 0; m < nD; m++) {
+      const uint64_t qm = mod[Dt[m]];
+      uint64_t h = 1;
+      for (int o = 0; o < nD; o++)
+        if (o != m) h = mulmod_h(h, mod[Dt[o]] % qm, qm);
+      yinv[m] = invmod_h(h, qm);
+      yinvs[m] = shoup_h(yinv[m], qm);
+      const int r = level + m;  // acc rows level, l, .., l + A - 1
+      rp[r] = (int16_t)Dt[m];
+      rpost[r] = mulmod_h(invmod_h(N % qm, qm), yinv[m], qm);
+      rposts[r] = shoup_h(rpost[r], qm);
+      for (int i = 0; i < l; i++) {
+        uint64_t hi = 1;
+        for (int o = 0; o < nD; o++)
+          if (o != m) hi = mulmod_h(hi, mod[Dt[o]] % mod[i], mod[i]);
+        mh[(size_t)m * l + i] = hi;
+        mhs[(size_t)m * l + i] = shoup_h(hi, mod[i]);
+      }
+    }
+    std::vector<uint64_t> mq(l), mqs(l);
+    std::vector<double> rinv(nD);
+    for (int m = 0; m < nD; m++) rinv[m] = 1.0 / (double)mod[Dt[m]];
+    for (int i = 0; i < l; i++) {
+      uint64_t Mi = 1;
+      for (int o = 0; o < nD; o++) Mi = mulmod_h(Mi, mod[Dt[o]] % mod[i], mod[i]);
+      minv[i] = i == level ? 0 : invmod_h(Mi, mod[i]);
+      minvs[i] = shoup_h(minv[i], mod[i]);
+      mq[i] = Mi;
+      mqs[i] = shoup_h(Mi, mod[i]);
+    }
+    T->rr_inv = upload(this, rinv);
+    T->rr_mq = upload(this, mq);
+    T->rr_mq_s = upload(this, mqs);
+    uint64_t Pq = 1;
+    for (int a = 0; a < A; a++) Pq = mulmod_h(Pq, mod[L + 1 + a] % mod[level], mod[level]);
+    T->rr_pq = Pq;
+    T->rr_pq_s = shoup_h(Pq, mod[level]);
+    T->rr_pattern = upload(this, rp);
+    T->rr_post = upload(this, rpost);
+    T->rr_post_s = upload(this, rposts);
+    T->rr_yinv = upload(this, yinv);
+    T->rr_yinv_s = upload(this, yinvs);
+    T->rr_mh = upload(this, mh);
+    T->rr_mh_s = upload(this, mhs);
+    T->rr_minv = upload(this, minv);
+    T->rr_minv_s = upload(this, minvs);
+  }
   auto& ref = *T;
   conv[level] = std::move(T);
   return ref;

@@ -15,6 +15,9 @@
 namespace ck {
 
 // Per-modulus constants visible to kernels.
+// most key-switching digits a key inner product takes (keys staged in shared memory)
+constexpr int MAX_DIGITS = 32;
+
 struct Mod {
   uint64_t q;
   uint64_t mu;   // floor(2^(2s) / q), Barrett
@@ -61,6 +64,20 @@ struct ConvTables {
   DevBuf md_pinv, md_pinv_s;  // [l]: P^-1 mod q_i
   DevBuf xs_post, xs_post_s;  // [l]: N^-1 Dhat_i^-1 mod q_i (fused ModUp)
   DevBuf md_post, md_post_s;  // [rows]: N^-1 Phat_a^-1 mod p_a on P rows (fused ModDown)
+  // HMult's merged relinearise + rescale: division by M = P q_level with the
+  // dropped moduli D = {q_level, p_0 .. p_{alpha-1}} (rows level .. level+alpha)
+  DevBuf rr_pattern;          // int16 [rows]: modulus of the D rows, -1 elsewhere
+  DevBuf rr_post, rr_post_s;  // [rows]: N^-1 (M/m)^-1 mod m on the D rows (fused)
+  DevBuf rr_yinv, rr_yinv_s;  // [alpha+1]: (M/m)^-1 mod m (unfused)
+  DevBuf rr_mh, rr_mh_s;      // [alpha+1][l]: (M/m) mod q_i
+  DevBuf rr_minv, rr_minv_s;  // [l]: M^-1 mod q_i
+  uint64_t rr_pq = 0, rr_pq_s = 0;  // P mod q_level and its Shoup companion
+  // centred conversions: overflow u = floor(sum_m v_m / m + 1/2) in double,
+  // then u [M]_{q_i} subtracted (M = P for ModDown, P q_level merged)
+  DevBuf md_inv;              // double [alpha]: 1 / p_a
+  DevBuf md_pq, md_pq_s;      // [l]: P mod q_i
+  DevBuf rr_inv;              // double [alpha+1]: 1 / q_level, 1 / p_a
+  DevBuf rr_mq, rr_mq_s;      // [l]: M mod q_i
 };
 
 // Kernel kinds timed by the optional per-launch CUDA-event profiler.
@@ -68,7 +85,7 @@ enum KernelKind {
   K_NTT_SMALL, K_NTT_FWD, K_NTT_INV, K_MODUP_NTT, K_MODDOWN_NTT, K_RESCALE_NTT,
   K_MODUP, K_INNER, K_MD_CONV, K_MD_FINISH, K_TENSOR, K_MUL_PT, K_ADD, K_MUL_INT,
   K_LINCOMB, K_ROT_FINISH, K_AUTO, K_RS_SPREAD, K_RS_FINISH, K_INT_RNS, K_ENCODE,
-  K_SAMPLE, K_CRYPT, K_COPY, K_KIND_COUNT
+  K_SAMPLE, K_CRYPT, K_COPY, K_RR_NTT, K_RR_TOP, K_OVERFLOW, K_KIND_COUNT
 };
 const char* kernel_kind_name(int k);
 
@@ -194,9 +211,14 @@ void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* patt
                       const uint64_t* post, const uint64_t* posts, size_t active = SIZE_MAX);
 void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, int level,
                      uint64_t* ext);
-void ntt_moddown_fused(Ctx& c, const uint64_t* acc, size_t BK, int level, uint64_t* out);
+// ov: [BK][N] overflow of the centred P -> Q conversion (k_overflow)
+void ntt_moddown_fused(Ctx& c, const uint64_t* acc, const uint8_t* ov, size_t BK, int level,
+                       uint64_t* out);
 void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t polys, int level,
                        uint64_t* out);
+// out[B][2][level][N] = (d_k q_level^-1 + (acc_k - Conv_D(acc_D)) M^-1), transformed
+void ntt_relin_rescale_fused(Ctx& c, const uint64_t* acc, const uint64_t* d, const uint8_t* ov,
+                             size_t B, int level, uint64_t* out);
 
 // ---- elementwise (elementwise.cu). Ciphertext batches are [B][polys][l][N].
 void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t rows, int l,
@@ -217,6 +239,10 @@ void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext);
 // out[B][2][l][N] = ModDown(<sigma_g(ext), key>); galois 0 = no automorphism.
 void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
                    uint64_t galois, uint64_t* out);
+// HMult's relinearise + rescale in one division by P q_level: d is the tensor
+// product [B][3][level+1][N], ext the ModUp of its d2; out [B][2][level][N].
+void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B, int level,
+                       const uint64_t* key, uint64_t* out);
 
 // ---- encoding (encode.cu)
 // v: device doubles [B][nv]; writes pt [B][level+1][N] at `scale`. Returns

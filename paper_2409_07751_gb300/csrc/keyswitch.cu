@@ -118,11 +118,21 @@ __global__ void __launch_bounds__(IP_THREADS)
   }
 }
 
-// thread per (bk, n): y_a = [acc_P[a] Phat_a^{-1}]_{p_a}; conv_i = sum_a y_a Phat_a mod q_i
+// overflow of the centred conversion, u = floor(sum_m v_m inv_m + 1/2) in
+// double precision, m ascending, no contraction (the oracle's expression)
+__device__ __forceinline__ uint64_t conv_overflow(const uint64_t* v, const double* inv, int n) {
+  double sf = 0.0;
+  for (int m = 0; m < n; m++) sf = __dadd_rn(sf, __dmul_rn(__ull2double_rn(v[m]), inv[m]));
+  return (uint64_t)floor(sf + 0.5);
+}
+
+// thread per (bk, n): y_a = [acc_P[a] Phat_a^{-1}]_{p_a};
+// conv_i = sum_a y_a Phat_a - u P mod q_i (centred conversion)
 __global__ void moddown_conv_kernel(const uint64_t* acc, uint64_t* conv, size_t BK, int log_n,
                                     int l, int alpha, int rows, int L, const Mod* mods,
                                     const uint64_t* yinv, const uint64_t* yinvs,
-                                    const uint64_t* ph, const uint64_t* phs) {
+                                    const uint64_t* ph, const uint64_t* phs, const double* inv,
+                                    const uint64_t* pq, const uint64_t* pqs) {
   const size_t N = (size_t)1 << log_n;
   GRID_LOOP(idx, BK * N) {
     const size_t n = idx & (N - 1);
@@ -132,6 +142,7 @@ __global__ void moddown_conv_kernel(const uint64_t* acc, uint64_t* conv, size_t 
       const uint64_t x = acc[(bk * rows + l + a) * N + n];
       y[a] = mul_shoup(x, yinv[a], yinvs[a], mods[L + 1 + a].q);
     }
+    const uint64_t u = conv_overflow(y, inv, alpha);
     for (int i = 0; i < l; i++) {
       const uint64_t q = mods[i].q;
       uint64_t s = 0;
@@ -139,8 +150,22 @@ __global__ void moddown_conv_kernel(const uint64_t* acc, uint64_t* conv, size_t 
         const size_t ti = (size_t)a * (L + 1) + i;
         s = add_mod(s, mul_shoup(y[a], ph[ti], phs[ti], q), q);
       }
-      conv[(bk * l + i) * N + n] = s;
+      conv[(bk * l + i) * N + n] = sub_mod(s, mul_shoup(u, pq[i], pqs[i], q), q);
     }
+  }
+}
+
+// fused paths: u per (bk, n) from `count` rows starting at `first`, which
+// already hold v_m (inverse-transformed and scaled by (M/m)^-1)
+__global__ void overflow_kernel(const uint64_t* acc, uint8_t* ov, size_t BK, int log_n, int first,
+                                int count, int rows, const double* inv) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(idx, BK * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bk = idx >> log_n;
+    uint64_t v[MAX_ALPHA + 1];
+    for (int m = 0; m < count; m++) v[m] = acc[(bk * rows + first + m) * N + n];
+    ov[idx] = (uint8_t)conv_overflow(v, inv, count);
   }
 }
 
@@ -156,6 +181,71 @@ __global__ void moddown_finish_kernel(const uint64_t* acc, const uint64_t* conv,
     const uint64_t q = mods[i].q;
     const uint64_t a = acc[(bk * rows + i) * N + n];
     out[idx] = mul_shoup(sub_mod(a, conv[idx], q), pinv[i], pinvs[i], q);
+  }
+}
+
+// merged relinearise + rescale: acc row `level` of (b, k) += [P]_{q_level} d_k[level]
+__global__ void rr_top_kernel(uint64_t* acc, const uint64_t* d, size_t B, int log_n, int level,
+                              int rows, uint64_t q, uint64_t pq, uint64_t pqs) {
+  const size_t N = (size_t)1 << log_n;
+  const int l = level + 1;
+  GRID_LOOP(idx, B * 2 * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bk = idx >> log_n;
+    const size_t b = bk / 2, k = bk % 2;
+    uint64_t* a = acc + (bk * rows + level) * N + n;
+    *a = add_mod(mul_shoup(d[((b * 3 + k) * l + level) * N + n], pq, pqs, q), *a, q);
+  }
+}
+
+// unfused: thread per (bk, n): y_m = [acc_m (M/m)^-1]_m over the D rows
+// (coefficient form), conv_i = sum_m y_m [M/m]_{q_i} - u [M]_{q_i}, i < level
+__global__ void rr_conv_kernel(const uint64_t* acc, uint64_t* conv, size_t BK, int log_n,
+                               int level, int alpha, int rows, const Mod* mods, const int16_t* dmod,
+                               const uint64_t* yinv, const uint64_t* yinvs, const uint64_t* mh,
+                               const uint64_t* mhs, const double* inv, const uint64_t* mq,
+                               const uint64_t* mqs) {
+  const size_t N = (size_t)1 << log_n;
+  const int l = level + 1;
+  GRID_LOOP(idx, BK * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bk = idx >> log_n;
+    uint64_t y[MAX_ALPHA + 1];
+    for (int m = 0; m <= alpha; m++) {
+      const uint64_t x = acc[(bk * rows + level + m) * N + n];
+      y[m] = mul_shoup(x, yinv[m], yinvs[m], mods[dmod[level + m]].q);
+    }
+    const uint64_t u = conv_overflow(y, inv, alpha + 1);
+    for (int i = 0; i < level; i++) {
+      const uint64_t q = mods[i].q;
+      uint64_t s = 0;
+      for (int m = 0; m <= alpha; m++) {
+        const size_t ti = (size_t)m * l + i;
+        s = add_mod(s, mul_shoup(y[m], mh[ti], mhs[ti], q), q);
+      }
+      conv[(bk * level + i) * N + n] = sub_mod(s, mul_shoup(u, mq[i], mqs[i], q), q);
+    }
+  }
+}
+
+// unfused: out_k[i] = d_k[i] q_level^-1 + (acc_k[i] - conv_i) M^-1
+__global__ void rr_finish_kernel(const uint64_t* acc, const uint64_t* d, const uint64_t* conv,
+                                 uint64_t* out, size_t BK, int log_n, int level, int rows,
+                                 const Mod* mods, const uint64_t* minv, const uint64_t* minvs,
+                                 const uint64_t* qlinv, const uint64_t* qlinvs) {
+  const size_t N = (size_t)1 << log_n;
+  const int l = level + 1;
+  GRID_LOOP(idx, BK * level * N) {
+    const size_t n = idx & (N - 1);
+    const size_t bi = idx >> log_n;
+    const int i = (int)(bi % level);
+    const size_t bk = bi / level;
+    const size_t b = bk / 2, k = bk % 2;
+    const uint64_t q = mods[i].q;
+    const uint64_t a = acc[(bk * rows + i) * N + n];
+    const uint64_t dv = d[((b * 3 + k) * l + i) * N + n];
+    out[idx] = add_mod(mul_shoup(dv, qlinv[i], qlinvs[i], q),
+                       mul_shoup(sub_mod(a, conv[idx], q), minv[i], minvs[i], q), q);
   }
 }
 
@@ -185,15 +275,15 @@ void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext) {
               T.beta * T.rows, B * ((size_t)T.beta * T.rows - l));
 }
 
-void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
-                   uint64_t galois, uint64_t* out) {
+// acc[B][2][rows][N] = <sigma_g(ext), key> over QP_l
+static DevBuf key_product(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
+                          uint64_t galois) {
   ConvTables& T = c.tables(level);
   const int l = T.l, rows = T.rows;
-  if (T.beta > 32) throw Error(CKKS_ERR_UNSUPPORTED, "more than 32 digits");
+  if (T.beta > MAX_DIGITS) throw Error(CKKS_ERR_UNSUPPORTED, "more than 32 digits");
   const uint32_t* perm = galois ? c.perm(galois) : nullptr;
   DevBuf acc(&c, B * 2 * rows * c.N * 8);
   const double W8 = (double)c.N * 8.0;
-  {
   Launch L_(c, K_INNER, W8 * rows * ((double)B * T.beta + 2.0 * T.beta + 2.0 * B),
             2.0 * (double)B * T.beta * rows * (double)c.N);
   const size_t ip_total = (size_t)rows * c.N;
@@ -201,11 +291,76 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
   inner_product_kernel<<<(unsigned)ip_blocks, IP_THREADS, 2 * T.beta * IP_THREADS * 8, c.stream>>>(
       ext, key, acc.u64(), B, c.log_n, l, T.beta, rows, c.L, c.n_qp, c.dmod(), perm);
   CK_CUDA(cudaGetLastError());
+  return acc;
+}
+
+void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B, int level,
+                       const uint64_t* key, uint64_t* out) {
+  if (level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+  if (c.alpha + 1 > MAX_ALPHA + 1) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
+  ConvTables& T = c.tables(level);
+  const int rows = T.rows;
+  DevBuf acc = key_product(c, ext, B, level, key, 0);
+  const double W8 = (double)c.N * 8.0;
+  {
+    Launch L_(c, K_RR_TOP, W8 * 2.0 * B * 3.0, 2.0 * B * (double)c.N);
+    rr_top_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+        acc.u64(), d, B, c.log_n, level, rows, c.mod[level], T.rr_pq, T.rr_pq_s);
+    CK_CUDA(cudaGetLastError());
   }
+  const int16_t* pat = static_cast<const int16_t*>(T.rr_pattern.p);
+  const size_t active = B * 2 * (size_t)(c.alpha + 1);
+  if (ntt_fused_available(c)) {
+    ntt_inverse_post(c, acc.u64(), B * 2 * rows, pat, rows, T.rr_post.u64(), T.rr_post_s.u64(),
+                     active);
+    DevBuf ov(&c, B * 2 * c.N);
+    {
+      Launch L_(c, K_OVERFLOW, W8 * B * 2.0 * (c.alpha + 1.0) + B * 2.0 * c.N);
+      overflow_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+          acc.u64(), static_cast<uint8_t*>(ov.p), B * 2, c.log_n, level, c.alpha + 1, rows,
+          static_cast<const double*>(T.rr_inv.p));
+      CK_CUDA(cudaGetLastError());
+    }
+    ntt_relin_rescale_fused(c, acc.u64(), d, static_cast<const uint8_t*>(ov.p), B, level, out);
+    return;
+  }
+  ntt_inverse(c, acc.u64(), B * 2 * rows, pat, rows, active);
+  DevBuf conv(&c, B * 2 * (size_t)level * c.N * 8);
+  {
+    Launch L_(c, K_MD_CONV, W8 * B * 2.0 * (c.alpha + 1.0 + level));
+    rr_conv_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+        acc.u64(), conv.u64(), B * 2, c.log_n, level, c.alpha, rows, c.dmod(), pat,
+        T.rr_yinv.u64(), T.rr_yinv_s.u64(), T.rr_mh.u64(), T.rr_mh_s.u64(),
+        static_cast<const double*>(T.rr_inv.p), T.rr_mq.u64(), T.rr_mq_s.u64());
+    CK_CUDA(cudaGetLastError());
+  }
+  ntt_forward(c, conv.u64(), B * 2 * (size_t)level, c.iota(), level);
+  Launch L2_(c, K_MD_FINISH, W8 * B * 2.0 * 4.0 * level);
+  rr_finish_kernel<<<grid_for(B * 2 * (size_t)level * c.N), TPB, 0, c.stream>>>(
+      acc.u64(), d, conv.u64(), out, B * 2, c.log_n, level, rows, c.dmod(), T.rr_minv.u64(),
+      T.rr_minv_s.u64(), c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
+      c.d_rs_invs.u64() + (size_t)level * (c.L + 1));
+  CK_CUDA(cudaGetLastError());
+}
+
+void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
+                   uint64_t galois, uint64_t* out) {
+  ConvTables& T = c.tables(level);
+  const int l = T.l, rows = T.rows;
+  DevBuf acc = key_product(c, ext, B, level, key, galois);
+  const double W8 = (double)c.N * 8.0;
   if (ntt_fused_available(c)) {
     ntt_inverse_post(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows,
                      T.md_post.u64(), T.md_post_s.u64(), B * 2 * (size_t)c.alpha);
-    ntt_moddown_fused(c, acc.u64(), B * 2, level, out);
+    DevBuf ov(&c, B * 2 * c.N);
+    {
+      Launch L_(c, K_OVERFLOW, W8 * B * 2.0 * c.alpha + B * 2.0 * c.N);
+      overflow_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+          acc.u64(), static_cast<uint8_t*>(ov.p), B * 2, c.log_n, l, c.alpha, rows,
+          static_cast<const double*>(T.md_inv.p));
+      CK_CUDA(cudaGetLastError());
+    }
+    ntt_moddown_fused(c, acc.u64(), static_cast<const uint8_t*>(ov.p), B * 2, level, out);
     return;
   }
   ntt_inverse(c, acc.u64(), B * 2 * rows, static_cast<const int16_t*>(T.pq_pattern.p), rows,
@@ -215,7 +370,8 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
   Launch L_(c, K_MD_CONV, W8 * B * 2.0 * (c.alpha + l));
   moddown_conv_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
       acc.u64(), conv.u64(), B * 2, c.log_n, l, c.alpha, rows, c.L, c.dmod(), c.d_md_yinv.u64(),
-      c.d_md_yinv_s.u64(), c.d_md_ph.u64(), c.d_md_ph_s.u64());
+      c.d_md_yinv_s.u64(), c.d_md_ph.u64(), c.d_md_ph_s.u64(),
+      static_cast<const double*>(T.md_inv.p), T.md_pq.u64(), T.md_pq_s.u64());
   CK_CUDA(cudaGetLastError());
   }
   ntt_forward(c, conv.u64(), B * 2 * l, c.iota(), l);

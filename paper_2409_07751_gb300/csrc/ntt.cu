@@ -33,6 +33,15 @@ constexpr int CHUNK_LOG = 12;
 constexpr int CHUNK = 1 << CHUNK_LOG;  // N2
 constexpr int ROW_THREADS = 512;       // one radix-8 group of each of two chunks per thread
 
+// CTAs per cluster (one row per cluster). Forward: two chunks per CTA (64 KiB
+// of shared memory, at most 64 registers per thread), so two CTAs share an SM;
+// inverse: four chunks per CTA, one CTA per SM.
+template <int N1>
+__host__ __device__ constexpr int fwd_cs() { return N1 >= 4 ? N1 / 2 : 1; }
+template <int N1>
+__host__ __device__ constexpr int inv_cs() { return N1 >= 4 ? N1 / 4 : 1; }
+constexpr int FWD_CTAS_PER_SM = 2;
+
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
   return a * w - __umul64hi(a, ws) * q;  // in [0, 2q) for any a < 2^64
 }
@@ -52,15 +61,28 @@ __device__ __forceinline__ void gs_lazy(uint64_t& x, uint64_t& y, uint64_t w, ui
   x = s >= q2 ? s - q2 : s;
   y = shoup_lazy(u - v + q2, w, ws, q);
 }
-// Forward butterfly without the reduction of x, for moduli q < 2^44: both
-// outputs grow by less than 2q per stage, so 16 stages from inputs below 4q
-// stay below 36q < 2^50 (the Shoup product accepts any input below 2^64).
+// Shoup product whose quotient is estimated from three of the four 32-bit
+// partial products of y * ws (the low product and the carries out of the
+// middle ones are dropped): with y ws = y1 s1 2^64 + (y1 s0 + y0 s1) 2^32 +
+// y0 s0, Q' = y1 s1 + hi(y1 s0) + hi(y0 s1) satisfies Q - 2 <= Q' <= Q for
+// the exact Q = floor(y ws / 2^64), so y w - Q' q lies in [0, 4q) for any
+// y < 2^64 (exact Shoup: [0, 2q)).
+__device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_t ws, uint64_t q) {
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  const uint32_t s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
+  const uint64_t Q = (uint64_t)y1 * s1 + __umulhi(y1, s0) + __umulhi(y0, s1);
+  return y * w - Q * q;
+}
+
+// Forward butterfly without the reduction of x, for moduli q < 2^50: with
+// t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
+// from inputs below q stay below 65q < 2^57.
 __device__ __forceinline__ void ct_grow(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
   const uint64_t u = x;
-  const uint64_t t = shoup_lazy(y, w, ws, q);
+  const uint64_t t = shoup_approx(y, w, ws, q);
   x = u + t;
-  y = u - t + q2;
+  y = u - t + 2 * q2;
 }
 template <bool GROW>
 __device__ __forceinline__ void ct_step(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
@@ -154,7 +176,7 @@ __device__ __forceinline__ uint32_t node_base(uint32_t ls, int log_n) {
   return off;
 }
 
-template <bool INV>
+template <bool INV, bool GROW = false>
 __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
                                        int log_n, const ulonglong2* t8, uint64_t q, uint64_t q2) {
   const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
@@ -169,13 +191,13 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
   for (int k = 0; k < 7; k++) tt[k] = T[k];
   if (!INV) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) ct_lazy(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
-    ct_lazy(x[0], x[2], tt[1].x, tt[1].y, q, q2);
-    ct_lazy(x[1], x[3], tt[1].x, tt[1].y, q, q2);
-    ct_lazy(x[4], x[6], tt[2].x, tt[2].y, q, q2);
-    ct_lazy(x[5], x[7], tt[2].x, tt[2].y, q, q2);
+    for (int k = 0; k < 4; k++) ct_step<GROW>(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
+    ct_step<GROW>(x[0], x[2], tt[1].x, tt[1].y, q, q2);
+    ct_step<GROW>(x[1], x[3], tt[1].x, tt[1].y, q, q2);
+    ct_step<GROW>(x[4], x[6], tt[2].x, tt[2].y, q, q2);
+    ct_step<GROW>(x[5], x[7], tt[2].x, tt[2].y, q, q2);
 #pragma unroll
-    for (int k = 0; k < 4; k++) ct_lazy(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
+    for (int k = 0; k < 4; k++) ct_step<GROW>(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
   } else {
 #pragma unroll
     for (int k = 0; k < 4; k++) gs_lazy(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
@@ -304,6 +326,10 @@ struct Row {
   int n_src;
   uint64_t k, ks;    // epilogue constant
   uint64_t aux;      // rescale: q of the dropped prime
+  const uint64_t* src3;  // second epilogue source row (merged relinearise + rescale)
+  uint64_t k2, k2s;      // its constant
+  const uint8_t* ov;     // conversion overflow per coefficient (centred conversions)
+  uint64_t km, kms;      // [M]_q subtracted ov times
 };
 
 constexpr int MAX_SRC = 16;
@@ -378,6 +404,9 @@ struct DescModDown {
   const uint64_t* phs;
   const uint64_t* pinv;  // [l]
   const uint64_t* pinvs;
+  const uint8_t* ov;     // [BK][N]: u = floor(sum_a v_a / p_a + 1/2)
+  const uint64_t* pq;    // [l]: P mod q_i
+  const uint64_t* pqs;
   int l, rows, alpha, L;
   size_t N;
   __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
@@ -390,6 +419,9 @@ struct DescModDown {
     r.n_src = alpha;
     r.k = pinv[i];
     r.ks = pinvs[i];
+    r.ov = ov + bk * N;
+    r.km = pq[i];
+    r.kms = pqs[i];
     if (threadIdx.x < (unsigned)alpha) {
       kc[threadIdx.x] = ph[(size_t)threadIdx.x * (L + 1) + i];
       kc[MAX_SRC + threadIdx.x] = phs[(size_t)threadIdx.x * (L + 1) + i];
@@ -401,7 +433,7 @@ struct DescModDown {
     uint64_t s = 0;
     for (int a = 0; a < r.n_src; a++)
       s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
-    return s;
+    return sub_mod(s, mul_shoup((uint64_t)r.ov[i], r.km, r.kms, m), m);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
@@ -444,7 +476,7 @@ template <int N1, class D, bool GROW>
 __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ulonglong2* t8,
                                          uint64_t q, const uint64_t* kc, const ulonglong2* ctw,
                                          uint64_t* sm) {
-  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  constexpr int CS = fwd_cs<N1>();
   constexpr int CPC = N1 / CS;
   const uint64_t q2 = 2 * q;
   const uint64_t w1s = GROW ? ~0ull / q : 0;  // floor(2^64 / q) for odd q
@@ -487,7 +519,8 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
     uint64_t* s = sm + lc * CHUNK;
 #pragma unroll
     for (int ls = 9; ls >= 0; ls -= 3) {
-      round8x2<false, GROW>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8<false, GROW>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8<false, GROW>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
       __syncthreads();
     }
     for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS) {
@@ -497,7 +530,63 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
   }
 }
 
-// Forward NTT of one row per cluster of CS CTAs (CS = N1/4, or 1 for N1 <= 4).
+// HMult's relinearise + rescale, output row i < level of (b, k):
+//   d_k[i] q_level^-1 + (acc_k[i] - NTT(sum_m y_m [M/m]_{q_i})) M^-1,
+// y_m the D rows of acc (level .. level+alpha) already inverse-transformed and
+// scaled by (M/m)^-1, with y_level = P d_k + acc_k on q_level.
+struct DescRelinRescale {
+  const uint64_t* acc;    // [BK][rows][N]
+  const uint64_t* d;      // [B][3][level+1][N] tensor product
+  uint64_t* out;          // [BK][level][N]
+  const uint64_t* mh;     // [alpha+1][level+1]: (M/m) mod q_i
+  const uint64_t* mhs;
+  const uint64_t* minv;   // [level+1]: M^-1 mod q_i
+  const uint64_t* minvs;
+  const uint64_t* qlinv;  // [L+1]: q_level^-1 mod q_t
+  const uint64_t* qlinvs;
+  const uint8_t* ov;      // [BK][N]: u = floor(sum_m v_m / m + 1/2)
+  const uint64_t* mq;     // [level+1]: M mod q_i
+  const uint64_t* mqs;
+  int level, rows, alpha;
+  size_t N;
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t, uint32_t) const {
+    const int i = (int)(blk % level);
+    const size_t bk = blk / level;
+    const size_t b = bk / 2, k = bk % 2;
+    const int l = level + 1;
+    r.mi = i;
+    r.mid = out + (bk * level + i) * N;
+    r.src = acc + (bk * rows + level) * N;
+    r.n_src = alpha + 1;
+    r.src2 = acc + (bk * rows + i) * N;
+    r.src3 = d + ((b * 3 + k) * l + i) * N;
+    r.k = minv[i];
+    r.ks = minvs[i];
+    r.k2 = qlinv[i];
+    r.k2s = qlinvs[i];
+    r.ov = ov + bk * N;
+    r.km = mq[i];
+    r.kms = mqs[i];
+    if (threadIdx.x < (unsigned)(alpha + 1)) {
+      kc[threadIdx.x] = mh[(size_t)threadIdx.x * l + i];
+      kc[MAX_SRC + threadIdx.x] = mhs[(size_t)threadIdx.x * l + i];
+    }
+    return true;
+  }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc) const {
+    const uint64_t m = r.aux;
+    uint64_t s = 0;
+    for (int a = 0; a < r.n_src; a++)
+      s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
+    return sub_mod(s, mul_shoup((uint64_t)r.ov[i], r.km, r.kms, m), m);
+  }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
+    r.mid[i] = add_mod(mul_shoup(r.src3[i], r.k2, r.k2s, q),
+                       mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q), q);
+  }
+};
+
+// Forward NTT of one row per cluster of CS = fwd_cs<N1>() CTAs, two chunks per CTA.
 // CTA `rank` owns chunks [rank*CPC, (rank+1)*CPC) of the row in shared memory.
 // Column phase: the CTA transforms columns [rank*CHUNK/CS, ...) from the
 // prologue loads and writes element s of each column into the shared memory
@@ -506,10 +595,10 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
 // writes the results through the epilogue. The row never round-trips
 // through global memory.
 template <int N1, class D>
-__global__ void __launch_bounds__(ROW_THREADS, 1)
+__global__ void __launch_bounds__(ROW_THREADS, FWD_CTAS_PER_SM)
     ntt_fwd_cl(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws,
                const ulonglong2* tw8, size_t nodes) {
-  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  constexpr int CS = fwd_cs<N1>();
   extern __shared__ uint64_t sm[];  // CPC = N1 / CS chunks
   __shared__ uint64_t kc[2 * MAX_SRC];
   __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
@@ -526,7 +615,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
   if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)r.mi * N + g], tws[(size_t)r.mi * N + g]);
   __syncthreads();
   // every CTA of a cluster works on the same row, so the branch is uniform
-  if (q < (1ull << 44))
+  if (q < (1ull << 50))
     fwd_rows<N1, D, true>(d, r, log_n, t8, q, kc, ctw, sm);
   else
     fwd_rows<N1, D, false>(d, r, log_n, t8, q, kc, ctw, sm);
@@ -542,7 +631,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
                const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts,
                const ulonglong2* tw8, size_t nodes) {
-  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
+  constexpr int CS = inv_cs<N1>();
   constexpr int CPC = N1 / CS;
   extern __shared__ uint64_t sm[];
   __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
@@ -602,9 +691,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
   if constexpr (CS > 1) cg::this_cluster().sync();  // peers may still read this CTA's chunks
 }
 
-template <int N1, class K, class... Args>
+template <int N1, int CS, class K, class... Args>
 void launch_cl(Ctx& c, K kernel, size_t n_rows, Args... args) {
-  constexpr int CS = N1 >= 4 ? N1 / 4 : 1;
   constexpr int CPC = N1 / CS;
   const size_t smem = (size_t)CPC * CHUNK * 8;
   static bool attr[64] = {};
@@ -638,10 +726,10 @@ void launch_fwd(Ctx& c, size_t n_rows, const D& d) {
   const int ln = c.log_n;
   const Mod* md = c.dmod();
   switch (c.log_n - CHUNK_LOG) {
-    case 1: launch_cl<2>(c, ntt_fwd_cl<2, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
-    case 2: launch_cl<4>(c, ntt_fwd_cl<4, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
-    case 3: launch_cl<8>(c, ntt_fwd_cl<8, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
-    case 4: launch_cl<16>(c, ntt_fwd_cl<16, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 1: launch_cl<2, fwd_cs<2>()>(c, ntt_fwd_cl<2, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 2: launch_cl<4, fwd_cs<4>()>(c, ntt_fwd_cl<4, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 3: launch_cl<8, fwd_cs<8>()>(c, ntt_fwd_cl<8, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 4: launch_cl<16, fwd_cs<16>()>(c, ntt_fwd_cl<16, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
 }
@@ -658,10 +746,10 @@ void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, i
   const int ln = c.log_n;
   const Mod* md = c.dmod();
   switch (c.log_n - CHUNK_LOG) {
-    case 1: launch_cl<2>(c, ntt_inv_cl<2>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 2: launch_cl<4>(c, ntt_inv_cl<4>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 3: launch_cl<8>(c, ntt_inv_cl<8>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 4: launch_cl<16>(c, ntt_inv_cl<16>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 1: launch_cl<2, inv_cs<2>()>(c, ntt_inv_cl<2>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 2: launch_cl<4, inv_cs<4>()>(c, ntt_inv_cl<4>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 3: launch_cl<8, inv_cs<8>()>(c, ntt_inv_cl<8>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 4: launch_cl<16, inv_cs<16>()>(c, ntt_inv_cl<16>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
 }
@@ -724,14 +812,30 @@ void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, in
   launch_fwd(c, B * T.beta * T.rows, dsc);
 }
 
-void ntt_moddown_fused(Ctx& c, const uint64_t* acc, size_t BK, int level, uint64_t* out) {
+void ntt_moddown_fused(Ctx& c, const uint64_t* acc, const uint8_t* ov, size_t BK, int level,
+                       uint64_t* out) {
   ConvTables& T = c.tables(level);
   const double W8 = (double)c.N * 8.0;
   Launch L_(c, K_MODDOWN_NTT, W8 * (double)BK * (c.alpha + 2.0 * T.l),
             (double)BK * T.l * ((double)(c.N / 2) * c.log_n + (c.alpha + 1.0) * c.N));
   DescModDown dsc{acc, out, c.d_md_ph.u64(), c.d_md_ph_s.u64(), T.md_pinv.u64(), T.md_pinv_s.u64(),
-                  T.l, T.rows, c.alpha, c.L, c.N};
+                  ov, T.md_pq.u64(), T.md_pq_s.u64(), T.l, T.rows, c.alpha, c.L, c.N};
   launch_fwd(c, BK * T.l, dsc);
+}
+
+void ntt_relin_rescale_fused(Ctx& c, const uint64_t* acc, const uint64_t* d, const uint8_t* ov,
+                             size_t B, int level, uint64_t* out) {
+  ConvTables& T = c.tables(level);
+  if (c.alpha + 1 > MAX_SRC) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 15");
+  const double W8 = (double)c.N * 8.0;
+  const double BK = 2.0 * (double)B;
+  Launch L_(c, K_RR_NTT, W8 * BK * (c.alpha + 1.0 + 3.0 * level),
+            BK * level * ((double)(c.N / 2) * c.log_n + (c.alpha + 3.0) * c.N));
+  DescRelinRescale dsc{acc, d, out, T.rr_mh.u64(), T.rr_mh_s.u64(), T.rr_minv.u64(),
+                       T.rr_minv_s.u64(), c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
+                       c.d_rs_invs.u64() + (size_t)level * (c.L + 1), ov, T.rr_mq.u64(),
+                       T.rr_mq_s.u64(), level, T.rows, c.alpha, c.N};
+  launch_fwd(c, 2 * B * level, dsc);
 }
 
 void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t polys, int level,

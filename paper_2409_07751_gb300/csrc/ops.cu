@@ -211,6 +211,28 @@ static Ct relinearise(Ctx& c, const ckks_keys& keys, const DevBuf& d, size_t B, 
   return r;
 }
 
+// d: [B][3][l][N] at `level` -> relinearised and rescaled to level - 1 in one
+// division by P q_level (ModUp of d2, key product, merged ModDown + rescale)
+static Ct relin_rescale(Ctx& c, const ckks_keys& keys, const DevBuf& d, size_t B, int level,
+                        double scale) {
+  if (level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+  const int l = level + 1;
+  ConvTables& T = c.tables(level);
+  DevBuf d2(&c, B * l * c.N * 8);
+  CK_CUDA(cudaMemcpy2DAsync(d2.p, (size_t)l * c.N * 8, d.u64() + 2 * (size_t)l * c.N,
+                            3 * (size_t)l * c.N * 8, (size_t)l * c.N * 8, B,
+                            cudaMemcpyDeviceToDevice, c.stream));
+  DevBuf ext(&c, B * T.beta * T.rows * c.N * 8);
+  modup(c, d2.u64(), B, level, ext.u64());
+  d2.reset();
+  double s = scale / (double)c.mod[level];
+  const double dl = c.delta[level - 1];
+  if (fabs(s / dl - 1.0) < SNAP) s = dl;
+  Ct r = ct_alloc(c, B, level - 1, s);
+  relin_rescale_ext(c, d.u64(), ext.u64(), B, level, keys.relin.u64(), r->d.u64());
+  return r;
+}
+
 Ct op_mul_relin(Ctx& c, const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
   DevBuf d = tensor(c, a, b);
   return relinearise(c, keys, d, a.B, a.level, a.scale * b.scale);
@@ -220,8 +242,8 @@ Ct op_mul(Ctx& c, const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
   const int lv = std::min(a.level, b.level);
   Ct a2 = op_level_down(c, a, lv);
   Ct b2 = op_level_down(c, b, lv);
-  Ct m = op_mul_relin(c, keys, *a2, *b2);
-  return op_rescale(c, *m);
+  DevBuf d = tensor(c, *a2, *b2);
+  return relin_rescale(c, keys, d, a2->B, lv, a2->scale * b2->scale);
 }
 
 Ct op_mul_sum(Ctx& c, const ckks_keys& keys,
@@ -241,8 +263,7 @@ Ct op_mul_sum(Ctx& c, const ckks_keys& keys,
       k_tensor(c, a->d.u64(), b->d.u64(), acc.u64(), B, lv + 1, true);
     }
   }
-  Ct r = relinearise(c, keys, acc, B, lv, scale);
-  return op_rescale(c, *r);
+  return relin_rescale(c, keys, acc, B, lv, scale);
 }
 
 std::vector<Ct> op_rotate_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,

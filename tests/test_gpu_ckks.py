@@ -19,6 +19,8 @@ PARAMS = {
     "n16k": dict(log_n=14, n_scale=3, n_special=2),
     "n32k": dict(log_n=15, n_scale=4, n_special=1),
     "n64k": dict(log_n=16, n_scale=3, n_special=2),
+    # the digit layout the autotuner picks within log2 QP <= 1740 at N = 2^16
+    "n64k_a5": dict(log_n=16, n_scale=6, n_special=5, p_bits=48),
 }
 
 
@@ -35,8 +37,9 @@ _cache = {}
 def pair(G, name, steps=(1, -1, 3, -5)):
     if name not in _cache:
         p = PARAMS[name]
-        gctx = G.Context(p["log_n"], p["n_scale"], p["n_special"])
-        octx = O.Ctx(O.Params(p["log_n"], p["n_scale"], p["n_special"]))
+        pb = p.get("p_bits", 60)
+        gctx = G.Context(p["log_n"], p["n_scale"], p["n_special"], p_bits=pb)
+        octx = O.Ctx(O.Params(p["log_n"], p["n_scale"], p["n_special"], p_bits=pb))
         gk = G.Keys(gctx, 7, steps)
         ok = O.Keys(octx, 7, steps)
         _cache[name] = (gctx, octx, gk, ok)
@@ -46,8 +49,9 @@ def pair(G, name, steps=(1, -1, 3, -5)):
 @pytest.mark.parametrize("name", list(PARAMS))
 def test_context_matches_oracle(G, name):
     p = PARAMS[name]
-    gctx = G.Context(p["log_n"], p["n_scale"], p["n_special"])
-    octx = O.Ctx(O.Params(p["log_n"], p["n_scale"], p["n_special"]))
+    pb = p.get("p_bits", 60)
+    gctx = G.Context(p["log_n"], p["n_scale"], p["n_special"], p_bits=pb)
+    octx = O.Ctx(O.Params(p["log_n"], p["n_scale"], p["n_special"], p_bits=pb))
     assert (gctx.moduli == octx.moduli).all()
     assert (gctx.delta == octx.delta).all()
     gctx.close()
@@ -115,7 +119,7 @@ def _same(gc, oc):
     assert (gc.export()[0] == oc.data).all()
 
 
-@pytest.mark.parametrize("name", ["n32", "n4k", "n8k", "n16k", "n32k", "n64k"])
+@pytest.mark.parametrize("name", ["n32", "n4k", "n8k", "n16k", "n32k", "n64k", "n64k_a5"])
 def test_ops_bit_exact(G, name):
     gctx, octx, gk, ok = pair(G, name)
     L = gctx.L
@@ -198,3 +202,16 @@ def test_errors(G):
     with pytest.raises(G.CkksError) as e:
         G.encrypt(gctx, gk, [1e12], gctx.L, seed=1)
     assert e.value.code == -7
+
+
+def test_autotune_keyswitch_layout(G):
+    """The autotuner times only layouts within the log2 QP bound whose special
+    modulus covers the largest digit, and returns the fastest of them."""
+    alpha, p_bits, tried = G.autotune_keyswitch(16, 36, 1740, batch=2)
+    assert alpha in tried and len(tried) >= 3 and 1 not in tried  # alpha = 1: 37 digits
+    assert tried[alpha] == min(tried.values())
+    for a in tried:
+        p = min(60, (1740 - 60 - 36 * 40) // a)
+        assert p >= 30 and a * p >= 60 + (a - 1) * 40
+    assert p_bits == min(60, (1740 - 60 - 36 * 40) // alpha)
+    print("digit layouts (alpha: ms per HMult+HRot, batch 2):", tried)
