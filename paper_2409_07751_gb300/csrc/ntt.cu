@@ -33,14 +33,30 @@ constexpr int CHUNK_LOG = 12;
 constexpr int CHUNK = 1 << CHUNK_LOG;  // N2
 constexpr int ROW_THREADS = 512;       // one radix-8 group of each of two chunks per thread
 
-// CTAs per cluster (one row per cluster). Forward: two chunks per CTA (64 KiB
-// of shared memory, at most 64 registers per thread), so two CTAs share an SM;
-// inverse: four chunks per CTA, one CTA per SM.
+// CTAs per cluster (one row per cluster): two chunks (64 KiB of shared
+// memory) per CTA and at most 64 registers per thread, so two CTAs share an SM.
 template <int N1>
 __host__ __device__ constexpr int fwd_cs() { return N1 >= 4 ? N1 / 2 : 1; }
 template <int N1>
-__host__ __device__ constexpr int inv_cs() { return N1 >= 4 ? N1 / 4 : 1; }
-constexpr int FWD_CTAS_PER_SM = 2;
+__host__ __device__ constexpr int inv_cs() { return N1 >= 4 ? N1 / 2 : 1; }
+constexpr int CTAS_PER_SM = 2;
+
+// 32-bit address of this CTA's shared-memory location p in the cluster window
+// of CTA `rank` (a register instead of a 64-bit generic pointer per peer)
+__device__ __forceinline__ uint32_t dsmem_addr(const void* p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint64_t ld_dsmem(uint32_t addr) {
+  uint64_t v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_dsmem(uint32_t addr, uint64_t v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
   return a * w - __umul64hi(a, ws) * q;  // in [0, 2q) for any a < 2^64
@@ -482,14 +498,9 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
   const uint64_t w1s = GROW ? ~0ull / q : 0;  // floor(2^64 / q) for odd q
   const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
   const uint32_t g = threadIdx.x;
-  uint64_t* own[CS];
-  if constexpr (CS > 1) {
-    cg::cluster_group cl = cg::this_cluster();
+  uint32_t own[CS];  // cluster-window address of each CTA's chunks
 #pragma unroll
-    for (int k = 0; k < CS; k++) own[k] = cl.map_shared_rank(sm, k);
-  } else {
-    own[0] = sm;
-  }
+  for (int k = 0; k < CS; k++) own[k] = CS > 1 ? dsmem_addr(sm, k) : 0;
   constexpr uint32_t COLS = CHUNK / CS;
   for (uint32_t c = rank * COLS + g; c < (rank + 1) * COLS; c += ROW_THREADS) {
     uint64_t x[N1];
@@ -507,7 +518,13 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
       }
     }
 #pragma unroll
-    for (int s = 0; s < N1; s++) own[s / CPC][(s % CPC) * CHUNK + swz(c)] = x[s];
+    for (int s = 0; s < N1; s++) {
+      const uint32_t e = (s % CPC) * CHUNK + swz(c);
+      if constexpr (CS > 1)
+        st_dsmem(own[s / CPC] + e * 8, x[s]);
+      else
+        sm[e] = x[s];
+    }
   }
   if constexpr (CS > 1)
     cg::this_cluster().sync();
@@ -595,7 +612,7 @@ struct DescRelinRescale {
 // writes the results through the epilogue. The row never round-trips
 // through global memory.
 template <int N1, class D>
-__global__ void __launch_bounds__(ROW_THREADS, FWD_CTAS_PER_SM)
+__global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
     ntt_fwd_cl(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws,
                const ulonglong2* tw8, size_t nodes) {
   constexpr int CS = fwd_cs<N1>();
@@ -626,7 +643,7 @@ __global__ void __launch_bounds__(ROW_THREADS, FWD_CTAS_PER_SM)
 // its share of the columns, reading the elements from the owners' shared
 // memory, and writes the row scaled by post[row % P] (default N^-1).
 template <int N1>
-__global__ void __launch_bounds__(ROW_THREADS, 1)
+__global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
     ntt_inv_cl(uint64_t* base, int log_n, const int16_t* pattern, int P, const Mod* mods,
                const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
                const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts,
@@ -657,24 +674,26 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     __syncthreads();
 #pragma unroll
     for (int ls = 0; ls <= 9; ls += 3) {
-      round8x2<true>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8<true>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8<true>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
       __syncthreads();
     }
   }
-  const uint64_t* own[CS];
-  if constexpr (CS > 1) {
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
+  uint32_t own[CS];  // cluster-window address of each CTA's chunks
+  if constexpr (CS > 1) cg::this_cluster().sync();
 #pragma unroll
-    for (int k = 0; k < CS; k++) own[k] = cl.map_shared_rank(sm, k);
-  } else {
-    own[0] = sm;
-  }
+  for (int k = 0; k < CS; k++) own[k] = CS > 1 ? dsmem_addr(sm, k) : 0;
   constexpr uint32_t COLS = CHUNK / CS;
   for (uint32_t c = rank * COLS + g; c < (rank + 1) * COLS; c += ROW_THREADS) {
     uint64_t x[N1];
 #pragma unroll
-    for (int s = 0; s < N1; s++) x[s] = own[s / CPC][(s % CPC) * CHUNK + swz(c)];
+    for (int s = 0; s < N1; s++) {
+      const uint32_t e = (s % CPC) * CHUNK + swz(c);
+      if constexpr (CS > 1)
+        x[s] = ld_dsmem(own[s / CPC] + e * 8);
+      else
+        x[s] = sm[e];
+    }
 #pragma unroll
     for (int m = N1 / 2; m >= 1; m >>= 1) {
       const int t1 = N1 / (2 * m);
