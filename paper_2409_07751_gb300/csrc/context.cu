@@ -343,6 +343,7 @@ Ctx::~Ctx() {
   for (auto e : ev_pool) cudaEventDestroy(e);
   conv.clear();
   perms.clear();
+  scaled.clear();
   d_mod.reset();
   d_tw.reset();
   d_tws.reset();
@@ -510,6 +511,29 @@ ConvTables& Ctx::tables(int level) {
   auto& ref = *T;
   conv[level] = std::move(T);
   return ref;
+}
+
+const uint64_t* Ctx::scaled_consts(int r, int64_t k) {
+  auto key = std::make_pair(r, k);
+  auto it = scaled.find(key);
+  if (it != scaled.end()) return it->second->u64();
+  auto res = [&](uint64_t q) {  // k mod q for the signed k
+    const uint64_t m = (uint64_t)(k < 0 ? -(k + 1) : k) % q;
+    return k < 0 ? (q - 1 - m) % q : m;
+  };
+  std::vector<uint64_t> v(2 + 2 * (size_t)r);
+  const uint64_t qr = mod[r];
+  v[0] = mulmod_h(invmod_h(N % qr, qr), res(qr), qr);
+  v[1] = shoup_h(v[0], qr);
+  for (int t = 0; t < r; t++) {
+    const uint64_t q = mod[t];
+    v[2 + t] = mulmod_h(res(q), invmod_h(qr % q, q), q);
+    v[2 + r + t] = shoup_h(v[2 + t], q);
+  }
+  auto b = std::make_unique<DevBuf>(upload(this, v));
+  const uint64_t* p = b->u64();
+  scaled[key] = std::move(b);
+  return p;
 }
 
 uint64_t Ctx::galois(int64_t step) const {

@@ -124,6 +124,9 @@ struct Ctx {
   DevBuf d_md_ph, d_md_ph_s;      // [alpha][L+1]: Phat_a mod q_i
   std::map<int, std::unique_ptr<ConvTables>> conv;
   std::map<uint64_t, std::unique_ptr<DevBuf>> perms;  // galois -> uint32[N]
+  // rescale of k c by q_r: (r, k) -> [N^-1 k mod q_r, Shoup, k q_r^-1 mod q_t (t < r), Shoup]
+  std::map<std::pair<int, int64_t>, std::unique_ptr<DevBuf>> scaled;
+  const uint64_t* scaled_consts(int r, int64_t k);
   DevBuf d_flag;            // int32 device status word (encoding overflow)
   DevBuf d_rs_inv, d_rs_invs;     // [(L+1)][(L+1)]: q_l^-1 mod q_t at [l][t]
   DevBuf d_pmod;                  // [L+1]: P mod q_t
@@ -207,15 +210,23 @@ void ntt_inverse(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, 
 // Fused row kernels (N >= 8192): ModUp conversion in the forward NTT's
 // loads; ModDown / rescale subtract-and-scale in its stores.
 bool ntt_fused_available(const Ctx& c);
+// inverse NTT with a per-row post factor (instead of N^-1); out of place
+// when src is given (row i of period p read from src + p src_stride + i N)
 void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
-                      const uint64_t* post, const uint64_t* posts, size_t active = SIZE_MAX);
-void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, int level,
-                     uint64_t* ext);
+                      const uint64_t* post, const uint64_t* posts, size_t active = SIZE_MAX,
+                      const uint64_t* src = nullptr, size_t src_stride = 0);
+void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t d_stride, size_t B,
+                     int level, uint64_t* ext);
 // ov: [BK][N] overflow of the centred P -> Q conversion (k_overflow)
 void ntt_moddown_fused(Ctx& c, const uint64_t* acc, const uint8_t* ov, size_t BK, int level,
                        uint64_t* out);
 void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t polys, int level,
                        uint64_t* out);
+// rescale by q_level of k c (c: poly p at in + p in_stride, limbs 0..level);
+// `last` holds the coefficient form of k c_level; kinv[t] = k q_level^-1 mod q_t
+void ntt_rescale_scaled_fused(Ctx& c, const uint64_t* in, size_t in_stride, const uint64_t* last,
+                              size_t polys, int level, const uint64_t* kinv, const uint64_t* kinvs,
+                              uint64_t* out);
 // out[B][2][level][N] = (d_k q_level^-1 + (acc_k - Conv_D(acc_D)) M^-1), transformed
 void ntt_relin_rescale_fused(Ctx& c, const uint64_t* acc, const uint64_t* d, const uint8_t* ov,
                              size_t B, int level, uint64_t* out);
@@ -234,8 +245,9 @@ void k_int_to_rns(Ctx& c, const int64_t* v, uint64_t* out, size_t polys, int row
                   const int16_t* pattern);
 
 // ---- key switching (keyswitch.cu)
-// d: [B][l][N] NTT; ext out: [B][beta][l+alpha][N] NTT.
-void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext);
+// d: batch element b at d + b d_stride (default l N words), [l][N] NTT;
+// ext out: [B][beta][l+alpha][N] NTT.
+void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext, size_t d_stride = 0);
 // out[B][2][l][N] = ModDown(<sigma_g(ext), key>); galois 0 = no automorphism.
 void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
                    uint64_t galois, uint64_t* out);

@@ -251,23 +251,39 @@ __global__ void rr_finish_kernel(const uint64_t* acc, const uint64_t* d, const u
 
 }  // namespace
 
-void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext) {
+void modup(Ctx& c, const uint64_t* d, size_t B, int level, uint64_t* ext, size_t d_stride) {
   ConvTables& T = c.tables(level);
   const int l = T.l;
   if (c.alpha > MAX_ALPHA) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
+  if (d_stride == 0) d_stride = (size_t)l * c.N;
   DevBuf xc(&c, B * l * c.N * 8);
-  CK_CUDA(cudaMemcpyAsync(xc.p, d, xc.bytes, cudaMemcpyDeviceToDevice, c.stream));
   if (ntt_fused_available(c)) {
-    ntt_inverse_post(c, xc.u64(), B * l, c.iota(), l, T.xs_post.u64(), T.xs_post_s.u64());
-    ntt_modup_fused(c, xc.u64(), d, B, level, ext);
+    // the inverse transform reads d in place and writes the scaled coefficients to xc
+    ntt_inverse_post(c, xc.u64(), B * l, c.iota(), l, T.xs_post.u64(), T.xs_post_s.u64(), SIZE_MAX,
+                     d, d_stride);
+    ntt_modup_fused(c, xc.u64(), d, d_stride, B, level, ext);
     return;
+  }
+  {
+    Launch L_(c, K_COPY, 2.0 * (double)xc.bytes);
+    CK_CUDA(cudaMemcpy2DAsync(xc.p, (size_t)l * c.N * 8, d, d_stride * 8, (size_t)l * c.N * 8, B,
+                              cudaMemcpyDeviceToDevice, c.stream));
+  }
+  DevBuf dc;  // the unfused kernel reads d densely
+  const uint64_t* dd = d;
+  if (d_stride != (size_t)l * c.N) {
+    dc = DevBuf(&c, B * l * c.N * 8);
+    Launch L_(c, K_COPY, 2.0 * (double)dc.bytes);
+    CK_CUDA(cudaMemcpy2DAsync(dc.p, (size_t)l * c.N * 8, d, d_stride * 8, (size_t)l * c.N * 8, B,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    dd = dc.u64();
   }
   ntt_inverse(c, xc.u64(), B * l, c.iota(), l);
   const double W8 = (double)c.N * 8.0;
   {
   Launch L_(c, K_MODUP, W8 * (double)B * (2.0 * l + (double)T.beta * T.rows));
   modup_kernel<<<grid_for(B * T.beta * c.N), TPB, 0, c.stream>>>(
-      xc.u64(), d, ext, B, c.log_n, l, c.alpha, T.beta, T.rows, c.L, c.dmod(), T.dhinv.u64(),
+      xc.u64(), dd, ext, B, c.log_n, l, c.alpha, T.beta, T.rows, c.L, c.dmod(), T.dhinv.u64(),
       T.dhinv_s.u64(), T.dh.u64(), T.dh_s.u64());
   CK_CUDA(cudaGetLastError());
   }

@@ -371,10 +371,11 @@ struct DescPlain {
 // ModUp target row: sum_a xs[a][i] * [Dhat_a]_{m} mod m, then NTT; digit rows copy d.
 struct DescModUp {
   const uint64_t* xs;  // [B][l][N] coefficients already scaled by N^-1 Dhat^-1 (the iNTT post factor)
-  const uint64_t* d;   // [B][l][N] NTT form
+  const uint64_t* d;   // batch element b at d + b dstride: [l][N] NTT form
   uint64_t* ext;       // [B][beta][rows][N]
   const uint64_t* dh;  // [beta][alpha][rows]
   const uint64_t* dhs;
+  size_t dstride;
   int l, beta, rows, alpha, L;
   size_t N;
   __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
@@ -384,7 +385,7 @@ struct DescModUp {
     const int lo = j * alpha, hi = min((j + 1) * alpha, l);
     uint64_t* out = ext + (((size_t)b * beta + j) * rows + rr) * N;
     if (rr >= lo && rr < hi) {
-      const uint64_t* src = d + ((size_t)b * l + rr) * N;
+      const uint64_t* src = d + b * dstride + (size_t)rr * N;
       const size_t per = N / nparts;
       for (size_t i = part * per + threadIdx.x; i < (part + 1) * per; i += blockDim.x) out[i] = src[i];
       return false;
@@ -484,6 +485,45 @@ struct DescRescale {
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+  }
+};
+
+// Rescale of k c by q_level for an integer k, output row t of poly p:
+//   c_t [k q_level^-1]_{q_t} - NTT(centred(last) mod q_t) [q_level^-1]_{q_t},
+// with `last` the coefficient form of k c_level (the inverse transform's post
+// factor carries k) and c read in place (poly p at in + p in_stride).
+struct DescRescaleScaled {
+  const uint64_t* in;
+  size_t in_stride;
+  const uint64_t* last;   // [polys][N]
+  uint64_t* out;          // [polys][level][N]
+  const uint64_t* inv;    // [level]: q_level^-1 mod q_t
+  const uint64_t* invs;
+  const uint64_t* kinv;   // [level]: k q_level^-1 mod q_t
+  const uint64_t* kinvs;
+  uint64_t ql;
+  int level;
+  size_t N;
+  __device__ bool setup(uint32_t blk, Row& r, uint64_t*, uint32_t, uint32_t) const {
+    const int t = (int)(blk % level);
+    const size_t p = blk / level;
+    r.mi = t;
+    r.mid = out + (p * level + t) * N;
+    r.src = last + p * N;
+    r.src2 = in + p * in_stride + (size_t)t * N;
+    r.k = inv[t];
+    r.ks = invs[t];
+    r.k2 = kinv[t];
+    r.k2s = kinvs[t];
+    return true;
+  }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*) const {
+    const uint64_t x = r.src[i];
+    const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
+    return smod64(v, r.aux);
+  }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
+    r.mid[i] = sub_mod(mul_shoup(r.src2[i], r.k2, r.k2s, q), mul_shoup(v, r.k, r.ks, q), q);
   }
 };
 
@@ -644,7 +684,8 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
 // memory, and writes the row scaled by post[row % P] (default N^-1).
 template <int N1>
 __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
-    ntt_inv_cl(uint64_t* base, int log_n, const int16_t* pattern, int P, const Mod* mods,
+    ntt_inv_cl(uint64_t* base, const uint64_t* src, size_t src_stride, int log_n,
+               const int16_t* pattern, int P, const Mod* mods,
                const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
                const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts,
                const ulonglong2* tw8, size_t nodes) {
@@ -660,6 +701,8 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
   const uint64_t q = mods[mi].q, q2 = 2 * q;
   const ulonglong2* t8 = tw8 + (size_t)mi * nodes * 7;
   uint64_t* a = base + row * N;
+  // source rows: in place, or row i of period p at src + p src_stride + i N
+  const uint64_t* as = src ? src + (row / P) * src_stride + (row % P) * N : a;
   const uint64_t pv = post ? post[row % P] : ninv[mi];
   const uint64_t pvs = post ? posts[row % P] : ninvs[mi];
   const uint32_t g = threadIdx.x;
@@ -668,7 +711,7 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
   for (int lc = 0; lc < CPC; lc += 2) {
     const uint32_t chunk = rank * CPC + lc;
     uint64_t* s = sm + lc * CHUNK;
-    const uint64_t* ac = a + (size_t)chunk * CHUNK;
+    const uint64_t* ac = as + (size_t)chunk * CHUNK;
     for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS)
       s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))] = ac[i];
     __syncthreads();
@@ -754,7 +797,8 @@ void launch_fwd(Ctx& c, size_t n_rows, const D& d) {
 }
 
 void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, int P,
-                const uint64_t* post, const uint64_t* posts) {
+                const uint64_t* post, const uint64_t* posts, const uint64_t* src = nullptr,
+                size_t src_stride = 0) {
   if (n_rows == 0) return;
   const uint64_t* tw = c.d_itw.u64();
   const uint64_t* tws = c.d_itws.u64();
@@ -765,10 +809,10 @@ void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, i
   const int ln = c.log_n;
   const Mod* md = c.dmod();
   switch (c.log_n - CHUNK_LOG) {
-    case 1: launch_cl<2, inv_cs<2>()>(c, ntt_inv_cl<2>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 2: launch_cl<4, inv_cs<4>()>(c, ntt_inv_cl<4>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 3: launch_cl<8, inv_cs<8>()>(c, ntt_inv_cl<8>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 4: launch_cl<16, inv_cs<16>()>(c, ntt_inv_cl<16>, n_rows, base, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 1: launch_cl<2, inv_cs<2>()>(c, ntt_inv_cl<2>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 2: launch_cl<4, inv_cs<4>()>(c, ntt_inv_cl<4>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 3: launch_cl<8, inv_cs<8>()>(c, ntt_inv_cl<8>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 4: launch_cl<16, inv_cs<16>()>(c, ntt_inv_cl<16>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
 }
@@ -811,14 +855,15 @@ bool ntt_fused_available(const Ctx& c) {
 }
 
 void ntt_inverse_post(Ctx& c, uint64_t* base, size_t n_rows, const int16_t* pattern, int P,
-                      const uint64_t* post, const uint64_t* posts, size_t active) {
+                      const uint64_t* post, const uint64_t* posts, size_t active,
+                      const uint64_t* src, size_t src_stride) {
   const double rws = (double)std::min(active, n_rows);
   Launch L_(c, K_NTT_INV, 2.0 * rws * (double)c.N * 8.0, rws * ((double)(c.N / 2) * c.log_n + c.N));
-  launch_inv(c, n_rows, base, pattern, P, post, posts);
+  launch_inv(c, n_rows, base, pattern, P, post, posts, src, src_stride);
 }
 
-void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, int level,
-                     uint64_t* ext) {
+void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t d_stride, size_t B,
+                     int level, uint64_t* ext) {
   ConvTables& T = c.tables(level);
   if (c.alpha > MAX_SRC) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
   const double W8 = (double)c.N * 8.0;
@@ -827,7 +872,8 @@ void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t B, in
   const double out_rows = (double)B * ((double)T.beta * T.rows - T.l);
   Launch L_(c, K_MODUP_NTT, W8 * (double)B * (2.0 * T.l + (double)T.beta * T.rows),
             out_rows * ((double)(c.N / 2) * c.log_n + (double)c.alpha * c.N));
-  DescModUp dsc{xs, d, ext, T.dh.u64(), T.dh_s.u64(), T.l, T.beta, T.rows, c.alpha, c.L, c.N};
+  DescModUp dsc{xs, d, ext, T.dh.u64(), T.dh_s.u64(), d_stride, T.l, T.beta, T.rows, c.alpha, c.L,
+                c.N};
   launch_fwd(c, B * T.beta * T.rows, dsc);
 }
 
@@ -864,6 +910,18 @@ void ntt_rescale_fused(Ctx& c, const uint64_t* in, const uint64_t* last, size_t 
             (double)polys * level * ((double)(c.N / 2) * c.log_n + c.N));
   DescRescale dsc{in, last, out, c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
                   c.d_rs_invs.u64() + (size_t)level * (c.L + 1), c.mod[level], level, c.N};
+  launch_fwd(c, polys * level, dsc);
+}
+
+void ntt_rescale_scaled_fused(Ctx& c, const uint64_t* in, size_t in_stride, const uint64_t* last,
+                              size_t polys, int level, const uint64_t* kinv, const uint64_t* kinvs,
+                              uint64_t* out) {
+  const double W8 = (double)c.N * 8.0;
+  Launch L_(c, K_RESCALE_NTT, W8 * (double)polys * (1.0 + 2.0 * level),
+            (double)polys * level * ((double)(c.N / 2) * c.log_n + 2.0 * c.N));
+  DescRescaleScaled dsc{in, in_stride, last, out, c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
+                        c.d_rs_invs.u64() + (size_t)level * (c.L + 1), kinv, kinvs, c.mod[level],
+                        level, c.N};
   launch_fwd(c, polys * level, dsc);
 }
 

@@ -111,21 +111,42 @@ Ct op_mul_pt(Ctx& c, const ckks_ct& a, const uint64_t* pt, double pt_scale) {
   return op_rescale(c, *t);
 }
 
+// rescale by q_r of k a restricted to limbs 0..r (r <= a.level), the product
+// carrying `scale`: the limb drop and the integer factor are folded into the
+// rescale's transforms (same residues as mod-drop, multiply, rescale)
+static Ct scale_rescale(Ctx& c, const ckks_ct& a, int r, int64_t k, double scale) {
+  if (r < 1 || r > a.level) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+  if (!ntt_fused_available(c)) {
+    Ct b = r < a.level ? op_mod_drop(c, a, r) : nullptr;
+    Ct t = op_mul_int(c, b ? *b : a, k);
+    t->scale = scale;
+    return op_rescale(c, *t);
+  }
+  double s = scale / (double)c.mod[r];
+  const double d = c.delta[r - 1];
+  if (fabs(s / d - 1.0) < SNAP) s = d;
+  const size_t polys = a.B * 2;
+  const size_t stride = (size_t)(a.level + 1) * c.N;
+  const uint64_t* kc = c.scaled_consts(r, k);
+  DevBuf last(&c, polys * c.N * 8);
+  ntt_inverse_post(c, last.u64(), polys, c.iota() + r, 1, kc, kc + 1, SIZE_MAX,
+                   a.d.u64() + (size_t)r * c.N, stride);
+  Ct out = ct_alloc(c, a.B, r - 1, s);
+  ntt_rescale_scaled_fused(c, a.d.u64(), stride, last.u64(), polys, r, kc + 2, kc + 2 + r,
+                           out->d.u64());
+  return out;
+}
+
 Ct op_mul_const(Ctx& c, const ckks_ct& a, double v) {
   const double S = plain_scale(c, a.scale, a.level);
-  Ct t = op_mul_int(c, a, round_const(v, S));
-  t->scale = a.scale * S;
-  return op_rescale(c, *t);
+  return scale_rescale(c, a, a.level, round_const(v, S), a.scale * S);
 }
 
 Ct op_level_down(Ctx& c, const ckks_ct& a, int level) {
   if (level == a.level && fabs(a.scale / c.delta[level] - 1.0) < SNAP) return ct_copy(c, a);
   if (level >= a.level) throw Error(CKKS_ERR_LEVEL, "level_down needs a lower level");
-  Ct b = op_mod_drop(c, a, level + 1);
-  const double S = plain_scale(c, b->scale, level + 1);
-  Ct t = op_mul_int(c, *b, round_const(1.0, S));
-  t->scale = b->scale * S;
-  return op_rescale(c, *t);
+  const double S = plain_scale(c, a.scale, level + 1);
+  return scale_rescale(c, a, level + 1, round_const(1.0, S), a.scale * S);
 }
 
 Ct op_lincomb(Ctx& c, const std::vector<const ckks_ct*>& in, const std::vector<double>& k,
@@ -218,13 +239,9 @@ static Ct relin_rescale(Ctx& c, const ckks_keys& keys, const DevBuf& d, size_t B
   if (level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
   const int l = level + 1;
   ConvTables& T = c.tables(level);
-  DevBuf d2(&c, B * l * c.N * 8);
-  CK_CUDA(cudaMemcpy2DAsync(d2.p, (size_t)l * c.N * 8, d.u64() + 2 * (size_t)l * c.N,
-                            3 * (size_t)l * c.N * 8, (size_t)l * c.N * 8, B,
-                            cudaMemcpyDeviceToDevice, c.stream));
   DevBuf ext(&c, B * T.beta * T.rows * c.N * 8);
-  modup(c, d2.u64(), B, level, ext.u64());
-  d2.reset();
+  // d2 of batch element b sits at d + (3b + 2) l N
+  modup(c, d.u64() + 2 * (size_t)l * c.N, B, level, ext.u64(), 3 * (size_t)l * c.N);
   double s = scale / (double)c.mod[level];
   const double dl = c.delta[level - 1];
   if (fabs(s / dl - 1.0) < SNAP) s = dl;
@@ -272,7 +289,6 @@ std::vector<Ct> op_rotate_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
   const int l = a.level + 1;
   ConvTables& T = c.tables(a.level);
   DevBuf ext;
-  DevBuf c1;
   for (int64_t t : steps) {
     const uint64_t g = c.galois(t);
     if (g == 1) {
@@ -282,12 +298,9 @@ std::vector<Ct> op_rotate_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
     auto it = keys.galois.find(g);
     if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
     if (!ext.p) {
-      c1 = DevBuf(&c, a.B * l * c.N * 8);
-      CK_CUDA(cudaMemcpy2DAsync(c1.p, (size_t)l * c.N * 8, a.d.u64() + (size_t)l * c.N,
-                                2 * (size_t)l * c.N * 8, (size_t)l * c.N * 8, a.B,
-                                cudaMemcpyDeviceToDevice, c.stream));
       ext = DevBuf(&c, a.B * T.beta * T.rows * c.N * 8);
-      modup(c, c1.u64(), a.B, a.level, ext.u64());
+      // c1 of batch element b sits at a + (2b + 1) l N
+      modup(c, a.d.u64() + (size_t)l * c.N, a.B, a.level, ext.u64(), 2 * (size_t)l * c.N);
     }
     Ct ks = ct_alloc(c, a.B, a.level, a.scale);
     keyswitch_ext(c, ext.u64(), a.B, a.level, it->second->u64(), g, ks->d.u64());
