@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 # sets (low of y*w, high of y*w', low of t*q) and 10 adds, compares and selects
 # for the 64-bit lazy corrections.
 ALU_INSTR_PER_MODMUL = 20
+# DRAM bytes (read + write, ncu) over algorithmic bytes of one launch of the
+# fused ModUp forward NTT, measured on a 13-limb, batch-8 HMult (the bench's
+# launch is too large for a full capture); traffic scales with the units
+# processed, so a full launch's traffic is this ratio times its algorithmic
+# bytes. None until measured on the current kernel build.
+MODUP_TRAFFIC_RATIO = None
 
 METRIC = "encrypted KAN inferences/s"
 UNIT = "inferences/s"
@@ -144,7 +150,10 @@ def serve_arm(a):
     from paper_2409_07751_gb300 import workloads as W
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = G.Context(a.log_n, a.levels, 4)
+    alpha, p_bits = a.alpha, 60
+    if alpha == 0:
+        alpha, p_bits, _ = G.autotune_keyswitch(a.log_n, a.levels, a.max_qp_bits, batch=8)
+    ctx = G.Context(a.log_n, a.levels, alpha, p_bits=p_bits)
     ctx.set_stream(stream.cuda_stream)
     specs = [("kan_2_5_1", lambda n, s: W.uniform_inputs(n, 2, seed=s), 15, [3], (-4.0, 4.0), 0.5),
              ("kan_784_64_10", lambda n, s: W.blob_images(n, seed=s), 15, [3, 3, 3], None, 0.3),
@@ -178,7 +187,7 @@ def serve_arm(a):
         now = time.perf_counter() - t0
         while nxt < len(arrivals) and arrivals[nxt] <= now:
             mid, ct = request(nxt)
-            pending[srv.submit(mid, ct)] = arrivals[nxt]
+            pending[srv.submit(mid, ct)] = (arrivals[nxt], int(pick[nxt]))
             nxt += 1
         if not pending:
             time.sleep(max(0.0, min(0.01, arrivals[nxt] - now)))
@@ -189,13 +198,31 @@ def serve_arm(a):
         for rid in list(pending):
             out = srv.take(rid)
             if out is not None:
-                t_arr = pending.pop(rid)
-                lat.append((t_arr, done - t_arr))
+                t_arr, which = pending.pop(rid)
+                lat.append((t_arr, done - t_arr, which))
                 out.close()
     wall = time.perf_counter() - t0
     st = srv.status()
     warm = 5.0 if a.duration > 10.0 else 0.0  # arrivals in the first 5 s are warm-up
-    kept = [l for t, l in lat if t >= warm]
+    kept = [l for t, l, _ in lat if t >= warm]
+    names = [sp[0] for sp in specs]
+    per_model = {}
+    for j, name in enumerate(names):
+        lj = [l for t, l, w in lat if w == j and t >= warm]
+        per_model[name] = {"requests": len([1 for _, _, w in lat if w == j]),
+                           "p50_ms": 1000 * float(np.percentile(lj, 50)) if lj else None}
+
+    # the plain form on the same request mix: one request at a time through
+    # kan_infer, no batching across requests
+    n_plain = min(40, len(arrivals))
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    for i in range(n_plain):
+        mid, ct = request(i)
+        _, gm_i, keys_i, _, _ = models[pick[i]]
+        G.kan_infer(ctx, keys_i, gm_i, [ct]).close()
+        torch.cuda.synchronize()
+    plain_rate = n_plain / (time.perf_counter() - tp)
     print(json.dumps({
         "metric": "encrypted KAN inferences/s (serving mix)", "value": len(lat) / wall,
         "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
@@ -203,9 +230,13 @@ def serve_arm(a):
                        "p99": 1000 * float(np.percentile(kept, 99)),
                        "excluded_warmup_s": warm, "requests_counted": len(kept)},
         "requests": len(lat), "wall_s": wall, "hbm_peak_admitted_bytes": st["hbm_peak"],
+        "per_model": per_model,
+        "plain_form": {"value": plain_rate, "unit": UNIT, "requests": n_plain,
+                       "how": "one request at a time through kan_infer, same mix"},
         "config": {"workload": "Poisson serving mix", "rate_per_s": a.rate, "duration_s": a.duration,
                    "mix": {"kan_2_5_1": 0.5, "kan_784_64_10": 0.3, "kan_3072_64_10": 0.2},
-                   "n_poly": 1 << a.log_n, "levels": a.levels}}), flush=True)
+                   "n_poly": 1 << a.log_n, "levels": a.levels, "alpha": alpha,
+                   "p_bits": p_bits}}), flush=True)
 
 
 def kernel_arm(a):
@@ -592,8 +623,11 @@ def main():
         clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         alu_peak = sms * 4 * 32 * clk / ALU_INSTR_PER_MODMUL / 1e9
         alu = mm / (ms / 1000.0) / 1e9
+        traffic = None
+        if dom == "modup_ntt" and MODUP_TRAFFIC_RATIO is not None:
+            traffic = MODUP_TRAFFIC_RATIO * by / n
         roofline = {"kernel": dom, "bound": "alu", "achieved": alu, "peak": alu_peak,
-                    "unit": "Gmodmul/s", "frac": alu / alu_peak, "traffic": None, "hbm": hbm,
+                    "unit": "Gmodmul/s", "frac": alu / alu_peak, "traffic": traffic, "hbm": hbm,
                     "modmul_per_launch": mm / n}
     else:
         roofline = dict({"kernel": dom, "bound": "hbm", "traffic": None}, **hbm)

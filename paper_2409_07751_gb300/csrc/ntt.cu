@@ -69,14 +69,6 @@ __device__ __forceinline__ void ct_lazy(uint64_t& x, uint64_t& y, uint64_t w, ui
   x = u + t;
   y = u - t + q2;
 }
-// x, y in [0, 2q) -> [0, 2q)
-__device__ __forceinline__ void gs_lazy(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
-                                        uint64_t q, uint64_t q2) {
-  const uint64_t u = x, v = y;
-  uint64_t s = u + v;
-  x = s >= q2 ? s - q2 : s;
-  y = shoup_lazy(u - v + q2, w, ws, q);
-}
 // Shoup product whose quotient is estimated from three of the four 32-bit
 // partial products of y * ws (the low product and the carries out of the
 // middle ones are dropped): with y ws = y1 s1 2^64 + (y1 s0 + y0 s1) 2^32 +
@@ -90,6 +82,17 @@ __device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_
   return y * w - Q * q;
 }
 
+// x, y in [0, 2q) -> [0, 2q)
+// (the product by the three-product quotient lies in [0, 4q); one
+// conditional subtraction brings it back below 2q)
+__device__ __forceinline__ void gs_lazy(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
+                                        uint64_t q, uint64_t q2) {
+  const uint64_t u = x, v = y;
+  uint64_t s = u + v;
+  x = s >= q2 ? s - q2 : s;
+  const uint64_t t = shoup_approx(u - v + q2, w, ws, q);
+  y = t >= q2 ? t - q2 : t;
+}
 // Forward butterfly without the reduction of x, for moduli q < 2^50: with
 // t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
 // from inputs below q stay below 65q < 2^57.
@@ -228,111 +231,6 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
   for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
 }
 
-// The same round on group g of two chunks at once (chunk and chunk + 1, in
-// shared memory at sm and sm + CHUNK): two independent dependency chains per
-// thread, interleaved by the compiler.
-template <bool INV, bool GROW = false>
-__device__ __forceinline__ void round8x2(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
-                                         int log_n, const ulonglong2* t8, uint64_t q,
-                                         uint64_t q2) {
-  const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
-  const uint32_t base = (blk8 << (ls + 3)) + r;
-  const uint32_t per = CHUNK >> (ls + 3);
-  const uint32_t nb = node_base(ls, log_n);
-  uint64_t x[2][8];
-  ulonglong2 tt[2][7];
-#pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const ulonglong2* T = t8 + (size_t)(nb + (chunk + h) * per + blk8) * 7;
-#pragma unroll
-    for (int k = 0; k < 8; k++) x[h][k] = sm[h * CHUNK + swz(base + ((uint32_t)k << ls))];
-#pragma unroll
-    for (int k = 0; k < 7; k++) tt[h][k] = T[k];
-  }
-  if (!INV) {
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-#pragma unroll
-      for (int h = 0; h < 2; h++) ct_step<GROW>(x[h][k], x[h][k + 4], tt[h][0].x, tt[h][0].y, q, q2);
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      ct_step<GROW>(x[h][0], x[h][2], tt[h][1].x, tt[h][1].y, q, q2);
-      ct_step<GROW>(x[h][1], x[h][3], tt[h][1].x, tt[h][1].y, q, q2);
-      ct_step<GROW>(x[h][4], x[h][6], tt[h][2].x, tt[h][2].y, q, q2);
-      ct_step<GROW>(x[h][5], x[h][7], tt[h][2].x, tt[h][2].y, q, q2);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-#pragma unroll
-      for (int h = 0; h < 2; h++)
-        ct_step<GROW>(x[h][2 * k], x[h][2 * k + 1], tt[h][3 + k].x, tt[h][3 + k].y, q, q2);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-#pragma unroll
-      for (int h = 0; h < 2; h++)
-        gs_lazy(x[h][2 * k], x[h][2 * k + 1], tt[h][3 + k].x, tt[h][3 + k].y, q, q2);
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      gs_lazy(x[h][0], x[h][2], tt[h][1].x, tt[h][1].y, q, q2);
-      gs_lazy(x[h][1], x[h][3], tt[h][1].x, tt[h][1].y, q, q2);
-      gs_lazy(x[h][4], x[h][6], tt[h][2].x, tt[h][2].y, q, q2);
-      gs_lazy(x[h][5], x[h][7], tt[h][2].x, tt[h][2].y, q, q2);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-#pragma unroll
-      for (int h = 0; h < 2; h++) gs_lazy(x[h][k], x[h][k + 4], tt[h][0].x, tt[h][0].y, q, q2);
-  }
-#pragma unroll
-  for (int h = 0; h < 2; h++)
-#pragma unroll
-    for (int k = 0; k < 8; k++) sm[h * CHUNK + swz(base + ((uint32_t)k << ls))] = x[h][k];
-}
-
-// column transform of N1 elements (stride CHUNK) in registers
-// forward: x[s] = ld(c + s*CHUNK) -> stages -> mid[c + s*CHUNK] (lazy, [0,4q))
-template <int N1, class D, class R>
-__device__ __forceinline__ void column_fwd(const D& d, const R& r, uint32_t c, const uint64_t* w,
-                                           const uint64_t* ws, uint64_t q, uint64_t q2,
-                                           const uint64_t* kc) {
-  uint64_t x[N1];
-#pragma unroll
-  for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc);
-#pragma unroll
-  for (int m = 1; m < N1; m <<= 1) {
-    const int t1 = N1 / (2 * m);
-#pragma unroll
-    for (int i = 0; i < m; i++) {
-      const uint64_t wv = w[m + i], wsv = ws[m + i];
-#pragma unroll
-      for (int jj = 0; jj < t1; jj++) ct_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < N1; s++) r.mid[c + (size_t)s * CHUNK] = x[s];
-}
-
-template <int N1>
-__device__ __forceinline__ void column_inv(uint64_t* a, const uint64_t* w, const uint64_t* ws,
-                                           uint64_t q, uint64_t q2, uint64_t post, uint64_t posts) {
-  uint64_t x[N1];
-#pragma unroll
-  for (int s = 0; s < N1; s++) x[s] = a[(size_t)s * CHUNK];
-#pragma unroll
-  for (int m = N1 / 2; m >= 1; m >>= 1) {
-    const int t1 = N1 / (2 * m);
-#pragma unroll
-    for (int i = 0; i < m; i++) {
-      const uint64_t wv = w[m + i], wsv = ws[m + i];
-#pragma unroll
-      for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], wv, wsv, q, q2);
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < N1; s++) a[(size_t)s * CHUNK] = mul_shoup(x[s], post, posts, q);
-}
-
 // Per-CTA row description produced by a descriptor's setup().
 struct Row {
   int mi;            // modulus index
@@ -362,7 +260,7 @@ struct DescPlain {
     r.mid = base + (size_t)blk * N;
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*) const { return r.mid[i]; }
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*, bool) const { return r.mid[i]; }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
     r.mid[i] = v;
   }
@@ -401,9 +299,14 @@ struct DescModUp {
     }
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc) const {
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
     const uint64_t m = r.aux;
     uint64_t acc = 0;
+    if (grow) {  // lazy: each term below 4m, the sum below 4 alpha m (the transform tolerates it)
+      for (int a = 0; a < r.n_src; a++)
+        acc += shoup_approx(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
+      return acc;
+    }
     for (int a = 0; a < r.n_src; a++)
       acc = add_mod(acc, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
     return acc;
@@ -445,7 +348,7 @@ struct DescModDown {
     }
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc) const {
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
     const uint64_t m = r.aux;
     uint64_t s = 0;
     for (int a = 0; a < r.n_src; a++)
@@ -478,7 +381,7 @@ struct DescRescale {
     r.ks = invs[t];
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*) const {
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*, bool) const {
     const uint64_t x = r.src[i];
     const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
     return smod64(v, r.aux);
@@ -517,7 +420,7 @@ struct DescRescaleScaled {
     r.k2s = kinvs[t];
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*) const {
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*, bool) const {
     const uint64_t x = r.src[i];
     const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
     return smod64(v, r.aux);
@@ -545,7 +448,7 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
   for (uint32_t c = rank * COLS + g; c < (rank + 1) * COLS; c += ROW_THREADS) {
     uint64_t x[N1];
 #pragma unroll
-    for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc);
+    for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc, GROW);
 #pragma unroll
     for (int m = 1; m < N1; m <<= 1) {
       const int t1 = N1 / (2 * m);
@@ -630,7 +533,7 @@ struct DescRelinRescale {
     }
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc) const {
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
     const uint64_t m = r.aux;
     uint64_t s = 0;
     for (int a = 0; a < r.n_src; a++)
