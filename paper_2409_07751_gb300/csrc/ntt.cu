@@ -83,15 +83,12 @@ __device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_
 }
 
 // x, y in [0, 2q) -> [0, 2q)
-// (the product by the three-product quotient lies in [0, 4q); one
-// conditional subtraction brings it back below 2q)
 __device__ __forceinline__ void gs_lazy(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
   const uint64_t u = x, v = y;
   uint64_t s = u + v;
   x = s >= q2 ? s - q2 : s;
-  const uint64_t t = shoup_approx(u - v + q2, w, ws, q);
-  y = t >= q2 ? t - q2 : t;
+  y = shoup_lazy(u - v + q2, w, ws, q);
 }
 // Forward butterfly without the reduction of x, for moduli q < 2^50: with
 // t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
