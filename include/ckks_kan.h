@@ -180,7 +180,10 @@ int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct** out);
  * on the GPU race, so serialize them. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, size_t batch, int level,
                          uint64_t* d_out);
-/* Eq. 8 complete: bring both to the lower level, multiply, relinearise, rescale. */
+/* Eq. 8 complete: bring both to the lower level, multiply, relinearise and
+ * rescale. The relinearisation's division by P and the rescale's division by
+ * q_level are one rounded division by P q_level (centred basis conversion of
+ * the dropped limbs), level - 1 on output. */
 int ckks_mul(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const ckks_ct* b,
              ckks_ct** out);
 /* Eq. 9: slot-wise product with real vector v (n values, rest 0) encoded at

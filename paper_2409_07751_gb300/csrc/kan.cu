@@ -628,7 +628,7 @@ extern "C" {
 int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layers,
                      kan_model** out) {
   try {
-    if (!ctx || !layers || !out || n_layers == 0) return CKKS_ERR_INVALID_ARG;
+    if (!ctx || !layers || !out || n_layers == 0) throw Error(CKKS_ERR_INVALID_ARG, "bad argument");
     auto M = std::make_unique<kan_model>();
     M->ctx = &ctx->c;
     const int S = (int)(ctx->c.N / 2);
@@ -637,9 +637,10 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
       if (d.n_in < 1 || d.n_out < 1 || d.G < 1 || d.k < 0 || !d.coef || !d.w_s || !d.w_b ||
           !d.silu_cheb || d.silu_degree < 1 || !d.comp || d.n_comp < 1 || !(d.R > 0) ||
           !(d.silu_hi > d.silu_lo) || !(d.grid_hi > d.grid_lo))
-        return CKKS_ERR_INVALID_ARG;
+        throw Error(CKKS_ERR_INVALID_ARG, "invalid layer description");
       for (int i = 0; i < d.n_comp; i++)
-        if (d.comp[i] < 1 || d.comp[i] > 8) return CKKS_ERR_INVALID_ARG;
+        if (d.comp[i] < 1 || d.comp[i] > 8)
+          throw Error(CKKS_ERR_INVALID_ARG, "comparison orders must be 1..8");
       Layer L;
       L.n_in = d.n_in;
       L.n_out = d.n_out;
@@ -665,10 +666,11 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
         L.K = 1;
         L.n_c = L.n_in;
       } else {
-        if (li != 0) return CKKS_ERR_UNSUPPORTED;  // only the client can split an input
+        if (li != 0)  // only the client can split an input
+          throw Error(CKKS_ERR_UNSUPPORTED, "a hidden layer does not fit the slots");
         L.K = (L.n_in + cap - 1) / cap;
         L.n_c = cap;
-        if (L.K > 16) return CKKS_ERR_UNSUPPORTED;
+        if (L.K > 16) throw Error(CKKS_ERR_UNSUPPORTED, "more than 16 input chunks");
       }
       // per chunk ch (inputs ch*n_c + i, zero beyond n_in): W_b columns and
       // W_f[o][m n_c + i] = w_s[o][i] c[o][i][m]  (W' P, Algorithm 3 / Eq. 13)

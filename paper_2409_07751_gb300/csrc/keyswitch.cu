@@ -88,9 +88,36 @@ __global__ void __launch_bounds__(IP_THREADS)
       kw[(2 * j + 1) * IP_THREADS + tid] = key[(((size_t)j * 2 + 1) * n_qp + mi) * N + n];
     }
     const bool lazy = m.s >= 33;
+    const bool split = lazy && m.s <= 48;
     for (size_t b = 0; b < B; b++) {
       const uint64_t* e0 = ext + ((b * beta) * rows + r) * N + src;
-      if (lazy) {
+      if (split) {
+        // e, k < 2^48: e k = e0 k0 + (e0 k1 + e1 k0) 2^32 + e1 k1 2^64 with
+        // 16-bit e1, k1; the partial products are summed apart (the halves
+        // of e0 k0 separately, so no sum carries) and combined once
+        uint64_t a0[2] = {0, 0}, a1[2] = {0, 0}, bm[2] = {0, 0}, cc[2] = {0, 0};
+        for (int j = 0; j < beta; j++) {
+          const uint64_t e = e0[(size_t)j * rows * N];
+          const uint32_t el = (uint32_t)e, eh = (uint32_t)(e >> 32);
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const uint64_t k = kw[(2 * j + h) * IP_THREADS + tid];
+            const uint32_t kl = (uint32_t)k, kh = (uint32_t)(k >> 32);
+            const uint64_t p = (uint64_t)el * kl;
+            a0[h] += (uint32_t)p;
+            a1[h] += p >> 32;
+            bm[h] += (uint64_t)el * kh + (uint64_t)eh * kl;
+            cc[h] += (uint64_t)eh * kh;
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const uint64_t mid = a1[h] + bm[h];
+          const uint64_t lo = a0[h] + (mid << 32);
+          const uint64_t hi = cc[h] + (mid >> 32) + (lo < a0[h] ? 1 : 0);
+          acc[((b * 2 + h) * rows + r) * N + n] = reduce_wide(lo, hi, m);
+        }
+      } else if (lazy) {
         uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
         for (int j = 0; j < beta; j++) {
           const uint64_t e = e0[(size_t)j * rows * N];

@@ -174,6 +174,12 @@ def test_level_exhausted_is_an_error(G):
     assert e.value.code == -2
     with pytest.raises(G.CkksError):
         G.kan_infer(gctx, gk, gm, [])
+    # a hidden layer wider than the slots allow cannot be split by the server
+    wide = calibrate.calibrate(W.make_model("t", widths=[3, 40, 2], G=3, k=2),
+                               W.uniform_inputs(64, 3), 7, [1])
+    with pytest.raises(G.CkksError) as e:
+        G.Model(gctx, wide)
+    assert e.value.code == -9 and "hidden layer" in str(e.value)
 
 
 def test_kan_4_8_4_1_batched_uneven_levels(G):
