@@ -46,7 +46,26 @@ MODUP_TRAFFIC_RATIO = 390.0 / 394.3
 
 METRIC = "encrypted KAN inferences/s"
 UNIT = "inferences/s"
-WORKLOAD = "encrypted KAN [4,8,4,1] G=5 k=3, CKKS N=2^16, 36 levels, batch 64 at uneven levels"
+# the configurations: c2 is the headline workload, the others are measured on request
+WORKLOADS = {
+    "c1": dict(desc="encrypted KAN [2,5,1] G=5 k=3, plain method (one input per launch), CKKS "
+                    "N=2^15, q0 + 18 x 40-bit primes, one 60-bit special prime",
+               model="kan_2_5_1", inputs="uniform", log_n=15, levels=18, alpha=1, batch=1,
+               degree=15, comp=[3], fixed=(-4.0, 4.0), uneven=False),
+    "c2": dict(desc="encrypted KAN [4,8,4,1] G=5 k=3, CKKS N=2^16, 36 levels, batch 64 at "
+                    "uneven levels",
+               model="kan_4_8_4_1", inputs="uniform", log_n=16, levels=36, alpha=0, batch=64,
+               degree=27, comp=[3], fixed=None, uneven=True),
+    "c3": dict(desc="encrypted KAN [784,64,10] G=5 k=3 on synthetic 28x28 blob images, CKKS "
+                    "N=2^16, 36 levels, batch 32",
+               model="kan_784_64_10", inputs="blob", log_n=16, levels=36, alpha=0, batch=32,
+               degree=15, comp=[3, 3, 3], fixed=None, uneven=False),
+    "c4": dict(desc="encrypted KAN [3072,64,10] G=10 k=3 on synthetic 3x32x32 images (two "
+                    "ciphertexts per image), CKKS N=2^16, 36 levels, batch 16",
+               model="kan_3072_64_10", inputs="cifar", log_n=16, levels=36, alpha=0, batch=16,
+               degree=15, comp=[3, 3, 3], fixed=None, uneven=False),
+}
+WORKLOAD = WORKLOADS["c2"]["desc"]
 
 
 def args_():
@@ -73,6 +92,9 @@ def args_():
                    help="key-switching digit size (special primes); 0 = autotune within --max-qp-bits")
     p.add_argument("--max-qp-bits", type=int, default=1740,
                    help="bound on log2(QP) for the digit-layout autotuner (128-bit budget)")
+    p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                   help="configuration to time (c2, the default, is the headline workload; "
+                        "sets log-n, levels, batch and alpha)")
     p.add_argument("--table3", action="store_true",
                    help="one KAN layer per (n_i, g, k) shape: lazy combination vs the naive method")
     p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
@@ -296,9 +318,12 @@ def kernel_arm(a):
 
 
 def config(a):
-    return {"workload": WORKLOAD, "model": "kan_4_8_4_1", "n_poly": 1 << a.log_n,
-            "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": 27, "comparison": "f_3",
-            "input_levels": "uniform over [L - slack, L]", "parallelism": "replicas (request sharding)",
+    wl = workload(a)
+    return {"workload": wl["desc"], "model": wl["model"], "n_poly": 1 << a.log_n,
+            "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": wl["degree"],
+            "comparison": " o ".join("f_%d" % n for n in wl["comp"]),
+            "input_levels": "uniform over [L - slack, L]" if wl["uneven"] else "all at L",
+            "parallelism": "replicas (request sharding)",
             "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)",
             "schedule": "CUDA graph per layer" if getattr(a, "graphs", False) else "eager",
             "alpha": getattr(a, "alpha", 4), "p_bits": getattr(a, "p_bits", 60),
@@ -323,12 +348,26 @@ def reduce_max(value, dist, device):
     return float(t.item())
 
 
+def workload(a):
+    return WORKLOADS[getattr(a, "workload", "c2")]
+
+
 def model_and_inputs(a, rank):
     from paper_2409_07751_gb300 import workloads as W
-    model = W.make_model("kan_4_8_4_1")
-    Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
-    X = W.uniform_inputs(a.batch, 4, seed=shard_plan(rank, a.batch)["input_seed"])
+    wl = workload(a)
+    model = W.make_model(wl["model"])
+    n_in = model[0]["n_in"]
+    gen = {"uniform": lambda n, s: W.uniform_inputs(n, n_in, seed=s),
+           "blob": lambda n, s: W.blob_images(n, seed=s),
+           "cifar": lambda n, s: W.cifar_like_images(n, seed=s)}[wl["inputs"]]
+    Xcal = gen(256 if wl["inputs"] == "uniform" else 64, W.SEED_INPUTS + 1000)
+    X = gen(a.batch, shard_plan(rank, a.batch)["input_seed"])
     return model, Xcal, X
+
+
+def calibrate_for(a, calibrate, model, Xcal):
+    wl = workload(a)
+    return calibrate(model, Xcal, wl["degree"], wl["comp"], fixed_range=wl["fixed"])
 
 
 # ------------------------------------------------------------------ clocks
@@ -410,7 +449,10 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
     def skip_modup(ctx, poly, level):
         return None
 
-    small = O.Ctx(O.Params(11, a.levels, 4))
+    # the [2,5,1] and [4,8,4,1] schedules are the same at N = 2^11; the image
+    # models' packing and chunking depend on the ring, so they count on theirs
+    small = O.Ctx(O.Params(11 if workload(a)["model"] in ("kan_2_5_1", "kan_4_8_4_1") else a.log_n,
+                           a.levels, 4))
 
     class Fake:
         pass
@@ -419,6 +461,9 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
     fk.relin = None
     fk.galois = {small.galois(t): None for t in kan_he.model_rotations(model_he, small.slots)}
     x = O.Ct(np.zeros((2, a.levels + 1, small.N), np.uint64), a.levels, small.delta[a.levels])
+    K = kan_he.chunking(model_he[0], small.slots)[0]
+    if K > 1:
+        x = [x] * K
     O._ks, O._ks_rescale, O._modup = count_ks, count_ksr, skip_modup
     try:
         kan_he.infer(small, fk, x, model_he)
@@ -435,6 +480,9 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
     data = np.stack([np.stack([rng.integers(0, ctx.q[t], ctx.N, dtype=np.uint64)
                                for t in range(a.levels + 1)]) for _ in range(2)])
     ct = O.Ct(data, a.levels, ctx.delta[a.levels])
+    K = kan_he.chunking(model_he[0], ctx.slots)[0]
+    if K > 1:
+        ct = [ct] * K
     rates = []
     for it in range(warmup + steps):
         done = {"n": 0}
@@ -500,7 +548,7 @@ def reference_arm(a):
     if not a.alpha:
         a.alpha, a.p_bits = 5, 48
     model, Xcal, _ = model_and_inputs(a, 0)
-    m = OC.calibrate(model, Xcal, 27, [3])
+    m = calibrate_for(a, OC.calibrate, model, Xcal)
     per_step = max(5.0, min(a.cpu_budget, 150.0 / max(1, a.steps + a.warmup)))
     t0 = time.perf_counter()
     v, sample, procs = oracle_all_cores(m, a, per_step, steps=a.steps, warmup=a.warmup)
@@ -519,6 +567,11 @@ def reference_arm(a):
 # ------------------------------------------------------------------ GPU arm
 def main():
     a = args_()
+    wl = workload(a)
+    if a.workload != "c2":
+        a.log_n, a.levels, a.batch = wl["log_n"], wl["levels"], wl["batch"]
+        if a.alpha == 0:
+            a.alpha = wl["alpha"]
     if a.impl == "reference":
         return reference_arm(a)
     if a.kernel:
@@ -555,18 +608,27 @@ def main():
     ctx = G.Context(a.log_n, a.levels, a.alpha, p_bits=a.p_bits, device=local)
     ctx.set_stream(stream.cuda_stream)
     model, Xcal, X = model_and_inputs(a, rank)
-    m = G.calibrate(model, Xcal, 27, [3])
+    m = calibrate_for(a, G.calibrate, model, Xcal)
     gm = G.Model(ctx, m)
     gm.set_graphs(a.graphs)
     depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
     slack = a.levels - depth
     plan = shard_plan(rank, a.batch)
-    levels = W.uneven_levels(a.batch, a.levels, slack, seed=plan["level_seed"])
+    if wl["uneven"]:
+        levels = W.uneven_levels(a.batch, a.levels, slack, seed=plan["level_seed"])
+    else:
+        levels = np.full(a.batch, a.levels)
     keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+    K = gm.layer_chunks(0)[0]
+
+    def packed(rows):  # the first layer's rows of each input (K chunks of a wide input)
+        return np.concatenate([np.atleast_2d(gm.pack_input(r)) for r in rows])
+
     cts = []
     for lv in sorted(set(int(x) for x in levels)):
         sel = np.nonzero(levels == lv)[0]
-        cts.append(G.encrypt(ctx, keys, X[sel], lv, W.SEED_ENC, first_index=int(sel[0]) + plan["first_index"]))
+        cts.append(G.encrypt(ctx, keys, packed(X[sel]), lv, W.SEED_ENC,
+                             first_index=K * (int(sel[0]) + plan["first_index"])))
 
     def step():
         out = G.kan_infer(ctx, keys, gm, cts)
@@ -661,7 +723,7 @@ def main():
     # ---------------- the plain form: one request at a time, fusion off
     plain = None
     if not a.no_micro:
-        one = G.encrypt(ctx, keys, X[:1], a.levels, 9, 0)
+        one = G.encrypt(ctx, keys, packed(X[:1]), a.levels, 9, 0)
         gm.set_graphs(False)
         plain = {}
         for fused in (False, True):
@@ -756,7 +818,7 @@ def main():
             "slack": slack}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import calibrate as OC
-        mo = OC.calibrate(model, Xcal, 27, [3])
+        mo = calibrate_for(a, OC.calibrate, model, Xcal)
         v1, sample1, _ = oracle_sample(mo, a, a.cpu_budget)
         v, sample, procs = oracle_all_cores(mo, a, a.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
