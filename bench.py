@@ -644,9 +644,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---------------- timed region
+    # ---------------- timed region (no per-launch events: they cost time
+    # between small kernels), then the same K steps again with per-launch
+    # CUDA events for the per-kind durations of the roofline
     before = ctx.launch_counts()
-    ctx.profile(True)
     clk = Clocks(local)
     barrier()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
@@ -657,13 +658,23 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    prof = ctx.profile_collect()
-    ctx.profile(False)
     after = ctx.launch_counts()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
     elapsed = reduce_max(ev[0].elapsed_time(ev[-1]), dist, "cuda")
     launches = sum(after[k] - before[k] for k in after if k != "copy")
     value = world * a.batch * a.steps / (elapsed / 1000.0)
+    ctx.profile(True)
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i in range(a.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    profiled_ms = p0.elapsed_time(p1)
+    prof = ctx.profile_collect()
+    ctx.profile(False)
 
     # roofline of the dominant kernel kind
     peaks = {}
@@ -697,6 +708,7 @@ def main():
     roofline.update({"algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
                      "share_of_kernel_time": ms / total_ms,
                      "kernel_ms_per_step": total_ms / a.steps,
+                     "profiled_ms_per_step": profiled_ms / a.steps,
                      "copy_ms_per_step": prof.get("copy", (0.0,))[0] / a.steps})
     shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])}
     # per kind: ms per step, algorithmic GB/s and G modmul/s over its launches
@@ -801,8 +813,16 @@ def main():
         torch.cuda.synchronize()
         barrier()
         el = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+        # the host-to-device part alone (import of the step's inputs)
+        t_h = time.perf_counter()
+        for _ in range(2):
+            for b, B, lv, sc in hin:
+                G.Ciphertext.import_from(ctx, b.data_ptr(), B, lv, sc).close()
+        torch.cuda.synchronize()
+        h2d_ms = (time.perf_counter() - t_h) * 1000.0 / 2
         e2e = {"value": world * a.batch * a.steps / (el / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_words * 8,
+               "h2d_ms_per_step": h2d_ms, "h2d_GBps": h2d / (h2d_ms / 1000.0) / 1e9,
                "path": "ckks_ct_import -> kan_infer -> ckks_ct_export"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
