@@ -59,11 +59,11 @@ WORKLOADS = {
     "c3": dict(desc="encrypted KAN [784,64,10] G=5 k=3 on synthetic 28x28 blob images, CKKS "
                     "N=2^16, 36 levels, batch 32",
                model="kan_784_64_10", inputs="blob", log_n=16, levels=36, alpha=0, batch=32,
-               degree=15, comp=[3, 3, 3], fixed=None, uneven=False),
+               degree=15, comp=[3, 3, 3, 3], fixed=None, uneven=False),
     "c4": dict(desc="encrypted KAN [3072,64,10] G=10 k=3 on synthetic 3x32x32 images (two "
                     "ciphertexts per image), CKKS N=2^16, 36 levels, batch 16",
                model="kan_3072_64_10", inputs="cifar", log_n=16, levels=36, alpha=0, batch=16,
-               degree=15, comp=[3, 3, 3], fixed=None, uneven=False),
+               degree=15, comp=[3, 3, 3, 3], fixed=None, uneven=False),
 }
 WORKLOAD = WORKLOADS["c2"]["desc"]
 
@@ -179,8 +179,9 @@ def serve_arm(a):
     ctx = G.Context(a.log_n, a.levels, alpha, p_bits=p_bits)
     ctx.set_stream(stream.cuda_stream)
     specs = [("kan_2_5_1", lambda n, s: W.uniform_inputs(n, 2, seed=s), 15, [3], (-4.0, 4.0), 0.5),
-             ("kan_784_64_10", lambda n, s: W.blob_images(n, seed=s), 15, [3, 3, 3], None, 0.3),
-             ("kan_3072_64_10", lambda n, s: W.cifar_like_images(n, seed=s), 15, [3, 3, 3], None, 0.2)]
+             ("kan_784_64_10", lambda n, s: W.blob_images(n, seed=s), 15, [3, 3, 3, 3], None, 0.3),
+             ("kan_3072_64_10", lambda n, s: W.cifar_like_images(n, seed=s), 15, [3, 3, 3, 3], None,
+              0.2)]
     srv = G.Server(ctx, int(200e9))
     models = []
     for i, (name, gen, deg, comp, fr, share) in enumerate(specs):
@@ -812,6 +813,31 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        el_serial = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+        # pipelined: the next batch's inputs are copied on a second stream
+        # while the current batch computes (the library's stream waits for
+        # each copy through an event); every copy is inside the timed region
+        cstream = torch.cuda.Stream()
+
+        def imports():
+            return [G.Ciphertext.import_from_async(ctx, b.data_ptr(), B, lv, sc, cstream.cuda_stream)
+                    for b, B, lv, sc in hin]
+
+        barrier()
+        e0.record(stream)
+        cstream.wait_event(e0)
+        nxt = imports()
+        for i in range(a.steps):
+            ins = nxt
+            out = G.kan_infer(ctx, keys, gm, ins)
+            nxt = imports() if i + 1 < a.steps else None
+            out.export_to(hout.data_ptr(), out_words)
+            for c in ins:
+                c.close()
+            out.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
         el = reduce_max(e0.elapsed_time(e1), dist, "cuda")
         # the host-to-device part alone (import of the step's inputs)
         t_h = time.perf_counter()
@@ -823,7 +849,9 @@ def main():
         e2e = {"value": world * a.batch * a.steps / (el / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_words * 8,
                "h2d_ms_per_step": h2d_ms, "h2d_GBps": h2d / (h2d_ms / 1000.0) / 1e9,
-               "path": "ckks_ct_import -> kan_infer -> ckks_ct_export"}
+               "serial_value": world * a.batch * a.steps / (el_serial / 1000.0),
+               "path": "ckks_ct_import_async on a copy stream (next batch overlapped with the "
+                       "current one) -> kan_infer -> ckks_ct_export"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": elapsed / a.steps, "higher_is_better": True,

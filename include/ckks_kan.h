@@ -150,6 +150,14 @@ int ckks_ct_info(const ckks_ct* ct, size_t* batch, int* level, double* scale);
 int ckks_ct_export(const ckks_ct* ct, uint64_t* host, size_t cap_words);
 int ckks_ct_import(ckks_ctx* ctx, const uint64_t* host, size_t batch, int level, double scale,
                    ckks_ct** out);
+/* Asynchronous import for pipelining inputs with computation: the copy (and
+ * the device allocation) run in the order of `copy_stream` (a cudaStream_t),
+ * and the library's stream waits for the copy before any later work, so the
+ * copy of the next batch overlaps the computation of the current one. The
+ * caller keeps `host` (pinned memory for true asynchrony) unchanged until the
+ * copy has completed (e.g. until copy_stream is synchronized). */
+int ckks_ct_import_async(ckks_ctx* ctx, const uint64_t* host, size_t batch, int level,
+                         double scale, void* copy_stream, ckks_ct** out);
 /* Sub-batch [first, first+count) of a batch, copied. */
 int ckks_ct_slice(ckks_ctx* ctx, const ckks_ct* ct, size_t first, size_t count, ckks_ct** out);
 int ckks_ct_destroy(ckks_ct* ct);

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ckks_ct_info": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "ckks_ct_export": (c_i32, [c_vp, c_vp, c_sz]),
     "ckks_ct_import": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_dbl, PP]),
+    "ckks_ct_import_async": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_dbl, c_vp, PP]),
     "ckks_ct_slice": (c_i32, [c_vp, c_vp, c_sz, c_sz, PP]),
     "ckks_ct_destroy": (c_i32, [c_vp]),
     "ckks_add": (c_i32, [c_vp, c_vp, c_vp, PP]),
@@ -270,6 +271,14 @@ class Ciphertext:
     def import_from(ctx, host_ptr, batch, level, scale):
         h = c_vp()
         check(lib().ckks_ct_import(ctx.h, host_ptr, batch, level, scale, ctypes.byref(h)))
+        return Ciphertext(ctx, h)
+
+    @staticmethod
+    def import_from_async(ctx, host_ptr, batch, level, scale, copy_stream_ptr):
+        """Copy on `copy_stream_ptr`; the library's stream waits for it."""
+        h = c_vp()
+        check(lib().ckks_ct_import_async(ctx.h, host_ptr, batch, level, scale, copy_stream_ptr,
+                                         ctypes.byref(h)))
         return Ciphertext(ctx, h)
 
     def slice(self, first, count):

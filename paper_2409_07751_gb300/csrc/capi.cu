@@ -279,6 +279,34 @@ int ckks_ct_import(ckks_ctx* ctx, const uint64_t* host, size_t batch, int level,
   });
 }
 
+int ckks_ct_import_async(ckks_ctx* ctx, const uint64_t* host, size_t batch, int level,
+                         double scale, void* copy_stream, ckks_ct** out) {
+  return guard([&] {
+    need(ctx && host && out && copy_stream, "NULL argument");
+    need(batch >= 1, "batch must be >= 1");
+    need(level >= 0 && level <= ctx->c.L, "level out of range");
+    Ctx& c = ctx->c;
+    cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+    auto r = std::make_unique<ckks_ct>();
+    r->ctx = &c;
+    r->B = batch;
+    r->level = level;
+    r->scale = scale;
+    // allocated in the copy stream's order (freed later in the library's)
+    const size_t bytes = batch * 2 * (size_t)(level + 1) * c.N * 8;
+    CK_CUDA(cudaMallocAsync(&r->d.p, bytes, cs));
+    r->d.ctx = &c;
+    r->d.bytes = bytes;
+    CK_CUDA(cudaMemcpyAsync(r->d.p, host, bytes, cudaMemcpyHostToDevice, cs));
+    cudaEvent_t e;
+    CK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK_CUDA(cudaEventRecord(e, cs));
+    CK_CUDA(cudaStreamWaitEvent(c.stream, e, 0));
+    CK_CUDA(cudaEventDestroy(e));
+    *out = r.release();
+  });
+}
+
 int ckks_ct_slice(ckks_ctx* ctx, const ckks_ct* ct, size_t first, size_t count, ckks_ct** out) {
   return guard([&] {
     need(ctx && ct && out, "NULL argument");

@@ -215,3 +215,16 @@ def test_autotune_keyswitch_layout(G):
         assert p >= 30 and a * p >= 60 + (a - 1) * 40
     assert p_bits == min(60, (1740 - 60 - 36 * 40) // alpha)
     print("digit layouts (alpha: ms per HMult+HRot, batch 2):", tried)
+
+
+def test_async_import_is_ordered_before_later_work(G):
+    """ckks_ct_import_async copies on a caller stream; the library's stream
+    waits for the copy, so an op issued right after sees the imported words."""
+    import torch
+    gctx, octx, gk, ok = pair(G, "n64k")
+    x, ox, gx = _both(G, gctx, octx, gk, ok, gctx.L, 1, 0)
+    host = torch.from_numpy(ox.data.view(np.int64).copy()).pin_memory()
+    cs = torch.cuda.Stream()
+    c = G.Ciphertext.import_from_async(gctx, host.data_ptr(), 1, gctx.L, ox.scale, cs.cuda_stream)
+    _same(G.rescale(gctx, c), O.rescale(octx, ox))
+    assert (c.export()[0] == ox.data).all()

@@ -26,12 +26,13 @@ def _split(m, x, dec):
     silu = np.abs(kan_plain.forward(m, x, "poly", "exact") - ex).max()
     comp = np.abs(kan_plain.forward(m, x, "exact", "poly") - ex).max()
     noise = np.abs(dec - hef).max()
+    total = np.abs(dec - ex).max()
     print("error split: silu %.3g comparison %.3g ckks-noise %.3g total-vs-exact %.3g"
-          % (silu, comp, noise, np.abs(dec - ex).max()))
-    return noise
+          % (silu, comp, noise, total))
+    return noise, total
 
 
-def _run(G, log_n, L, alpha, model, X, levels, degree, comp, fixed=None, tol=1e-4):
+def _run(G, log_n, L, alpha, model, X, levels, degree, comp, fixed=None, tol=1e-4, exact_tol=None):
     Xcal = X[len(levels):]
     m = G.calibrate(model, Xcal, degree, comp, fixed_range=fixed)
     ctx = G.Context(log_n, L, alpha)
@@ -44,7 +45,10 @@ def _run(G, log_n, L, alpha, model, X, levels, degree, comp, fixed=None, tol=1e-
     out = G.kan_infer(ctx, keys, gm, cts)
     assert out.level == min(levels) - depth
     dec = G.decrypt(ctx, keys, out, m[-1]["n_out"])
-    assert _split(m, x, dec) < tol
+    noise, total = _split(m, x, dec)
+    assert noise < tol
+    if exact_tol is not None:
+        assert total < exact_tol
 
 
 def test_c1_kan_2_5_1_n32k(G):
@@ -67,10 +71,10 @@ def test_c2_kan_4_8_4_1_n64k_uneven(G):
 def test_c4_kan_3072_64_10_chunked(G):
     """[3072,64,10], G=10, k=3 on synthetic 3x32x32 images, N=2^16, 36
     levels: 3072 * 16 > 2^15 slots, so each image is two ciphertexts of 2048
-    inputs (the second zero-padded), batch of 2 images."""
+    inputs (the second zero-padded), batch of 2 images; comparison f_3^4."""
     model = W.make_model("kan_3072_64_10")
     X = W.cifar_like_images(34)
-    m = G.calibrate(model, X[2:], 15, [3, 3, 3])
+    m = G.calibrate(model, X[2:], 15, [3, 3, 3, 3])
     ctx = G.Context(16, 36, 4)
     gm = G.Model(ctx, m)
     keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
@@ -83,12 +87,14 @@ def test_c4_kan_3072_64_10_chunked(G):
     out = G.kan_infer(ctx, keys, gm, [ct])
     assert out.batch == 2
     dec = G.decrypt(ctx, keys, out, 10)
-    assert _split(m, X[:2], dec) < 1e-3
+    assert _split(m, X[:2], dec)[0] < 1e-3
 
 
 def test_c3_kan_784_64_10_images(G):
     """[784,64,10], G=5, k=3 on synthetic 28x28 blob images, N=2^16,
-    36 levels; 784 * 16 copies repeat-packed into 2^15 slots."""
+    36 levels; 784 * 16 copies repeat-packed into 2^15 slots. The comparison
+    composite f_3^4 uses the whole 36-level budget (2 layers of depth 18) and
+    brings the decryption within 1e-3 of the exact FP64 KAN."""
     model = W.make_model("kan_784_64_10")
     X = W.blob_images(66)
-    _run(G, 16, 36, 4, model, X, [36, 36], 15, [3, 3, 3], tol=1e-3)
+    _run(G, 16, 36, 4, model, X, [36, 36], 15, [3, 3, 3, 3], tol=1e-3, exact_tol=1e-3)
