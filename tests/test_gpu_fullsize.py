@@ -98,3 +98,64 @@ def test_c3_kan_784_64_10_images(G):
     model = W.make_model("kan_784_64_10")
     X = W.blob_images(66)
     _run(G, 16, 36, 4, model, X, [36, 36], 15, [3, 3, 3, 3], tol=1e-3, exact_tol=1e-3)
+
+
+def test_c2_bench_launch_configuration(G):
+    """The bench's own launch: [4,8,4,1], N=2^16, 36 levels with the digit
+    layout the autotuner picks (alpha = 5, 48-bit special primes), 64 inputs
+    at uneven levels from the bench's seeds, one kan_infer. Decryptions equal
+    the HE-friendly FP64 KAN within CKKS noise for every input whose SiLU
+    inputs stay inside the fitted ranges of Eq. 11; an input that leaves a
+    range (the range is clipped to the calibration extremes) evaluates the
+    degree-27 Chebyshev polynomial where it grows fast, which amplifies the
+    noise, and is held to 1e-3."""
+    model = W.make_model("kan_4_8_4_1")
+    Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
+    X = W.uniform_inputs(64, 4, seed=W.SEED_INPUTS)
+    m = G.calibrate(model, Xcal, 27, [3])
+    ctx = G.Context(16, 36, 5, p_bits=48)
+    gm = G.Model(ctx, m)
+    depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
+    levels = W.uneven_levels(64, 36, 36 - depth, seed=W.SEED_INPUTS + 1)
+    keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
+    cts = []
+    for lv in sorted(set(int(v) for v in levels)):
+        sel = np.nonzero(levels == lv)[0]
+        cts.append((sel, G.encrypt(ctx, keys, X[sel], lv, W.SEED_ENC, int(sel[0]))))
+    out = G.kan_infer(ctx, keys, gm, [c for _, c in cts])
+    assert out.batch == 64 and out.level == min(levels) - depth
+    dec = G.decrypt(ctx, keys, out, 1)
+    order = np.concatenate([sel for sel, _ in cts])  # the batch is the concatenation
+    hef, acts = kan_plain.forward(m, X[order], "poly", "poly", collect=True)
+    inside = np.ones(64, bool)
+    for L, a in zip(m, acts):
+        y = (2 * a - (L["silu_lo"] + L["silu_hi"])) / (L["silu_hi"] - L["silu_lo"])
+        inside &= np.abs(y).max(axis=1) <= 1.0
+    err = np.abs(dec - hef).max(axis=1)
+    print("inputs outside a SiLU range:", order[~inside], "their error", err[~inside],
+          "max error inside %.3g" % err[inside].max())
+    assert inside.sum() >= 60
+    assert err[inside].max() < 1e-4
+    assert err.max() < 1e-3
+
+
+def test_full_chain_hmult_hrot_sampled_bit_exact(G):
+    """Sampled parity at the full chain in the bench's layout (N=2^16,
+    q0 + 36 x 40-bit, alpha = 5, 48-bit special primes): HMult and HRot of a
+    batch of 8 at the top level; batch elements 0 and 7 are recomputed by
+    the oracle and must match word for word."""
+    from oracle import ckks as O
+    ctx = G.Context(16, 36, 5, p_bits=48)
+    octx = O.Ctx(O.Params(16, 36, 5, p_bits=48))
+    gk = G.Keys(ctx, 7, [1])
+    ok = O.Keys(octx, 7, [1])
+    X = np.random.default_rng(5).uniform(-1, 1, (8, ctx.slots))
+    g = G.encrypt(ctx, gk, X, 36, 9, 0)
+    gd, md = g.export(), G.mul(ctx, gk, g, g).export()
+    rd = G.rotate(ctx, gk, g, 1).export()
+    for b in (0, 7):
+        oc = O.encrypt(octx, ok, X[b], 36, 9, b)
+        assert (gd[b] == oc.data).all(), b
+        assert (md[b] == O.mul(octx, ok, oc, oc).data).all(), b
+        if b == 0:
+            assert (rd[b] == O.rotate(octx, ok, oc, 1).data).all()
