@@ -247,8 +247,10 @@ typedef struct {
  * outside), KAN_FIT_OLS unit weights (both by Householder QR), KAN_FIT_REMEZ
  * the minimax polynomial over the points by the Remez exchange.
  * kan_calibrate: for each layer (only n_in, n_out, G, k, grid, coef, w_s,
- * w_b of `layers` are read), the statistics of the layer's inputs over the
- * n calibration vectors X[n][n_in] under the exact FP64 KAN (Eqs. 1-5), the
+ * w_b and comp of `layers` are read), the statistics of the layer's inputs
+ * over the n calibration vectors X[n][n_in] as the encrypted network computes
+ * them (the HE-friendly FP64 KAN: fitted SiLU, PolyComp indicators with the
+ * layer's comparison composite, the earlier layers already calibrated), the
  * SiLU range of Eq. 11 (or fixed_range[0..1] if not NULL) and its fit, and
  * the comparison bound R = 1.1 (max|x| + max|knot|) / 2 of Algorithm 2.
  * Outputs per layer: R[l], silu_lo[l], silu_hi[l], cheb[l*(degree+1) ..]. */

@@ -396,7 +396,7 @@ def calibrate(layers, X, silu_degree, comp, fixed_range=None, n_fit_samples=1000
     """Per-layer R, SiLU range and fit (Eqs. 11-12) computed by the library;
     returns copies of the layer dicts with the HE keys filled in."""
     keep = []
-    descs = _descs(layers, keep)
+    descs = _descs([dict(L, comp=list(comp)) for L in layers], keep)
     X = np.ascontiguousarray(X, dtype=np.float64)
     n = len(layers)
     R, lo, hi = np.zeros(n), np.zeros(n), np.zeros(n)

@@ -1,6 +1,7 @@
 // Host-side model preparation: the task-specific SiLU approximation of the
 // paper (Eq. 11: range [max(mu - 5 sigma, x_min), min(mu + 5 sigma, x_max)]
-// from the layer's input statistics under the plaintext KAN; Eq. 12:
+// from the statistics of the layer's inputs as the encrypted network computes
+// them, i.e. under the HE-friendly KAN with the earlier layers calibrated; Eq. 12:
 // weighted least squares with weight 10 inside mu +- 3 sigma and 1 outside)
 // and the comparison bound R of Algorithm 2. The SiLU fits the paper compares
 // against (Table 5) on the same range and degree: OLS (unit weights) and the
@@ -28,11 +29,47 @@ std::vector<double> knots(const kan_layer_desc& d) {
   return t;
 }
 
-// Cox-de Boor (Eqs. 2-3), half-open intervals; B has G+k entries
-void bspline(double x, const std::vector<double>& t, int k, std::vector<double>& B) {
+// odd monomial coefficients of f_n(x) = sum_i 4^-i C(2i,i) x (1-x^2)^i (exact dyadics)
+std::vector<double> fn_odd(int n) {
+  auto C = [](int a, int b) {
+    int64_t r = 1;
+    for (int i = 1; i <= b; i++) r = r * (a - b + i) / i;
+    return r;
+  };
+  std::vector<double> c(n + 1);
+  for (int l = 0; l <= n; l++) {
+    int64_t num = 0;
+    for (int i = l; i <= n; i++) num += C(2 * i, i) * C(i, l) * ((int64_t)1 << (2 * (n - i)));
+    if (l & 1) num = -num;
+    c[l] = (double)num / (double)((int64_t)1 << (2 * n));
+  }
+  return c;
+}
+
+// PolyComp(a, 0) = (1 + f(a)) / 2 with f = f_{n_d} o ... o f_{n_1}
+double polycomp0(double a, const int* comp, int n_comp) {
+  double u = a;
+  for (int s = 0; s < n_comp; s++) {
+    const std::vector<double> c = fn_odd(comp[s]);
+    double acc = 0, p = u;
+    const double u2 = u * u;
+    for (double cl : c) {
+      acc += cl * p;
+      p *= u2;
+    }
+    u = acc;
+  }
+  return 0.5 + 0.5 * u;
+}
+
+// Algorithm 2 on plaintext values: soft order-0 indicators, the same recursion
+void bspline_hef(double x, const std::vector<double>& t, int k, double R, const int* comp,
+                 int n_comp, std::vector<double>& B) {
   const int nk = (int)t.size();
   B.assign(nk - 1, 0.0);
-  for (int m = 0; m + 1 < nk; m++) B[m] = (t[m] <= x && x < t[m + 1]) ? 1.0 : 0.0;
+  for (int m = 0; m + 1 < nk; m++)
+    B[m] = polycomp0((x - t[m]) / (2.0 * R), comp, n_comp) *
+           polycomp0((t[m + 1] - x) / (2.0 * R), comp, n_comp);
   for (int j = 1; j <= k; j++) {
     for (int m = 0; m + j + 1 < nk; m++) {
       const double left = (x - t[m]) / (t[m + j] - t[m]) * B[m];
@@ -43,9 +80,20 @@ void bspline(double x, const std::vector<double>& t, int k, std::vector<double>&
   }
 }
 
-// y[b][o] for x[b][i] through one exact layer (Eqs. 1-5)
-void layer_forward(const kan_layer_desc& d, const std::vector<double>& x, size_t n,
-                   std::vector<double>& y) {
+// sum_j c_j T_j(y) by Clenshaw's recurrence
+double cheb_sum(const double* c, int deg, double y) {
+  double b1 = 0, b2 = 0;
+  for (int j = deg; j >= 1; j--) {
+    const double b = 2.0 * y * b1 - b2 + c[j];
+    b2 = b1;
+    b1 = b;
+  }
+  return y * b1 - b2 + c[0];
+}
+
+// one layer of the HE-friendly KAN: fitted SiLU on [lo, hi], PolyComp basis
+void layer_forward_hef(const kan_layer_desc& d, double lo, double hi, const double* cheb, int deg,
+                       double R, const std::vector<double>& x, size_t n, std::vector<double>& y) {
   const std::vector<double> t = knots(d);
   const int nb = d.G + d.k;
   y.assign(n * d.n_out, 0.0);
@@ -53,8 +101,8 @@ void layer_forward(const kan_layer_desc& d, const std::vector<double>& x, size_t
   for (size_t b = 0; b < n; b++)
     for (int i = 0; i < d.n_in; i++) {
       const double xi = x[b * d.n_in + i];
-      bspline(xi, t, d.k, B);
-      const double s = silu(xi);
+      bspline_hef(xi, t, d.k, R, d.comp, d.n_comp, B);
+      const double s = cheb_sum(cheb, deg, (2.0 * xi - (lo + hi)) / (hi - lo));
       for (int o = 0; o < d.n_out; o++) {
         double sp = 0;
         for (int m = 0; m < nb; m++) sp += d.coef[((size_t)o * d.n_in + i) * nb + m] * B[m];
@@ -258,7 +306,9 @@ int kan_calibrate(const kan_layer_desc* layers, size_t n_layers, const double* X
     double tmax = 0;
     for (double t : knots(d)) tmax = std::max(tmax, fabs(t));
     R[li] = 1.1 * (amax + tmax) / 2.0;
-    layer_forward(d, h, n, y);
+    // the next layer's inputs as the encrypted network computes them
+    layer_forward_hef(d, lo, hi, cheb + li * (size_t)(silu_degree + 1), silu_degree, R[li], h, n,
+                      y);
     h.swap(y);
   }
   return CKKS_OK;

@@ -103,12 +103,11 @@ def test_c3_kan_784_64_10_images(G):
 def test_c2_bench_launch_configuration(G):
     """The bench's own launch: [4,8,4,1], N=2^16, 36 levels with the digit
     layout the autotuner picks (alpha = 5, 48-bit special primes), 64 inputs
-    at uneven levels from the bench's seeds, one kan_infer. Decryptions equal
-    the HE-friendly FP64 KAN within CKKS noise for every input whose SiLU
-    inputs stay inside the fitted ranges of Eq. 11; an input that leaves a
-    range (the range is clipped to the calibration extremes) evaluates the
-    degree-27 Chebyshev polynomial where it grows fast, which amplifies the
-    noise, and is held to 1e-3."""
+    at uneven levels from the bench's seeds, one kan_infer. All 64
+    decryptions are within 1e-5 of the HE-friendly FP64 KAN. The SiLU ranges
+    are calibrated on that network's own activations, so the affine-mapped
+    SiLU inputs stay in [-1, 1] up to rounding; the largest errors are
+    printed with how far those inputs reach (ymax) and their level."""
     model = W.make_model("kan_4_8_4_1")
     Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
     X = W.uniform_inputs(64, 4, seed=W.SEED_INPUTS)
@@ -127,16 +126,16 @@ def test_c2_bench_launch_configuration(G):
     dec = G.decrypt(ctx, keys, out, 1)
     order = np.concatenate([sel for sel, _ in cts])  # the batch is the concatenation
     hef, acts = kan_plain.forward(m, X[order], "poly", "poly", collect=True)
-    inside = np.ones(64, bool)
+    ymax = np.zeros(64)
     for L, a in zip(m, acts):
         y = (2 * a - (L["silu_lo"] + L["silu_hi"])) / (L["silu_hi"] - L["silu_lo"])
-        inside &= np.abs(y).max(axis=1) <= 1.0
+        ymax = np.maximum(ymax, np.abs(y).max(axis=1))
     err = np.abs(dec - hef).max(axis=1)
-    print("inputs outside a SiLU range:", order[~inside], "their error", err[~inside],
-          "max error inside %.3g" % err[inside].max())
-    assert inside.sum() >= 60
-    assert err[inside].max() < 1e-4
-    assert err.max() < 1e-3
+    worst = np.argsort(-err)[:4]
+    print("largest errors:", [(int(order[i]), float(err[i]), float(ymax[i]),
+                               int(levels[order[i]])) for i in worst])
+    assert ymax.max() < 1.01
+    assert err.max() < 1e-5
 
 
 def test_full_chain_hmult_hrot_sampled_bit_exact(G):
