@@ -41,7 +41,7 @@ extern "C" {
 #define CKKS_ERR_OUT_OF_MEMORY -5
 #define CKKS_ERR_CUDA -6
 #define CKKS_ERR_OVERFLOW -7     /* a value does not fit its encoding scale */
-#define CKKS_ERR_TIMEOUT -8
+#define CKKS_ERR_TIMEOUT -8       /* a time-bounded wait ran out (device or serving) */
 #define CKKS_ERR_UNSUPPORTED -9
 
 typedef struct ckks_ctx ckks_ctx;
@@ -90,7 +90,18 @@ int ckks_set_stream(ckks_ctx* ctx, void* stream);
  * conversion, transform and pointwise launches, the plain form. Results are
  * identical word for word either way; only speed changes. */
 int ckks_set_fusion(ckks_ctx* ctx, int enabled);
+/* Waits for the context's stream. Kernels that wait on asynchronous copies
+ * (the TMA-staged key inner product of every key switch) bound each wait to
+ * about two seconds; one that runs out records it in a device status word,
+ * leaves its outputs unwritten and returns. ckks_synchronize then returns
+ * CKKS_ERR_TIMEOUT (once; the word is cleared): every result computed since
+ * the previous ckks_synchronize is invalid, the context stays usable. */
 int ckks_synchronize(ckks_ctx* ctx);
+/* Self-test of that path: one CTA waits, with a limit of limit_cycles SM
+ * clock cycles (1 .. 2^32), on an mbarrier phase that nothing completes.
+ * Returns CKKS_ERR_TIMEOUT when the wait ran out and was reported as above
+ * (the expected result), CKKS_OK if it was not. */
+int ckks_selftest_wait(ckks_ctx* ctx, long long limit_cycles);
 
 /* ------------------------------------------------------------ raw kernels
  * Forward (inverse != 0: inverse) negacyclic NTT of n_rows rows of N uint64

@@ -39,6 +39,7 @@ SIGNATURES = {
     "ckks_set_stream": (c_i32, [c_vp, c_vp]),
     "ckks_set_fusion": (c_i32, [c_vp, c_i32]),
     "ckks_synchronize": (c_i32, [c_vp]),
+    "ckks_selftest_wait": (c_i32, [c_vp, c_i64]),
     "ckks_ntt": (c_i32, [c_vp, c_vp, c_sz, c_i32, c_i32]),
     "ckks_kernel_kind_count": (c_i32, []),
     "ckks_kernel_kind_name": (ctypes.c_char_p, [c_i32]),
@@ -158,6 +159,11 @@ class Context:
 
     def synchronize(self):
         check(lib().ckks_synchronize(self.h))
+
+    def selftest_wait(self, limit_cycles):
+        """Runs one bounded device wait that cannot complete; returns the
+        library's status code (CKKS_ERR_TIMEOUT = -8 is the expected one)."""
+        return int(lib().ckks_selftest_wait(self.h, int(limit_cycles)))
 
     def set_stream(self, stream_ptr):
         check(lib().ckks_set_stream(self.h, stream_ptr))

@@ -111,6 +111,18 @@ int ckks_synchronize(ckks_ctx* ctx) {
   return guard([&] {
     need(ctx != nullptr, "ctx is NULL");
     CK_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    ctx->c.check_waits();
+  });
+}
+
+int ckks_selftest_wait(ckks_ctx* ctx, long long limit_cycles) {
+  return guard([&] {
+    need(ctx != nullptr, "ctx is NULL");
+    need(limit_cycles >= 1 && limit_cycles <= (1ll << 32), "limit_cycles out of range");
+    CK_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    ctx->c.check_waits();
+    wait_selftest(ctx->c, limit_cycles);
+    ctx->c.check_waits();
   });
 }
 

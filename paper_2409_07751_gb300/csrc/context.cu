@@ -554,10 +554,32 @@ const uint32_t* Ctx::perm(uint64_t g) {
     const uint64_t e2 = (g * e) % M;
     p[j] = brv_h((uint32_t)((e2 - 1) / 2), log_n);
   }
+  // The staged key inner product copies, for each aligned tile of T outputs
+  // (T = 16 .. 256), the aligned tile of T sources: the permutation must map
+  // every such tile into one tile. It does (only the low log2 T bits of the
+  // index are permuted); checked here so a copy can never miss a source.
+  for (int s = 4; s <= 8 && s <= log_n; s++) {
+    const uint32_t mask = ~((1u << s) - 1);
+    for (uint64_t j = 0; j < N; j++)
+      if ((p[j] & mask) != (p[j & mask] & mask))
+        throw Error(CKKS_ERR_UNSUPPORTED, "automorphism table is not tile-local");
+  }
   auto b = std::make_unique<DevBuf>(upload(this, p));
   const uint32_t* r = static_cast<const uint32_t*>(b->p);
   perms[g] = std::move(b);
   return r;
+}
+
+void Ctx::check_waits() {
+  unsigned w = 0;
+  CK_CUDA(cudaMemcpyAsync(&w, wait_status(), 4, cudaMemcpyDeviceToHost, stream));
+  CK_CUDA(cudaStreamSynchronize(stream));
+  if (w) {
+    CK_CUDA(cudaMemsetAsync(wait_status(), 0, 4, stream));
+    throw Error(CKKS_ERR_TIMEOUT,
+                "a device wait for staged copies ran past its limit; results since the last "
+                "synchronize are invalid");
+  }
 }
 
 }  // namespace ck

@@ -127,7 +127,10 @@ struct Ctx {
   // rescale of k c by q_r: (r, k) -> [N^-1 k mod q_r, Shoup, k q_r^-1 mod q_t (t < r), Shoup]
   std::map<std::pair<int, int64_t>, std::unique_ptr<DevBuf>> scaled;
   const uint64_t* scaled_consts(int r, int64_t k);
-  DevBuf d_flag;            // int32 device status word (encoding overflow)
+  DevBuf d_flag;            // int32 device status words: [0] encoding overflow,
+                            // [1] a time-bounded device wait ran out
+  unsigned* wait_status() const { return static_cast<unsigned*>(d_flag.p) + 1; }
+  void check_waits();       // after a stream synchronize: CKKS_ERR_TIMEOUT if [1] set
   DevBuf d_rs_inv, d_rs_invs;     // [(L+1)][(L+1)]: q_l^-1 mod q_t at [l][t]
   DevBuf d_pmod;                  // [L+1]: P mod q_t
 
@@ -253,6 +256,8 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
                    uint64_t galois, uint64_t* out);
 // HMult's relinearise + rescale in one division by P q_level: d is the tensor
 // product [B][3][level+1][N], ext the ModUp of its d2; out [B][2][level][N].
+// one CTA whose bounded mbarrier wait runs out (self-test of the status word)
+void wait_selftest(Ctx& c, long long limit);
 void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B, int level,
                        const uint64_t* key, uint64_t* out);
 

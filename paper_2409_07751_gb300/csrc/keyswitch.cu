@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "modarith.cuh"
+#include "tma.cuh"
 
 namespace ck {
 
@@ -65,10 +66,91 @@ __global__ void modup_kernel(const uint64_t* xc, const uint64_t* d, uint64_t* ex
 
 constexpr int IP_THREADS = 128;
 
+template <int NB, class F>
+__device__ __forceinline__ void for_digits(int beta, F body) {
+  if constexpr (NB > 0) {
+#pragma unroll
+    for (int j = 0; j < NB; j++) body(j);
+  } else {
+    for (int j = 0; j < beta; j++) body(j);
+  }
+}
+
+// The two outputs (key halves h = 0, 1) of one coefficient of the key inner
+// product: o_h = sum_j e_j k_{j,h} mod m over the beta digits. e_at(j) and
+// k_at(j, h) fetch the operands. Moduli of 33..48 bits sum 32-bit partial
+// products apart and reduce once; wider moduli sum 128-bit products;
+// narrower ones reduce every product. NB > 0: the digit count is the
+// compile-time NB (loops unrolled).
+template <int NB = 0, class EF, class KF>
+__device__ __forceinline__ void ip_point(EF e_at, KF k_at, int beta, const Mod& m, uint64_t& o0,
+                                         uint64_t& o1) {
+  const bool lazy = m.s >= 33;
+  const bool split = lazy && m.s <= 48;
+  if (split) {
+    // e, k < 2^48: e k = e0 k0 + (e0 k1 + e1 k0) 2^32 + e1 k1 2^64 with
+    // 16-bit e1, k1; the partial products are summed apart (the halves
+    // of e0 k0 separately, so no sum carries) and combined once
+    uint64_t a0[2] = {0, 0}, a1[2] = {0, 0}, bm[2] = {0, 0}, cc[2] = {0, 0};
+    for_digits<NB>(beta, [&](int j) {
+      const uint64_t e = e_at(j);
+      const uint32_t el = (uint32_t)e, eh = (uint32_t)(e >> 32);
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const uint64_t k = k_at(j, h);
+        const uint32_t kl = (uint32_t)k, kh = (uint32_t)(k >> 32);
+        const uint64_t p = (uint64_t)el * kl;
+        a0[h] += (uint32_t)p;
+        a1[h] += p >> 32;
+        bm[h] += (uint64_t)el * kh + (uint64_t)eh * kl;
+        cc[h] += (uint64_t)eh * kh;
+      }
+    });
+    // the sum x = hi 2^64 + lo has hi < 2^37 (beta <= 32 products below
+    // 2^96), so x' = hi [2^64]_m + lo < 2^64 + 2^85 is below 2^(2s) for
+    // s = 33 .. 48 and one Barrett reduction gives x mod m
+    uint64_t o[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint64_t mid = a1[h] + bm[h];
+      const uint64_t lo = a0[h] + (mid << 32);
+      const uint64_t hi = cc[h] + (mid >> 32) + (lo < a0[h] ? 1 : 0);
+      const uint64_t plo = hi * m.t64, phi = __umul64hi(hi, m.t64);
+      const uint64_t slo = plo + lo;
+      o[h] = reduce128(slo, phi + (slo < plo ? 1 : 0), m);
+    }
+    o0 = o[0];
+    o1 = o[1];
+  } else if (lazy) {
+    uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+    for_digits<NB>(beta, [&](int j) {
+      const uint64_t e = e_at(j);
+      const uint64_t k0 = k_at(j, 0), k1 = k_at(j, 1);
+      uint64_t p = e * k0;
+      h0 += __umul64hi(e, k0) + ((l0 + p) < l0 ? 1 : 0);
+      l0 += p;
+      p = e * k1;
+      h1 += __umul64hi(e, k1) + ((l1 + p) < l1 ? 1 : 0);
+      l1 += p;
+    });
+    o0 = reduce_wide(l0, h0, m);
+    o1 = reduce_wide(l1, h1, m);
+  } else {
+    uint64_t a0 = 0, a1 = 0;
+    for_digits<NB>(beta, [&](int j) {
+      const uint64_t e = e_at(j);
+      a0 = add_mod(a0, mul_mod(e, k_at(j, 0), m), m.q);
+      a1 = add_mod(a1, mul_mod(e, k_at(j, 1), m), m.q);
+    });
+    o0 = a0;
+    o1 = a1;
+  }
+}
+
 // thread per (r, n); loops over the batch so each key word is read from HBM
 // once per launch. The thread's 2*beta key words sit in shared memory (a
-// private slice per thread, so no synchronization); products are summed as
-// 128-bit values and reduced once per output (moduli of >= 33 bits).
+// private slice per thread, so no synchronization). Used when fusion is off
+// or an operand is not 16-byte aligned.
 // ext: [B][beta][rows][N]; key: [beta_max][2][n_qp][N]; acc: [B][2][rows][N]
 __global__ void __launch_bounds__(IP_THREADS)
     inner_product_kernel(const uint64_t* ext, const uint64_t* key, uint64_t* acc, size_t B,
@@ -87,62 +169,128 @@ __global__ void __launch_bounds__(IP_THREADS)
       kw[(2 * j) * IP_THREADS + tid] = key[(((size_t)j * 2 + 0) * n_qp + mi) * N + n];
       kw[(2 * j + 1) * IP_THREADS + tid] = key[(((size_t)j * 2 + 1) * n_qp + mi) * N + n];
     }
-    const bool lazy = m.s >= 33;
-    const bool split = lazy && m.s <= 48;
     for (size_t b = 0; b < B; b++) {
       const uint64_t* e0 = ext + ((b * beta) * rows + r) * N + src;
-      if (split) {
-        // e, k < 2^48: e k = e0 k0 + (e0 k1 + e1 k0) 2^32 + e1 k1 2^64 with
-        // 16-bit e1, k1; the partial products are summed apart (the halves
-        // of e0 k0 separately, so no sum carries) and combined once
-        uint64_t a0[2] = {0, 0}, a1[2] = {0, 0}, bm[2] = {0, 0}, cc[2] = {0, 0};
-        for (int j = 0; j < beta; j++) {
-          const uint64_t e = e0[(size_t)j * rows * N];
-          const uint32_t el = (uint32_t)e, eh = (uint32_t)(e >> 32);
-#pragma unroll
-          for (int h = 0; h < 2; h++) {
-            const uint64_t k = kw[(2 * j + h) * IP_THREADS + tid];
-            const uint32_t kl = (uint32_t)k, kh = (uint32_t)(k >> 32);
-            const uint64_t p = (uint64_t)el * kl;
-            a0[h] += (uint32_t)p;
-            a1[h] += p >> 32;
-            bm[h] += (uint64_t)el * kh + (uint64_t)eh * kl;
-            cc[h] += (uint64_t)eh * kh;
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const uint64_t mid = a1[h] + bm[h];
-          const uint64_t lo = a0[h] + (mid << 32);
-          const uint64_t hi = cc[h] + (mid >> 32) + (lo < a0[h] ? 1 : 0);
-          acc[((b * 2 + h) * rows + r) * N + n] = reduce_wide(lo, hi, m);
-        }
-      } else if (lazy) {
-        uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
-        for (int j = 0; j < beta; j++) {
-          const uint64_t e = e0[(size_t)j * rows * N];
-          const uint64_t k0 = kw[(2 * j) * IP_THREADS + tid], k1 = kw[(2 * j + 1) * IP_THREADS + tid];
-          uint64_t p = e * k0;
-          h0 += __umul64hi(e, k0) + ((l0 + p) < l0 ? 1 : 0);
-          l0 += p;
-          p = e * k1;
-          h1 += __umul64hi(e, k1) + ((l1 + p) < l1 ? 1 : 0);
-          l1 += p;
-        }
-        acc[((b * 2 + 0) * rows + r) * N + n] = reduce_wide(l0, h0, m);
-        acc[((b * 2 + 1) * rows + r) * N + n] = reduce_wide(l1, h1, m);
-      } else {
-        uint64_t a0 = 0, a1 = 0;
-        for (int j = 0; j < beta; j++) {
-          const uint64_t e = e0[(size_t)j * rows * N];
-          a0 = add_mod(a0, mul_mod(e, kw[(2 * j) * IP_THREADS + tid], m), m.q);
-          a1 = add_mod(a1, mul_mod(e, kw[(2 * j + 1) * IP_THREADS + tid], m), m.q);
-        }
-        acc[((b * 2 + 0) * rows + r) * N + n] = a0;
-        acc[((b * 2 + 1) * rows + r) * N + n] = a1;
-      }
+      uint64_t o0, o1;
+      ip_point([&](int j) { return e0[(size_t)j * rows * N]; },
+               [&](int j, int h) { return kw[(2 * j + h) * IP_THREADS + tid]; }, beta, m, o0, o1);
+      acc[((b * 2 + 0) * rows + r) * N + n] = o0;
+      acc[((b * 2 + 1) * rows + r) * N + n] = o1;
     }
   }
+}
+
+// TMA-staged key inner product. One CTA per (row r, tile of T consecutive
+// coefficients), one thread per coefficient. Thread 0 stages the tile's
+// 2 beta key words by bulk copies once, then streams the batch: the beta
+// extension tiles of element b land in stage b % S (S stages in flight),
+// each stage completed on its own mbarrier. With a Galois automorphism the
+// T outputs of an aligned tile read an aligned tile of T sources (the NTT
+// -domain permutation only permutes the low log2 T index bits, checked when
+// the table is built), so the copies stay contiguous.
+// smem: keys [2 beta][T], then [S][beta][T].
+// BETA > 0 (digit counts up to IP_REG_BETA): the thread's key words move
+// from shared memory into registers once, and the digit loops unroll.
+constexpr int IP_TMA_MAX_T = 256;
+constexpr int IP_TMA_MAX_STAGES = 4;
+constexpr int IP_REG_BETA = 8;
+
+template <int BETA>
+__global__ void __launch_bounds__(IP_TMA_MAX_T, 2)
+    inner_product_tma(const uint64_t* ext, const uint64_t* key, uint64_t* acc, int B, int log_n,
+                      int l, int beta, int rows, int L, int n_qp, const Mod* mods,
+                      const uint32_t* perm, int stages, long long limit, unsigned* status) {
+  extern __shared__ __align__(128) uint64_t ipsm[];
+  __shared__ __align__(8) uint64_t bars[1 + IP_TMA_MAX_STAGES];
+  const int T = blockDim.x;
+  const size_t N = (size_t)1 << log_n;
+  const size_t tiles = N / (size_t)T;
+  const int r = (int)(blockIdx.x / tiles);
+  const size_t n0 = (blockIdx.x % tiles) * (size_t)T;
+  const int tid = threadIdx.x;
+  const size_t n = n0 + tid;
+  const int mi = r < l ? r : L + 1 + (r - l);
+  const size_t src0 = perm ? (perm[n0] & ~(uint32_t)(T - 1)) : n0;
+  const int sidx = perm ? (int)(perm[n] - src0) : tid;
+  uint64_t* kw = ipsm;                            // [2 beta][T]
+  uint64_t* xs = ipsm + (size_t)2 * beta * T;     // [S][beta][T]
+  const uint32_t tile = (uint32_t)T * 8u;
+  const uint32_t kbar = smem_addr(&bars[0]);
+  auto stage_bar = [&](int s) { return smem_addr(&bars[1 + s]); };
+  auto issue = [&](int b) {  // thread 0: element b's beta tiles into stage b % S
+    const int s = b % stages;
+    mbar_expect_tx(stage_bar(s), (uint32_t)beta * tile);
+    for (int j = 0; j < beta; j++)
+      bulk_load(smem_addr(xs + ((size_t)s * beta + j) * T),
+                ext + (((size_t)b * beta + j) * rows + r) * N + src0, tile, stage_bar(s));
+  };
+  // on a timed-out wait: thread 0 waits (bounded) for every copy still in
+  // flight into this CTA's shared memory, records the failure, and the CTA
+  // returns with its outputs unwritten
+  auto drain = [&](bool keys_pending, int b_first) {
+    if (tid != 0) return;
+    if (keys_pending) mbar_wait(kbar, 0, limit);
+    for (int b = b_first; b < B && b < b_first + stages; b++)
+      mbar_wait(stage_bar(b % stages), (uint32_t)(b / stages) & 1u, limit);
+    atomicOr(status, 1u);
+  };
+  if (tid == 0) {
+    mbar_init(kbar, 1);
+    for (int s = 0; s < stages; s++) mbar_init(stage_bar(s), 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(kbar, 2u * (uint32_t)beta * tile);
+    for (int j = 0; j < beta; j++)
+      for (int h = 0; h < 2; h++)
+        bulk_load(smem_addr(kw + (size_t)(2 * j + h) * T),
+                  key + (((size_t)j * 2 + h) * n_qp + mi) * N + n0, tile, kbar);
+    for (int b = 0; b < B && b < stages; b++) issue(b);
+  }
+  const Mod m = mods[mi];
+  if (__syncthreads_or(!mbar_wait(kbar, 0, limit))) {
+    drain(true, 0);
+    return;
+  }
+  uint64_t kr[2 * (BETA > 0 ? BETA : 1)];
+  if constexpr (BETA > 0) {
+#pragma unroll
+    for (int i = 0; i < 2 * BETA; i++) kr[i] = kw[(size_t)i * T + tid];
+  }
+  for (int b = 0; b < B; b++) {
+    const int s = b % stages;
+    if (__syncthreads_or(!mbar_wait(stage_bar(s), (uint32_t)(b / stages) & 1u, limit))) {
+      drain(false, b);
+      return;
+    }
+    const uint64_t* x = xs + (size_t)s * beta * T + sidx;
+    uint64_t o0, o1;
+    if constexpr (BETA > 0)
+      ip_point<BETA>([&](int j) { return x[(size_t)j * T]; },
+                     [&](int j, int h) { return kr[2 * j + h]; }, beta, m, o0, o1);
+    else
+      ip_point([&](int j) { return x[(size_t)j * T]; },
+               [&](int j, int h) { return kw[(size_t)(2 * j + h) * T + tid]; }, beta, m, o0,
+               o1);
+    acc[(((size_t)b * 2 + 0) * rows + r) * N + n] = o0;
+    acc[(((size_t)b * 2 + 1) * rows + r) * N + n] = o1;
+    __syncthreads();  // stage s fully read before it is refilled
+    if (tid == 0 && b + stages < B) issue(b + stages);
+  }
+}
+
+// an mbarrier phase that no arrival or copy completes: the bounded wait runs
+// out and is reported like a stalled staged copy
+__global__ void wait_selftest_kernel(long long limit, unsigned* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_addr(&bar), 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (__syncthreads_or(!mbar_wait(smem_addr(&bar), 0, limit)) && threadIdx.x == 0)
+    atomicOr(status, 1u);
 }
 
 // overflow of the centred conversion, u = floor(sum_m v_m inv_m + 1/2) in
@@ -329,12 +477,48 @@ static DevBuf key_product(Ctx& c, const uint64_t* ext, size_t B, int level, cons
   const double W8 = (double)c.N * 8.0;
   Launch L_(c, K_INNER, W8 * rows * ((double)B * T.beta + 2.0 * T.beta + 2.0 * B),
             2.0 * (double)B * T.beta * rows * (double)c.N);
+  const bool aligned = ((reinterpret_cast<uintptr_t>(ext) | reinterpret_cast<uintptr_t>(key) |
+                         reinterpret_cast<uintptr_t>(acc.p)) & 15) == 0;
+  if (c.fused && aligned && c.N >= 16 && B <= (size_t)INT32_MAX) {
+    // tile width T and stage count S: two CTAs per SM within 227 KiB
+    const int S = (int)std::min<size_t>(3, B);
+    size_t Tw = std::min<size_t>(IP_TMA_MAX_T, c.N);
+    while (Tw > 16 && (size_t)(2 + S) * T.beta * Tw * 8 > 110 * 1024) Tw /= 2;
+    const size_t smem = (size_t)(2 + S) * T.beta * Tw * 8;
+    const size_t blocks = (size_t)rows * (c.N / Tw);
+    auto go = [&](auto kernel) {
+      CK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   110 * 1024));
+      kernel<<<(unsigned)blocks, (unsigned)Tw, smem, c.stream>>>(
+          ext, key, acc.u64(), (int)B, c.log_n, l, T.beta, rows, c.L, c.n_qp, c.dmod(), perm, S,
+          WAIT_LIMIT_CYCLES, c.wait_status());
+    };
+    switch (T.beta) {
+      case 1: go(inner_product_tma<1>); break;
+      case 2: go(inner_product_tma<2>); break;
+      case 3: go(inner_product_tma<3>); break;
+      case 4: go(inner_product_tma<4>); break;
+      case 5: go(inner_product_tma<5>); break;
+      case 6: go(inner_product_tma<6>); break;
+      case 7: go(inner_product_tma<7>); break;
+      case 8: go(inner_product_tma<8>); break;
+      default: go(inner_product_tma<0>); break;
+    }
+    static_assert(IP_REG_BETA == 8, "dispatch covers digit counts 1 .. 8");
+    CK_CUDA(cudaGetLastError());
+    return acc;
+  }
   const size_t ip_total = (size_t)rows * c.N;
   const size_t ip_blocks = std::min<size_t>((ip_total + IP_THREADS - 1) / IP_THREADS, 152 * 64);
   inner_product_kernel<<<(unsigned)ip_blocks, IP_THREADS, 2 * T.beta * IP_THREADS * 8, c.stream>>>(
       ext, key, acc.u64(), B, c.log_n, l, T.beta, rows, c.L, c.n_qp, c.dmod(), perm);
   CK_CUDA(cudaGetLastError());
   return acc;
+}
+
+void wait_selftest(Ctx& c, long long limit) {
+  wait_selftest_kernel<<<1, 32, 0, c.stream>>>(limit, c.wait_status());
+  CK_CUDA(cudaGetLastError());
 }
 
 void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B, int level,

@@ -90,6 +90,25 @@ __device__ __forceinline__ void gs_lazy(uint64_t& x, uint64_t& y, uint64_t w, ui
   x = s >= q2 ? s - q2 : s;
   y = shoup_lazy(u - v + q2, w, ws, q);
 }
+// Inverse butterfly without the reduction of x, for moduli q < 2^48: with
+// every input of stage s below c = 2^s q (a multiple of q), x' = u + v < 2c
+// and y' = [(u - v + c) w] in [0, 2q), so the inputs of stage s + 1 are below
+// 2^(s+1) q; after the 16 stages of N = 2^16 every value is below
+// 2^16 q < 2^64, and the output scaling (any 64-bit input) reduces fully.
+__device__ __forceinline__ void gs_grow(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
+                                        uint64_t q, uint64_t c) {
+  const uint64_t u = x, v = y;
+  x = u + v;
+  y = shoup_lazy(u - v + c, w, ws, q);
+}
+template <bool GROW>
+__device__ __forceinline__ void gs_step(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
+                                        uint64_t q, uint64_t q2, uint64_t c) {
+  if (GROW)
+    gs_grow(x, y, w, ws, q, c);
+  else
+    gs_lazy(x, y, w, ws, q, q2);
+}
 // Forward butterfly without the reduction of x, for moduli q < 2^50: with
 // t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
 // from inputs below q stay below 65q < 2^57.
@@ -215,14 +234,17 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
 #pragma unroll
     for (int k = 0; k < 4; k++) ct_step<GROW>(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
   } else {
+    // stages ls, ls + 1, ls + 2 of the inverse (bounds 2^s q when growing)
+    const uint64_t c0 = GROW ? q << ls : 0;
 #pragma unroll
-    for (int k = 0; k < 4; k++) gs_lazy(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
-    gs_lazy(x[0], x[2], tt[1].x, tt[1].y, q, q2);
-    gs_lazy(x[1], x[3], tt[1].x, tt[1].y, q, q2);
-    gs_lazy(x[4], x[6], tt[2].x, tt[2].y, q, q2);
-    gs_lazy(x[5], x[7], tt[2].x, tt[2].y, q, q2);
+    for (int k = 0; k < 4; k++)
+      gs_step<GROW>(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2, c0);
+    gs_step<GROW>(x[0], x[2], tt[1].x, tt[1].y, q, q2, c0 << 1);
+    gs_step<GROW>(x[1], x[3], tt[1].x, tt[1].y, q, q2, c0 << 1);
+    gs_step<GROW>(x[4], x[6], tt[2].x, tt[2].y, q, q2, c0 << 1);
+    gs_step<GROW>(x[5], x[7], tt[2].x, tt[2].y, q, q2, c0 << 1);
 #pragma unroll
-    for (int k = 0; k < 4; k++) gs_lazy(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
+    for (int k = 0; k < 4; k++) gs_step<GROW>(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2, c0 << 2);
   }
 #pragma unroll
   for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
@@ -578,35 +600,15 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
     fwd_rows<N1, D, false>(d, r, log_n, t8, q, kc, ctw, sm);
 }
 
-// Inverse NTT of pattern-selected rows, one row per cluster: each CTA loads
-// and transforms its own chunks, then (after a cluster barrier) transforms
-// its share of the columns, reading the elements from the owners' shared
-// memory, and writes the row scaled by post[row % P] (default N^-1).
-template <int N1>
-__global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
-    ntt_inv_cl(uint64_t* base, const uint64_t* src, size_t src_stride, int log_n,
-               const int16_t* pattern, int P, const Mod* mods,
-               const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
-               const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts,
-               const ulonglong2* tw8, size_t nodes) {
+// Both phases of the inverse transform of one row (see ntt_inv_cl).
+template <int N1, bool GROW>
+__device__ __forceinline__ void inv_rows(uint64_t* a, const uint64_t* as, uint64_t* sm,
+                                         const ulonglong2* ctw, const ulonglong2* t8, int log_n,
+                                         uint64_t q, uint64_t pv, uint64_t pvs, uint32_t rank) {
   constexpr int CS = inv_cs<N1>();
   constexpr int CPC = N1 / CS;
-  extern __shared__ uint64_t sm[];
-  __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
-  const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
-  const size_t row = blockIdx.x / CS;
-  const int mi = pattern[row % P];
-  if (mi < 0) return;  // same decision on every CTA of the cluster
-  const size_t N = (size_t)N1 * CHUNK;
-  const uint64_t q = mods[mi].q, q2 = 2 * q;
-  const ulonglong2* t8 = tw8 + (size_t)mi * nodes * 7;
-  uint64_t* a = base + row * N;
-  // source rows: in place, or row i of period p at src + p src_stride + i N
-  const uint64_t* as = src ? src + (row / P) * src_stride + (row % P) * N : a;
-  const uint64_t pv = post ? post[row % P] : ninv[mi];
-  const uint64_t pvs = post ? posts[row % P] : ninvs[mi];
+  const uint64_t q2 = 2 * q;
   const uint32_t g = threadIdx.x;
-  if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)mi * N + g], tws[(size_t)mi * N + g]);
   // chunks in pairs (CPC is even): one group of each chunk per thread
   for (int lc = 0; lc < CPC; lc += 2) {
     const uint32_t chunk = rank * CPC + lc;
@@ -617,8 +619,8 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
     __syncthreads();
 #pragma unroll
     for (int ls = 0; ls <= 9; ls += 3) {
-      round8<true>(s, g, ls, chunk, log_n, t8, q, q2);
-      round8<true>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
+      round8<true, GROW>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8<true, GROW>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
       __syncthreads();
     }
   }
@@ -640,17 +642,54 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
 #pragma unroll
     for (int m = N1 / 2; m >= 1; m >>= 1) {
       const int t1 = N1 / (2 * m);
+      const uint64_t cs = GROW ? (q << CHUNK_LOG) * (uint64_t)t1 : 0;  // stage 12 + log2 t1
 #pragma unroll
       for (int i = 0; i < m; i++) {
         const ulonglong2 tv = ctw[m + i];
 #pragma unroll
-        for (int jj = 0; jj < t1; jj++) gs_lazy(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
+        for (int jj = 0; jj < t1; jj++)
+          gs_step<GROW>(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2, cs);
       }
     }
 #pragma unroll
     for (int s = 0; s < N1; s++) a[c + (size_t)s * CHUNK] = mul_shoup(x[s], pv, pvs, q);
   }
   if constexpr (CS > 1) cg::this_cluster().sync();  // peers may still read this CTA's chunks
+}
+
+// Inverse NTT of pattern-selected rows, one row per cluster: each CTA loads
+// and transforms its own chunks, then (after a cluster barrier) transforms
+// its share of the columns, reading the elements from the owners' shared
+// memory, and writes the row scaled by post[row % P] (default N^-1).
+template <int N1>
+__global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
+    ntt_inv_cl(uint64_t* base, const uint64_t* src, size_t src_stride, int log_n,
+               const int16_t* pattern, int P, const Mod* mods,
+               const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
+               const uint64_t* ninvs, const uint64_t* post, const uint64_t* posts,
+               const ulonglong2* tw8, size_t nodes) {
+  constexpr int CS = inv_cs<N1>();
+  extern __shared__ uint64_t sm[];
+  __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
+  const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
+  const size_t row = blockIdx.x / CS;
+  const int mi = pattern[row % P];
+  if (mi < 0) return;  // same decision on every CTA of the cluster
+  const size_t N = (size_t)N1 * CHUNK;
+  const uint64_t q = mods[mi].q;
+  const ulonglong2* t8 = tw8 + (size_t)mi * nodes * 7;
+  uint64_t* a = base + row * N;
+  // source rows: in place, or row i of period p at src + p src_stride + i N
+  const uint64_t* as = src ? src + (row / P) * src_stride + (row % P) * N : a;
+  const uint64_t pv = post ? post[row % P] : ninv[mi];
+  const uint64_t pvs = post ? posts[row % P] : ninvs[mi];
+  const uint32_t g = threadIdx.x;
+  if (g < (uint32_t)N1) ctw[g] = make_ulonglong2(tw[(size_t)mi * N + g], tws[(size_t)mi * N + g]);
+  // every CTA of a cluster works on the same row, so the branch is uniform
+  if (q < (1ull << 48))
+    inv_rows<N1, true>(a, as, sm, ctw, t8, log_n, q, pv, pvs, rank);
+  else
+    inv_rows<N1, false>(a, as, sm, ctw, t8, log_n, q, pv, pvs, rank);
 }
 
 template <int N1, int CS, class K, class... Args>

@@ -228,3 +228,33 @@ def test_async_import_is_ordered_before_later_work(G):
     c = G.Ciphertext.import_from_async(gctx, host.data_ptr(), 1, gctx.L, ox.scale, cs.cuda_stream)
     _same(G.rescale(gctx, c), O.rescale(octx, ox))
     assert (c.export()[0] == ox.data).all()
+
+
+def test_staged_inner_product_batch_over_stages(G):
+    """A batch of 7 runs the TMA-staged key inner product through every
+    stage more than once (three stages, so each mbarrier completes two or
+    three phases); HMult and hoisted rotations of all 7 equal the oracle."""
+    gctx, octx, gk, ok = pair(G, "n8k")
+    rng = np.random.default_rng(21)
+    L = gctx.L
+    ocs = [O.encrypt(octx, ok, rng.uniform(-1, 1, gctx.slots), L, 3, i) for i in range(7)]
+    data = np.stack([o.data for o in ocs])
+    g = G.Ciphertext.import_(gctx, data, L, ocs[0].scale)
+    md = G.mul(gctx, gk, g, g).export()
+    rs = [h.export() for h in G.rotate_hoisted(gctx, gk, g, [1, -5])]
+    for i, o in enumerate(ocs):
+        assert (md[i] == O.mul(octx, ok, o, o).data).all(), i
+        assert (rs[0][i] == O.rotate(octx, ok, o, 1).data).all(), i
+        assert (rs[1][i] == O.rotate(octx, ok, o, -5).data).all(), i
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(G):
+    """A device wait that cannot complete runs out after its cycle limit, the
+    kernel returns, the host reads CKKS_ERR_TIMEOUT once, and the context
+    keeps computing bit-exact results."""
+    gctx, octx, gk, ok = pair(G, "n4k")
+    assert gctx.selftest_wait(1 << 20) == -8
+    gctx.synchronize()  # the status word was cleared by the report
+    x, ox, gx = _both(G, gctx, octx, gk, ok, gctx.L, 4, 0)
+    _same(G.rotate(gctx, gk, gx, 1), O.rotate(octx, ok, ox, 1))
+    gctx.synchronize()
