@@ -130,32 +130,33 @@ def bsgs_matvec(ctx, keys, v, M, plan):
 
 # ------------------------------------------------------------------ polynomials
 def eval_odd(ctx, keys, u, c, const=0.0):
-    """sum_l c[l] u^(2l+1) + const: each term is (c_l u) times the binary
-    powers u^2, u^4, ... of 2l in ascending order; terms summed at the lowest
-    level."""
+    """sum_l c[l] u^(2l+1) + const. The coefficient list is padded to 2^K
+    and split in halves: p = A + u^(2^K) B with A, B the odd polynomials of
+    the lower and upper halves, recursively; a single coefficient is c_l u
+    (one constant product). Each level of the recursion costs one depth, so
+    the result is at depth K + 1 = ceil(log2(deg + 1)); f_3 (degree 7) takes
+    5 ciphertext products (u^2, u^4 and three splits). Reading: the paper
+    fixes the comparison polynomial, not its evaluation order."""
+    K = max(0, math.ceil(math.log2(len(c))))
+    c = list(c) + [0.0] * ((1 << K) - len(c))
     pw = {1: u}
-    need = max(2 * l for l, cl in enumerate(c) if cl != 0.0)
-    b = 2
-    while b <= need:
-        pw[b] = ckks.mul(ctx, keys, pw[b // 2], pw[b // 2])
-        b *= 2
-    terms = []
-    for l, cl in enumerate(c):
-        if cl == 0.0:
-            continue
-        T = ckks.mul_const(ctx, u, cl)
-        e, b = 2 * l, 2
-        while e:
-            if e & b:
-                T = ckks.mul(ctx, keys, T, pw[b])
-                e ^= b
-            b *= 2
-        terms.append(T)
-    lv = min(t.level for t in terms)
-    out = None
-    for T in terms:
-        T = ckks.level_down(ctx, T, lv)
-        out = T if out is None else ckks.add(ctx, out, T)
+    for k in range(1, K + 1):  # u^(2^k)
+        pw[1 << k] = ckks.mul(ctx, keys, pw[1 << (k - 1)], pw[1 << (k - 1)])
+
+    def rec(lo, k):
+        if k == 0:
+            return ckks.mul_const(ctx, u, c[lo]) if c[lo] != 0.0 else None
+        half = 1 << (k - 1)
+        A = rec(lo, k - 1)
+        B = rec(lo + half, k - 1)
+        if B is None:
+            return A
+        P = ckks.mul(ctx, keys, B, pw[1 << k])
+        if A is None:
+            return P
+        return ckks.add(ctx, ckks.level_down(ctx, A, P.level), P)
+
+    out = rec(0, K)
     if const != 0.0:
         out = ckks.add_const(ctx, out, const)
     return out

@@ -215,37 +215,36 @@ Ct bsgs_matvec(kan_model& M, int li, int tag, const Plan& p, int nch, DV&& dval,
   return z;
 }
 
-Ct eval_odd(Ctx& c, const ckks_keys& keys, const ckks_ct& u, const std::vector<double>& cf,
+// sum_l cf[l] u^(2l+1) + cst: the coefficients, padded to 2^K, split in
+// halves, p = A + u^(2^K) B with A and B the odd polynomials of the lower and
+// upper halves, recursively; one coefficient is a constant product. Depth
+// K + 1 = ceil(log2(degree + 1)); f_3 takes 5 ciphertext products.
+Ct odd_split(Ctx& c, const ckks_keys& keys, const ckks_ct& u, const std::vector<double>& cf,
+             const std::vector<Ct>& pw, int lo, int k) {
+  if (k == 0) return cf[lo] != 0.0 ? op_mul_const(c, u, cf[lo]) : Ct();
+  const int half = 1 << (k - 1);
+  Ct A = odd_split(c, keys, u, cf, pw, lo, k - 1);
+  Ct B = odd_split(c, keys, u, cf, pw, lo + half, k - 1);
+  if (!B) return A;
+  Ct P = op_mul(c, keys, *B, *pw[k]);
+  if (!A) return P;
+  Ct Ad = op_level_down(c, *A, P->level);
+  return op_add(c, *Ad, *P, false);
+}
+
+Ct eval_odd(Ctx& c, const ckks_keys& keys, const ckks_ct& u, const std::vector<double>& cf0,
             double cst) {
-  std::map<int, Ct> pw;
-  int need = 0;
-  for (size_t l = 0; l < cf.size(); l++)
-    if (cf[l] != 0.0) need = std::max(need, (int)(2 * l));
-  for (int b = 2; b <= need; b *= 2) {
-    const ckks_ct& h = b == 2 ? u : *pw[b / 2];
-    pw[b] = op_mul(c, keys, h, h);
+  int K = 0;
+  while ((size_t)1 << K < cf0.size()) K++;
+  std::vector<double> cf(cf0);
+  cf.resize((size_t)1 << K, 0.0);
+  std::vector<Ct> pw(K + 1);  // pw[k] = u^(2^k), k >= 1
+  for (int k = 1; k <= K; k++) {
+    const ckks_ct& h = k == 1 ? u : *pw[k - 1];
+    pw[k] = op_mul(c, keys, h, h);
   }
-  std::vector<Ct> terms;
-  for (size_t l = 0; l < cf.size(); l++) {
-    if (cf[l] == 0.0) continue;
-    Ct T = op_mul_const(c, u, cf[l]);
-    int e = 2 * (int)l, b = 2;
-    while (e) {
-      if (e & b) {
-        T = op_mul(c, keys, *T, *pw[b]);
-        e ^= b;
-      }
-      b *= 2;
-    }
-    terms.push_back(std::move(T));
-  }
-  int lv = terms[0]->level;
-  for (auto& t : terms) lv = std::min(lv, t->level);
-  Ct out;
-  for (auto& t : terms) {
-    Ct d = op_level_down(c, *t, lv);
-    out = out ? op_add(c, *out, *d, false) : std::move(d);
-  }
+  Ct out = odd_split(c, keys, u, cf, pw, 0, K);
+  if (!out) throw Error(CKKS_ERR_INVALID_ARG, "comparison polynomial without coefficients");
   if (cst != 0.0) out = op_add_const(c, *out, cst);
   return out;
 }

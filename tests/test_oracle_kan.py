@@ -164,6 +164,30 @@ def test_he_polynomials(he_small):
         assert np.abs(ckks.decrypt(ctx, keys, out) - kan_plain.polycomp0(y, stages)).max() < 1e-5
 
 
+def test_he_odd_polynomial_split_evaluation(he_small, monkeypatch):
+    """eval_odd equals sum_l c_l y^(2l+1) for 1..8 coefficients (zeros
+    included), at depth ceil(log2(degree + 1)), with 5 ciphertext products
+    for f_3 (degree 7: u^2, u^4 and one per split)."""
+    ctx = he_small
+    keys = ckks.Keys(ctx, 2)
+    rng = np.random.default_rng(6)
+    y = rng.uniform(-1, 1, ctx.slots)
+    c = ckks.encrypt(ctx, keys, y, ctx.L, 2)
+    for n in range(1, 9):
+        cf = list(rng.normal(size=n))
+        if n >= 3:
+            cf[1] = 0.0
+        out = kan_he.eval_odd(ctx, keys, c, cf, 0.25)
+        ref = 0.25 + sum(cl * y ** (2 * l + 1) for l, cl in enumerate(cf))
+        assert np.abs(ckks.decrypt(ctx, keys, out) - ref).max() < 1e-5, n
+        assert ctx.L - out.level == math.ceil(math.log2(2 * n)), n
+    calls = []
+    real = ckks.mul
+    monkeypatch.setattr(ckks, "mul", lambda *a: calls.append(1) or real(*a))
+    kan_he.eval_odd(ctx, keys, c, kan_plain.fn_coeffs(3))
+    assert len(calls) == 5
+
+
 def test_he_bsgs_matvec(he_small):
     ctx = he_small
     rng = np.random.default_rng(5)
