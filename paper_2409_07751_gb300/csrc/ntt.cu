@@ -211,19 +211,10 @@ __device__ __forceinline__ uint32_t node_base(uint32_t ls, int log_n) {
   return off;
 }
 
-template <bool INV, bool GROW = false>
-__device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
-                                       int log_n, const ulonglong2* t8, uint64_t q, uint64_t q2) {
-  const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
-  const uint32_t base = (blk8 << (ls + 3)) + r;
-  const uint32_t B8 = (chunk << (CHUNK_LOG - ls - 3)) + blk8;
-  const ulonglong2* T = t8 + (size_t)(node_base(ls, log_n) + B8) * 7;
-  uint64_t x[8];
-#pragma unroll
-  for (int k = 0; k < 8; k++) x[k] = sm[swz(base + ((uint32_t)k << ls))];
-  ulonglong2 tt[7];
-#pragma unroll
-  for (int k = 0; k < 7; k++) tt[k] = T[k];
+// The three butterfly layers of a round on the group's 8 words x.
+template <bool INV, bool GROW>
+__device__ __forceinline__ void bfly8(uint64_t* x, const ulonglong2* tt, uint32_t ls, uint64_t q,
+                                      uint64_t q2) {
   if (!INV) {
 #pragma unroll
     for (int k = 0; k < 4; k++) ct_step<GROW>(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
@@ -246,8 +237,57 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
 #pragma unroll
     for (int k = 0; k < 4; k++) gs_step<GROW>(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2, c0 << 2);
   }
+}
+
+__device__ __forceinline__ void load_tw8(ulonglong2* tt, const ulonglong2* t8, uint32_t ls,
+                                         uint32_t B8, int log_n) {
+  const ulonglong2* T = t8 + (size_t)(node_base(ls, log_n) + B8) * 7;
+#pragma unroll
+  for (int k = 0; k < 7; k++) tt[k] = T[k];
+}
+
+template <bool INV, bool GROW = false>
+__device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
+                                       int log_n, const ulonglong2* t8, uint64_t q, uint64_t q2) {
+  const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
+  const uint32_t base = (blk8 << (ls + 3)) + r;
+  uint64_t x[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) x[k] = sm[swz(base + ((uint32_t)k << ls))];
+  ulonglong2 tt[7];
+  load_tw8(tt, t8, ls, (chunk << (CHUNK_LOG - ls - 3)) + blk8, log_n);
+  bfly8<INV, GROW>(x, tt, ls, q, q2);
 #pragma unroll
   for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
+}
+
+// The inverse's first round (distances 1, 2, 4): group g is the 8
+// consecutive words 8g .. 8g+7 of the chunk, read straight from global
+// memory (16-byte loads when the chunk is 16-byte aligned) instead of
+// through a shared-memory copy.
+template <bool GROW>
+__device__ __forceinline__ void round8_inv_first(uint64_t* sm, const uint64_t* src, uint32_t g,
+                                                 uint32_t chunk, int log_n, const ulonglong2* t8,
+                                                 uint64_t q, uint64_t q2, bool vec) {
+  const uint32_t base = g << 3;
+  uint64_t x[8];
+  if (vec) {
+    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(src + base);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const ulonglong2 p = v[k];
+      x[2 * k] = p.x;
+      x[2 * k + 1] = p.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = src[base + k];
+  }
+  ulonglong2 tt[7];
+  load_tw8(tt, t8, 0, (chunk << (CHUNK_LOG - 3)) + g, log_n);
+  bfly8<true, GROW>(x, tt, 0, q, q2);
+#pragma unroll
+  for (int k = 0; k < 8; k++) sm[swz(base + (uint32_t)k)] = x[k];
 }
 
 // Per-CTA row description produced by a descriptor's setup().
@@ -502,6 +542,9 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
       round8<false, GROW>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
       __syncthreads();
     }
+    // stored through shared memory so that a warp writes 256 contiguous
+    // bytes per instruction (the last round's groups are 8 consecutive
+    // words per thread, which would make every store instruction strided)
     for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS) {
       const uint64_t v = s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))];
       d.store(r, chunk * CHUNK + i, GROW ? reduce_full(v, q, w1s) : reduce4(v, q, q2), q, kc);
@@ -614,11 +657,12 @@ __device__ __forceinline__ void inv_rows(uint64_t* a, const uint64_t* as, uint64
     const uint32_t chunk = rank * CPC + lc;
     uint64_t* s = sm + lc * CHUNK;
     const uint64_t* ac = as + (size_t)chunk * CHUNK;
-    for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS)
-      s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))] = ac[i];
+    const bool vec = (reinterpret_cast<uintptr_t>(ac) & 15) == 0;
+    round8_inv_first<GROW>(s, ac, g, chunk, log_n, t8, q, q2, vec);
+    round8_inv_first<GROW>(s + CHUNK, ac + CHUNK, g, chunk + 1, log_n, t8, q, q2, vec);
     __syncthreads();
 #pragma unroll
-    for (int ls = 0; ls <= 9; ls += 3) {
+    for (int ls = 3; ls <= 9; ls += 3) {
       round8<true, GROW>(s, g, ls, chunk, log_n, t8, q, q2);
       round8<true, GROW>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
       __syncthreads();
