@@ -380,6 +380,7 @@ ConvTables& Ctx::tables(int level) {
   T->rows = rows;
   std::vector<uint64_t> dhinv((size_t)beta * A, 0), dhinvs((size_t)beta * A, 0);
   std::vector<uint64_t> dh((size_t)beta * A * rows, 0), dhs((size_t)beta * A * rows, 0);
+  std::vector<uint64_t> dhw((size_t)beta * A * rows, 0), dhws((size_t)beta * A * rows, 0);
   std::vector<int16_t> pat((size_t)beta * rows);
   auto row_mod = [&](int r) { return r < l ? r : L + 1 + (r - l); };
   for (int j = 0; j < beta; j++) {
@@ -398,6 +399,10 @@ ConvTables& Ctx::tables(int level) {
           if (k != i) hm = mulmod_h(hm, mod[k] % m, m);
         dh[((size_t)j * A + (i - lo)) * rows + r] = hm;
         dhs[((size_t)j * A + (i - lo)) * rows + r] = shoup_h(hm, m);
+        // the forward transform's first twiddle psi^(brv 1) = psi^(N/2)
+        const uint64_t hw = mulmod_h(hm, powmod_h(psi[row_mod(r)], N / 2, m), m);
+        dhw[((size_t)j * A + (i - lo)) * rows + r] = hw;
+        dhws[((size_t)j * A + (i - lo)) * rows + r] = shoup_h(hw, m);
       }
     }
     for (int r = 0; r < rows; r++)
@@ -416,6 +421,8 @@ ConvTables& Ctx::tables(int level) {
   T->dhinv_s = upload(this, dhinvs);
   T->dh = upload(this, dh);
   T->dh_s = upload(this, dhs);
+  T->dhw = upload(this, dhw);
+  T->dhw_s = upload(this, dhws);
   T->ext_pattern = upload(this, pat);
   T->pq_pattern = upload(this, pq);
   T->md_pinv = upload(this, pinv);

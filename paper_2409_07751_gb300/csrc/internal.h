@@ -59,6 +59,7 @@ struct ConvTables {
   // target row r: acc += v * [Dhat]_{m_r}.
   DevBuf dhinv, dhinv_s;   // [beta][alpha]
   DevBuf dh, dh_s;         // [beta][alpha][rows]
+  DevBuf dhw, dhw_s;       // [beta][alpha][rows]: dh times psi^(N/2) of the row's modulus
   DevBuf ext_pattern;      // int16 [beta*rows]: modulus index of the row, -1 = digit row
   DevBuf pq_pattern;       // int16 [rows]: -1 for Q rows, special modulus for P rows
   DevBuf md_pinv, md_pinv_s;  // [l]: P^-1 mod q_i

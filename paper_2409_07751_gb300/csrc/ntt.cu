@@ -309,6 +309,7 @@ constexpr int MAX_SRC = 16;
 
 // plain forward NTT of pattern-selected rows
 struct DescPlain {
+  static constexpr bool FOLD1 = false;  // see DescModUp
   uint64_t* base;
   const int16_t* pattern;
   int P;
@@ -327,6 +328,11 @@ struct DescPlain {
 
 // ModUp target row: sum_a xs[a][i] * [Dhat_a]_{m} mod m, then NTT; digit rows copy d.
 struct DescModUp {
+  // The forward transform's first stage multiplies the upper half of the
+  // row by the single twiddle w = psi^(N/2); the upper half is loaded with
+  // the constants [Dhat_a w]_m instead (load_w), so that stage is a plain
+  // sum and difference (moduli below 2^50).
+  static constexpr bool FOLD1 = true;
   const uint64_t* xs;  // [B][l][N] coefficients already scaled by N^-1 Dhat^-1 (the iNTT post factor)
   const uint64_t* d;   // batch element b at d + b dstride: [l][N] NTT form
   uint64_t* ext;       // [B][beta][rows][N]
@@ -335,6 +341,8 @@ struct DescModUp {
   size_t dstride;
   int l, beta, rows, alpha, L;
   size_t N;
+  const uint64_t* dhw;  // [beta][alpha][rows]: [Dhat_a psi^(N/2)]_m
+  const uint64_t* dhws;
   __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
     const int rr = (int)(blk % rows);
     const int j = (int)((blk / rows) % beta);
@@ -355,6 +363,8 @@ struct DescModUp {
       const size_t ti = ((size_t)(j * alpha) + threadIdx.x) * rows + rr;
       kc[threadIdx.x] = dh[ti];
       kc[MAX_SRC + threadIdx.x] = dhs[ti];
+      kc[2 * MAX_SRC + threadIdx.x] = dhw[ti];
+      kc[3 * MAX_SRC + threadIdx.x] = dhws[ti];
     }
     return true;
   }
@@ -370,6 +380,13 @@ struct DescModUp {
       acc = add_mod(acc, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
     return acc;
   }
+  // the upper-half load times w (moduli below 2^50): below 4 n_src m
+  __device__ uint64_t load_w(const Row& r, uint32_t i, const uint64_t* kc) const {
+    uint64_t acc = 0;
+    for (int a = 0; a < r.n_src; a++)
+      acc += shoup_approx(r.src[(size_t)a * N + i], kc[2 * MAX_SRC + a], kc[3 * MAX_SRC + a], r.aux);
+    return acc;
+  }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
     r.mid[i] = v;
   }
@@ -377,6 +394,7 @@ struct DescModUp {
 
 // ModDown output row i of (b,k): (acc_i - NTT(sum_a y_a [Phat_a]_{q_i})) * P^-1
 struct DescModDown {
+  static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* acc;  // [BK][rows][N]; P rows already inverse-transformed and scaled
   uint64_t* out;        // [BK][l][N]
   const uint64_t* ph;   // [alpha][L+1]
@@ -421,6 +439,7 @@ struct DescModDown {
 
 // Rescale output row t of poly p: (c_t - NTT(centred(last) mod q_t)) * q_level^-1
 struct DescRescale {
+  static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* in;    // [polys][level+1][N]
   const uint64_t* last;  // [polys][N] coefficient form of limb `level`
   uint64_t* out;         // [polys][level][N]
@@ -455,6 +474,7 @@ struct DescRescale {
 // with `last` the coefficient form of k c_level (the inverse transform's post
 // factor carries k) and c read in place (poly p at in + p in_stride).
 struct DescRescaleScaled {
+  static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* in;
   size_t in_stride;
   const uint64_t* last;   // [polys][N]
@@ -506,10 +526,26 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
   constexpr uint32_t COLS = CHUNK / CS;
   for (uint32_t c = rank * COLS + g; c < (rank + 1) * COLS; c += ROW_THREADS) {
     uint64_t x[N1];
+    int m0 = 1;  // first column stage still to run
+    if constexpr (D::FOLD1 && GROW) {
+      // first stage folded into the loads: t = w y comes from load_w, and
+      // u - t + cw with cw = 4 n_src q (a multiple of q above t) stays >= 0
+      const uint64_t cw = 4 * (uint64_t)r.n_src * q;
 #pragma unroll
-    for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc, GROW);
+      for (int s = 0; s < N1 / 2; s++) {
+        const uint64_t u = d.load(r, c + (uint32_t)s * CHUNK, kc, true);
+        const uint64_t t = d.load_w(r, c + (uint32_t)(s + N1 / 2) * CHUNK, kc);
+        x[s] = u + t;
+        x[s + N1 / 2] = u - t + cw;
+      }
+      m0 = 2;
+    } else {
+#pragma unroll
+      for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc, GROW);
+    }
 #pragma unroll
     for (int m = 1; m < N1; m <<= 1) {
+      if (m < m0) continue;
       const int t1 = N1 / (2 * m);
 #pragma unroll
       for (int i = 0; i < m; i++) {
@@ -557,6 +593,7 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
 // y_m the D rows of acc (level .. level+alpha) already inverse-transformed and
 // scaled by (M/m)^-1, with y_level = P d_k + acc_k on q_level.
 struct DescRelinRescale {
+  static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* acc;    // [BK][rows][N]
   const uint64_t* d;      // [B][3][level+1][N] tensor product
   uint64_t* out;          // [BK][level][N]
@@ -622,7 +659,7 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
                const ulonglong2* tw8, size_t nodes) {
   constexpr int CS = fwd_cs<N1>();
   extern __shared__ uint64_t sm[];  // CPC = N1 / CS chunks
-  __shared__ uint64_t kc[2 * MAX_SRC];
+  __shared__ uint64_t kc[4 * MAX_SRC];
   __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
   const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
   const uint32_t row = blockIdx.x / CS;
@@ -856,7 +893,7 @@ void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t d_str
   Launch L_(c, K_MODUP_NTT, W8 * (double)B * (2.0 * T.l + (double)T.beta * T.rows),
             out_rows * ((double)(c.N / 2) * c.log_n + (double)c.alpha * c.N));
   DescModUp dsc{xs, d, ext, T.dh.u64(), T.dh_s.u64(), d_stride, T.l, T.beta, T.rows, c.alpha, c.L,
-                c.N};
+                c.N, T.dhw.u64(), T.dhw_s.u64()};
   launch_fwd(c, B * T.beta * T.rows, dsc);
 }
 
