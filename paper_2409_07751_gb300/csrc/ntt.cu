@@ -392,6 +392,25 @@ struct DescModUp {
   }
 };
 
+// Centred basis conversion of the n_src rows at r.src into modulus m = r.aux:
+// sum_a y_a kc[a] - u [M]_m, with u = r.ov[i] (ModDown, merged division).
+// Exact: in [0, m). Growth-tolerant transforms (m < 2^50) take the lazy form:
+// three-product Shoup terms (each below 4m) plus 256 m - u [M]_m (u <= 255),
+// a value congruent to the exact one and below (4 n_src + 256) m < 2^60.
+__device__ __forceinline__ uint64_t conv_load(const Row& r, uint32_t i, const uint64_t* kc,
+                                              bool grow, size_t N) {
+  const uint64_t m = r.aux;
+  uint64_t s = 0;
+  if (grow) {
+    for (int a = 0; a < r.n_src; a++)
+      s += shoup_approx(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
+    return s + (256 * m - (uint64_t)r.ov[i] * r.km);
+  }
+  for (int a = 0; a < r.n_src; a++)
+    s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
+  return sub_mod(s, mul_shoup((uint64_t)r.ov[i], r.km, r.kms, m), m);
+}
+
 // ModDown output row i of (b,k): (acc_i - NTT(sum_a y_a [Phat_a]_{q_i})) * P^-1
 struct DescModDown {
   static constexpr bool FOLD1 = false;  // see DescModUp
@@ -426,11 +445,7 @@ struct DescModDown {
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
-    const uint64_t m = r.aux;
-    uint64_t s = 0;
-    for (int a = 0; a < r.n_src; a++)
-      s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
-    return sub_mod(s, mul_shoup((uint64_t)r.ov[i], r.km, r.kms, m), m);
+    return conv_load(r, i, kc, grow, N);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
@@ -633,11 +648,7 @@ struct DescRelinRescale {
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
-    const uint64_t m = r.aux;
-    uint64_t s = 0;
-    for (int a = 0; a < r.n_src; a++)
-      s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
-    return sub_mod(s, mul_shoup((uint64_t)r.ov[i], r.km, r.kms, m), m);
+    return conv_load(r, i, kc, grow, N);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     r.mid[i] = add_mod(mul_shoup(r.src3[i], r.k2, r.k2s, q),
