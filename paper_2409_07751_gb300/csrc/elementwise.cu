@@ -36,6 +36,17 @@ __global__ void mul_pt_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* o
   }
 }
 
+// acc += a * pt (the baby-step accumulation of a diagonal matvec, one pass)
+__global__ void mul_pt_acc_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* acc,
+                                  size_t total, int log_n, int l, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, total) {
+    const int t = (int)((i >> log_n) % l);
+    const uint64_t q = mods[t].q;
+    acc[i] = add_mod(acc[i], mul_mod(a[i], pt[(size_t)t * N + (i & (N - 1))], mods[t]), q);
+  }
+}
+
 constexpr int LC_TERMS = 16;
 struct LincombRes {
   uint64_t v[LC_TERMS][MAX_LIMBS];
@@ -159,6 +170,19 @@ __global__ void mul_pt_grouped_kernel(const uint64_t* a, PtSet pts, int K, uint6
   }
 }
 
+// acc += a * pts[b % K] per batch element b (chunked first layers)
+__global__ void mul_pt_acc_grouped_kernel(const uint64_t* a, PtSet pts, int K, uint64_t* acc,
+                                          size_t total, int log_n, int l, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = 2 * (size_t)l * N;
+  GRID_LOOP(i, total) {
+    const int t = (int)((i >> log_n) % l);
+    const int ch = (int)((i / per) % K);
+    acc[i] = add_mod(acc[i], mul_mod(a[i], pts.p[ch][(size_t)t * N + (i & (N - 1))], mods[t]),
+                     mods[t].q);
+  }
+}
+
 // out[b] = sum_{c < K} in[b K + c]  (per ciphertext of `per` words)
 __global__ void chunk_sum_kernel(const uint64_t* in, uint64_t* out, size_t B, int K, int log_n,
                                  int l, const Mod* mods) {
@@ -246,6 +270,15 @@ void k_mul_pt(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size
   CK_CUDA(cudaGetLastError());
 }
 
+void k_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, size_t rows,
+                  int l) {
+  const size_t total = rows * c.N;
+  Launch L_(c, K_MUL_PT, 3.0 * total * 8, (double)total);
+  mul_pt_acc_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, acc, total, c.log_n, l,
+                                                           c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
 void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows, int l) {
   const size_t total = rows * c.N;
   Launch L_(c, K_MUL_INT, 2.0 * total * 8);
@@ -318,6 +351,18 @@ void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_
   Launch L_(c, K_MUL_PT, 2.0 * total * 8, (double)total);
   mul_pt_grouped_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, P, (int)pts.size(), out, total,
                                                                 c.log_n, l, c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_mul_pt_acc_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_t*>& pts,
+                          uint64_t* acc, size_t B, int l) {
+  if (pts.empty() || pts.size() > 16) throw Error(CKKS_ERR_UNSUPPORTED, "1..16 plaintexts");
+  PtSet P{};
+  for (size_t k = 0; k < pts.size(); k++) P.p[k] = pts[k];
+  const size_t total = B * 2 * (size_t)l * c.N;
+  Launch L_(c, K_MUL_PT, 3.0 * total * 8, (double)total);
+  mul_pt_acc_grouped_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, P, (int)pts.size(), acc,
+                                                                    total, c.log_n, l, c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 

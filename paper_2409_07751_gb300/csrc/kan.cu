@@ -185,7 +185,6 @@ Ct bsgs_matvec(kan_model& M, int li, int tag, const Plan& p, int nch, DV&& dval,
   for (int i = 0; i < p.g2; i++) {
     const double Spt = plain_scale(c, v.scale, lv);
     Ct acc = ct_alloc(c, v.B, lv, v.scale * Spt);
-    Ct prod = ct_alloc(c, v.B, lv, v.scale * Spt);
     for (int j = 0; j < p.g1; j++) {
       const int t = p.g1 * i + j;
       std::vector<const uint64_t*> pts;
@@ -197,12 +196,17 @@ Ct bsgs_matvec(kan_model& M, int li, int tag, const Plan& p, int nch, DV&& dval,
           return d;
         }));
       }
-      uint64_t* dst = j == 0 ? acc->d.u64() : prod->d.u64();
-      if (nch == 1)
-        k_mul_pt(c, baby[j]->d.u64(), pts[0], dst, rows, lv + 1);
-      else  // batch element b uses the diagonals of its chunk b % K
-        k_mul_pt_grouped(c, baby[j]->d.u64(), pts, dst, v.B, lv + 1);
-      if (j > 0) k_add(c, acc->d.u64(), prod->d.u64(), acc->d.u64(), rows, lv + 1, false);
+      // batch element b uses the diagonals of its chunk b % K (grouped forms)
+      if (j == 0) {
+        if (nch == 1)
+          k_mul_pt(c, baby[j]->d.u64(), pts[0], acc->d.u64(), rows, lv + 1);
+        else
+          k_mul_pt_grouped(c, baby[j]->d.u64(), pts, acc->d.u64(), v.B, lv + 1);
+      } else if (nch == 1) {
+        k_mul_pt_acc(c, baby[j]->d.u64(), pts[0], acc->d.u64(), rows, lv + 1);
+      } else {
+        k_mul_pt_acc_grouped(c, baby[j]->d.u64(), pts, acc->d.u64(), v.B, lv + 1);
+      }
     }
     Ct inner = op_rescale(c, *acc);
     if (i > 0) inner = op_rotate(c, keys, *inner, (int64_t)p.g1 * i);

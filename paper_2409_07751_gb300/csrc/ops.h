@@ -61,6 +61,11 @@ void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::ve
 void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
                      uint64_t* out, size_t B, int l);
 // batch element b of a [B][2][l][N] batch multiplied by pts[b % pts.size()]
+// acc += a * pt (one pass), and the per-chunk form of it
+void k_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, size_t rows,
+                  int l);
+void k_mul_pt_acc_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_t*>& pts,
+                          uint64_t* acc, size_t B, int l);
 void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_t*>& pts,
                       uint64_t* out, size_t B, int l);
 // out[b] = sum_c in[b K + c]
