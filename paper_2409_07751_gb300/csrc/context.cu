@@ -457,6 +457,7 @@ ConvTables& Ctx::tables(int level) {
       pqs[i] = shoup_h(P, mod[i]);
     }
     T->md_inv = upload(this, inv);
+    T->md_inv_h = inv;
     T->md_pq = upload(this, pq);
     T->md_pq_s = upload(this, pqs);
   }
@@ -499,6 +500,7 @@ ConvTables& Ctx::tables(int level) {
       mqs[i] = shoup_h(Mi, mod[i]);
     }
     T->rr_inv = upload(this, rinv);
+    T->rr_inv_h = rinv;
     T->rr_mq = upload(this, mq);
     T->rr_mq_s = upload(this, mqs);
     uint64_t Pq = 1;

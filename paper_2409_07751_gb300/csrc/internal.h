@@ -76,6 +76,7 @@ struct ConvTables {
   // centred conversions: overflow u = floor(sum_m v_m / m + 1/2) in double,
   // then u [M]_{q_i} subtracted (M = P for ModDown, P q_level merged)
   DevBuf md_inv;              // double [alpha]: 1 / p_a
+  std::vector<double> md_inv_h, rr_inv_h;  // host copies of md_inv and rr_inv
   DevBuf md_pq, md_pq_s;      // [l]: P mod q_i
   DevBuf rr_inv;              // double [alpha+1]: 1 / q_level, 1 / p_a
   DevBuf rr_mq, rr_mq_s;      // [l]: M mod q_i

@@ -330,18 +330,46 @@ __global__ void moddown_conv_kernel(const uint64_t* acc, uint64_t* conv, size_t 
   }
 }
 
+// The same u, decided in single precision wherever that is certain. Each
+// term v_m / m < 1 is within 3.0001 u of its float product (u = 2^-24: the
+// conversions of v_m and 1/m and the product), the running sums of at most
+// 17 terms (partial sums below 17) add at most 152 u, and t = s + 1/2 one
+// more rounding below 18 u: |t - (S + 1/2)| < 221 u < 1.4e-5 for the exact
+// S = sum_m v_m / m. When the fraction of t is more than 2^-10 from an
+// integer, floor(t) = floor(S + 1/2) = the double expression's result (that
+// one is within 1e-13 of S + 1/2); otherwise the double expression decides.
+struct InvF {
+  float v[MAX_ALPHA + 1];  // float(1 / m)
+};
+__device__ __forceinline__ uint64_t conv_overflow_fast(const uint64_t* v, const double* inv,
+                                                       const InvF& invf, int n) {
+  float s = 0.0f;
+  for (int m = 0; m < n; m++) s = __fadd_rn(s, __fmul_rn(__ull2float_rn(v[m]), invf.v[m]));
+  const float t = __fadd_rn(s, 0.5f);
+  const float f = floorf(t);
+  const float fr = t - f;  // exact (Sterbenz)
+  if (fr > 0x1p-10f && fr < 1.0f - 0x1p-10f) return (uint64_t)f;
+  return conv_overflow(v, inv, n);
+}
+
 // fused paths: u per (bk, n) from `count` rows starting at `first`, which
 // already hold v_m (inverse-transformed and scaled by (M/m)^-1)
 __global__ void overflow_kernel(const uint64_t* acc, uint8_t* ov, size_t BK, int log_n, int first,
-                                int count, int rows, const double* inv) {
+                                int count, int rows, const double* inv, InvF invf) {
   const size_t N = (size_t)1 << log_n;
   GRID_LOOP(idx, BK * N) {
     const size_t n = idx & (N - 1);
     const size_t bk = idx >> log_n;
     uint64_t v[MAX_ALPHA + 1];
     for (int m = 0; m < count; m++) v[m] = acc[(bk * rows + first + m) * N + n];
-    ov[idx] = (uint8_t)conv_overflow(v, inv, count);
+    ov[idx] = (uint8_t)conv_overflow_fast(v, inv, invf, count);
   }
+}
+
+InvF inv_float(const std::vector<double>& inv) {
+  InvF f{};
+  for (size_t m = 0; m < inv.size() && m < (size_t)(MAX_ALPHA + 1); m++) f.v[m] = (float)inv[m];
+  return f;
 }
 
 __global__ void moddown_finish_kernel(const uint64_t* acc, const uint64_t* conv, uint64_t* out,
@@ -545,7 +573,7 @@ void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B,
       Launch L_(c, K_OVERFLOW, W8 * B * 2.0 * (c.alpha + 1.0) + B * 2.0 * c.N);
       overflow_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
           acc.u64(), static_cast<uint8_t*>(ov.p), B * 2, c.log_n, level, c.alpha + 1, rows,
-          static_cast<const double*>(T.rr_inv.p));
+          static_cast<const double*>(T.rr_inv.p), inv_float(T.rr_inv_h));
       CK_CUDA(cudaGetLastError());
     }
     ntt_relin_rescale_fused(c, acc.u64(), d, static_cast<const uint8_t*>(ov.p), B, level, out);
@@ -584,7 +612,7 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
       Launch L_(c, K_OVERFLOW, W8 * B * 2.0 * c.alpha + B * 2.0 * c.N);
       overflow_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
           acc.u64(), static_cast<uint8_t*>(ov.p), B * 2, c.log_n, l, c.alpha, rows,
-          static_cast<const double*>(T.md_inv.p));
+          static_cast<const double*>(T.md_inv.p), inv_float(T.md_inv_h));
       CK_CUDA(cudaGetLastError());
     }
     ntt_moddown_fused(c, acc.u64(), static_cast<const uint8_t*>(ov.p), B * 2, level, out);
