@@ -18,30 +18,29 @@ inline unsigned grid_for(size_t total) {
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (total); idx += (size_t)gridDim.x * blockDim.x)
 
 __global__ void add_kernel(const uint64_t* a, const uint64_t* b, uint64_t* out, size_t total,
-                           int log_n, int l, const Mod* mods, bool sub) {
+                           int log_n, DivU32 l, const Mod* mods, bool sub) {
   GRID_LOOP(i, total) {
-    const int t = (int)((i >> log_n) % l);
+    const int t = (int)umod((uint32_t)(i >> log_n), l);
     const uint64_t q = mods[t].q;
     out[i] = sub ? sub_mod(a[i], b[i], q) : add_mod(a[i], b[i], q);
   }
 }
 
 __global__ void mul_pt_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t total,
-                              int log_n, int l, const Mod* mods) {
+                              int log_n, DivU32 l, const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
   GRID_LOOP(i, total) {
-    const size_t row = i >> log_n;
-    const int t = (int)(row % l);
+    const int t = (int)umod((uint32_t)(i >> log_n), l);
     out[i] = mul_mod(a[i], pt[(size_t)t * N + (i & (N - 1))], mods[t]);
   }
 }
 
 // acc += a * pt (the baby-step accumulation of a diagonal matvec, one pass)
 __global__ void mul_pt_acc_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* acc,
-                                  size_t total, int log_n, int l, const Mod* mods) {
+                                  size_t total, int log_n, DivU32 l, const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
   GRID_LOOP(i, total) {
-    const int t = (int)((i >> log_n) % l);
+    const int t = (int)umod((uint32_t)(i >> log_n), l);
     const uint64_t q = mods[t].q;
     acc[i] = add_mod(acc[i], mul_mod(a[i], pt[(size_t)t * N + (i & (N - 1))], mods[t]), q);
   }
@@ -53,50 +52,51 @@ struct LincombRes {
 };
 
 __global__ void mul_int_kernel(const uint64_t* a, LimbRes k, uint64_t* out, size_t total,
-                               int log_n, int l, const Mod* mods) {
+                               int log_n, DivU32 l, const Mod* mods) {
   GRID_LOOP(i, total) {
-    const int t = (int)((i >> log_n) % l);
+    const int t = (int)umod((uint32_t)(i >> log_n), l);
     out[i] = mul_mod(a[i], k.v[t], mods[t]);
   }
 }
 
 // poly 0 of each batch element += k (a constant polynomial is constant in NTT form)
-__global__ void add_int_c0_kernel(uint64_t* a, LimbRes k, size_t B, int log_n, int l,
+__global__ void add_int_c0_kernel(uint64_t* a, LimbRes k, size_t B, int log_n, DivU32 l,
                                   const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
-  const size_t per = (size_t)l * N;
+  const size_t per = (size_t)l.d * N;
   GRID_LOOP(i, B * per) {
-    const size_t b = i / per, r = i % per;
-    const int t = (int)(r >> log_n);
+    const uint32_t row = (uint32_t)(i >> log_n);
+    const size_t b = udiv(row, l);
+    const int t = (int)(row - (uint32_t)b * l.d);
+    const size_t r = ((size_t)t << log_n) | (i & (N - 1));
     uint64_t* p = a + b * 2 * per + r;
     *p = add_mod(*p, k.v[t], mods[t].q);
   }
 }
 
 __global__ void add_pt_c0_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t B,
-                                 int log_n, int l, const Mod* mods) {
+                                 int log_n, DivU32 l2, const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
-  const size_t per = (size_t)l * N;
-  GRID_LOOP(i, B * 2 * per) {
-    const size_t b = i / (2 * per), r = i % (2 * per);
-    if (r < per) {
-      const int t = (int)(r >> log_n);
-      out[i] = add_mod(a[i], pt[r], mods[t].q);
-    } else {
+  const uint32_t l = l2.d / 2;
+  GRID_LOOP(i, B * l2.d * N) {
+    const uint32_t t = umod((uint32_t)(i >> log_n), l2);  // row within (poly 0, poly 1)
+    if (t < l)
+      out[i] = add_mod(a[i], pt[((size_t)t << log_n) | (i & (N - 1))], mods[t].q);
+    else
       out[i] = a[i];
-    }
-    (void)b;
   }
 }
 
 // (a0, a1) x (b0, b1) -> (a0 b0, a0 b1 + a1 b0, a1 b1)
 __global__ void tensor_kernel(const uint64_t* a, const uint64_t* b, uint64_t* out, size_t B,
-                              int log_n, int l, const Mod* mods, bool acc) {
+                              int log_n, DivU32 l, const Mod* mods, bool acc) {
   const size_t N = (size_t)1 << log_n;
-  const size_t per = (size_t)l * N;
+  const size_t per = (size_t)l.d * N;
   GRID_LOOP(i, B * per) {
-    const size_t bb = i / per, r = i % per;
-    const int t = (int)(r >> log_n);
+    const uint32_t row = (uint32_t)(i >> log_n);
+    const size_t bb = udiv(row, l);
+    const int t = (int)(row - (uint32_t)bb * l.d);
+    const size_t r = ((size_t)t << log_n) | (i & (N - 1));
     const Mod m = mods[t];
     const uint64_t* pa = a + bb * 2 * per + r;
     const uint64_t* pb = b + bb * 2 * per + r;
@@ -121,9 +121,9 @@ struct Ptrs {
 };
 
 __global__ void lincomb_kernel(Ptrs in, LincombRes k, int K, uint64_t* out, size_t total,
-                               int log_n, int l, const Mod* mods) {
+                               int log_n, DivU32 l, const Mod* mods) {
   GRID_LOOP(i, total) {
-    const int t = (int)((i >> log_n) % l);
+    const int t = (int)umod((uint32_t)(i >> log_n), l);
     const Mod m = mods[t];
     uint64_t acc = 0;
     for (int j = 0; j < K; j++) acc = add_mod(acc, mul_mod(in.p[j][i], k.v[j][t], m), m.q);
@@ -142,12 +142,14 @@ __global__ void automorphism_kernel(const uint64_t* in, uint64_t* out, size_t to
 
 // out = (sigma(a0) + ks0, ks1) per batch element
 __global__ void rotate_finish_kernel(const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
-                                     uint64_t* out, size_t B, int log_n, int l, const Mod* mods) {
+                                     uint64_t* out, size_t B, int log_n, DivU32 l, const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
-  const size_t per = (size_t)l * N;
+  const size_t per = (size_t)l.d * N;
   GRID_LOOP(i, B * per) {
-    const size_t b = i / per, r = i % per;
-    const int t = (int)(r >> log_n);
+    const uint32_t row = (uint32_t)(i >> log_n);
+    const size_t b = udiv(row, l);
+    const int t = (int)(row - (uint32_t)b * l.d);
+    const size_t r = ((size_t)t << log_n) | (i & (N - 1));
     const size_t row0 = b * 2 * per + (r & ~(N - 1));
     const uint64_t src = a[row0 + perm[r & (N - 1)]];
     out[b * 2 * per + r] = add_mod(src, ks[b * 2 * per + r], mods[t].q);
@@ -160,24 +162,26 @@ struct PtSet {
   const uint64_t* p[16];
 };
 __global__ void mul_pt_grouped_kernel(const uint64_t* a, PtSet pts, int K, uint64_t* out,
-                                      size_t total, int log_n, int l, const Mod* mods) {
+                                      size_t total, int log_n, DivU32 l, DivU32 l2,
+                                      const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
-  const size_t per = 2 * (size_t)l * N;
   GRID_LOOP(i, total) {
-    const int t = (int)((i >> log_n) % l);
-    const int ch = (int)((i / per) % K);
+    const uint32_t row = (uint32_t)(i >> log_n);
+    const int t = (int)umod(row, l);
+    const int ch = (int)(udiv(row, l2) % (uint32_t)K);
     out[i] = mul_mod(a[i], pts.p[ch][(size_t)t * N + (i & (N - 1))], mods[t]);
   }
 }
 
 // acc += a * pts[b % K] per batch element b (chunked first layers)
 __global__ void mul_pt_acc_grouped_kernel(const uint64_t* a, PtSet pts, int K, uint64_t* acc,
-                                          size_t total, int log_n, int l, const Mod* mods) {
+                                          size_t total, int log_n, DivU32 l, DivU32 l2,
+                                          const Mod* mods) {
   const size_t N = (size_t)1 << log_n;
-  const size_t per = 2 * (size_t)l * N;
   GRID_LOOP(i, total) {
-    const int t = (int)((i >> log_n) % l);
-    const int ch = (int)((i / per) % K);
+    const uint32_t row = (uint32_t)(i >> log_n);
+    const int t = (int)umod(row, l);
+    const int ch = (int)(udiv(row, l2) % (uint32_t)K);
     acc[i] = add_mod(acc[i], mul_mod(a[i], pts.p[ch][(size_t)t * N + (i & (N - 1))], mods[t]),
                      mods[t].q);
   }
@@ -185,11 +189,16 @@ __global__ void mul_pt_acc_grouped_kernel(const uint64_t* a, PtSet pts, int K, u
 
 // out[b] = sum_{c < K} in[b K + c]  (per ciphertext of `per` words)
 __global__ void chunk_sum_kernel(const uint64_t* in, uint64_t* out, size_t B, int K, int log_n,
-                                 int l, const Mod* mods) {
-  const size_t per = 2 * (size_t)l << log_n;
+                                 DivU32 l2, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const size_t per = (size_t)l2.d << log_n;
+  const uint32_t l = l2.d / 2;
   GRID_LOOP(i, B * per) {
-    const size_t b = i / per, r = i % per;
-    const int t = (int)((r >> log_n) % l);
+    const uint32_t row = (uint32_t)(i >> log_n);
+    const size_t b = udiv(row, l2);
+    const uint32_t rr = row - (uint32_t)b * l2.d;  // row within (poly 0, poly 1)
+    const int t = (int)(rr < l ? rr : rr - l);
+    const size_t r = ((size_t)rr << log_n) | (i & (N - 1));
     const uint64_t q = mods[t].q;
     uint64_t s = in[(b * K) * per + r];
     for (int c = 1; c < K; c++) s = add_mod(s, in[(b * K + c) * per + r], q);
@@ -259,14 +268,16 @@ void k_add(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t r
            bool sub) {
   const size_t total = rows * c.N;
   Launch L_(c, K_ADD, 3.0 * total * 8);
-  add_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, b, out, total, c.log_n, l, c.dmod(), sub);
+  add_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, b, out, total, c.log_n, divu(l), c.dmod(),
+                                                    sub);
   CK_CUDA(cudaGetLastError());
 }
 
 void k_mul_pt(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t rows, int l) {
   const size_t total = rows * c.N;
   Launch L_(c, K_MUL_PT, 2.0 * total * 8);
-  mul_pt_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, out, total, c.log_n, l, c.dmod());
+  mul_pt_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, out, total, c.log_n, divu(l),
+                                                       c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
@@ -274,7 +285,7 @@ void k_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, 
                   int l) {
   const size_t total = rows * c.N;
   Launch L_(c, K_MUL_PT, 3.0 * total * 8, (double)total);
-  mul_pt_acc_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, acc, total, c.log_n, l,
+  mul_pt_acc_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, acc, total, c.log_n, divu(l),
                                                            c.dmod());
   CK_CUDA(cudaGetLastError());
 }
@@ -283,29 +294,29 @@ void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows,
   const size_t total = rows * c.N;
   Launch L_(c, K_MUL_INT, 2.0 * total * 8);
   mul_int_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, limb_res(c, k, l), out, total, c.log_n,
-                                                        l, c.dmod());
+                                                        divu(l), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l) {
   Launch L_(c, K_ADD, 2.0 * B * l * c.N * 8);
   add_int_c0_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, limb_res(c, k, l), B, c.log_n,
-                                                                 l, c.dmod());
+                                                                 divu(l), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_add_pt_c0(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* out, size_t B, int l) {
   Launch L_(c, K_ADD, 5.0 * B * l * c.N * 8);
-  add_pt_c0_kernel<<<grid_for(B * 2 * l * c.N), TPB, 0, c.stream>>>(a, pt, out, B, c.log_n, l,
-                                                                     c.dmod());
+  add_pt_c0_kernel<<<grid_for(B * 2 * l * c.N), TPB, 0, c.stream>>>(a, pt, out, B, c.log_n,
+                                                                     divu(2 * l), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_tensor(Ctx& c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t B, int l,
               bool accumulate) {
   Launch L_(c, K_TENSOR, (accumulate ? 10.0 : 7.0) * B * l * c.N * 8);
-  tensor_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, b, out, B, c.log_n, l, c.dmod(),
-                                                             accumulate);
+  tensor_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, b, out, B, c.log_n, divu(l),
+                                                             c.dmod(), accumulate);
   CK_CUDA(cudaGetLastError());
 }
 
@@ -324,7 +335,7 @@ void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::ve
   const size_t total = rows * c.N;
   Launch L_(c, K_LINCOMB, (in.size() + 1.0) * total * 8);
   lincomb_kernel<<<grid_for(total), TPB, 0, c.stream>>>(P, C, (int)in.size(), out, total, c.log_n,
-                                                        l, c.dmod());
+                                                        divu(l), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
@@ -350,7 +361,8 @@ void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_
   const size_t total = B * 2 * (size_t)l * c.N;
   Launch L_(c, K_MUL_PT, 2.0 * total * 8, (double)total);
   mul_pt_grouped_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, P, (int)pts.size(), out, total,
-                                                                c.log_n, l, c.dmod());
+                                                                c.log_n, divu(l), divu(2 * l),
+                                                                c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
@@ -362,14 +374,16 @@ void k_mul_pt_acc_grouped(Ctx& c, const uint64_t* a, const std::vector<const uin
   const size_t total = B * 2 * (size_t)l * c.N;
   Launch L_(c, K_MUL_PT, 3.0 * total * 8, (double)total);
   mul_pt_acc_grouped_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, P, (int)pts.size(), acc,
-                                                                    total, c.log_n, l, c.dmod());
+                                                                    total, c.log_n, divu(l),
+                                                                    divu(2 * l), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
 void k_chunk_sum(Ctx& c, const uint64_t* in, uint64_t* out, size_t B, int K, int l) {
   const size_t total = B * 2 * (size_t)l * c.N;
   Launch L_(c, K_ADD, (K + 1.0) * total * 8);
-  chunk_sum_kernel<<<grid_for(total), TPB, 0, c.stream>>>(in, out, B, K, c.log_n, l, c.dmod());
+  chunk_sum_kernel<<<grid_for(total), TPB, 0, c.stream>>>(in, out, B, K, c.log_n, divu(2 * l),
+                                                          c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 
@@ -377,7 +391,7 @@ void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32
                      uint64_t* out, size_t B, int l) {
   Launch L_(c, K_ROT_FINISH, 5.0 * B * l * c.N * 8);
   rotate_finish_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, ks, perm, out, B, c.log_n,
-                                                                    l, c.dmod());
+                                                                    divu(l), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 

@@ -70,6 +70,27 @@ __device__ __forceinline__ uint64_t smod64(int64_t v, uint64_t q) {
   return m ? q - m : 0;
 }
 
+// Division of a 32-bit n by a fixed divisor d >= 1 with a precomputed
+// multiplier (the round-up method of Granlund and Montgomery, 1994): with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
+// n / d = (hi32(n m) + n) >> s for every n < 2^32 (the sum in 64 bits).
+// Kernels use it for the row -> (batch element, limb) split of their index.
+struct DivU32 {
+  uint32_t d, m, s;
+};
+inline DivU32 divu(int d) {
+  DivU32 r{(uint32_t)d, 0, 0};
+  while ((1ull << r.s) < r.d) r.s++;
+  r.m = (uint32_t)(((1ull << 32) * ((1ull << r.s) - r.d)) / r.d + 1);
+  return r;
+}
+__device__ __forceinline__ uint32_t udiv(uint32_t n, const DivU32& D) {
+  return (uint32_t)(((uint64_t)__umulhi(n, D.m) + n) >> D.s);
+}
+__device__ __forceinline__ uint32_t umod(uint32_t n, const DivU32& D) {
+  return n - udiv(n, D) * D.d;
+}
+
 // per-limb residues of host constants, passed by value to kernels
 constexpr int MAX_LIMBS = 64;
 struct LimbRes {
