@@ -55,7 +55,7 @@ __global__ void mul_int_kernel(const uint64_t* a, LimbRes k, uint64_t* out, size
                                int log_n, DivU32 l, const Mod* mods) {
   GRID_LOOP(i, total) {
     const int t = (int)umod((uint32_t)(i >> log_n), l);
-    out[i] = mul_mod(a[i], k.v[t], mods[t]);
+    out[i] = mul_shoup(a[i], k.v[t], k.s[t], mods[t].q);
   }
 }
 
@@ -258,6 +258,7 @@ LimbRes limb_res(const Ctx& c, int64_t k, int l) {
       const uint64_t m = ((uint64_t)(-(k + 1)) + 1) % q;
       r.v[t] = m ? q - m : 0;
     }
+    r.s[t] = shoup_h(r.v[t], q);
   }
   return r;
 }

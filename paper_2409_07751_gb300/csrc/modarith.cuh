@@ -95,6 +95,7 @@ __device__ __forceinline__ uint32_t umod(uint32_t n, const DivU32& D) {
 constexpr int MAX_LIMBS = 64;
 struct LimbRes {
   uint64_t v[MAX_LIMBS];
+  uint64_t s[MAX_LIMBS];  // Shoup companions floor(v 2^64 / q_t)
 };
 
 }  // namespace ck
