@@ -98,6 +98,9 @@ def args_():
                         "sets log-n, levels, batch and alpha)")
     p.add_argument("--table3", action="store_true",
                    help="one KAN layer per (n_i, g, k) shape: lazy combination vs the naive method")
+    p.add_argument("--oracle-micro", action="store_true",
+                   help="with --impl reference: also time the oracle's NTT per limb, HMult and "
+                        "HRot at the top level (single thread; about a minute)")
     p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
     p.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals for --serve")
     return p.parse_args()
@@ -563,7 +566,38 @@ def reference_arm(a):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if a.oracle_micro:
+        line["oracle_micro"] = oracle_micro(a)
     print(json.dumps(line), flush=True)
+
+
+def oracle_micro(a):
+    """Single-threaded oracle op times at the workload's ring and top level,
+    in the digit layout of the reference arm: forward and inverse NTT per
+    limb, HMult (tensor, merged relinearise-rescale) and HRot of one
+    ciphertext. Keys and inputs are seeded; one run of each op."""
+    import numpy as np
+    from oracle import ckks as O
+    ctx = O.Ctx(O.Params(a.log_n, a.levels, a.alpha, p_bits=a.p_bits))
+    keys = O.Keys(ctx, 7, [1])
+    v = np.random.default_rng(5).uniform(-1, 1, ctx.slots)
+    x = O.encrypt(ctx, keys, v, a.levels, 9, 0)
+    limbs = a.levels + 1
+    rows = np.random.default_rng(6).integers(0, 2**39, (limbs, 1 << a.log_n), dtype=np.uint64)
+    out = {"n_poly": 1 << a.log_n, "limbs": limbs, "alpha": a.alpha, "p_bits": a.p_bits,
+           "threads": 1}
+    for name, inv in (("ntt_ms_per_limb", 0), ("intt_ms_per_limb", 1)):
+        t0 = time.perf_counter()
+        for t in range(limbs):
+            ctx.L_.or_ntt_limb(ctx.h, rows[t].ctypes.data, t, inv)
+        out[name] = 1000.0 * (time.perf_counter() - t0) / limbs
+    t0 = time.perf_counter()
+    O.mul(ctx, keys, x, x)
+    out["hmult_ms"] = 1000.0 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    O.rotate(ctx, keys, x, 1)
+    out["hrot_ms"] = 1000.0 * (time.perf_counter() - t0)
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
