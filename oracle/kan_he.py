@@ -31,6 +31,14 @@ def pow2ceil(n):
     return 1 << max(0, (int(n) - 1).bit_length())
 
 
+def rep_bits(layer):
+    """J of Algorithm 1: 2^J >= the ColTile blocks Algorithm 2 compares,
+    g + 2k (one per order-0 basis function), or g + 2k + 1 for the
+    difference form of B_{m,0}, which compares against every knot."""
+    blocks = layer["G"] + 2 * layer["k"] + (1 if layer.get("b0") == "difference" else 0)
+    return math.ceil(math.log2(blocks))
+
+
 # ------------------------------------------------------------------ Algorithm 3
 def permutation_matrix(n_r, n_c):
     """Algorithm 3 (1-indexed in the paper): P[(r-1)n_c + c][(c-1)n_r + r] = 1."""
@@ -234,7 +242,7 @@ def layer_rotations(layer, slots):
     K, n_c = chunking(layer, slots)
     n_o, G, k = layer["n_out"], layer["G"], layer["k"]
     n_i = n_c
-    J = math.ceil(math.log2(G + 2 * k))
+    J = rep_bits(layer)
     steps = {-n_i * 2 ** (j - 1) for j in range(1, J + 1)}
     steps.add(n_i)
     plans = [(n_o, n_i * (G + k)), (n_o, n_i)]
@@ -255,9 +263,9 @@ def layer_eval(ctx, keys, x, layer):
     S = ctx.slots
     n_i, n_o, G, k = layer["n_in"], layer["n_out"], layer["G"], layer["k"]
     R = layer["R"]
-    J = math.ceil(math.log2(G + 2 * k))
+    J = rep_bits(layer)
     if n_i * 2 ** J > S:
-        raise ValueError("repeat packing needs n_i * 2^ceil(log2(g+2k)) <= N/2")
+        raise ValueError("repeat packing needs n_i * 2^J <= N/2")
     mask = np.ones(n_i)
 
     # SiLU branch: y = affine(x) on the masked slots, replicated to period npad
@@ -280,14 +288,24 @@ def layer_eval(ctx, keys, x, layer):
     r = G + 2 * k + 1
     g1 = coltile(Gm, 1, r)
     g2 = coltile(Gm, 2, r + 1)
-    a1 = ckks.add_plain(ctx, xr, -g1 / (2.0 * R))
-    a2 = ckks.add_plain(ctx, ckks.mul_int(ctx, xr, -1), g2 / (2.0 * R))
-    s1 = polycomp0(ctx, keys, a1, layer["comp"])
-    s2 = polycomp0(ctx, keys, a2, layer["comp"])
-    b = ckks.mul(ctx, keys, s1, s2)
+    if layer.get("b0") == "difference":
+        # B_{m,0} = s_m - s_{m+1}, s_m = PolyComp(x - t_m) over the g + 2k + 1
+        # knots: one comparison, and rot(s, n_i) brings block m + 1 to block
+        # m (no product, one level fewer); block g + 2k is left with garbage
+        # that the recursion's zero coefficients (or the k = 0 mask) remove
+        g0 = coltile(Gm, 1, r + 1)
+        s_ = polycomp0(ctx, keys, ckks.add_plain(ctx, xr, -g0 / (2.0 * R)), layer["comp"])
+        b = ckks.sub(ctx, s_, ckks.rotate(ctx, keys, s_, n_i))
+    else:
+        a1 = ckks.add_plain(ctx, xr, -g1 / (2.0 * R))
+        a2 = ckks.add_plain(ctx, ckks.mul_int(ctx, xr, -1), g2 / (2.0 * R))
+        s1 = polycomp0(ctx, keys, a1, layer["comp"])
+        s2 = polycomp0(ctx, keys, a2, layer["comp"])
+        b = ckks.mul(ctx, keys, s1, s2)
     if k == 0:
-        # order-0 basis: outside its n_i g valid slots b holds PolyComp(0)^2 =
-        # 1/4, which the matvec's replication would fold in; zero it (1 level)
+        # order-0 basis: outside its n_i g valid slots b holds leftovers
+        # (PolyComp(0)^2 = 1/4 in the product form), which the matvec's
+        # replication would fold in; zero it (1 level)
         b = ckks.mul_plain(ctx, b, np.ones(n_i * G))
     for j in range(1, k + 1):
         t1 = coltile(Gm, 1, r - j)
@@ -329,7 +347,7 @@ def chunking(layer, slots):
     """(K, n_c): a layer whose repeat-packed input n_i 2^ceil(log2(g+2k))
     exceeds the slots takes K input ciphertexts of n_c = slots / 2^J inputs
     each (the last one zero-padded); otherwise (1, n_i)."""
-    J = math.ceil(math.log2(layer["G"] + 2 * layer["k"]))
+    J = rep_bits(layer)
     cap = slots >> J
     n_i = layer["n_in"]
     if n_i <= cap:

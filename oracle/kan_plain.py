@@ -72,12 +72,22 @@ def polycomp0(a, stages):
     return 0.5 + 0.5 * u
 
 
-def bspline_hef(x, t, k, R, stages):
-    """Algorithm 2 on plaintext values: soft order-0 indicators, same recursion."""
+def bspline_hef(x, t, k, R, stages, b0="product"):
+    """Algorithm 2 on plaintext values: soft order-0 indicators, same recursion.
+
+    b0 = "product": B_{m,0} = PolyComp(x - t_m) PolyComp(t_{m+1} - x) as in
+    Algorithm 2. b0 = "difference": B_{m,0} = s_m - s_{m+1} with
+    s_m = PolyComp(x - t_m), one comparison per knot and no product; the two
+    agree for exact comparisons (PolyComp(-a) = 1 - PolyComp(a) since f is
+    odd, and s_m s_{m+1} = s_{m+1} for exact steps at t_m < t_{m+1})."""
     x = np.asarray(x, dtype=np.float64)[..., None]
-    s1 = polycomp0((x - t[:-1]) / (2.0 * R), stages)
-    s2 = polycomp0((t[1:] - x) / (2.0 * R), stages)
-    B = s1 * s2
+    if b0 == "difference":
+        s = polycomp0((x - t) / (2.0 * R), stages)
+        B = s[..., :-1] - s[..., 1:]
+    else:
+        s1 = polycomp0((x - t[:-1]) / (2.0 * R), stages)
+        s2 = polycomp0((t[1:] - x) / (2.0 * R), stages)
+        B = s1 * s2
     for j in range(1, k + 1):
         left = (x - t[: -(j + 1)]) / (t[j:-1] - t[: -(j + 1)]) * B[..., :-1]
         right = (t[j + 1:] - x) / (t[j + 1:] - t[1:-j]) * B[..., 1:]
@@ -101,7 +111,7 @@ def layer_forward(layer, x, silu_mode="exact", basis_mode="exact"):
     if basis_mode == "exact":
         B = bspline_exact(x, t, layer["k"])
     else:
-        B = bspline_hef(x, t, layer["k"], layer["R"], layer["comp"])
+        B = bspline_hef(x, t, layer["k"], layer["R"], layer["comp"], layer.get("b0", "product"))
     base = sx @ layer["w_b"].T
     spline = np.einsum("bim,oim,oi->bo", B, layer["coef"], layer["w_s"])
     return base + spline

@@ -375,6 +375,9 @@ def rotate_hoisted(ctx, keys, a, steps):
 def _descs(layers, keep):
     descs = (KanLayerDesc * len(layers))()
     for d, L in zip(descs, layers):
+        if L.get("b0", "product") != "product":
+            raise ValueError("the library builds the order-0 basis in Algorithm 2's product "
+                             "form; b0=%r is not available" % (L["b0"],))
         arrs = [np.ascontiguousarray(L[k], dtype=np.float64) for k in ("coef", "w_s", "w_b")]
         cheb = np.ascontiguousarray(L.get("silu_cheb", [0.0, 0.0]), dtype=np.float64)
         comp = np.ascontiguousarray(L.get("comp", [1]), dtype=np.int32)

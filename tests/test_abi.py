@@ -39,3 +39,15 @@ def test_library_exports_every_declared_symbol():
 def test_binding_signatures_cover_the_header():
     from paper_2409_07751_gb300 import ckks
     assert declared() <= set(ckks.SIGNATURES)
+
+
+def test_model_descriptor_rejects_unsupported_b0_form():
+    """Layers asking for the difference form of the order-0 basis are
+    refused by the binding instead of being evaluated in another form."""
+    import pytest
+    from paper_2409_07751_gb300 import ckks, workloads as W
+    m = W.make_model("t", widths=[3, 2], G=3, k=2)
+    ckks._descs(m, [])  # the product form builds
+    m[0]["b0"] = "difference"
+    with pytest.raises(ValueError):
+        ckks._descs(m, [])

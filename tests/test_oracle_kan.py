@@ -52,6 +52,27 @@ def test_alg2_with_exact_comparison_is_cox_de_boor(monkeypatch):
         assert np.abs(kan_plain.bspline_hef(x, t, k, 2.0, [3]) - kan_plain.bspline_exact(x, t, k)).max() < 1e-13
 
 
+def test_b0_difference_form_with_exact_comparison_is_cox_de_boor(monkeypatch):
+    """The difference form B_{m,0} = s_m - s_{m+1} of the order-0 basis,
+    with PolyComp replaced by the exact step, also reproduces Eq. 3."""
+    monkeypatch.setattr(kan_plain, "polycomp0", lambda a, stages: (a > 0).astype(float))
+    for G, k in [(5, 3), (10, 5), (3, 2), (4, 0)]:
+        L = _layer(G, k)
+        t = kan_plain.knots(L)
+        x = np.random.default_rng(2).uniform(-1, 1, 300)
+        B = kan_plain.bspline_hef(x, t, k, 2.0, [3], b0="difference")
+        assert np.abs(B - kan_plain.bspline_exact(x, t, k)).max() < 1e-13
+
+
+def test_polycomp_odd_symmetry():
+    """PolyComp(-a) = 1 - PolyComp(a) for the odd composites, the identity
+    under which the product and difference forms of B_{m,0} coincide for
+    exact steps."""
+    a = np.random.default_rng(3).uniform(-1, 1, 1000)
+    for stages in ([1], [3], [3, 3], [2, 5]):
+        assert np.abs(kan_plain.polycomp0(-a, stages) - (1.0 - kan_plain.polycomp0(a, stages))).max() < 1e-15
+
+
 def test_fn_closed_forms():
     assert kan_plain.fn_coeffs(1) == [1.5, -0.5]
     assert kan_plain.fn_coeffs(2) == [15 / 8, -10 / 8, 3 / 8]
@@ -216,6 +237,30 @@ def test_he_kan_matches_hef(he_small):
         dec = ckks.decrypt(ctx, keys, out, 2)
         hef = kan_plain.forward(m, X[b:b + 1], "poly", "poly")[0]
         assert np.abs(dec - hef).max() < 1e-5
+
+
+@pytest.mark.parametrize("G_,k_", [(3, 2), (4, 0)])
+def test_he_kan_b0_difference_form_matches_hef(he_small, G_, k_):
+    """With B_{m,0} = s_m - s_{m+1} (one comparison per knot, rot(s, n_i)
+    for s_{m+1}, no product) the encrypted network equals the HE-friendly
+    KAN of the same form and, where the spline branch is the deeper one
+    (k >= 1 here), ends one level higher per layer than the product form."""
+    ctx = he_small
+    model = W.make_model("t", widths=[3, 4, 2], G=G_, k=k_)
+    for L in model:
+        L["b0"] = "difference"
+    X = W.uniform_inputs(100, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    keys = ckks.Keys(ctx, 1, rot_steps=kan_he.model_rotations(m, ctx.slots))
+    c = ckks.encrypt(ctx, keys, X[0], ctx.L, 2, 0)
+    out = kan_he.infer(ctx, keys, c, m)
+    dec = ckks.decrypt(ctx, keys, out, 2)
+    hef = kan_plain.forward(m, X[:1], "poly", "poly")[0]
+    assert np.abs(dec - hef).max() < 1e-5
+    mp = [dict(L, b0="product") for L in m]
+    keys_p = ckks.Keys(ctx, 1, rot_steps=kan_he.model_rotations(mp, ctx.slots))
+    out_p = kan_he.infer(ctx, keys_p, ckks.encrypt(ctx, keys_p, X[0], ctx.L, 2, 0), mp)
+    assert out.level - out_p.level == (len(m) if k_ >= 1 else 0)
 
 
 @pytest.mark.parametrize("G_,k_", [(1, 0), (4, 0), (2, 1)])
