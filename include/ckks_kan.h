@@ -194,9 +194,12 @@ int ckks_rescale(ckks_ctx* ctx, const ckks_ct* in, ckks_ct** out);
  * memory is a fixed 64 MiB device array inside the library (8 Mi words, held
  * by every GPU that loads the library until exit); sizes needing more than
  * 2 * batch * N * (level + 1) <= 8 Mi words are rejected with
+ * CKKS_ERR_INVALID_ARG. d_in and d_out must not overlap (the output's limb
+ * stride differs from the input's); overlapping buffers are rejected with
  * CKKS_ERR_INVALID_ARG. The first call on a device looks the array up (do it
  * before any stream capture). All calls share the array: calls that overlap
- * on the GPU race, so serialize them. */
+ * on the GPU race, so serialize them. The calling thread's current device is
+ * left as it was. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, size_t batch, int level,
                          uint64_t* d_out);
 /* Eq. 8 complete: bring both to the lower level, multiply, relinearise and

@@ -16,7 +16,8 @@
 // the array: two calls that overlap on the GPU (different streams, or
 // different host threads) race on it and must be serialized by the caller.
 // Both scratch regions are fully written before they are read, so nothing
-// in the array needs clearing between calls.
+// in the array needs clearing between calls. The calling thread's current
+// device is the same after the call as before it.
 #include <mutex>
 
 #include "ops.h"
@@ -39,12 +40,27 @@ uint64_t* scratch_on(int device) {
   if (device < 0 || device >= MAX_DEVICES) throw Error(CKKS_ERR_UNSUPPORTED, "device ordinal >= 64");
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    CK_CUDA(cudaSetDevice(device));
+    void* p = nullptr;  // `device` is current (set by the caller below)
     CK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_scratch_addr[device] = static_cast<uint64_t*>(p);
   }
   return g_scratch_addr[device];
+}
+
+// Restores the calling thread's current device when the call returns.
+struct CurrentDeviceGuard {
+  int prev = -1;
+  CurrentDeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~CurrentDeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool overlaps(const uint64_t* a, size_t na, const uint64_t* b, size_t nb) {
+  const uintptr_t a0 = (uintptr_t)a, a1 = a0 + na * 8, b0 = (uintptr_t)b, b1 = b0 + nb * 8;
+  return a0 < b1 && b0 < a1;
 }
 
 }  // namespace
@@ -55,9 +71,16 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, size_t 
     if (!ctx || !d_in || !d_out || batch == 0) return CKKS_ERR_INVALID_ARG;
     Ctx& c = ctx->c;
     if (level < 1 || level > c.L) return CKKS_ERR_LEVEL;
+    // 2 batch N (level + 1) scratch words, bounded before it is formed so
+    // that no product can wrap around
+    const size_t per_ct = 2 * c.N * (size_t)(1 + level);
+    if (batch > NOALLOC_SCRATCH_WORDS / per_ct) return CKKS_ERR_INVALID_ARG;
     const size_t polys = 2 * batch;
-    const size_t need = polys * c.N * (size_t)(1 + level);
-    if (need > NOALLOC_SCRATCH_WORDS) return CKKS_ERR_INVALID_ARG;
+    // the output limbs are strided differently from the input's: in place
+    // (or any overlap) would read words already overwritten
+    if (overlaps(d_in, batch * per_ct, d_out, polys * c.N * (size_t)level))
+      return CKKS_ERR_INVALID_ARG;
+    CurrentDeviceGuard restore;
     CK_CUDA(cudaSetDevice(c.device));
     uint64_t* last = scratch_on(c.device);
     uint64_t* R = last + polys * c.N;
