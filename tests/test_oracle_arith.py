@@ -424,6 +424,81 @@ def test_relin_rescale_is_one_division_by_p_ql(small):
         assert exact >= 0.99 * len(range(0, ctx.N, 3))
 
 
+def _auto_coef(a, g, m):
+    """a(X) -> a(X^g) mod (X^N + 1, m) on coefficients, from the definition."""
+    N = len(a)
+    out = [0] * N
+    for i, v in enumerate(a):
+        e = (i * g) % (2 * N)
+        if e < N:
+            out[e] = (out[e] + int(v)) % m
+        else:
+            out[e - N] = (out[e - N] - int(v)) % m
+    return np.array(out, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("step", [0, 1, -3])
+def test_moddown_is_rounded_division_by_p(small, step):
+    """Key inner product + ModDown: out_k = round(acc_k / P) over Q_l, with
+    acc_k = sum_j sigma_g(ext_j) key_j[k] the exact value over QP_l. The
+    automorphism of the hoisted rotation is applied to the ModUp rows here in
+    the coefficient domain from its definition (X -> X^g), the inner product
+    by big-integer arithmetic, and the value checked by CRT: the centred
+    conversion makes the division round to nearest (off by one only within
+    ~1e-15 of a half-integer, where the overflow's double sum can round
+    either way)."""
+    ctx, keys = small
+    L = lib()
+    rng = np.random.default_rng(20 + step)
+    lv = ctx.L
+    l, A = lv + 1, ctx.alpha
+    R = l + A
+    beta = (l + A - 1) // A
+    mod_idx = list(range(l)) + [ctx.L + 1 + k for k in range(A)]
+    qp = [int(ctx.moduli[t]) for t in mod_idx]
+    g = 0 if step == 0 else ctx.galois(step)
+    key = keys.relin if g == 0 else keys.galois[g]
+    d = np.stack([rng.integers(0, ctx.q[t], ctx.N, dtype=np.uint64) for t in range(l)])
+    ext = ckks._modup(ctx, d, lv)
+    out = ckks._ks(ctx, ext, lv, key, g)
+    # sigma_g(ext) in NTT form, through the coefficient domain
+    sig = ext.copy()
+    if g:
+        for j in range(beta):
+            for r in range(R):
+                row = _coef(ctx, [ext[j * R + r]], [mod_idx[r]])[0]
+                row = _auto_coef(row, g, qp[r])
+                L.or_ntt_limb(ctx.h, ptr(row), mod_idx[r], 0)
+                sig[j * R + r] = row
+    P = 1
+    for a in range(A):
+        P *= int(ctx.moduli[ctx.L + 1 + a])
+    Qo = 1
+    for t in range(l):
+        Qo *= int(ctx.q[t])
+    for k in range(2):
+        acc = []
+        for r in range(R):
+            a = np.zeros(ctx.N, dtype=object)
+            for j in range(beta):
+                a = (a + sig[j * R + r].astype(object) * key[j, k, mod_idx[r]].astype(object)) % qp[r]
+            acc.append(np.array(list(a), dtype=np.uint64))
+        yc = _coef(ctx, acc, mod_idx)
+        oc = _coef(ctx, out[k], list(range(l)))
+        exact = 0
+        pts = range(0, ctx.N, 2)
+        for n in pts:
+            Y, _ = _crt([yc[r][n] for r in range(R)], qp)
+            O, _ = _crt([oc[t][n] for t in range(l)], ctx.q[:l])
+            rem = Y % P
+            if 2 * rem > P:
+                rem -= P  # centred remainder: Y - rem = P round(Y / P)
+            ok = [(O * P - (Y - rem) + u * P) % Qo == 0 for u in (0, -1, 1)]
+            assert any(ok), (k, n)
+            exact += ok[0]
+        assert exact >= 0.99 * len(pts)
+
+
 def test_keyswitch_rounding_is_unbiased():
     """ModDown (rotation) and HMult's division round to nearest: the error
     of a rotation stays at the level of fresh encryption noise at every slot

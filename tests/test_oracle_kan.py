@@ -86,6 +86,27 @@ def test_fn_closed_forms():
     assert np.allclose(s, [0, 0, 1, 1], atol=1e-3)
 
 
+@pytest.mark.parametrize("name,data", [("kan_2_5_1", "uniform"), ("kan_4_8_4_1", "uniform"),
+                                       ("kan_784_64_10", "blobs")])
+def test_comparison_bound_keeps_polycomp_inputs_in_range(name, data):
+    """Algorithm 2 feeds (x_rep - g1)/(2R) and (g2 - x_rep)/(2R) to PolyComp,
+    which is accurate only on [-1, 1] (B-spline approximation section: inputs
+    are scaled into [-1, 1] with R chosen from the data, larger than needed).
+    Over the calibration set, every input x of every layer compared with
+    every knot t_m gives |x - t_m| / (2R) <= 1/1.1 (the reading's 10 % margin),
+    and the bound is attained: R is no larger than that margin requires."""
+    model = W.make_model(name)
+    n_in = model[0]["n_in"]
+    X = W.uniform_inputs(256, n_in) if data == "uniform" else W.blob_images(64)
+    m = calibrate.calibrate(model, X, 15, [3])
+    _, acts = kan_plain.forward(m, X, "poly", "poly", collect=True)
+    for L, a in zip(m, acts):
+        t = kan_plain.knots(L)
+        u = np.abs(a[..., None] - t) / (2.0 * L["R"])
+        assert u.max() <= (1.0 / 1.1) * (1.0 + 1e-14)
+        assert u.max() >= (1.0 / 1.1) * (1.0 - 1e-12)
+
+
 def test_alg3_permutation_and_eq13():
     n_r, n_c = 4, 6
     P = kan_he.permutation_matrix(n_r, n_c)
