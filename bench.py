@@ -31,11 +31,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Instructions a lazy (Harvey) 64-bit modular multiply-and-butterfly needs on
-# 32-bit integer lanes: 10 multiply-adds for the three 64x64 partial-product
-# sets (low of y*w, high of y*w', low of t*q) and 10 adds, compares and selects
-# for the 64-bit lazy corrections.
-ALU_INSTR_PER_MODMUL = 20
 # DRAM bytes (read + write, ncu) over algorithmic bytes of one launch of the
 # fused ModUp forward NTT, measured on a 13-limb, batch-8 HMult (the bench's
 # launch is too large for a full capture); traffic scales with the units
@@ -82,6 +77,9 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-micro", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other configurations (C1, C3, C4, C5 serving, Table 3 shapes) "
+                        "that the default run measures after the headline")
     p.add_argument("--kernel", default=None, choices=["ntt", "intt", "hmult"],
                    help="time one kernel kind alone (NTT limbs/s) instead of the network")
     p.add_argument("--rows", type=int, default=592, help="limbs per launch for --kernel")
@@ -257,7 +255,13 @@ def serve_arm(a):
         "latency_ms": {"p50": 1000 * float(np.percentile(kept, 50)),
                        "p99": 1000 * float(np.percentile(kept, 99)),
                        "excluded_warmup_s": warm, "requests_counted": len(kept)},
-        "requests": len(lat), "wall_s": wall, "hbm_peak_admitted_bytes": st["hbm_peak"],
+        "requests": len(lat), "wall_s": wall, "hbm_peak_bytes": st["hbm_measured_peak"],
+        "hbm_peak_admitted_bytes": st["hbm_peak"], "hbm_budget_bytes": int(200e9),
+        "admission": {"footprint_bytes_per_request": {sp[0]: srv.footprint(mm[0])
+                                                      for sp, mm in zip(specs, models)},
+                      "how": "measured per model at kan_server_add_model (device pool "
+                             "watermark over one network run at the top level); hbm_peak_bytes "
+                             "is the largest rise of the pool's used bytes over one step"},
         "per_model": per_model,
         "plain_form": {"value": plain_rate, "unit": UNIT, "requests": n_plain,
                        "how": "one request at a time through kan_infer, same mix"},
@@ -440,15 +444,16 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
 
     real_ks, real_ksr, real_modup = O._ks, O._ks_rescale, O._modup
 
-    # total key switches of one inference (same schedule, small ring, no arithmetic)
-    counter = {"n": 0}
+    # the key switches of one inference and their levels (same schedule,
+    # small ring, no arithmetic)
+    counter = {"levels": []}
 
     def count_ks(ctx, ext, level, key, g):
-        counter["n"] += 1
+        counter["levels"].append(level)
         return np.zeros((2, level + 1, ctx.N), np.uint64)
 
     def count_ksr(ctx, d, ext, level, key):
-        counter["n"] += 1
+        counter["levels"].append(level)
         return np.zeros((2, level, ctx.N), np.uint64)
 
     def skip_modup(ctx, poly, level):
@@ -474,9 +479,20 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
         kan_he.infer(small, fk, x, model_he)
     finally:
         O._ks, O._ks_rescale, O._modup = real_ks, real_ksr, real_modup
-    total = counter["n"]
-
+    total = len(counter["levels"])
     ctx = O.Ctx(O.Params(a.log_n, a.levels, getattr(a, "alpha", 0) or 4, p_bits=getattr(a, "p_bits", 60)))
+
+    def weight(level):
+        # transforms of one key switch at `level` (l limbs, beta digits):
+        # ModUp's l inverse and beta (l + alpha) - l forward, ModDown's
+        # 2 alpha inverse and 2 l forward; the schedule's other work (rescales,
+        # plaintext products) also grows with l and is timed inside the sample
+        l, A = level + 1, ctx.alpha
+        beta = -(-l // A)
+        return l + beta * (l + A) - l + 2 * A + 2 * l
+
+    total_w = sum(weight(lv) for lv in counter["levels"])
+
     Z = np.zeros((ctx.beta_max, 2, ctx.n_qp, ctx.N), np.uint64)
     keys = Fake()
     keys.relin = Z
@@ -490,22 +506,23 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
         ct = [ct] * K
     rates = []
     for it in range(warmup + steps):
-        done = {"n": 0}
+        done = {"n": 0, "w": 0.0}
         t0 = time.perf_counter()
 
-        def tick():
+        def tick(level):
             done["n"] += 1
+            done["w"] += weight(level)
             if time.perf_counter() - t0 > budget_s:
                 raise _Stop()
 
         def timed_ks(ctx_, ext, level, key, g):
             r = real_ks(ctx_, ext, level, key, g)
-            tick()
+            tick(level)
             return r
 
         def timed_ksr(ctx_, d, ext, level, key):
             r = real_ksr(ctx_, d, ext, level, key)
-            tick()
+            tick(level)
             return r
 
         O._ks, O._ks_rescale = timed_ks, timed_ksr
@@ -517,11 +534,30 @@ def oracle_sample(model_he, a, budget_s, steps=1, warmup=0):
             O._ks, O._ks_rescale = real_ks, real_ksr
         el = time.perf_counter() - t0
         if it >= warmup:
-            rates.append((done["n"] / total) / el)
+            rates.append((done["w"] / total_w) / el)
     sample = ("first %d of %d key switches of one inference (N=2^%d, %d levels), single thread, "
-              "random keys and input, %.0f s budget per sample" % (done["n"], total, a.log_n, a.levels,
-                                                                    budget_s))
+              "random keys and input, %.0f s budget per sample; fraction done = their share of the "
+              "schedule's key-switch transforms weighted by level (%.4f)"
+              % (done["n"], total, a.log_n, a.levels, budget_s, done["w"] / total_w))
     return statistics.mean(rates), sample, total
+
+
+def c1_oracle_full():
+    """One whole encrypted [2,5,1] inference by the oracle, single thread, at
+    its full size (N=2^15, q0 + 18 x 40-bit primes, one special prime):
+    seconds for kan_he.infer alone (keys and the encryption made first)."""
+    from oracle import calibrate as OC, ckks as O, kan_he
+    from paper_2409_07751_gb300 import workloads as W
+    wl = WORKLOADS["c1"]
+    model = W.make_model(wl["model"])
+    Xcal = W.uniform_inputs(256, 2, seed=W.SEED_INPUTS + 1000)
+    m = OC.calibrate(model, Xcal, wl["degree"], wl["comp"], fixed_range=wl["fixed"])
+    ctx = O.Ctx(O.Params(wl["log_n"], wl["levels"], wl["alpha"]))
+    keys = O.Keys(ctx, W.SEED_KEYS, kan_he.model_rotations(m, ctx.slots))
+    x = O.encrypt(ctx, keys, W.uniform_inputs(1, 2)[0], wl["levels"], W.SEED_ENC, 0)
+    t0 = time.perf_counter()
+    kan_he.infer(ctx, keys, x, m)
+    return time.perf_counter() - t0
 
 
 def _oracle_worker(job):
@@ -600,6 +636,63 @@ def oracle_micro(a):
     return out
 
 
+# ------------------------------------------------------------------ other configurations
+EXTRA_RUNS = [
+    ("c1", ["--workload", "c1", "--steps", "20", "--warmup", "3"], 300),
+    ("c3", ["--workload", "c3", "--steps", "3", "--warmup", "3"], 600),
+    ("c4", ["--workload", "c4", "--steps", "3", "--warmup", "3"], 600),
+    ("c5_serve", ["--serve", "--rate", "20", "--duration", "30"], 900),
+    ("table3", ["--table3"], 600),
+]
+
+
+def _summary(name, line):
+    if "error" in line:
+        return line
+    if name in ("c1", "c3", "c4"):
+        return {k: line.get(k) for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                           "latency_ms", "depth", "clocks")} | {
+            "batch": line["config"]["batch_per_gpu"], "workload": line["config"]["workload"],
+            "alpha": line["config"]["alpha"], "p_bits": line["config"]["p_bits"],
+            "dominant_kernel": {k: line["roofline"].get(k) for k in ("kernel", "frac", "unit")}}
+    if name == "c5_serve":
+        return {k: line.get(k) for k in ("value", "unit", "latency_ms", "requests", "wall_s",
+                                           "hbm_peak_bytes", "hbm_budget_bytes", "admission",
+                                           "plain_form", "per_model", "config")}
+    return {"rows": [{k: r[k] for k in ("n_i", "g", "k", "lazy_ms", "naive_ms", "speedup")}
+                     for r in line.get("rows", [])], "unit": "ms per layer",
+            "levels": line.get("levels"), "n_poly": line.get("n_poly")}
+
+
+def extras(device):
+    """The other configurations, each a short child run of this script on
+    the same GPU (its own context, keys and models), summarised; the SM clocks
+    are sampled over the whole phase."""
+    out = {}
+    clk = Clocks(device)
+    t0 = time.perf_counter()
+    for name, args, limit in EXTRA_RUNS:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py")] + args
+        if name in ("c1", "c3", "c4"):
+            cmd += ["--no-micro", "--no-e2e", "--no-cpu-baseline", "--no-extras"]
+        t = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=limit)
+            lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode == 0 and lines:
+                line = json.loads(lines[-1])
+            else:
+                line = {"error": "rc %d: %s" % (r.returncode, r.stderr[-400:])}
+        except subprocess.TimeoutExpired:
+            line = {"error": "did not finish within %d s" % limit}
+        out[name] = _summary(name, line)
+        out[name]["wall_s"] = round(time.perf_counter() - t, 1)
+    out["clocks"] = clk.stop()
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    out["how"] = " ; ".join("%s: bench.py %s" % (n, " ".join(a)) for n, a, _ in EXTRA_RUNS)
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     a = args_()
@@ -617,9 +710,16 @@ def main():
     if a.table3:
         return table3_arm(a)
     import numpy as np
-    import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    c1_pool = c1_job = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        # the oracle's whole C1 inference runs on one host core while the
+        # GPU is timed (a spawned process, started before any CUDA call)
+        import multiprocessing as mp
+        c1_pool = mp.get_context("spawn").Pool(1)
+        c1_job = c1_pool.apply_async(c1_oracle_full)
+    import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
@@ -724,23 +824,24 @@ def main():
     ms, by, n, mm = kinds[dom]
     achieved = by / (ms / 1000.0) / 1e9
     total_ms = sum(v[0] for v in kinds.values())
-    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    traffic = None
+    if dom == "modup_ntt" and MODUP_TRAFFIC_RATIO is not None:
+        traffic = MODUP_TRAFFIC_RATIO * by / n
+    # the fraction is taken against HBM (algorithmic bytes / launch time /
+    # measured copy bandwidth); the integer roofline of the same launches is
+    # reported beside it against the measured register-only butterfly rate
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    int_peaks = {"products_per_s": ctx.int_peak(0), "butterflies_per_s": ctx.int_peak(1),
+                 "shoup_products_per_s": ctx.int_peak(2)}
     if mm > 0:
-        # integer-issue roofline: SMs x 4 schedulers x 32 lanes x max SM clock,
-        # at ALU_INSTR_PER_MODMUL instructions per lazy 64-bit modular multiply
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        alu_peak = sms * 4 * 32 * clk / ALU_INSTR_PER_MODMUL / 1e9
         alu = mm / (ms / 1000.0) / 1e9
-        traffic = None
-        if dom == "modup_ntt" and MODUP_TRAFFIC_RATIO is not None:
-            traffic = MODUP_TRAFFIC_RATIO * by / n
-        roofline = {"kernel": dom, "bound": "alu", "achieved": alu, "peak": alu_peak,
-                    "unit": "Gmodmul/s", "frac": alu / alu_peak, "traffic": traffic, "hbm": hbm,
-                    "modmul_per_launch": mm / n}
-    else:
-        roofline = dict({"kernel": dom, "bound": "hbm", "traffic": None}, **hbm)
+        bpk = int_peaks["butterflies_per_s"] / 1e9
+        roofline["alu"] = {"achieved": alu, "unit": "G modmul/s", "peak": bpk, "frac": alu / bpk,
+                           "peak_source": "measured: register-only lazy forward butterflies "
+                                          "(ckks_int_peak kind 1)",
+                           "modmul_per_launch": mm / n}
     roofline.update({"algorithmic_bytes_per_launch": by / n, "avg_launch_ms": ms / n,
                      "share_of_kernel_time": ms / total_ms,
                      "kernel_ms_per_step": total_ms / a.steps,
@@ -750,7 +851,10 @@ def main():
     # per kind: ms per step, algorithmic GB/s and G modmul/s over its launches
     rates = {k: {"ms_per_step": round(v[0] / a.steps, 2),
                  "GBps": round(v[1] / (v[0] / 1000.0) / 1e9, 1) if v[0] > 0 else None,
-                 "Gmodmul_per_s": round(v[3] / (v[0] / 1000.0) / 1e9, 1) if v[0] > 0 and v[3] else None}
+                 "Gmodmul_per_s": round(v[3] / (v[0] / 1000.0) / 1e9, 1) if v[0] > 0 and v[3] else None,
+                 "hbm_frac": round(v[1] / (v[0] / 1000.0) / 1e9 / peak, 4) if v[0] > 0 else None,
+                 "alu_frac": round(v[3] / (v[0] / 1000.0) / int_peaks["butterflies_per_s"], 4)
+                 if v[0] > 0 and v[3] else None}
              for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])[:8]}
 
     def timed(fn, reps):
@@ -897,16 +1001,28 @@ def main():
             "roofline": roofline, "kernel_time_shares": shares, "kernel_rates": rates,
             "gpu_launches": launches,
             "clocks": clocks, "e2e": e2e, "plain_form": plain, "graph_replay": graph_replay,
-            "keyswitch_autotune_ms": tuned, "micro": micro, "depth": depth,
+            "keyswitch_autotune_ms": tuned, "micro": micro, "int_peaks": int_peaks, "depth": depth,
             "slack": slack}
+    if rank == 0 and world == 1 and not a.no_extras and a.workload == "c2":
+        line["configs"] = extras(local)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import calibrate as OC
         mo = calibrate_for(a, OC.calibrate, model, Xcal)
         v1, sample1, _ = oracle_sample(mo, a, a.cpu_budget)
         v, sample, procs = oracle_all_cores(mo, a, a.cpu_budget)
+        c1 = None
+        try:
+            c1_s = c1_job.get(timeout=900)
+            c1 = {"value": 1.0 / c1_s, "unit": UNIT, "seconds": c1_s, "cores": 1,
+                  "sample": "full inference: one whole encrypted [2,5,1] inference (N=2^15, 18 "
+                            "levels), single thread, run while the GPU was timed"}
+        except Exception as e:  # reported, not hidden
+            c1 = {"error": repr(e)}
+        c1_pool.terminate()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
                                 "sample": "%d processes, each: %s" % (procs, sample),
-                                "single_thread": {"value": v1, "cores": 1, "sample": sample1}}
+                                "single_thread": {"value": v1, "cores": 1, "sample": sample1},
+                                "c1_full_inference": c1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -128,6 +128,15 @@ int ckks_profile_collect(ckks_ctx* ctx, double* ms, double* bytes, uint64_t* lau
  * key inner-product products); modmuls may be NULL. */
 int ckks_profile_collect2(ckks_ctx* ctx, double* ms, double* bytes, double* modmuls,
                           uint64_t* launches, int cap);
+/* Measured integer-pipe peak of the context's device (the denominator of the
+ * integer roofline; the paper has no counterpart): register-only chains of
+ * kind 0, 64 x 64 -> 128-bit products (low and high words), *per_s in
+ * products/s; kind 1, the forward NTT's lazy butterfly (three-product Shoup
+ * multiply and both sums, one full reduction of each word per 16 stages),
+ * in butterflies/s; kind 2, the three-product Shoup multiply alone (the
+ * basis-conversion product), in products/s. Timed with CUDA events over
+ * several launches of SMs x resident-blocks CTAs on the context's stream. */
+int ckks_int_peak(ckks_ctx* ctx, int kind, double* per_s);
 
 /* ------------------------------------------------------------ keys
  * Secret-key generation from `seed` (ternary secret, ChaCha20 stream), the
@@ -323,7 +332,12 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model,
  * Continuous batching of encrypted inference requests (the serving pattern
  * of the build; the paper itself times single inputs). Requests are admitted
  * first-come first-served while the sum of their device-memory footprints
- * (32 x the input ciphertext's bytes) stays within hbm_budget_bytes. Each
+ * stays within hbm_budget_bytes. A model's footprint per request is measured
+ * by kan_server_add_model: the network runs once (after a run that fills the
+ * model's plaintext caches) on a zero ciphertext at the top level, and the
+ * rise of the device memory pool's used-bytes watermark is recorded (the
+ * bytes a request needs beyond its input ciphertext; models are measured
+ * and served with CUDA-graph replay off, the default). Each
  * kan_server_step evaluates one layer for every active request, batching
  * requests of the same model, layer and level into one evaluation; requests
  * submitted meanwhile join at the next step. Results are word-for-word those
@@ -334,15 +348,24 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model,
 typedef struct kan_server kan_server;
 int kan_server_create(ckks_ctx* ctx, size_t hbm_budget_bytes, kan_server** out);
 int kan_server_destroy(kan_server* server);
+/* Runs the model twice on the device to measure its footprint (above);
+ * LEVEL if the model is deeper than the chain. */
 int kan_server_add_model(kan_server* server, kan_model* model, const ckks_keys* keys,
                          int* model_id);
+/* The measured footprint of one request of the model, in bytes. */
+int kan_server_footprint(const kan_server* server, int model_id, size_t* bytes);
 /* `in` holds one request (batch 1 ciphertext, copied); errors: LEVEL if its
- * level is below the model's depth, OUT_OF_MEMORY if it alone exceeds the budget. */
+ * level is below the model's depth, OUT_OF_MEMORY if its footprint exceeds
+ * the whole budget (it is refused, never admitted alone). */
 int kan_server_submit(kan_server* server, int model_id, const ckks_ct* in, uint64_t* request_id);
 int kan_server_step(kan_server* server, size_t* completed);
 int kan_server_take(kan_server* server, uint64_t request_id, ckks_ct** out);
+/* hbm_in_use / hbm_peak: the admitted footprints now / at most (never above
+ * the budget); hbm_measured_peak: the largest rise of the device pool's used
+ * bytes over one kan_server_step, as allocated. Any pointer may be NULL. */
 int kan_server_status(const kan_server* server, size_t* waiting, size_t* active,
-                      size_t* finished, size_t* hbm_in_use, size_t* hbm_peak);
+                      size_t* finished, size_t* hbm_in_use, size_t* hbm_peak,
+                      size_t* hbm_measured_peak);
 
 #ifdef __cplusplus
 }

@@ -47,6 +47,7 @@ SIGNATURES = {
     "ckks_profile_enable": (c_i32, [c_vp, c_i32]),
     "ckks_profile_collect": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32]),
     "ckks_profile_collect2": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32]),
+    "ckks_int_peak": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_dbl)]),
     "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
@@ -90,7 +91,8 @@ SIGNATURES = {
     "kan_server_submit": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "kan_server_step": (c_i32, [c_vp, c_vp]),
     "kan_server_take": (c_i32, [c_vp, c_u64, PP]),
-    "kan_server_status": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "kan_server_status": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "kan_server_footprint": (c_i32, [c_vp, c_i32, c_vp]),
 }
 
 PENDING = 1
@@ -190,6 +192,13 @@ class Context:
 
     def profile(self, on):
         check(lib().ckks_profile_enable(self.h, 1 if on else 0))
+
+    def int_peak(self, kind):
+        """Measured integer peak: kind 0 64-bit products/s, 1 lazy forward
+        butterflies/s, 2 three-product Shoup multiplies/s."""
+        v = c_dbl()
+        check(lib().ckks_int_peak(self.h, int(kind), ctypes.byref(v)))
+        return v.value
 
     def profile_collect(self):
         """{kind: (ms, algorithmic bytes, launches, modular multiplications)}
@@ -534,6 +543,13 @@ class Server:
         return Ciphertext(self.ctx, h)
 
     def status(self):
-        v = [c_sz() for _ in range(5)]
+        v = [c_sz() for _ in range(6)]
         check(lib().kan_server_status(self.h, *[ctypes.byref(x) for x in v]))
-        return dict(zip(("waiting", "active", "finished", "hbm_in_use", "hbm_peak"), (x.value for x in v)))
+        return dict(zip(("waiting", "active", "finished", "hbm_in_use", "hbm_peak",
+                         "hbm_measured_peak"), (x.value for x in v)))
+
+    def footprint(self, model_id):
+        """Measured device bytes one request of the model needs."""
+        v = c_sz()
+        check(lib().kan_server_footprint(self.h, int(model_id), ctypes.byref(v)))
+        return v.value

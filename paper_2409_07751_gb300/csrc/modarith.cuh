@@ -57,6 +57,34 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
   uint64_t r = a * w - t * q;
   return r >= q ? r - q : r;
 }
+// Shoup product whose quotient is estimated from three of the four 32-bit
+// partial products of y * ws (the low product and the carries out of the
+// middle ones are dropped): with y ws = y1 s1 2^64 + (y1 s0 + y0 s1) 2^32 +
+// y0 s0, Q' = y1 s1 + hi(y1 s0) + hi(y0 s1) satisfies Q - 2 <= Q' <= Q for
+// the exact Q = floor(y ws / 2^64), so y w - Q' q lies in [0, 4q) for any
+// y < 2^64 (exact Shoup: [0, 2q)).
+__device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_t ws, uint64_t q) {
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  const uint32_t s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
+  const uint64_t Q = (uint64_t)y1 * s1 + __umulhi(y1, s0) + __umulhi(y0, s1);
+  return y * w - Q * q;
+}
+
+// Forward butterfly without the reduction of x, for moduli q < 2^50: with
+// t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
+// from inputs below q stay below 65q < 2^57.
+__device__ __forceinline__ void ct_grow(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
+                                        uint64_t q, uint64_t q2) {
+  const uint64_t u = x;
+  const uint64_t t = shoup_approx(y, w, ws, q);
+  x = u + t;
+  y = u - t + 2 * q2;
+}
+// x < 2^64 -> x mod q, with w1s = floor(2^64 / q) (Shoup's product by 1)
+__device__ __forceinline__ uint64_t reduce_full(uint64_t x, uint64_t q, uint64_t w1s) {
+  const uint64_t t = x - __umul64hi(x, w1s) * q;
+  return t >= q ? t - q : t;
+}
 // reduction of an arbitrary 64-bit value (rarely used; plain division)
 __device__ __forceinline__ uint64_t reduce64(uint64_t a, uint64_t q) { return a % q; }
 // signed value -> residue (the division only runs when |v| >= q)

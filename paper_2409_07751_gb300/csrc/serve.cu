@@ -2,14 +2,25 @@
 //
 // Requests (one input ciphertext each, encrypted by their client) are
 // admitted first-come first-served while the sum of their device-memory
-// footprints stays within the HBM budget. Each scheduling step evaluates one
-// KAN layer for every active request: requests of the same model, at the
-// same layer and the same level are concatenated into one batch and run
-// through the layer together, then split back. A request that arrives while
-// others are mid-network joins at the next step at its own layer 0, so work
-// of requests at different stages overlaps step by step on the device.
-// Batching never changes a ciphertext: every batch element is computed
-// independently, word for word as when evaluated alone.
+// footprints stays within the HBM budget. A model's footprint per request is
+// measured when the model is added: the whole network runs once on a zero
+// ciphertext at the top level through the same per-layer path as a step, and
+// the rise of the device memory pool's used-bytes watermark over what was in
+// use before is recorded (the model's plaintext caches are filled by a first
+// run that is not counted). A batch of B requests needs at most B times that:
+// every buffer of the schedule grows with the batch. A request whose
+// footprint exceeds the whole budget is refused at submission. Each step's
+// measured rise of the watermark is kept, so the budget can be checked
+// against what the device actually allocated.
+//
+// Each scheduling step evaluates one KAN layer for every active request:
+// requests of the same model, at the same layer and the same level are
+// concatenated into one batch and run through the layer together, then split
+// back. A request that arrives while others are mid-network joins at the
+// next step at its own layer 0, so work of requests at different stages
+// overlaps step by step on the device. Batching never changes a ciphertext:
+// every batch element is computed independently, word for word as when
+// evaluated alone.
 #include <deque>
 #include <map>
 #include <tuple>
@@ -27,10 +38,24 @@ using namespace ck;
 
 namespace {
 
-// working set of one request while its layers run: the ciphertext plus the
-// key-switching extension (about beta*(l+alpha) limbs) and the schedule's
-// live temporaries, bounded here by 32 ciphertexts of the input's size
-constexpr double FOOTPRINT_FACTOR = 32.0;
+// Used-bytes accounting of the device's default memory pool, the pool every
+// stream-ordered allocation of the library comes from. The pool counts an
+// allocation when it is requested on the host, so no synchronisation is needed.
+struct PoolMeter {
+  cudaMemPool_t pool = nullptr;
+  explicit PoolMeter(int device) { CK_CUDA(cudaDeviceGetDefaultMemPool(&pool, device)); }
+  uint64_t get(cudaMemPoolAttr a) const {
+    uint64_t v = 0;
+    CK_CUDA(cudaMemPoolGetAttribute(pool, a, &v));
+    return v;
+  }
+  uint64_t used() const { return get(cudaMemPoolAttrUsedMemCurrent); }
+  uint64_t high() const { return get(cudaMemPoolAttrUsedMemHigh); }
+  void reset_high() const {
+    uint64_t z = 0;  // the watermark restarts from the current use
+    CK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &z));
+  }
+};
 
 struct Request {
   uint64_t id = 0;
@@ -46,7 +71,9 @@ struct Request {
 struct kan_server {
   Ctx* ctx = nullptr;
   size_t budget = 0, in_use = 0, peak_in_use = 0;
+  size_t measured_peak = 0;  // largest rise of the pool's used bytes over one step
   std::vector<std::pair<kan_model*, const ckks_keys*>> models;
+  std::vector<size_t> footprint;  // per model: measured bytes per request
   std::deque<std::unique_ptr<Request>> waiting;
   std::map<uint64_t, std::unique_ptr<Request>> active;
   std::map<uint64_t, std::unique_ptr<Request>> finished;
@@ -59,7 +86,7 @@ namespace {
 void admit(kan_server& S) {
   while (!S.waiting.empty()) {
     Request& r = *S.waiting.front();
-    if (S.in_use + r.footprint > S.budget && !S.active.empty()) break;  // wait for memory
+    if (S.in_use + r.footprint > S.budget) break;  // wait for memory (fits alone: checked at submit)
     S.in_use += r.footprint;
     S.peak_in_use = std::max(S.peak_in_use, S.in_use);
     const uint64_t id = r.id;
@@ -68,7 +95,50 @@ void admit(kan_server& S) {
   }
 }
 
+// One layer of one batch of requests of a model: concatenate, evaluate,
+// split back into per-request ciphertexts (the pieces replace the inputs).
+void run_group(Ctx& c, kan_model& M, const ckks_keys& K, int layer, std::vector<Ct*>& cts) {
+  std::vector<const ckks_ct*> parts;
+  for (Ct* p : cts) parts.push_back(p->get());
+  Ct in = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
+  const int chunks = kan_layer_chunks(M, layer);
+  Ct out = kan_eval_layer(M, layer, K, *in);
+  in.reset();
+  const size_t per = out->words() / out->B;
+  size_t off = 0;
+  for (Ct* p : cts) {
+    const size_t b = (*p)->B / chunks;  // a wide layer folds K chunk ciphertexts into one
+    Ct piece = ct_alloc(c, b, out->level, out->scale);
+    CK_CUDA(cudaMemcpyAsync(piece->d.p, out->d.u64() + off * per, b * per * 8,
+                            cudaMemcpyDeviceToDevice, c.stream));
+    off += b;
+    *p = std::move(piece);
+  }
+}
+
+// Bytes one request of model m needs beyond its input ciphertext, measured.
+size_t measure_footprint(kan_server& S, int m) {
+  Ctx& c = *S.ctx;
+  kan_model& M = *S.models[m].first;
+  const ckks_keys& K = *S.models[m].second;
+  const PoolMeter pm(c.device);
+  size_t need = 0;
+  for (int pass = 0; pass < 2; pass++) {  // the first pass fills the plaintext caches
+    Ct x = ct_alloc(c, (size_t)kan_layer_chunks(M, 0), c.L, c.delta[c.L]);
+    CK_CUDA(cudaMemsetAsync(x->d.p, 0, x->d.bytes, c.stream));
+    const uint64_t base = pm.used();
+    pm.reset_high();
+    std::vector<Ct*> one{&x};
+    for (int layer = 0; layer < kan_num_layers(M); layer++) run_group(c, M, K, layer, one);
+    need = (size_t)(pm.high() - base);
+  }
+  return need;
+}
+
 size_t step(kan_server& S) {
+  const PoolMeter pm(S.ctx->device);
+  const uint64_t base = pm.used();
+  pm.reset_high();
   admit(S);
   // group by (model, layer, level)
   std::map<std::tuple<int, int, int>, std::vector<Request*>> groups;
@@ -82,25 +152,16 @@ size_t step(kan_server& S) {
     std::vector<Request*>& rs = g.second;
     kan_model& M = *S.models[std::get<0>(g.first)].first;
     const ckks_keys& K = *S.models[std::get<0>(g.first)].second;
-    std::vector<const ckks_ct*> parts;
-    for (Request* r : rs) parts.push_back(r->ct.get());
-    Ct in = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
-    const int chunks = kan_layer_chunks(M, std::get<1>(g.first));
-    Ct out = kan_eval_layer(M, std::get<1>(g.first), K, *in);
+    std::vector<Ct*> cts;
+    for (Request* r : rs) cts.push_back(&r->ct);
+    run_group(c, M, K, std::get<1>(g.first), cts);
     S.batches++;
-    const size_t per = out->words() / out->B;
-    size_t off = 0;
     for (Request* r : rs) {
-      const size_t b = r->ct->B / chunks;  // a wide layer folds K chunk ciphertexts into one
-      Ct piece = ct_alloc(c, b, out->level, out->scale);
-      CK_CUDA(cudaMemcpyAsync(piece->d.p, out->d.u64() + off * per, b * per * 8,
-                              cudaMemcpyDeviceToDevice, c.stream));
-      off += b;
-      r->ct = std::move(piece);
       r->layer++;
       if (r->layer == kan_num_layers(M)) r->done = true;
     }
   }
+  S.measured_peak = std::max(S.measured_peak, (size_t)(pm.high() - base));
   for (auto it = S.active.begin(); it != S.active.end();) {
     if (it->second->done) {
       S.in_use -= it->second->footprint;
@@ -146,8 +207,13 @@ int kan_server_destroy(kan_server* s) {
 int kan_server_add_model(kan_server* s, kan_model* model, const ckks_keys* keys, int* model_id) {
   return guard([&] {
     if (!s || !model || !keys || !model_id) throw Error(CKKS_ERR_INVALID_ARG, "bad argument");
+    if (s->ctx->L < kan_total_depth(*model))
+      throw Error(CKKS_ERR_LEVEL, "the model is deeper than the chain");
     s->models.emplace_back(model, keys);
-    *model_id = (int)s->models.size() - 1;
+    const int m = (int)s->models.size() - 1;
+    s->footprint.push_back(0);
+    s->footprint[m] = measure_footprint(*s, m);
+    *model_id = m;
   });
 }
 
@@ -161,7 +227,7 @@ int kan_server_submit(kan_server* s, int model_id, const ckks_ct* in, uint64_t* 
     r->id = s->next_id++;
     r->model = model_id;
     r->ct = ct_copy(*s->ctx, *in);
-    r->footprint = (size_t)(FOOTPRINT_FACTOR * (double)r->ct->d.bytes);
+    r->footprint = s->footprint[model_id];
     if (r->footprint > s->budget) throw Error(CKKS_ERR_OUT_OF_MEMORY, "request exceeds the HBM budget");
     *request_id = r->id;
     s->waiting.push_back(std::move(r));
@@ -191,13 +257,20 @@ int kan_server_take(kan_server* s, uint64_t request_id, ckks_ct** out) {
 }
 
 int kan_server_status(const kan_server* s, size_t* waiting, size_t* active, size_t* finished,
-                      size_t* hbm_in_use, size_t* hbm_peak) {
+                      size_t* hbm_in_use, size_t* hbm_peak, size_t* hbm_measured_peak) {
   if (!s) return CKKS_ERR_INVALID_ARG;
   if (waiting) *waiting = s->waiting.size();
   if (active) *active = s->active.size();
   if (finished) *finished = s->finished.size();
   if (hbm_in_use) *hbm_in_use = s->in_use;
   if (hbm_peak) *hbm_peak = s->peak_in_use;
+  if (hbm_measured_peak) *hbm_measured_peak = s->measured_peak;
+  return CKKS_OK;
+}
+
+int kan_server_footprint(const kan_server* s, int model_id, size_t* bytes) {
+  if (!s || !bytes || model_id < 0 || model_id >= (int)s->models.size()) return CKKS_ERR_INVALID_ARG;
+  *bytes = s->footprint[model_id];
   return CKKS_OK;
 }
 

@@ -57,15 +57,32 @@ def test_mix_equals_alone(env):
 
 
 def test_admission_respects_budget(env):
+    """Footprints are measured on the device (the pool's used-bytes watermark
+    over a probe run of the network): with a budget of 1.5 footprints one
+    request runs at a time, the admitted sum and the bytes the device really
+    allocated in any step stay within the budget, and a request larger than
+    the whole budget is refused instead of being admitted alone."""
     G, ctx, (A, ka, na), _ = env
     one = _req(G, ctx, ka, na, 0, 17)
-    fp = 32 * one.words() * 8
-    srv = G.Server(ctx, fp + fp // 2)  # room for one request at a time
+    probe = G.Server(ctx, 1 << 40)
+    fp = probe.footprint(probe.add_model(A, ka))
+    # the run needs more than its output ciphertext and less than the
+    # hundreds of input-sized buffers a leak would show
+    assert one.words() * 8 < fp < 400 * one.words() * 8
+    budget = fp + fp // 2
+    srv = G.Server(ctx, budget)
     mid = srv.add_model(A, ka)
+    assert srv.footprint(mid) == fp  # the same schedule allocates the same bytes
     ids = [srv.submit(mid, _req(G, ctx, ka, na, i, 17)) for i in range(3)]
     for _ in range(20):
         srv.step()
-        assert srv.status()["hbm_peak"] <= fp + fp // 2
+        st = srv.status()
+        assert st["active"] <= 1
+        assert st["hbm_peak"] <= budget
+        assert 0 < st["hbm_measured_peak"] <= budget
     assert all(srv.take(i) is not None for i in ids)
-    with pytest.raises(G.CkksError):
-        G.Server(ctx, fp // 2).submit(0, one)  # no model 0 on that server
+    small = G.Server(ctx, fp // 2)
+    m2 = small.add_model(A, ka)
+    with pytest.raises(G.CkksError) as e:
+        small.submit(m2, one)
+    assert e.value.code == -5  # CKKS_ERR_OUT_OF_MEMORY
