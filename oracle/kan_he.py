@@ -6,9 +6,10 @@ Follows the paper's Method section step by step:
   ceil(log2(g+2k)) times add the ciphertext rotated right by n_i 2^(j-1).
   Reading: the 1/(2R) input scaling of Algorithm 2 (line 4) is folded into
   the mask, so the comparison inputs need no extra level.
-* Algorithm 2 (B-spline basis): ColTile'd knot vectors, PolyComp via the
-  composite f_{n_1} o ... o f_{n_d} (Cheon et al. closed form) with its last
-  stage returning (1 + f)/2, B0 = x1 (x) x2, then k recursion steps
+* Algorithm 2 (B-spline basis): ColTile'd knot vectors, PolyComp via a
+  composite of odd polynomials (minimax stages as in Lee et al., built by
+  polycomp.py, or Cheon et al.'s closed-form f_n) with its last stage
+  returning (1 + f)/2, B0 = x1 (x) x2, then k recursion steps
   b <- A1 (x_rep - t1) (x) b + A2 (t3 - x_rep) (x) rot(b, n_i). Reading: the two
   products of a step share one relinearisation; A1, A2 are zero outside the
   valid ColTile blocks.
@@ -24,7 +25,7 @@ import math
 import numpy as np
 
 from . import ckks
-from .kan_plain import fn_coeffs, knots
+from .kan_plain import knots, stage_coeffs
 
 
 def pow2ceil(n):
@@ -171,10 +172,11 @@ def eval_odd(ctx, keys, u, c, const=0.0):
 
 
 def polycomp0(ctx, keys, a, stages):
-    """PolyComp(a, 0) = (1 + f(a))/2 with f = f_{n_d} o ... o f_{n_1}."""
+    """PolyComp(a, 0) = (1 + f(a))/2 with f the composite of the stages
+    (f_n by order n, or explicit odd coefficient lists), first stage first."""
     u = a
-    for s, n in enumerate(stages):
-        c = fn_coeffs(n)
+    for s, st in enumerate(stages):
+        c = stage_coeffs(st)
         if s == len(stages) - 1:
             u = eval_odd(ctx, keys, u, [0.5 * x for x in c], 0.5)
         else:

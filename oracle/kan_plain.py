@@ -15,7 +15,8 @@ A model is a list of layer dicts with keys:
   coef [n_out, n_in, G+k], w_s [n_out, n_in], w_b [n_out, n_in]
 and, for the HE-friendly form,
   R (comparison bound), silu_lo, silu_hi, silu_cheb (Chebyshev coefficients),
-  comp (list of composite stage orders n for f_n).
+  comp (composite stages: orders n for f_n, or odd coefficient lists),
+  b0 ("product", Algorithm 2's form, or "difference").
 """
 import numpy as np
 
@@ -64,11 +65,20 @@ def eval_odd(x, c):
     return sum(cl * x ** (2 * l + 1) for l, cl in enumerate(c))
 
 
+def stage_coeffs(stage):
+    """Odd monomial coefficients of one composite stage: an order n names
+    f_n; a sequence gives the coefficients themselves (a minimax stage)."""
+    if isinstance(stage, (int, np.integer)):
+        return fn_coeffs(int(stage))
+    return [float(v) for v in stage]
+
+
 def polycomp0(a, stages):
-    """PolyComp(a, 0) ~ (1 + sign(a)) / 2 via the composite f_{n_1} o ... o f_{n_d}."""
+    """PolyComp(a, 0) ~ (1 + sign(a)) / 2 via the composite of the stages
+    (f_n by order, or explicit odd coefficient lists), first stage first."""
     u = np.asarray(a, dtype=np.float64)
-    for n in stages:
-        u = eval_odd(u, fn_coeffs(n))
+    for st in stages:
+        u = eval_odd(u, stage_coeffs(st))
     return 0.5 + 0.5 * u
 
 
