@@ -74,6 +74,10 @@ def lib():
         "or_modup": (None, [vp, vp, i32, vp]),
         "or_keyswitch_ext": (None, [vp, vp, i32, vp, u64, vp]),
         "or_relin_rescale": (None, [vp, vp, vp, i32, vp, vp]),
+        "or_div_p_ql": (None, [vp, vp, vp, i32, vp]),
+        "or_key_product": (None, [vp, vp, i32, vp, u64, vp]),
+        "or_qp_mul_plain_acc": (None, [vp, vp, vp, i32, vp]),
+        "or_qp_lift": (None, [vp, vp, i32, u64, vp, vp]),
         "or_ext_rows": (u64, [vp, i32]),
         "or_galois_elt": (u64, [vp, i64]),
     }

@@ -380,3 +380,77 @@ def rotate_many(ctx, keys, a, steps):
 
 def rotate(ctx, keys, a, step):
     return rotate_many(ctx, keys, a, [step])[step]
+
+
+# ---------------------------------------------------------------- double hoisting
+# The baby steps of a BSGS matrix-vector product can stay in the extended
+# basis QP_l (Bossuat et al. 2021, "double hoisting"; a reading of the BSGS
+# matvec's hoisted rotations): each rotation skips its ModDown, the diagonal
+# products and their sum are taken over QP_l, and the sum is divided by
+# P q_level once per giant step (the rescale of the diagonal products and the
+# ModDown of the rotations in one rounded division).
+def _qp_rows(ctx, level):
+    return list(range(level + 1)) + [ctx.L + 1 + k for k in range(ctx.alpha)]
+
+
+def encode_qp(ctx, v, level, scale):
+    """Plaintext of v over QP_level: [l + alpha][N] NTT form, the encoding's
+    integer coefficients reduced mod each Q limb and special prime (the Q
+    rows equal encode()'s)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    co = np.zeros(ctx.N, np.int64)
+    if ctx.L_.or_encode(ptr(v), len(v), ctx.log_n, scale, ptr(co)) != 0:
+        raise OverflowError("oracle: encoding overflow")
+    rows = _qp_rows(ctx, level)
+    out = np.zeros((len(rows), ctx.N), np.uint64)
+    for r, t in enumerate(rows):
+        out[r] = np.mod(co, np.int64(ctx.moduli[t])).astype(np.uint64)
+        ctx.L_.or_ntt_limb(ctx.h, ptr(out[r]), t, 0)
+    return out
+
+
+def rotate_many_qp(ctx, keys, a, steps):
+    """Rotations of `a` kept in QP_l (no ModDown): {t: [2][l + alpha][N]}
+    with R_t = (P sigma_t(c0) + acc_0, acc_1), acc the key inner product of
+    sigma_t(ModUp(c1)); R_t decrypts to P rot(a, t) under the secret over
+    QP_l. t = 0 (identity) gives (P c0, P c1)."""
+    lv, rows = a.level, a.level + 1 + ctx.alpha
+    out, ext = {}, None
+    for t in steps:
+        g = ctx.galois(t)
+        R = np.zeros((2, rows, ctx.N), np.uint64)
+        if g == 1:
+            for k in range(2):
+                ctx.L_.or_qp_lift(ctx.h, ptr(np.ascontiguousarray(a.data[k])), lv, 0, None, ptr(R[k]))
+        else:
+            if ext is None:
+                ext = _modup(ctx, a.data[1], lv)
+            if g not in keys.galois:
+                raise KeyError("missing Galois key for step %d" % t)
+            acc = np.zeros((2, rows, ctx.N), np.uint64)
+            ctx.L_.or_key_product(ctx.h, ptr(ext), lv, ptr(keys.galois[g]), g, ptr(acc))
+            ctx.L_.or_qp_lift(ctx.h, ptr(np.ascontiguousarray(a.data[0])), lv, g, ptr(acc[0]), ptr(R[0]))
+            R[1] = acc[1]
+        out[t] = R
+    return out
+
+
+def qp_mul_plain_acc(ctx, R, pt, level, acc):
+    """acc += R * pt over QP_level (in place)."""
+    ctx.L_.or_qp_mul_plain_acc(ctx.h, ptr(R), ptr(pt), level, ptr(acc))
+
+
+def div_p_ql(ctx, acc, level, scale):
+    """The QP_level pair acc ([2][l + alpha][N]) divided by P q_level with
+    rounding to nearest (centred conversion of the dropped limbs): a
+    ciphertext at level - 1 with scale `scale` / q_level (snapped to the
+    canonical scale within 2^-30)."""
+    if level < 1:
+        raise ValueError("level exhausted")
+    out = np.zeros((2, level, ctx.N), np.uint64)
+    ctx.L_.or_div_p_ql(ctx.h, None, ptr(np.ascontiguousarray(acc)), level, ptr(out))
+    s = scale / ctx.q[level]
+    d = ctx.delta[level - 1]
+    if abs(s / d - 1.0) < SNAP:
+        s = d
+    return Ct(out, level - 1, s)

@@ -894,11 +894,42 @@ static uint64_t* key_product(const or_ctx* c, const uint64_t* ext_in, int level,
  * This replaces ModDown by P followed by rescaling by q_l; the result
  * differs from that sequence only in the rounding of the division.
  */
+static void div_p_ql(const or_ctx* c, const uint64_t* d01, const uint64_t* acc, int level,
+                     uint64_t* out);
+
 void or_relin_rescale(const or_ctx* c, const uint64_t* d01, const uint64_t* ext_in, int level,
                       const uint64_t* key, uint64_t* out) {
+  uint64_t* acc = key_product(c, ext_in, level, key, 0);
+  div_p_ql(c, d01, acc, level, out);
+  free(acc);
+}
+
+/*
+ * The division of or_relin_rescale on its own: y = P d_k + acc_k over QP_l
+ * (d01 may be NULL: y = acc_k), out_k = round(y / (P q_l)) over Q_{l-1} by
+ * the centred conversion of the dropped limbs. acc: [2][l + alpha][N] (Q
+ * rows, then the special primes), NTT form; out: [2][level][N].
+ */
+void or_div_p_ql(const or_ctx* c, const uint64_t* d01, const uint64_t* acc, int level,
+                 uint64_t* out) {
+  div_p_ql(c, d01, acc, level, out);
+}
+
+/* the key inner product of or_keyswitch_ext without ModDown: acc_k over
+ * QP_l ([2][l + alpha][N], NTT form), the rows mapped by X -> X^g first
+ * when g != 0 */
+void or_key_product(const or_ctx* c, const uint64_t* ext_in, int level, const uint64_t* key,
+                    uint64_t g, uint64_t* acc_out) {
+  const int rows = level + 1 + c->alpha;
+  uint64_t* acc = key_product(c, ext_in, level, key, g);
+  memcpy(acc_out, acc, (uint64_t)2 * rows * c->N * sizeof(uint64_t));
+  free(acc);
+}
+
+static void div_p_ql(const or_ctx* c, const uint64_t* d01, const uint64_t* acc, int level,
+                     uint64_t* out) {
   const uint64_t N = c->N;
   const int l = level + 1, rows = l + c->alpha, A = c->alpha;
-  uint64_t* acc = key_product(c, ext_in, level, key, 0);
   /* the dropped moduli: D[0] = q_level, D[1 + a] = p_a */
   uint64_t* Dm = malloc((uint64_t)(A + 1) * sizeof(uint64_t));
   int* Dt = malloc((uint64_t)(A + 1) * sizeof(int));
@@ -913,7 +944,7 @@ void or_relin_rescale(const or_ctx* c, const uint64_t* d01, const uint64_t* ext_
       const uint64_t qm = Dm[m];
       uint64_t* ym = y + (uint64_t)m * N;
       const uint64_t* am = acc + ((uint64_t)k * rows + (m == 0 ? level : l + m - 1)) * N;
-      if (m == 0) { /* y = P d_k + acc_k on q_level */
+      if (m == 0 && d01) { /* y = P d_k + acc_k on q_level */
         uint64_t P = 1;
         for (int a = 0; a < A; a++) P = mulmod(P, c->mod[pidx(c, a)] % qm, qm);
         const uint64_t* dk = d01 + ((uint64_t)k * l + level) * N;
@@ -951,15 +982,14 @@ void or_relin_rescale(const or_ctx* c, const uint64_t* d01, const uint64_t* ext_
       or_ntt_forward(conv, c->log_n, q, c->psi[i]);
       const uint64_t Minv = invmod(M, q);
       const uint64_t* ai = acc + ((uint64_t)k * rows + i) * N;
-      const uint64_t* di = d01 + ((uint64_t)k * l + i) * N;
+      const uint64_t* di = d01 ? d01 + ((uint64_t)k * l + i) * N : NULL;
       uint64_t* o = out + ((uint64_t)k * level + i) * N;
       for (uint64_t n = 0; n < N; n++) {
-        const uint64_t yi = addmod(mulmod(P, di[n], q), ai[n], q);
+        const uint64_t yi = di ? addmod(mulmod(P, di[n], q), ai[n], q) : ai[n];
         o[n] = mulmod(submod(yi, conv[n], q), Minv, q);
       }
     }
   }
-  free(acc);
   free(Dm);
   free(Dt);
   free(y);
@@ -1032,6 +1062,55 @@ void or_keyswitch_ext(const or_ctx* c, const uint64_t* ext_in, int level, const 
   free(y);
   free(conv);
   free(u);
+}
+
+/*
+ * QP_l rows (the l = level + 1 Q limbs, then the alpha special primes) for
+ * the double-hoisted BSGS. or_qp_mul_plain_acc: acc_k += a_k * pt row by
+ * row mod the row's modulus (a, acc: [2][l + alpha][N]; pt: [l + alpha][N]).
+ * or_qp_lift: out = (P sigma_g(c0) + acc0) on the Q rows, acc0 on the special
+ * primes (sigma_g: X -> X^g in the NTT domain, none when g = 0; acc0 NULL is
+ * zero): the first polynomial of a rotation kept in QP_l.
+ */
+void or_qp_mul_plain_acc(const or_ctx* c, const uint64_t* a, const uint64_t* pt, int level,
+                         uint64_t* acc) {
+  const uint64_t N = c->N;
+  const int l = level + 1, rows = l + c->alpha;
+  for (int k = 0; k < 2; k++)
+    for (int r = 0; r < rows; r++) {
+      const uint64_t m = c->mod[r < l ? r : pidx(c, r - l)];
+      const uint64_t* ar = a + ((uint64_t)k * rows + r) * N;
+      const uint64_t* pr = pt + (uint64_t)r * N;
+      uint64_t* o = acc + ((uint64_t)k * rows + r) * N;
+      for (uint64_t n = 0; n < N; n++) o[n] = addmod(o[n], mulmod(ar[n], pr[n], m), m);
+    }
+}
+
+void or_qp_lift(const or_ctx* c, const uint64_t* c0, int level, uint64_t g, const uint64_t* acc0,
+                uint64_t* out) {
+  const uint64_t N = c->N;
+  const int l = level + 1, rows = l + c->alpha;
+  uint64_t* s = malloc((uint64_t)l * N * sizeof(uint64_t));
+  if (g != 0)
+    or_automorphism_polys(c, c0, l, g, s);
+  else
+    memcpy(s, c0, (uint64_t)l * N * sizeof(uint64_t));
+  for (int r = 0; r < rows; r++) {
+    uint64_t* o = out + (uint64_t)r * N;
+    const uint64_t* ar = acc0 ? acc0 + (uint64_t)r * N : NULL;
+    if (r >= l) {
+      for (uint64_t n = 0; n < N; n++) o[n] = ar ? ar[n] : 0;
+      continue;
+    }
+    const uint64_t q = c->mod[r];
+    uint64_t P = 1;
+    for (int a = 0; a < c->alpha; a++) P = mulmod(P, c->mod[pidx(c, a)] % q, q);
+    for (uint64_t n = 0; n < N; n++) {
+      const uint64_t v = mulmod(P, s[(uint64_t)r * N + n], q);
+      o[n] = ar ? addmod(v, ar[n], q) : v;
+    }
+  }
+  free(s);
 }
 
 uint64_t or_ext_rows(const or_ctx* c, int level) {

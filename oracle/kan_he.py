@@ -137,6 +137,40 @@ def bsgs_matvec(ctx, keys, v, M, plan):
     return z
 
 
+def bsgs_matvec_double(ctx, keys, v, M, plan):
+    """bsgs_matvec with double hoisting (layer option bsgs = "double"): the
+    baby-step rotations stay in QP_l (one ModUp, no ModDown), each giant
+    step's diagonal products are summed over QP_l with the diagonals encoded
+    over QP_l, and the sum is divided by P q_level once (ModDown and the
+    rescale of the products in one rounded division), then rotated by g1 i."""
+    S = ctx.slots
+    D = diagonals(M, plan, S)
+    g1, g2 = plan["g1"], plan["g2"]
+    lv = v.level
+    R = ckks.rotate_many_qp(ctx, keys, v, list(range(g1)))
+    Spt = ckks.plain_scale(ctx, v.scale, lv)
+    z = None
+    for i in range(g2):
+        acc = np.zeros_like(R[0])
+        for j in range(g1):
+            d = np.roll(D[g1 * i + j], g1 * i)  # rot(d, -g1 i)
+            ckks.qp_mul_plain_acc(ctx, R[j], ckks.encode_qp(ctx, d, lv, Spt), lv, acc)
+        inner = ckks.div_p_ql(ctx, acc, lv, v.scale * Spt)
+        if i > 0:
+            inner = ckks.rotate(ctx, keys, inner, g1 * i)
+        z = inner if z is None else ckks.add(ctx, z, inner)
+    for s in plan["folds"]:
+        z = ckks.add(ctx, z, ckks.rotate(ctx, keys, z, s))
+    return z
+
+
+def matvec(ctx, keys, v, M, plan, layer):
+    """The layer's BSGS form: hoisted (default) or double-hoisted."""
+    if layer.get("bsgs", "single") == "double":
+        return bsgs_matvec_double(ctx, keys, v, M, plan)
+    return bsgs_matvec(ctx, keys, v, M, plan)
+
+
 # ------------------------------------------------------------------ polynomials
 def eval_odd(ctx, keys, u, c, const=0.0):
     """sum_l c[l] u^(2l+1) + const. The coefficient list is padded to 2^K
@@ -278,7 +312,7 @@ def layer_eval(ctx, keys, x, layer):
     if plan_b["npad"] < S:
         y = ckks.add(ctx, y, ckks.rotate(ctx, keys, y, -plan_b["npad"]))
     v = eval_cheb(ctx, keys, y, layer["silu_cheb"])
-    yb = bsgs_matvec(ctx, keys, v, layer["w_b"], plan_b)
+    yb = matvec(ctx, keys, v, layer["w_b"], plan_b, layer)
 
     # Algorithm 1
     xr = ckks.mul_plain(ctx, x, mask / (2.0 * R))
@@ -332,14 +366,14 @@ def layer_eval(ctx, keys, x, layer):
         plan_p = bsgs_plan(n, n, S)
         if plan_p["npad"] < S:
             b = ckks.add(ctx, b, ckks.rotate(ctx, keys, b, -plan_p["npad"]))
-        b = bsgs_matvec(ctx, keys, b, permutation_matrix(n_i, G + k), plan_p)
+        b = matvec(ctx, keys, b, permutation_matrix(n_i, G + k), plan_p, layer)
         Ws = lazy_weights(layer)
     else:
         # fused linear layer (Eq. 13)
         Ws = fused_weights(layer)
     if plan_s["npad"] < S:
         b = ckks.add(ctx, b, ckks.rotate(ctx, keys, b, -plan_s["npad"]))
-    ys = bsgs_matvec(ctx, keys, b, Ws, plan_s)
+    ys = matvec(ctx, keys, b, Ws, plan_s, layer)
 
     lv = min(ys.level, yb.level)
     return ckks.add(ctx, ckks.level_down(ctx, ys, lv), ckks.level_down(ctx, yb, lv))

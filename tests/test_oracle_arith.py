@@ -499,6 +499,41 @@ def test_moddown_is_rounded_division_by_p(small, step):
         assert exact >= 0.99 * len(pts)
 
 
+def test_qp_rotation_divided_by_p_is_the_rotation(small):
+    """A rotation kept in QP_l for double hoisting, R = (P sigma(c0) + acc_0,
+    acc_1), divided by P with rounding to nearest (by CRT, big integers)
+    gives the hoisted rotation's words exactly: P sigma(c0) is a multiple
+    of P, so the rounding is that of ModDown on acc alone."""
+    ctx, keys = small
+    rng = np.random.default_rng(31)
+    lv = ctx.L
+    l, A = lv + 1, ctx.alpha
+    mod_idx = list(range(l)) + [ctx.L + 1 + k for k in range(A)]
+    qp = [int(ctx.moduli[t]) for t in mod_idx]
+    P = 1
+    for a in range(A):
+        P *= int(ctx.moduli[ctx.L + 1 + a])
+    Qo = 1
+    for t in range(l):
+        Qo *= int(ctx.q[t])
+    ct = ckks.encrypt(ctx, keys, rng.uniform(-1, 1, ctx.slots), lv, 3)
+    for step in (0, 2, -3):
+        R = ckks.rotate_many_qp(ctx, keys, ct, [step])[step]
+        rot = ckks.rotate(ctx, keys, ct, step).data if step else ct.data
+        for k in range(2):
+            yc = _coef(ctx, R[k], mod_idx)
+            oc = _coef(ctx, rot[k], list(range(l)))
+            exact = 0
+            for n in range(ctx.N):
+                Y, _ = _crt([yc[r][n] for r in range(len(qp))], qp)
+                O, _ = _crt([oc[t][n] for t in range(l)], ctx.q[:l])
+                rem = Y % P
+                if 2 * rem > P:
+                    rem -= P
+                exact += (O * P - (Y - rem)) % Qo == 0
+            assert exact >= 0.99 * ctx.N, (step, k)
+
+
 def test_keyswitch_rounding_is_unbiased():
     """ModDown (rotation) and HMult's division round to nearest: the error
     of a rotation stays at the level of fresh encryption noise at every slot

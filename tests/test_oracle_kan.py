@@ -246,6 +246,43 @@ def test_he_bsgs_matvec(he_small):
     assert np.abs(ckks.decrypt(ctx, keys, out, n_out) - M @ v[:n]).max() < 1e-6
 
 
+@pytest.mark.parametrize("n_out,n", [(5, 20), (16, 40), (2, 64)])
+def test_he_bsgs_matvec_double_hoisted(he_small, n_out, n):
+    """Double hoisting (baby steps kept in QP_l, one division by P q_l per
+    giant step): decrypts to the dense M v in FP64, like the hoisted form
+    (the two differ only in the rounding of their divisions), one level."""
+    ctx = he_small
+    rng = np.random.default_rng(5 + n)
+    M = rng.normal(size=(n_out, n))
+    plan = kan_he.bsgs_plan(n_out, n, ctx.slots)
+    steps = [-plan["npad"]] + list(range(1, plan["g1"])) + [plan["g1"] * i for i in range(1, plan["g2"])] + plan["folds"]
+    keys = ckks.Keys(ctx, 3, rot_steps=steps)
+    v = np.zeros(ctx.slots)
+    v[:n] = rng.uniform(-1, 1, n)
+    c = ckks.encrypt(ctx, keys, v, ctx.L, 2)
+    if plan["npad"] < ctx.slots:
+        c = ckks.add(ctx, c, ckks.rotate(ctx, keys, c, -plan["npad"]))
+    dbl = kan_he.bsgs_matvec_double(ctx, keys, c, M, plan)
+    one = kan_he.bsgs_matvec(ctx, keys, c, M, plan)
+    assert dbl.level == one.level == ctx.L - 1 and dbl.scale == one.scale
+    d = ckks.decrypt(ctx, keys, dbl, n_out)
+    assert np.abs(d - M @ v[:n]).max() < 1e-6
+    assert np.abs(d - ckks.decrypt(ctx, keys, one, n_out)).max() < 1e-6
+    assert not np.array_equal(dbl.data, one.data)  # a different rounding, not the same words
+
+
+def test_he_kan_double_hoisted_matches_hef(he_small):
+    ctx = he_small
+    model = [dict(L, bsgs="double") for L in W.make_model("t", widths=[3, 4, 2], G=3, k=2)]
+    X = W.uniform_inputs(100, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    keys = ckks.Keys(ctx, 1, rot_steps=kan_he.model_rotations(m, ctx.slots))
+    c = ckks.encrypt(ctx, keys, X[0], ctx.L, 2, 0)
+    out = kan_he.infer(ctx, keys, c, m)
+    hef = kan_plain.forward(m, X[:1], "poly", "poly")[0]
+    assert np.abs(ckks.decrypt(ctx, keys, out, 2) - hef).max() < 1e-5
+
+
 def test_he_kan_matches_hef(he_small):
     ctx = he_small
     model = W.make_model("t", widths=[3, 4, 2], G=3, k=2)
