@@ -47,19 +47,19 @@ WORKLOADS = {
     "c1": dict(desc="encrypted KAN [2,5,1] G=5 k=3, plain method (one input per launch), CKKS "
                     "N=2^15, q0 + 18 x 40-bit primes, one 60-bit special prime",
                model="kan_2_5_1", inputs="uniform", log_n=15, levels=18, alpha=1, batch=1,
-               degree=15, comp=[3], fixed=(-4.0, 4.0), uneven=False),
-    "c2": dict(desc="encrypted KAN [4,8,4,1] G=5 k=3, CKKS N=2^16, 36 levels, batch 64 at "
-                    "uneven levels",
+               degree=15, comp=((15,), 0.3), b0="difference", fixed=(-4.0, 4.0), uneven=False),
+    "c2": dict(desc="encrypted KAN [4,8,4,1] G=5 k=3, CKKS N=2^16, 36 levels, batch 64 "
+                    "(input levels over the chain's spare levels: none at this accuracy)",
                model="kan_4_8_4_1", inputs="uniform", log_n=16, levels=36, alpha=0, batch=64,
-               degree=27, comp=[3], fixed=None, uneven=True),
+               degree=27, comp=((7, 15), 0.12), b0="difference", fixed=None, uneven=True),
     "c3": dict(desc="encrypted KAN [784,64,10] G=5 k=3 on synthetic 28x28 blob images, CKKS "
                     "N=2^16, 36 levels, batch 32",
                model="kan_784_64_10", inputs="blob", log_n=16, levels=36, alpha=0, batch=32,
-               degree=15, comp=[3, 3, 3, 3], fixed=None, uneven=False),
+               degree=15, comp=((7, 7, 7, 7), 0.02), b0="product", fixed=None, uneven=False),
     "c4": dict(desc="encrypted KAN [3072,64,10] G=10 k=3 on synthetic 3x32x32 images (two "
                     "ciphertexts per image), CKKS N=2^16, 36 levels, batch 16",
                model="kan_3072_64_10", inputs="cifar", log_n=16, levels=36, alpha=0, batch=16,
-               degree=15, comp=[3, 3, 3, 3], fixed=None, uneven=False),
+               degree=15, comp=((7, 7, 7, 7), 0.02), b0="product", fixed=None, uneven=False),
 }
 WORKLOAD = WORKLOADS["c2"]["desc"]
 
@@ -180,9 +180,12 @@ def serve_arm(a):
         alpha, p_bits, _ = G.autotune_keyswitch(a.log_n, a.levels, a.max_qp_bits, batch=8)
     ctx = G.Context(a.log_n, a.levels, alpha, p_bits=p_bits)
     ctx.set_stream(stream.cuda_stream)
-    specs = [("kan_2_5_1", lambda n, s: W.uniform_inputs(n, 2, seed=s), 15, [3], (-4.0, 4.0), 0.5),
-             ("kan_784_64_10", lambda n, s: W.blob_images(n, seed=s), 15, [3, 3, 3, 3], None, 0.3),
-             ("kan_3072_64_10", lambda n, s: W.cifar_like_images(n, seed=s), 15, [3, 3, 3, 3], None,
+    # every model at the chain's 36 levels with two layers: the four-stage
+    # degree-7 minimax comparison (eps 0.02) in Algorithm 2's product form
+    stages = G.comp_minimax(0.02, (7, 7, 7, 7))[0]
+    specs = [("kan_2_5_1", lambda n, s: W.uniform_inputs(n, 2, seed=s), 15, stages, (-4.0, 4.0), 0.5),
+             ("kan_784_64_10", lambda n, s: W.blob_images(n, seed=s), 15, stages, None, 0.3),
+             ("kan_3072_64_10", lambda n, s: W.cifar_like_images(n, seed=s), 15, stages, None,
               0.2)]
     srv = G.Server(ctx, int(200e9))
     models = []
@@ -330,7 +333,8 @@ def config(a):
     wl = workload(a)
     return {"workload": wl["desc"], "model": wl["model"], "n_poly": 1 << a.log_n,
             "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": wl["degree"],
-            "comparison": " o ".join("f_%d" % n for n in wl["comp"]),
+            "comparison": "minimax composite, stage degrees %s, eps %g, B_{m,0} %s form"
+                          % ("-".join(str(d) for d in wl["comp"][0]), wl["comp"][1], wl["b0"]),
             "input_levels": "uniform over [L - slack, L]" if wl["uneven"] else "all at L",
             "parallelism": "replicas (request sharding)",
             "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)",
@@ -364,7 +368,7 @@ def workload(a):
 def model_and_inputs(a, rank):
     from paper_2409_07751_gb300 import workloads as W
     wl = workload(a)
-    model = W.make_model(wl["model"])
+    model = [dict(L, b0=wl["b0"]) for L in W.make_model(wl["model"])]
     n_in = model[0]["n_in"]
     gen = {"uniform": lambda n, s: W.uniform_inputs(n, n_in, seed=s),
            "blob": lambda n, s: W.blob_images(n, seed=s),
@@ -374,9 +378,22 @@ def model_and_inputs(a, rank):
     return model, Xcal, X
 
 
-def calibrate_for(a, calibrate, model, Xcal):
+def calibrate_for(a, calibrate, model, Xcal, design):
+    """The model's HE parameters: the comparison composite from `design`
+    (eps, degrees) -> stages, then calibrate(...)."""
     wl = workload(a)
-    return calibrate(model, Xcal, wl["degree"], wl["comp"], fixed_range=wl["fixed"])
+    degs, eps = wl["comp"]
+    stages = design(eps, degs)
+    return calibrate(model, Xcal, wl["degree"], stages, fixed_range=wl["fixed"])
+
+
+def gpu_design(G):
+    return lambda eps, degs: G.comp_minimax(eps, degs)[0]
+
+
+def oracle_design(eps, degs):
+    from oracle import polycomp
+    return polycomp.composite(eps, degs)[0]
 
 
 # ------------------------------------------------------------------ clocks
@@ -551,7 +568,9 @@ def c1_oracle_full():
     wl = WORKLOADS["c1"]
     model = W.make_model(wl["model"])
     Xcal = W.uniform_inputs(256, 2, seed=W.SEED_INPUTS + 1000)
-    m = OC.calibrate(model, Xcal, wl["degree"], wl["comp"], fixed_range=wl["fixed"])
+    model = [dict(L, b0=wl["b0"]) for L in model]
+    m = OC.calibrate(model, Xcal, wl["degree"], oracle_design(wl["comp"][1], wl["comp"][0]),
+                     fixed_range=wl["fixed"])
     ctx = O.Ctx(O.Params(wl["log_n"], wl["levels"], wl["alpha"]))
     keys = O.Keys(ctx, W.SEED_KEYS, kan_he.model_rotations(m, ctx.slots))
     x = O.encrypt(ctx, keys, W.uniform_inputs(1, 2)[0], wl["levels"], W.SEED_ENC, 0)
@@ -589,7 +608,7 @@ def reference_arm(a):
     if not a.alpha:
         a.alpha, a.p_bits = 5, 48
     model, Xcal, _ = model_and_inputs(a, 0)
-    m = calibrate_for(a, OC.calibrate, model, Xcal)
+    m = calibrate_for(a, OC.calibrate, model, Xcal, oracle_design)
     per_step = max(5.0, min(a.cpu_budget, 150.0 / max(1, a.steps + a.warmup)))
     t0 = time.perf_counter()
     v, sample, procs = oracle_all_cores(m, a, per_step, steps=a.steps, warmup=a.warmup)
@@ -744,7 +763,7 @@ def main():
     ctx = G.Context(a.log_n, a.levels, a.alpha, p_bits=a.p_bits, device=local)
     ctx.set_stream(stream.cuda_stream)
     model, Xcal, X = model_and_inputs(a, rank)
-    m = calibrate_for(a, G.calibrate, model, Xcal)
+    m = calibrate_for(a, G.calibrate, model, Xcal, gpu_design(G))
     gm = G.Model(ctx, m)
     gm.set_graphs(a.graphs)
     depth = sum(gm.layer_depth(i) for i in range(gm.n_layers))
@@ -1007,7 +1026,7 @@ def main():
         line["configs"] = extras(local)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         from oracle import calibrate as OC
-        mo = calibrate_for(a, OC.calibrate, model, Xcal)
+        mo = calibrate_for(a, OC.calibrate, model, Xcal, oracle_design)
         v1, sample1, _ = oracle_sample(mo, a, a.cpu_budget)
         v, sample, procs = oracle_all_cores(mo, a, a.cpu_budget)
         c1 = None

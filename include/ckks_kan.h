@@ -242,8 +242,9 @@ int ckks_rotate_hoisted(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in,
  * weights w_b[o][i]; the HE-friendly parameters are the comparison bound R
  * (Algorithm 2), the SiLU polynomial (Eqs. 11-12) as Chebyshev coefficients
  * on [silu_lo, silu_hi], and the comparison composite f_{comp[0]} o ... as
- * the orders n of f_n(x) = sum_i 4^-i C(2i,i) x (1-x^2)^i. All arrays are
- * row-major doubles, copied at model creation. */
+ * the orders n of f_n(x) = sum_i 4^-i C(2i,i) x (1-x^2)^i, or given by its
+ * stages' coefficients (comp_poly). All arrays are row-major doubles, copied
+ * at model creation. */
 typedef struct {
   int n_in, n_out, G, k;
   double grid_lo, grid_hi;
@@ -261,7 +262,37 @@ typedef struct {
    * the permutation P of Algorithm 3 (n_i(g+k) diagonals, one more level),
    * then W' on the row-major basis. */
   int naive;
+  /* Explicit comparison composite, used instead of comp when n_comp_poly > 0
+   * (comp may then be NULL): stage s, applied in order, is the odd polynomial
+   * sum_l c_l u^(2l+1) with the comp_poly_len[s] coefficients c_0, c_1, ..
+   * read in turn from comp_poly (for example from kan_comp_minimax); the
+   * last stage returns (1 + p) / 2. Stages of at most 32 coefficients. */
+  const double* comp_poly;
+  const int* comp_poly_len;
+  int n_comp_poly;
+  /* Order-0 basis of Algorithm 2. 0: the product B_{m,0} =
+   * PolyComp(x - t_m) PolyComp(t_{m+1} - x), as the algorithm prints it.
+   * 1: the difference B_{m,0} = s_m - s_{m+1}, s_m = PolyComp(x - t_m) over
+   * all g + 2k + 1 knots and s_{m+1} = rot(s, n_i): one comparison and no
+   * product (one level fewer); equal to the product form for exact
+   * comparisons since PolyComp(-a) = 1 - PolyComp(a) for an odd composite.
+   * Algorithm 1 then packs 2^ceil(log2(g + 2k + 1)) copies. */
+  int b0_form;
 } kan_layer_desc;
+
+/* PolyComp by composite minimax polynomials (Algorithm 2 cites Lee et al.'s
+ * minimax composites without degrees): stage 1 is the odd polynomial of
+ * degree degrees[0] with the least maximum error against 1 on [eps, A]
+ * (against sign on [-A, -eps] u [eps, A]; PolyComp's range is A = 1, and the
+ * comparison bound R keeps calibration inputs within 1/1.1 of it); stage
+ * s + 1 the same on the image
+ * of stage s's interval; each by the Remez exchange over 40001 points. coef
+ * receives the stages' odd monomial coefficients, (degrees[s] + 1) / 2 each,
+ * in order (the layout of kan_layer_desc.comp_poly); taus (may be NULL) the
+ * composite's maximum distance from 1 on [eps, A] after each stage. Odd
+ * degrees 1..63; INVALID_ARG if a stage leaves values <= 0 (eps too small). */
+int kan_comp_minimax(double eps, double A, const int* degrees, int n_stages, double* coef,
+                     double* taus);
 
 /* Host-only model preparation (no device work).
  * kan_silu_fit: Chebyshev coefficients cheb[0..degree] (basis of [lo, hi]
@@ -270,8 +301,9 @@ typedef struct {
  * outside), KAN_FIT_OLS unit weights (both by Householder QR), KAN_FIT_REMEZ
  * the minimax polynomial over the points by the Remez exchange.
  * kan_calibrate: for each layer (only n_in, n_out, G, k, grid, coef, w_s,
- * w_b and comp of `layers` are read), the statistics of the layer's inputs
- * over the n calibration vectors X[n][n_in] as the encrypted network computes
+ * w_b, the comparison composite and b0_form of `layers` are read), the
+ * statistics of the layer's inputs over the n calibration vectors
+ * X[n][n_in] as the encrypted network computes
  * them (the HE-friendly FP64 KAN: fitted SiLU, PolyComp indicators with the
  * layer's comparison composite, the earlier layers already calibrated), the
  * SiLU range of Eq. 11 (or fixed_range[0..1] if not NULL) and its fit, and
@@ -296,8 +328,9 @@ int kan_model_destroy(kan_model* model);
 int kan_model_rotations(const kan_model* model, int32_t* steps, size_t cap, size_t* n);
 /* Multiplicative depth (levels consumed) of one layer. */
 int kan_model_layer_depth(const kan_model* model, int layer, int* depth);
-/* Input chunking of one layer: when n_in * 2^J (J = ceil(log2(G + 2k)),
- * the repeat-packing factor of Algorithm 1) exceeds the slots, the layer
+/* Input chunking of one layer: when n_in * 2^J (J = ceil(log2(G + 2k)), or
+ * ceil(log2(G + 2k + 1)) in the difference form, the repeat-packing factor
+ * of Algorithm 1) exceeds the slots, the layer
  * takes *K > 1 input ciphertexts per request, each of *n_c consecutive inputs
  * (the last zero-padded), as consecutive batch elements; otherwise *K = 1 and
  * *n_c = n_in. Only layer 0 may be chunked. */

@@ -25,7 +25,9 @@ class KanLayerDesc(ctypes.Structure):
                 ("coef", c_vp), ("w_s", c_vp), ("w_b", c_vp),
                 ("R", c_dbl), ("silu_lo", c_dbl), ("silu_hi", c_dbl),
                 ("silu_cheb", c_vp), ("silu_degree", c_i32),
-                ("comp", c_vp), ("n_comp", c_i32), ("naive", c_i32)]
+                ("comp", c_vp), ("n_comp", c_i32), ("naive", c_i32),
+                ("comp_poly", c_vp), ("comp_poly_len", c_vp), ("n_comp_poly", c_i32),
+                ("b0_form", c_i32)]
 
 
 SIGNATURES = {
@@ -75,6 +77,7 @@ SIGNATURES = {
     "ckks_rotate": (c_i32, [c_vp, c_vp, c_vp, ctypes.c_int32, PP]),
     "ckks_rotate_hoisted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "kan_silu_fit": (c_i32, [c_dbl, c_dbl, c_dbl, c_dbl, c_i32, c_i32, c_i32, c_vp]),
+    "kan_comp_minimax": (c_i32, [c_dbl, c_dbl, c_vp, c_i32, c_vp, c_vp]),
     "kan_calibrate": (c_i32, [c_vp, c_sz, c_vp, c_sz, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp,
                               c_vp]),
     "kan_model_create": (c_i32, [c_vp, c_vp, c_sz, PP]),
@@ -384,12 +387,23 @@ def rotate_hoisted(ctx, keys, a, steps):
 def _descs(layers, keep):
     descs = (KanLayerDesc * len(layers))()
     for d, L in zip(descs, layers):
-        if L.get("b0", "product") != "product":
-            raise ValueError("the library builds the order-0 basis in Algorithm 2's product "
-                             "form; b0=%r is not available" % (L["b0"],))
+        b0 = L.get("b0", "product")
+        if b0 not in B0_FORMS:
+            raise ValueError("b0 must be 'product' or 'difference', not %r" % (b0,))
         arrs = [np.ascontiguousarray(L[k], dtype=np.float64) for k in ("coef", "w_s", "w_b")]
         cheb = np.ascontiguousarray(L.get("silu_cheb", [0.0, 0.0]), dtype=np.float64)
-        comp = np.ascontiguousarray(L.get("comp", [1]), dtype=np.int32)
+        stages = list(L.get("comp", [1]))
+        if all(isinstance(st, (int, np.integer)) for st in stages):
+            comp = np.ascontiguousarray(stages, dtype=np.int32)
+            poly = plen = None
+        else:  # explicit odd coefficient lists
+            if any(isinstance(st, (int, np.integer)) for st in stages):
+                raise ValueError("comparison stages are all f_n orders or all coefficient lists")
+            comp = np.zeros(1, np.int32)
+            cl = [np.ascontiguousarray(st, dtype=np.float64) for st in stages]
+            poly = np.ascontiguousarray(np.concatenate(cl))
+            plen = np.ascontiguousarray([len(c) for c in cl], dtype=np.int32)
+            keep += [poly, plen]
         keep += arrs + [cheb, comp]
         d.n_in, d.n_out, d.G, d.k = L["n_in"], L["n_out"], L["G"], L["k"]
         d.grid_lo, d.grid_hi = L["lo"], L["hi"]
@@ -398,7 +412,27 @@ def _descs(layers, keep):
         d.silu_cheb, d.silu_degree = _p(cheb), len(cheb) - 1
         d.comp, d.n_comp = _p(comp), len(comp)
         d.naive = 1 if L.get("naive") else 0
+        d.comp_poly, d.comp_poly_len = _p(poly), _p(plen)
+        d.n_comp_poly = 0 if poly is None else len(plen)
+        d.b0_form = B0_FORMS[b0]
     return descs
+
+
+B0_FORMS = {"product": 0, "difference": 1}
+
+
+def comp_minimax(eps, degrees, A=1.0):
+    """PolyComp stages by the library's minimax design (kan_comp_minimax):
+    (list of odd coefficient arrays, taus)."""
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    coef = np.zeros(int(sum((d + 1) // 2 for d in degrees)))
+    taus = np.zeros(len(degrees))
+    check(lib().kan_comp_minimax(float(eps), float(A), _p(deg), len(deg), _p(coef), _p(taus)))
+    out, off = [], 0
+    for d in degrees:
+        out.append(coef[off:off + (d + 1) // 2].copy())
+        off += (d + 1) // 2
+    return out, taus
 
 
 FIT_METHODS = {"wls": 0, "ols": 1, "remez": 2}

@@ -4,10 +4,11 @@
 //    replicated to the matvec period, the Chebyshev polynomial by baby/giant
 //    steps, then W_b by BSGS.
 //  Spline branch: Algorithm 1 (mask with 1/(2R) folded in, then doubling
-//    rotations by -n_i 2^(j-1)), Algorithm 2 (PolyComp through the composite
-//    f_n o ... whose last stage returns (1+f)/2, B0 = x1 (x) x2, k recursion
-//    steps sharing one relinearisation each), then W_f = W'P (Algorithm 3,
-//    Eq. 13) by BSGS.
+//    rotations by -n_i 2^(j-1)), Algorithm 2 (PolyComp through a composite of
+//    odd polynomials, minimax stages or f_n, whose last stage returns
+//    (1+f)/2; B0 = x1 (x) x2, or the difference of neighbouring knot
+//    comparisons s - rot(s, n_i); k recursion steps sharing one
+//    relinearisation each), then W_f = W'P (Algorithm 3, Eq. 13) by BSGS.
 //  Output: both branches moved to the lower level and added.
 // Plaintext vectors are encoded once per (tag, level, scale) and cached on
 // the device; a batch shares them.
@@ -70,7 +71,8 @@ struct Layer {
   int n_in, n_out, G, k;
   double lo, hi, R, silu_lo, silu_hi;
   std::vector<double> coef, w_s, w_b, cheb, knots;
-  std::vector<int> comp;
+  std::vector<std::vector<double>> comp;  // composite stages, odd monomial coefficients
+  int b0 = 0;  // order-0 basis: 0 product (Algorithm 2), 1 difference of knot comparisons
   // A wide first layer (n_in 2^ceil(log2(G+2k)) > N/2) takes K input
   // ciphertexts per request of n_c inputs each (the last zero-padded);
   // otherwise K = 1 and n_c = n_in. The schedule runs on n_c inputs.
@@ -162,7 +164,16 @@ std::vector<double> diagonals(const std::vector<double>& M, int n_out, int n, co
 }
 
 enum Tag { T_SILU_MUL = 1, T_SILU_ADD, T_MASK_R, T_G1, T_G2, T_U1M, T_U1A, T_U2M, T_U2A, T_DIAG_B, T_DIAG_S,
-           T_MASK_B0, T_DIAG_P, T_DIAG_W };
+           T_MASK_B0, T_DIAG_P, T_DIAG_W, T_G0 };
+
+// ColTile blocks Algorithm 1 must provide: one per order-0 basis function
+// (g + 2k), or one per knot (g + 2k + 1) for the difference form
+int rep_blocks(const Layer& L) { return L.G + 2 * L.k + (L.b0 == 1 ? 1 : 0); }
+int rep_bits(const Layer& L) {
+  int J = 0;
+  while ((1 << J) < rep_blocks(L)) J++;
+  return J;
+}
 
 // accessor of diagonals precomputed per chunk as [no][slots]
 auto stored_diag(const std::vector<std::vector<double>>& DC, int S) {
@@ -253,11 +264,12 @@ Ct eval_odd(Ctx& c, const ckks_keys& keys, const ckks_ct& u, const std::vector<d
   return out;
 }
 
-Ct polycomp0(Ctx& c, const ckks_keys& keys, const ckks_ct& a, const std::vector<int>& stages) {
+Ct polycomp0(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
+              const std::vector<std::vector<double>>& stages) {
   Ct u;
   const ckks_ct* cur = &a;
   for (size_t s = 0; s < stages.size(); s++) {
-    std::vector<double> cf = fn_coeffs(stages[s]);
+    std::vector<double> cf = stages[s];
     if (s + 1 == stages.size()) {
       for (auto& x : cf) x = 0.5 * x;
       u = eval_odd(c, keys, *cur, cf, 0.5);
@@ -342,9 +354,8 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   const int S = (int)(c.N / 2);
   const int n_i = L.n_c, G = L.G, k = L.k;  // inputs per ciphertext
   const double R = L.R;
-  int J = 0;
-  while ((1 << J) < G + 2 * k) J++;
-  if ((int64_t)n_i << J > S) throw Error(CKKS_ERR_UNSUPPORTED, "n_i * 2^ceil(log2(g+2k)) > N/2");
+  const int J = rep_bits(L);
+  if ((int64_t)n_i << J > S) throw Error(CKKS_ERR_UNSUPPORTED, "n_i * 2^J > N/2 (Algorithm 1)");
   if (x.level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
   if (x.B % L.K != 0) throw Error(CKKS_ERR_INVALID_ARG, "batch is not a multiple of the layer's chunks");
 
@@ -370,24 +381,42 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
 
   // Algorithm 2
   const int r = G + 2 * k + 1;
-  const uint64_t* p_g1 = cached_pt(M, li, T_G1, 0, xr->level, xr->scale, [&] {
-    std::vector<double> g1 = coltile(L, 1, r);
-    for (auto& t : g1) t = -t / (2.0 * R);
-    return g1;
-  });
-  Ct a1 = op_add_pt(c, *xr, p_g1);
-  const uint64_t* p_g2 = cached_pt(M, li, T_G2, 0, xr->level, xr->scale, [&] {
-    std::vector<double> g2 = coltile(L, 2, r + 1);
-    for (auto& t : g2) t = t / (2.0 * R);
-    return g2;
-  });
-  Ct a2 = op_add_pt(c, *op_mul_int(c, *xr, -1), p_g2);
-  Ct s1 = polycomp0(c, keys, *a1, L.comp);
-  Ct s2 = polycomp0(c, keys, *a2, L.comp);
-  Ct b = op_mul(c, keys, *s1, *s2);
+  Ct b;
+  if (L.b0 == 1) {
+    // B_{m,0} = s_m - s_{m+1}, s_m = PolyComp(x - t_m) against every knot
+    // (block m compares with t_m): one comparison, and rot(s, n_i) brings
+    // block m + 1 to block m (no product, one level fewer); the last block
+    // is left with leftovers that the recursion's zero coefficients (or the
+    // k = 0 mask) remove
+    const uint64_t* p_g0 = cached_pt(M, li, T_G0, 0, xr->level, xr->scale, [&] {
+      std::vector<double> g0 = coltile(L, 1, r + 1);
+      for (auto& t : g0) t = -t / (2.0 * R);
+      return g0;
+    });
+    Ct a0 = op_add_pt(c, *xr, p_g0);
+    Ct s0 = polycomp0(c, keys, *a0, L.comp);
+    b = op_add(c, *s0, *op_rotate(c, keys, *s0, n_i), true);
+  } else {
+    const uint64_t* p_g1 = cached_pt(M, li, T_G1, 0, xr->level, xr->scale, [&] {
+      std::vector<double> g1 = coltile(L, 1, r);
+      for (auto& t : g1) t = -t / (2.0 * R);
+      return g1;
+    });
+    Ct a1 = op_add_pt(c, *xr, p_g1);
+    const uint64_t* p_g2 = cached_pt(M, li, T_G2, 0, xr->level, xr->scale, [&] {
+      std::vector<double> g2 = coltile(L, 2, r + 1);
+      for (auto& t : g2) t = t / (2.0 * R);
+      return g2;
+    });
+    Ct a2 = op_add_pt(c, *op_mul_int(c, *xr, -1), p_g2);
+    Ct s1 = polycomp0(c, keys, *a1, L.comp);
+    Ct s2 = polycomp0(c, keys, *a2, L.comp);
+    b = op_mul(c, keys, *s1, *s2);
+  }
   if (k == 0) {
-    // order-0 basis: outside its n_i g valid slots b holds PolyComp(0)^2 =
-    // 1/4, which the matvec's replication would fold in; zero it (1 level)
+    // order-0 basis: outside its n_i g valid slots b holds leftovers
+    // (PolyComp(0)^2 = 1/4 in the product form), which the matvec's
+    // replication would fold in; zero it (1 level)
     const double Sb = plain_scale(c, b->scale, b->level);
     const uint64_t* p_b0 = cached_pt(M, li, T_MASK_B0, 0, b->level, Sb,
                                      [&] { return std::vector<double>((size_t)n_i * G, 1.0); });
@@ -579,21 +608,21 @@ int cheb_depth(int d) {
 
 int layer_depth(const Layer& L) {
   int dc = 0;
-  for (int n : L.comp) {
-    int lg = 0;
-    while ((2 << lg) <= 2 * n) lg++;
-    dc += 1 + lg;
+  for (const auto& st : L.comp) {  // an odd polynomial of 2^K coefficients: depth K + 1
+    int K = 0;
+    while (((size_t)1 << K) < st.size()) K++;
+    dc += K + 1;
   }
-  // k = 0 masks its basis instead of a recursion step; naive adds the P matvec
-  const int spline = 3 + dc + std::max(L.k, 1) + (L.naive ? 1 : 0);
+  // mask, comparison, B0 product (not in the difference form), recursion
+  // (k = 0 masks its basis instead of a recursion step), naive P matvec, W_f
+  const int spline = 1 + dc + (L.b0 == 1 ? 0 : 1) + std::max(L.k, 1) + (L.naive ? 1 : 0) + 1;
   const int silu = 2 + cheb_depth((int)L.cheb.size() - 1);
   return std::max(spline, silu);
 }
 
 std::vector<int> layer_rotations(const Layer& L, int slots) {
   std::set<int> s;
-  int J = 0;
-  while ((1 << J) < L.G + 2 * L.k) J++;
+  const int J = rep_bits(L);
   for (int j = 1; j <= J; j++) s.insert(-L.n_c * (1 << (j - 1)));
   s.insert(L.n_c);
   const int n_s = L.n_c * (L.G + L.k);
@@ -638,13 +667,29 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
     for (size_t li = 0; li < n_layers; li++) {
       const kan_layer_desc& d = layers[li];
       if (d.n_in < 1 || d.n_out < 1 || d.G < 1 || d.k < 0 || !d.coef || !d.w_s || !d.w_b ||
-          !d.silu_cheb || d.silu_degree < 1 || !d.comp || d.n_comp < 1 || !(d.R > 0) ||
-          !(d.silu_hi > d.silu_lo) || !(d.grid_hi > d.grid_lo))
+          !d.silu_cheb || d.silu_degree < 1 || !(d.R > 0) || !(d.silu_hi > d.silu_lo) ||
+          !(d.grid_hi > d.grid_lo) || (d.b0_form != 0 && d.b0_form != 1))
         throw Error(CKKS_ERR_INVALID_ARG, "invalid layer description");
-      for (int i = 0; i < d.n_comp; i++)
-        if (d.comp[i] < 1 || d.comp[i] > 8)
-          throw Error(CKKS_ERR_INVALID_ARG, "comparison orders must be 1..8");
       Layer L;
+      if (d.n_comp_poly > 0) {
+        if (!d.comp_poly || !d.comp_poly_len)
+          throw Error(CKKS_ERR_INVALID_ARG, "comparison stages without coefficients");
+        const double* cp = d.comp_poly;
+        for (int s = 0; s < d.n_comp_poly; s++) {
+          const int n = d.comp_poly_len[s];
+          if (n < 1 || n > 32) throw Error(CKKS_ERR_INVALID_ARG, "a comparison stage needs 1..32 coefficients");
+          L.comp.emplace_back(cp, cp + n);
+          cp += n;
+        }
+      } else {
+        if (!d.comp || d.n_comp < 1) throw Error(CKKS_ERR_INVALID_ARG, "no comparison composite");
+        for (int i = 0; i < d.n_comp; i++) {
+          if (d.comp[i] < 1 || d.comp[i] > 8)
+            throw Error(CKKS_ERR_INVALID_ARG, "comparison orders must be 1..8");
+          L.comp.push_back(fn_coeffs(d.comp[i]));
+        }
+      }
+      L.b0 = d.b0_form;
       L.n_in = d.n_in;
       L.n_out = d.n_out;
       L.G = d.G;
@@ -659,12 +704,9 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
       L.w_s.assign(d.w_s, d.w_s + (size_t)d.n_out * d.n_in);
       L.w_b.assign(d.w_b, d.w_b + (size_t)d.n_out * d.n_in);
       L.cheb.assign(d.silu_cheb, d.silu_cheb + d.silu_degree + 1);
-      L.comp.assign(d.comp, d.comp + d.n_comp);
       const double h = (L.hi - L.lo) / L.G;
       for (int m = 0; m <= L.G + 2 * L.k; m++) L.knots.push_back(L.lo + (double)(m - L.k) * h);
-      int J = 0;
-      while ((1 << J) < L.G + 2 * L.k) J++;
-      const int cap = S >> J;
+      const int cap = S >> rep_bits(L);
       if (L.n_in <= cap) {
         L.K = 1;
         L.n_c = L.n_in;

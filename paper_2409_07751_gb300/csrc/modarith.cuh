@@ -70,6 +70,21 @@ __device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_
   return y * w - Q * q;
 }
 
+// The same product with the remainder formed as y w + Q (2^64 - q) mod 2^64
+// in one chain of 32-bit pieces (nq = 2^64 - q): the two widening low
+// products summed, then the four cross products added to the high word.
+__device__ __forceinline__ uint64_t shoup_approx_nq(uint64_t y, uint64_t w, uint64_t ws, uint64_t nq) {
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  const uint32_t s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
+  const uint64_t Q = (uint64_t)y1 * s1 + __umulhi(y1, s0) + __umulhi(y0, s1);
+  const uint32_t Q0 = (uint32_t)Q, Q1 = (uint32_t)(Q >> 32);
+  const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+  const uint32_t n0 = (uint32_t)nq, n1 = (uint32_t)(nq >> 32);
+  const uint64_t lo = (uint64_t)y0 * w0 + (uint64_t)Q0 * n0;
+  const uint32_t hi = (uint32_t)(lo >> 32) + y0 * w1 + y1 * w0 + Q0 * n1 + Q1 * n0;
+  return ((uint64_t)hi << 32) | (uint32_t)lo;
+}
+
 // Forward butterfly without the reduction of x, for moduli q < 2^50: with
 // t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
 // from inputs below q stay below 65q < 2^57.

@@ -3,14 +3,16 @@ of encrypted KAN outputs at the configurations' full sizes, computed by the
 oracle alone (test infrastructure; nothing here touches the CUDA library).
 
 Cases (N = 2^16, q0 + 36 x 40-bit primes; seeds of the workloads module):
-  c2  [4,8,4,1], G=5, k=3, SiLU degree 27, comparison f_3, digit layout
-      alpha = 5 with 48-bit special primes (the batched bench's layout):
-      the whole three-layer inference of input 0 at level 36;
-  c3  [784,64,10], G=5, k=3 on the 28x28 blob images, SiLU degree 15,
-      comparison f_3^4, alpha = 4: layer 0 of image 0 (BSGS over n' = 8192);
-  c4  [3072,64,10], G=10, k=3 on the 3x32x32 images, SiLU degree 15,
-      comparison f_3^4, alpha = 4: layer 0 of image 0, split into two
-      ciphertexts of 2048 inputs (BSGS over n' = 32768, chunk sum).
+  c2     [4,8,4,1], G=5, k=3, SiLU degree 27, the minimax comparison of
+         degrees 7 and 15 (eps 0.12) in the difference form of B_{m,0}, digit
+         layout alpha = 5 with 48-bit special primes (the batched bench's
+         configuration): the whole three-layer inference of input 0 at level 36;
+  c2_f3  the same network with comparison f_3 in the product form;
+  c3     [784,64,10], G=5, k=3 on the 28x28 blob images, SiLU degree 15,
+         comparison f_3^4, alpha = 4: layer 0 of image 0 (BSGS over n' = 8192);
+  c4     [3072,64,10], G=10, k=3 on the 3x32x32 images, SiLU degree 15,
+         comparison f_3^4, alpha = 4: layer 0 of image 0, split into two
+         ciphertexts of 2048 inputs (BSGS over n' = 32768, chunk sum).
 
 Each case also stores a digest of the calibrated model (every array and
 parameter both sides are given), so a test can tell that it rebuilt the
@@ -31,7 +33,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from oracle import calibrate, ckks as O, kan_he  # noqa: E402
+from oracle import calibrate, ckks as O, kan_he, polycomp  # noqa: E402
 from paper_2409_07751_gb300 import workloads as W  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fullsize_digests.json")
@@ -40,6 +42,12 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fullsize_digests
 def case_setup(name):
     """(params kwargs, calibrated model, input rows, input level, scope)."""
     if name == "c2":
+        model = [dict(L, b0="difference") for L in W.make_model("kan_4_8_4_1")]
+        Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
+        m = calibrate.calibrate(model, Xcal, 27, polycomp.composite(0.12, (7, 15))[0])
+        x = W.uniform_inputs(64, 4, seed=W.SEED_INPUTS)[:1]
+        return dict(log_n=16, n_scale=36, n_special=5, p_bits=48), m, x, 36, "network"
+    if name == "c2_f3":
         model = W.make_model("kan_4_8_4_1")
         Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
         m = calibrate.calibrate(model, Xcal, 27, [3])
@@ -68,7 +76,13 @@ def model_digest(m):
             h.update(np.float64(L[key]).tobytes())
         for key in ("coef", "w_s", "w_b", "silu_cheb"):
             h.update(np.ascontiguousarray(L[key], dtype=np.float64).tobytes())
-        h.update(np.asarray(L["comp"], dtype=np.int64).tobytes())
+        comp = L["comp"]
+        if all(isinstance(st, (int, np.integer)) for st in comp):
+            h.update(np.asarray(comp, dtype=np.int64).tobytes())
+        else:
+            for st in comp:
+                h.update(np.asarray([len(st)], dtype=np.int64).tobytes())
+                h.update(np.ascontiguousarray(st, dtype=np.float64).tobytes())
         h.update(str(L.get("b0", "product")).encode())
     return h.hexdigest()
 
@@ -139,4 +153,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["c2", "c3", "c4"])
+    main(sys.argv[1:] or ["c2", "c2_f3", "c3", "c4"])

@@ -41,13 +41,24 @@ def test_binding_signatures_cover_the_header():
     assert declared() <= set(ckks.SIGNATURES)
 
 
-def test_model_descriptor_rejects_unsupported_b0_form():
-    """Layers asking for the difference form of the order-0 basis are
-    refused by the binding instead of being evaluated in another form."""
+def test_model_descriptor_b0_forms_and_stages():
+    """Both forms of the order-0 basis (Algorithm 2's product, the difference
+    of knot comparisons) marshal; another form, or a composite mixing f_n
+    orders with coefficient lists, is refused."""
+    import numpy as np
     import pytest
     from paper_2409_07751_gb300 import ckks, workloads as W
     m = W.make_model("t", widths=[3, 2], G=3, k=2)
-    ckks._descs(m, [])  # the product form builds
+    d = ckks._descs(m, [])
+    assert d[0].b0_form == 0 and d[0].n_comp_poly == 0
     m[0]["b0"] = "difference"
+    m[0]["comp"] = [np.array([1.5, -0.5]), np.array([2.0])]
+    d = ckks._descs(m, [])
+    assert d[0].b0_form == 1 and d[0].n_comp_poly == 2
+    m[0]["b0"] = "ratio"
+    with pytest.raises(ValueError):
+        ckks._descs(m, [])
+    m[0]["b0"] = "product"
+    m[0]["comp"] = [3, np.array([1.0])]
     with pytest.raises(ValueError):
         ckks._descs(m, [])

@@ -205,3 +205,57 @@ def test_kan_4_8_4_1_batched_uneven_levels(G):
     dec = G.decrypt(gctx, gk, gout, 1)
     hef = kan_plain.forward(m, x, "poly", "poly")
     assert np.abs(dec - hef).max() < 1e-4
+
+
+@pytest.mark.parametrize("b0,G_,k_", [("difference", 3, 2), ("product", 3, 2), ("difference", 4, 0),
+                                      ("difference", 2, 1)])
+def test_minimax_composite_and_b0_forms_bit_exact(G, b0, G_, k_):
+    """PolyComp by a minimax composite (degree 7 then 15, eps = 0.1) and
+    either order-0 form of Algorithm 2: one layer and the whole network equal
+    the oracle word for word; the difference form is one level shallower per
+    layer; decryptions match the HE-friendly FP64 KAN."""
+    from oracle import polycomp
+    stages, _ = polycomp.composite(0.1, (7, 15))
+    model = [dict(L, b0=b0) for L in W.make_model("t", widths=[3, 5, 2], G=G_, k=k_)]
+    X = W.uniform_inputs(64, 3)
+    m = calibrate.calibrate(model, X, 7, stages)
+    gctx, octx, gm, gk, ok = _setup(G, 7, 26, 2, m)
+    prod = G.Model(gctx, [dict(L, b0="product") for L in m])
+    for li in range(len(m)):
+        assert gm.layer_depth(li) == prod.layer_depth(li) - (1 if b0 == "difference" else 0)
+    oc = O.encrypt(octx, ok, X[0], octx.L, W.SEED_ENC, 0)
+    gc = G.Ciphertext.import_(gctx, oc.data, oc.level, oc.scale)
+    o1 = kan_he.layer_eval(octx, ok, oc, m[0])
+    g1 = G.kan_layer_eval(gctx, gk, gm, 0, gc)
+    assert g1.level == o1.level and g1.scale == o1.scale
+    assert (g1.export()[0] == o1.data).all()
+    gin = G.encrypt(gctx, gk, X[:2], octx.L, W.SEED_ENC, 0)
+    gout = G.kan_infer(gctx, gk, gm, [gin])
+    for b in range(2):
+        oo = kan_he.infer(octx, ok, O.encrypt(octx, ok, X[b], octx.L, W.SEED_ENC, b), m)
+        assert (gout.export()[b] == oo.data).all()
+    hef = kan_plain.forward(m, X[:2], "poly", "poly")
+    assert np.abs(G.decrypt(gctx, gk, gout, 2) - hef).max() < 1e-5
+
+
+def test_mixed_level_batch_equals_each_alone(G):
+    """kan_infer on inputs at four different levels (one handle each): the
+    batch is brought to the lowest level and run together; every output
+    equals, word for word, that input brought down to the same level
+    (ckks_level_down) and run alone, and equals the oracle."""
+    model = W.make_model("t", widths=[3, 5, 2], G=3, k=2)
+    X = W.uniform_inputs(64, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    gctx, octx, gm, gk, ok = _setup(G, 7, 20, 2, m)
+    levels = [20, 19, 17, 16]
+    cts = [G.encrypt(gctx, gk, X[b], lv, W.SEED_ENC, b) for b, lv in enumerate(levels)]
+    out = G.kan_infer(gctx, gk, gm, cts)
+    assert out.batch == 4
+    got = out.export()
+    low = min(levels)
+    for b, ct in enumerate(cts):
+        alone = G.kan_infer(gctx, gk, gm, [G.level_down(gctx, ct, low)])
+        assert alone.level == out.level
+        assert (alone.export()[0] == got[b]).all(), b
+        oc = O.level_down(octx, O.encrypt(octx, ok, X[b], levels[b], W.SEED_ENC, b), low)
+        assert (got[b] == kan_he.infer(octx, ok, oc, m).data).all(), b

@@ -4,7 +4,7 @@ comparison bound R, and the plaintext forward pass it runs on."""
 import numpy as np
 import pytest
 
-from oracle import calibrate as OC, silu_fit as OF
+from oracle import calibrate as OC, polycomp as OP, silu_fit as OF
 from paper_2409_07751_gb300 import workloads as W
 
 
@@ -62,3 +62,40 @@ def test_fit_methods_error_split(G):
     assert out["remez"][1] <= min(out["wls"][1], out["ols"][1]) * 1.0001
     assert out["ols"][0] <= min(out["wls"][0], out["remez"][0]) * 1.0001
     assert out["wls"][2] <= min(out["ols"][2], out["remez"][2])
+
+
+@pytest.mark.parametrize("eps,degs", [(0.1, (7, 15)), (0.15, (7, 7)), (0.02, (7, 7, 7, 7)),
+                                      (0.02, (7, 15, 15)), (0.3, (15,)), (0.2, (1, 3))])
+def test_comp_minimax_matches_oracle(G, eps, degs):
+    """The library's composite minimax design (kan_comp_minimax) against the
+    oracle's (pinned by closed form, LP and equioscillation): the same
+    stages and the same propagated errors."""
+    g, gt = G.comp_minimax(eps, degs)
+    o, ot = OP.composite(eps, degs)
+    # a last stage on a tiny interval has ill-conditioned coefficients, so
+    # the composites are compared by value (and each stage loosely)
+    for gs, os_ in zip(g, o):
+        assert np.abs(gs - np.array(os_)).max() <= 1e-7 * max(1.0, np.abs(os_).max())
+    a = np.linspace(-OP.A_DEFAULT, OP.A_DEFAULT, 200001)
+    ug, uo = a, a
+    for gs, os_ in zip(g, o):
+        ug, uo = OP.eval_odd(ug, gs), OP.eval_odd(uo, os_)
+    assert np.abs(ug - uo).max() < 1e-9
+    assert np.allclose(gt, ot, rtol=1e-3, atol=1e-13)
+
+
+@pytest.mark.parametrize("b0", ["product", "difference"])
+def test_calibrate_with_minimax_stages_matches_oracle(G, b0):
+    """kan_calibrate's HE-friendly forward with explicit composite stages and
+    either order-0 form gives the oracle's statistics, ranges and fits."""
+    stages, _ = OP.composite(0.1, (7, 15))
+    model = [dict(L, b0=b0) for L in W.make_model("kan_4_8_4_1")]
+    X = W.uniform_inputs(200, 4)
+    g = G.calibrate(model, X, 15, stages, n_fit_samples=3000)
+    o = OC.calibrate(model, X, 15, stages, n_samples=3000)
+    for gl, ol in zip(g, o):
+        assert gl["b0"] == ol["b0"] == b0
+        assert abs(gl["R"] - ol["R"]) < 1e-12 * ol["R"]
+        assert abs(gl["silu_lo"] - ol["silu_lo"]) < 1e-12
+        assert abs(gl["silu_hi"] - ol["silu_hi"]) < 1e-12
+        assert np.abs(gl["silu_cheb"] - ol["silu_cheb"]).max() < 1e-8
