@@ -14,9 +14,14 @@ Cases (N = 2^16, q0 + 36 x 40-bit primes; seeds of the workloads module):
          comparison f_3^4, alpha = 4: layer 0 of image 0, split into two
          ciphertexts of 2048 inputs (BSGS over n' = 32768, chunk sum).
 
-Each case also stores a digest of the calibrated model (every array and
-parameter both sides are given), so a test can tell that it rebuilt the
-same model. Run: python tests/golden/make_fullsize_digests.py [case ...]
+Each case also stores what the oracle calibrated (per layer R, the SiLU
+range and Chebyshev coefficients, the comparison stages), the encrypted input
+rows, a digest of the seeded weights and a digest of the whole model: the
+calibration's least squares, statistics and minimax design round differently
+on other machines (LAPACK, libm), so a test rebuilds the model from the
+seeded weights and these stored values rather than recalibrating. `--describe`
+adds these fields to the cases already in the file without rerunning them
+(the model digest proves the stored values are the digested model's). Run: python tests/golden/make_fullsize_digests.py [case ...]
 (the oracle needs tens of minutes per case; cases run in parallel
 processes). The Galois keys are generated when a rotation first needs them
 and only a few are kept, so a case fits in a few GB of host memory.
@@ -39,29 +44,31 @@ from paper_2409_07751_gb300 import workloads as W  # noqa: E402
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fullsize_digests.json")
 
 
-def case_setup(name):
-    """(params kwargs, calibrated model, input rows, input level, scope)."""
+def case_setup(name, calibrate_model=True):
+    """(params kwargs, calibrated model, input rows, input level, scope);
+    calibrate_model=False returns the seeded model uncalibrated."""
+    cal = calibrate.calibrate if calibrate_model else (lambda model, *a, **k: [dict(L) for L in model])
     if name == "c2":
         model = [dict(L, b0="difference") for L in W.make_model("kan_4_8_4_1")]
         Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
-        m = calibrate.calibrate(model, Xcal, 27, polycomp.composite(0.12, (7, 15))[0])
+        m = cal(model, Xcal, 27, polycomp.composite(0.12, (7, 15))[0])
         x = W.uniform_inputs(64, 4, seed=W.SEED_INPUTS)[:1]
         return dict(log_n=16, n_scale=36, n_special=5, p_bits=48), m, x, 36, "network"
     if name == "c2_f3":
         model = W.make_model("kan_4_8_4_1")
         Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
-        m = calibrate.calibrate(model, Xcal, 27, [3])
+        m = cal(model, Xcal, 27, [3])
         x = W.uniform_inputs(64, 4, seed=W.SEED_INPUTS)[:1]
         return dict(log_n=16, n_scale=36, n_special=5, p_bits=48), m, x, 36, "network"
     if name == "c3":
         model = W.make_model("kan_784_64_10")
         X = W.blob_images(66)
-        m = calibrate.calibrate(model, X[2:], 15, [3, 3, 3, 3])
+        m = cal(model, X[2:], 15, [3, 3, 3, 3])
         return dict(log_n=16, n_scale=36, n_special=4), m, X[:1], 36, "layer0"
     if name == "c4":
         model = W.make_model("kan_3072_64_10")
         X = W.cifar_like_images(34)
-        m = calibrate.calibrate(model, X[2:], 15, [3, 3, 3, 3])
+        m = cal(model, X[2:], 15, [3, 3, 3, 3])
         K, n_c = 2, 2048
         xp = np.pad(X[0], (0, K * n_c - 3072))
         return (dict(log_n=16, n_scale=36, n_special=4), m,
@@ -85,6 +92,40 @@ def model_digest(m):
                 h.update(np.ascontiguousarray(st, dtype=np.float64).tobytes())
         h.update(str(L.get("b0", "product")).encode())
     return h.hexdigest()
+
+
+def weights_digest(m):
+    h = hashlib.sha256()
+    for L in m:
+        for key in ("coef", "w_s", "w_b"):
+            h.update(np.ascontiguousarray(L[key], dtype=np.float64).tobytes())
+    return h.hexdigest()
+
+
+def describe(name):
+    """The stored values a test needs to rebuild case `name` exactly."""
+    params, m, x, level, scope = case_setup(name)
+    layers = []
+    for L in m:
+        comp = L["comp"]
+        layers.append(dict(
+            R=float(L["R"]), silu_lo=float(L["silu_lo"]), silu_hi=float(L["silu_hi"]),
+            silu_cheb=[float(v) for v in L["silu_cheb"]], b0=L.get("b0", "product"),
+            comp=[int(st) if isinstance(st, (int, np.integer)) else [float(v) for v in st]
+                  for st in comp]))
+    return dict(calibration=layers, inputs=[[float(v) for v in row] for row in np.asarray(x)],
+                weights_sha256=weights_digest(m), model_sha256=model_digest(m))
+
+
+def rebuild(name, stored):
+    """(params, model, input rows, level, scope) from the seeded weights and
+    the stored calibration; the caller checks the digests."""
+    params, m, x, level, scope = case_setup(name, calibrate_model=False)
+    for L, c in zip(m, stored["calibration"]):
+        L.update(R=c["R"], silu_lo=c["silu_lo"], silu_hi=c["silu_hi"],
+                 silu_cheb=np.array(c["silu_cheb"]), b0=c["b0"],
+                 comp=[st if isinstance(st, int) else list(st) for st in c["comp"]])
+    return params, m, np.array(stored["inputs"]), level, scope
 
 
 def limb_digests(data):
@@ -133,8 +174,8 @@ def run_case(name):
         out = kan_he.layer_eval_chunked(ctx, keys, cts, m[0])
     return name, dict(
         params=params, scope=scope, input_level=level, n_input_cts=len(cts),
-        model_sha256=model_digest(m), level=out.level, scale=out.scale,
-        limbs=limb_digests(out.data), oracle_seconds=round(time.time() - t0, 1))
+        level=out.level, scale=out.scale, limbs=limb_digests(out.data),
+        oracle_seconds=round(time.time() - t0, 1), **describe(name))
 
 
 def main(names):
@@ -152,5 +193,21 @@ def main(names):
                 f.write("\n")
 
 
+def main_describe():
+    with open(OUT) as f:
+        res = json.load(f)
+    for name, r in res.items():
+        d = describe(name)
+        if d["model_sha256"] != r["model_sha256"]:
+            raise SystemExit("%s: this machine calibrates another model than the digested one" % name)
+        r.update(d)
+    with open(OUT, "w") as f:
+        json.dump(res, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["c2", "c2_f3", "c3", "c4"])
+    if sys.argv[1:] == ["--describe"]:
+        main_describe()
+    else:
+        main(sys.argv[1:] or ["c2", "c2_f3", "c3", "c4"])

@@ -12,8 +12,11 @@ words are stored as digests). Cases:
   c4  [3072,64,10]: layer 0 in two ciphertexts of 2048 inputs, BSGS over
       n' = 32768 and the chunk sum.
 
-Both sides get the same calibrated model (checked by its digest), the same
-keys (seed 1) and the same encryptions (seed 2, index = chunk)."""
+Both sides get the same model: the seeded weights (checked by their digest)
+with the calibration the oracle computed, stored beside the digests (a
+calibration rerun on another machine rounds differently), checked by the
+whole model's digest; the same input rows, keys (seed 1) and encryptions
+(seed 2, index = chunk)."""
 import json
 import os
 import sys
@@ -42,8 +45,9 @@ def G():
 @pytest.mark.parametrize("name", ["c2", "c2_f3", "c3", "c4"])
 def test_fullsize_output_words_match_oracle_digests(G, name):
     ref = GOLDEN[name]
-    params, m, x, level, scope = D.case_setup(name)
+    params, m, x, level, scope = D.rebuild(name, ref)
     assert params == ref["params"] and scope == ref["scope"] and level == ref["input_level"]
+    assert D.weights_digest(m) == ref["weights_sha256"], "the seeded weights differ on this machine"
     assert D.model_digest(m) == ref["model_sha256"]
     ctx = G.Context(params["log_n"], params["n_scale"], params["n_special"],
                     p_bits=params.get("p_bits", 60))
