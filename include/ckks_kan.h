@@ -138,6 +138,20 @@ int ckks_profile_collect2(ckks_ctx* ctx, double* ms, double* bytes, double* modm
  * several launches of SMs x resident-blocks CTAs on the context's stream. */
 int ckks_int_peak(ckks_ctx* ctx, int kind, double* per_s);
 
+/* NTT launch shape (the paper has no counterpart; an implementation
+ * choice of the transforms): the clustered 2^15- and 2^16-point transforms
+ * run at 2 CTAs per SM (64 registers per thread) or 1 (up to 128), per slot:
+ * 0 plain forward, 1 ModUp, 2 ModDown, 3 rescale, 4 HMult's merged
+ * relinearise-rescale division, 5 inverse. ckks_autotune_ntt times a batch
+ * of `batch` ciphertexts at the top level (HMult, HRot, a constant product,
+ * a rescale, a plain forward transform) under both settings with per-launch
+ * CUDA events and keeps the faster per slot on the context (results are the
+ * same words either way); ms[0..5] are the slots' times at 2 CTAs per SM,
+ * ms[6..11] at 1, chosen[0..5] the kept setting (either may be NULL). Other
+ * ring sizes keep 2. ckks_set_ntt_shape sets one slot. */
+int ckks_autotune_ntt(ckks_ctx* ctx, int batch, double* ms, int* chosen);
+int ckks_set_ntt_shape(ckks_ctx* ctx, int slot, int ctas_per_sm);
+
 /* ------------------------------------------------------------ keys
  * Secret-key generation from `seed` (ternary secret, ChaCha20 stream), the
  * relinearisation key, and one Galois key per rotation step in rot_steps
@@ -278,6 +292,12 @@ typedef struct {
    * comparisons since PolyComp(-a) = 1 - PolyComp(a) for an odd composite.
    * Algorithm 1 then packs 2^ceil(log2(g + 2k + 1)) copies. */
   int b0_form;
+  /* Matvec form (the Lazy combination section's BSGS): 0 = baby-step
+   * rotations hoisted (one ModUp, a ModDown each); 1 = double hoisting: the
+   * baby steps stay in QP_l, the diagonal products of a giant step are summed
+   * over QP_l and divided by P q_l once (ModDown and rescale in one rounded
+   * division). Not for a chunked first layer (UNSUPPORTED). */
+  int bsgs_form;
 } kan_layer_desc;
 
 /* PolyComp by composite minimax polynomials (Algorithm 2 cites Lee et al.'s

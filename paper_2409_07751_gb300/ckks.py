@@ -27,7 +27,7 @@ class KanLayerDesc(ctypes.Structure):
                 ("silu_cheb", c_vp), ("silu_degree", c_i32),
                 ("comp", c_vp), ("n_comp", c_i32), ("naive", c_i32),
                 ("comp_poly", c_vp), ("comp_poly_len", c_vp), ("n_comp_poly", c_i32),
-                ("b0_form", c_i32)]
+                ("b0_form", c_i32), ("bsgs_form", c_i32)]
 
 
 SIGNATURES = {
@@ -50,6 +50,8 @@ SIGNATURES = {
     "ckks_profile_collect": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32]),
     "ckks_profile_collect2": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32]),
     "ckks_int_peak": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_dbl)]),
+    "ckks_autotune_ntt": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
+    "ckks_set_ntt_shape": (c_i32, [c_vp, c_i32, c_i32]),
     "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
@@ -202,6 +204,20 @@ class Context:
         v = c_dbl()
         check(lib().ckks_int_peak(self.h, int(kind), ctypes.byref(v)))
         return v.value
+
+    NTT_SLOTS = ("forward", "modup", "moddown", "rescale", "relin_rescale", "inverse")
+
+    def autotune_ntt(self, batch=8):
+        """CTAs per SM of each NTT slot chosen by measurement: ({slot: chosen},
+        {slot: (ms at 2 CTAs/SM, ms at 1)})."""
+        ms = np.zeros(12)
+        ch = np.zeros(6, np.int32)
+        check(lib().ckks_autotune_ntt(self.h, int(batch), _p(ms), _p(ch)))
+        return ({n: int(ch[i]) for i, n in enumerate(self.NTT_SLOTS)},
+                {n: (float(ms[i]), float(ms[6 + i])) for i, n in enumerate(self.NTT_SLOTS)})
+
+    def set_ntt_shape(self, slot, ctas_per_sm):
+        check(lib().ckks_set_ntt_shape(self.h, self.NTT_SLOTS.index(slot), int(ctas_per_sm)))
 
     def profile_collect(self):
         """{kind: (ms, algorithmic bytes, launches, modular multiplications)}
@@ -415,10 +431,15 @@ def _descs(layers, keep):
         d.comp_poly, d.comp_poly_len = _p(poly), _p(plen)
         d.n_comp_poly = 0 if poly is None else len(plen)
         d.b0_form = B0_FORMS[b0]
+        bsgs = L.get("bsgs", "single")
+        if bsgs not in BSGS_FORMS:
+            raise ValueError("bsgs must be 'single' or 'double', not %r" % (bsgs,))
+        d.bsgs_form = BSGS_FORMS[bsgs]
     return descs
 
 
 B0_FORMS = {"product": 0, "difference": 1}
+BSGS_FORMS = {"single": 0, "double": 1}
 
 
 def comp_minimax(eps, degrees, A=1.0):

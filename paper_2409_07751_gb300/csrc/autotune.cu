@@ -77,4 +77,76 @@ int ckks_autotune_keyswitch(int log_n, int q0_bits, int scale_bits, int n_scale,
   }
 }
 
+// NTT launch shape chosen by measurement: the clustered transforms run at
+// two CTAs per SM (64 registers per thread, 32 warps) or one (up to 128
+// registers: no spills in the fused descriptors, but half the warps). Each
+// descriptor kind is a slot; the workload (HMult, HRot, a constant product,
+// a rescale and a plain forward transform of a batch at the top level) runs
+// with every slot at one setting, then at the other, with per-launch CUDA
+// events; each slot keeps the faster. ms: [2][NTT_SLOT_COUNT] (row 0: two
+// CTAs per SM, row 1: one), chosen: [NTT_SLOT_COUNT].
+int ckks_autotune_ntt(ckks_ctx* ctx, int batch, double* ms, int* chosen) {
+  try {
+    if (!ctx || batch < 1) return CKKS_ERR_INVALID_ARG;
+    Ctx& c = ctx->c;
+    if (c.log_n < 15 || c.L < 2) {  // only the 2^15 and 2^16 transforms have both shapes
+      for (int s = 0; s < NTT_SLOT_COUNT; s++) {
+        if (chosen) chosen[s] = c.ntt_minb[s];
+      }
+      return CKKS_OK;
+    }
+    std::unique_ptr<ckks_keys> keys = keygen(c, 1, {1});
+    std::vector<double> v((size_t)batch * (c.N / 2), 0.25);
+    Ct x = encrypt(c, *keys, v.data(), (size_t)batch, c.N / 2, c.L, 2, 0);
+    const size_t rows = (size_t)batch * 2 * (c.L + 1);
+    DevBuf buf(&c, rows * c.N * 8);
+    CK_CUDA(cudaMemsetAsync(buf.p, 0, buf.bytes, c.stream));
+    auto work = [&]() {
+      op_mul(c, *keys, *x, *x);
+      op_rotate(c, *keys, *x, 1);
+      op_mul_const(c, *x, 0.5);
+      op_rescale(c, *x);
+      ntt_forward(c, buf.u64(), rows, c.iota(), c.L + 1);
+    };
+    static const int slot_of_kind[][2] = {{K_NTT_FWD, NTT_SLOT_FWD}, {K_MODUP_NTT, NTT_SLOT_MODUP},
+                                          {K_MODDOWN_NTT, NTT_SLOT_MODDOWN},
+                                          {K_RESCALE_NTT, NTT_SLOT_RESCALE},
+                                          {K_RR_NTT, NTT_SLOT_RELIN_RESCALE},
+                                          {K_NTT_INV, NTT_SLOT_INV}};
+    double t[2][NTT_SLOT_COUNT] = {};
+    const bool prof = c.prof;
+    for (int setting = 0; setting < 2; setting++) {
+      for (int s = 0; s < NTT_SLOT_COUNT; s++) c.ntt_minb[s] = setting == 0 ? 2 : 1;
+      work();  // warm-up (tables, attributes)
+      std::vector<double> k_ms(K_KIND_COUNT, 0.0);
+      CK_CUDA(cudaStreamSynchronize(c.stream));
+      ckks_profile_collect2(ctx, k_ms.data(), nullptr, nullptr, nullptr, K_KIND_COUNT);
+      c.prof = true;
+      for (int r = 0; r < 3; r++) work();
+      ckks_profile_collect2(ctx, k_ms.data(), nullptr, nullptr, nullptr, K_KIND_COUNT);
+      c.prof = prof;
+      for (auto& m : slot_of_kind) t[setting][m[1]] = k_ms[m[0]] / 3.0;
+    }
+    for (int s = 0; s < NTT_SLOT_COUNT; s++) {
+      c.ntt_minb[s] = t[1][s] < t[0][s] ? 1 : 2;
+      if (chosen) chosen[s] = c.ntt_minb[s];
+      if (ms) {
+        ms[s] = t[0][s];
+        ms[NTT_SLOT_COUNT + s] = t[1][s];
+      }
+    }
+    CK_CUDA(cudaStreamSynchronize(c.stream));
+    return CKKS_OK;
+  } catch (...) {
+    return api_error();
+  }
+}
+
+int ckks_set_ntt_shape(ckks_ctx* ctx, int slot, int ctas_per_sm) {
+  if (!ctx || slot < 0 || slot >= NTT_SLOT_COUNT || (ctas_per_sm != 1 && ctas_per_sm != 2))
+    return CKKS_ERR_INVALID_ARG;
+  ctx->c.ntt_minb[slot] = ctas_per_sm;
+  return CKKS_OK;
+}
+
 }  // extern "C"

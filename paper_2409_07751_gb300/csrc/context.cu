@@ -425,6 +425,9 @@ ConvTables& Ctx::tables(int level) {
   T->dhw_s = upload(this, dhws);
   T->ext_pattern = upload(this, pat);
   T->pq_pattern = upload(this, pq);
+  std::vector<int16_t> qp(rows);
+  for (int r = 0; r < rows; r++) qp[r] = (int16_t)row_mod(r);
+  T->qp_pattern = upload(this, qp);
   T->md_pinv = upload(this, pinv);
   T->md_pinv_s = upload(this, pinvs);
   std::vector<uint64_t> xp(l), xps(l), mp(rows, 0), mps(rows, 0);

@@ -46,6 +46,47 @@ __global__ void mul_pt_acc_kernel(const uint64_t* a, const uint64_t* pt, uint64_
   }
 }
 
+// QP_l rows (double-hoisted BSGS): row t of every polynomial uses modulus
+// pat[t]; acc = (first ? 0 : acc) + a * pt
+__global__ void qp_mul_pt_acc_kernel(const uint64_t* a, const uint64_t* pt, uint64_t* acc,
+                                     size_t total, int log_n, DivU32 rows, const int16_t* pat,
+                                     const Mod* mods, bool first) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, total) {
+    const int t = (int)umod((uint32_t)(i >> log_n), rows);
+    const Mod& m = mods[pat[t]];
+    const uint64_t v = mul_mod(a[i], pt[(size_t)t * N + (i & (N - 1))], m);
+    acc[i] = first ? v : add_mod(acc[i], v, m.q);
+  }
+}
+
+// A rotation kept in QP_l: on the Q rows t < l of polynomial 0,
+// R += P sigma(c0) (sigma by the NTT-domain permutation perm); the key
+// product already in R. identity (perm null): R_k = P c_k on the Q rows and
+// 0 on the special primes, for both polynomials.
+__global__ void qp_lift_kernel(const uint64_t* ct, uint64_t* R, const uint32_t* perm, size_t B,
+                               int log_n, int l, int rows, const uint64_t* pq,
+                               const uint64_t* pqs, const Mod* mods) {
+  const size_t N = (size_t)1 << log_n;
+  const int polys = perm ? 1 : 2;
+  GRID_LOOP(i, B * polys * rows * N) {
+    const size_t n = i & (N - 1);
+    const size_t row = i >> log_n;
+    const int t = (int)(row % rows);
+    const size_t bk = row / rows;
+    const size_t b = bk / polys, k = bk % polys;
+    uint64_t* o = R + ((b * 2 + k) * rows + t) * N + n;
+    if (t >= l) {
+      if (!perm) *o = 0;
+      continue;
+    }
+    const uint64_t q = mods[t].q;
+    const uint64_t* src = ct + ((b * 2 + k) * l + t) * N;
+    const uint64_t v = mul_shoup(src[perm ? perm[n] : n], pq[t], pqs[t], q);
+    *o = perm ? add_mod(*o, v, q) : v;
+  }
+}
+
 constexpr int LC_TERMS = 16;
 struct LincombRes {
   uint64_t v[LC_TERMS][MAX_LIMBS];
@@ -288,6 +329,27 @@ void k_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, 
   Launch L_(c, K_MUL_PT, 3.0 * total * 8, (double)total);
   mul_pt_acc_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, pt, acc, total, c.log_n, divu(l),
                                                            c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_qp_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, size_t polys,
+                     int level, bool first) {
+  ConvTables& T = c.tables(level);
+  const size_t total = polys * T.rows * c.N;
+  Launch L_(c, K_MUL_PT, (first ? 2.0 : 3.0) * total * 8, (double)total);
+  qp_mul_pt_acc_kernel<<<grid_for(total), TPB, 0, c.stream>>>(
+      a, pt, acc, total, c.log_n, divu(T.rows), static_cast<const int16_t*>(T.qp_pattern.p),
+      c.dmod(), first);
+  CK_CUDA(cudaGetLastError());
+}
+
+void k_qp_lift(Ctx& c, const uint64_t* ct, size_t B, int level, const uint32_t* perm, uint64_t* R) {
+  ConvTables& T = c.tables(level);
+  const int l = T.l;
+  const size_t total = B * (perm ? 1 : 2) * T.rows * c.N;
+  Launch L_(c, K_ROT_FINISH, (perm ? 3.0 : 2.0) * total * 8);
+  qp_lift_kernel<<<grid_for(total), TPB, 0, c.stream>>>(ct, R, perm, B, c.log_n, l, T.rows,
+                                                        T.md_pq.u64(), T.md_pq_s.u64(), c.dmod());
   CK_CUDA(cudaGetLastError());
 }
 

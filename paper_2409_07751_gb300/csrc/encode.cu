@@ -124,6 +124,11 @@ void run_stages(Ctx& c, double* xr, double* xi, size_t B, int sign) {
 }  // namespace
 
 int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double scale, uint64_t* pt) {
+  return encode_rows(c, d_v, B, nv, level + 1, c.iota(), scale, pt);
+}
+
+int encode_rows(Ctx& c, const double* d_v, size_t B, size_t nv, int rows, const int16_t* pattern,
+                double scale, uint64_t* pt) {
   const size_t n = c.N / 2;
   if (nv > n) throw Error(CKKS_ERR_INVALID_ARG, "more values than slots");
   DevBuf xr(&c, B * n * 8), xi(&c, B * n * 8), coef(&c, B * c.N * 8);
@@ -144,9 +149,8 @@ int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double sca
       c.log_n, static_cast<const double*>(c.d_fft.p), f, static_cast<int*>(c.d_flag.p));
   CK_CUDA(cudaGetLastError());
   }
-  const int l = level + 1;
-  k_int_to_rns(c, static_cast<int64_t*>(coef.p), pt, B, l, c.iota());
-  ntt_forward(c, pt, B * l, c.iota(), l);
+  k_int_to_rns(c, static_cast<int64_t*>(coef.p), pt, B, rows, pattern);
+  ntt_forward(c, pt, B * rows, pattern, rows);
   int flag = 0;
   CK_CUDA(cudaMemcpyAsync(&flag, c.d_flag.p, 4, cudaMemcpyDeviceToHost, c.stream));
   CK_CUDA(cudaStreamSynchronize(c.stream));

@@ -62,6 +62,7 @@ struct ConvTables {
   DevBuf dhw, dhw_s;       // [beta][alpha][rows]: dh times psi^(N/2) of the row's modulus
   DevBuf ext_pattern;      // int16 [beta*rows]: modulus index of the row, -1 = digit row
   DevBuf pq_pattern;       // int16 [rows]: -1 for Q rows, special modulus for P rows
+  DevBuf qp_pattern;       // int16 [rows]: the modulus of every QP_l row (Q limbs, then P)
   DevBuf md_pinv, md_pinv_s;  // [l]: P^-1 mod q_i
   DevBuf xs_post, xs_post_s;  // [l]: N^-1 Dhat_i^-1 mod q_i (fused ModUp)
   DevBuf md_post, md_post_s;  // [rows]: N^-1 Phat_a^-1 mod p_a on P rows (fused ModDown)
@@ -91,6 +92,12 @@ enum KernelKind {
 };
 const char* kernel_kind_name(int k);
 
+// NTT tuning slots: the clustered transform kernels per descriptor kind
+enum NttSlot {
+  NTT_SLOT_FWD, NTT_SLOT_MODUP, NTT_SLOT_MODDOWN, NTT_SLOT_RESCALE, NTT_SLOT_RELIN_RESCALE,
+  NTT_SLOT_INV, NTT_SLOT_COUNT
+};
+
 struct ProfRec {
   int kind;
   double bytes;
@@ -108,6 +115,8 @@ struct Ctx {
   // fused NTT kernels (basis conversion / rescale inside the transforms'
   // loads and stores); off = separate conversion and transform launches
   bool fused = true;
+  // CTAs per SM of the clustered transforms, per tuning slot (1 or 2)
+  int ntt_minb[NTT_SLOT_COUNT] = {2, 2, 2, 2, 2, 2};
   std::vector<uint64_t> mod, psi;
   std::vector<double> delta;
   // device tables
@@ -262,11 +271,21 @@ void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint6
 void wait_selftest(Ctx& c, long long limit);
 void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B, int level,
                        const uint64_t* key, uint64_t* out);
+// double-hoisted BSGS: the key inner product of sigma_g(ext) over QP_l
+// ([B][2][l + alpha][N], no ModDown), and the division of such a QP_l pair
+// by P q_level (its D rows are transformed in place); out [B][2][level][N]
+DevBuf keyswitch_qp(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
+                    uint64_t galois);
+void div_p_ql(Ctx& c, uint64_t* acc, size_t B, int level, uint64_t* out);
 
 // ---- encoding (encode.cu)
 // v: device doubles [B][nv]; writes pt [B][level+1][N] at `scale`. Returns
 // CKKS_ERR_OVERFLOW if a coefficient does not fit int64.
 int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double scale, uint64_t* pt);
+// the same integer coefficients reduced mod the moduli pattern[0 .. rows-1]
+// (e.g. a QP_l plaintext): pt [B][rows][N], NTT form
+int encode_rows(Ctx& c, const double* d_v, size_t B, size_t nv, int rows, const int16_t* pattern,
+                double scale, uint64_t* pt);
 // m: [B][N] limb-0 coefficient values (uint64 mod q0); out: device doubles [B][nv]
 void decode_limb0(Ctx& c, const uint64_t* m, size_t B, double scale, double* d_out, size_t nv);
 

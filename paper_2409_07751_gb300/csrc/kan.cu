@@ -73,6 +73,7 @@ struct Layer {
   std::vector<double> coef, w_s, w_b, cheb, knots;
   std::vector<std::vector<double>> comp;  // composite stages, odd monomial coefficients
   int b0 = 0;  // order-0 basis: 0 product (Algorithm 2), 1 difference of knot comparisons
+  int bsgs = 0;  // 0 hoisted baby steps, 1 double hoisting (baby steps kept in QP_l)
   // A wide first layer (n_in 2^ceil(log2(G+2k)) > N/2) takes K input
   // ciphertexts per request of n_c inputs each (the last zero-padded);
   // otherwise K = 1 and n_c = n_in. The schedule runs on n_c inputs.
@@ -137,6 +138,20 @@ const uint64_t* cached_pt(kan_model& M, int layer, int tag, int sub, int level, 
   if (it != M.pts.end()) return it->second->u64();
   std::vector<double> v = make();
   auto b = std::make_unique<DevBuf>(encode_vec(*M.ctx, v.data(), v.size(), level, scale));
+  const uint64_t* p = b->u64();
+  M.pts[key] = std::move(b);
+  return p;
+}
+
+// the same over QP_level (double hoisting)
+template <class F>
+const uint64_t* cached_pt_qp(kan_model& M, int layer, int tag, int sub, int level, double scale,
+                             F&& make) {
+  auto key = std::make_tuple(layer * 1000 + tag, sub, level, 1, dbits(scale));
+  auto it = M.pts.find(key);
+  if (it != M.pts.end()) return it->second->u64();
+  std::vector<double> v = make();
+  auto b = std::make_unique<DevBuf>(encode_vec_qp(*M.ctx, v.data(), v.size(), level, scale));
   const uint64_t* p = b->u64();
   M.pts[key] = std::move(b);
   return p;
@@ -228,6 +243,78 @@ Ct bsgs_matvec(kan_model& M, int li, int tag, const Plan& p, int nch, DV&& dval,
     z = op_add(c, *z, *r, false);
   }
   return z;
+}
+
+// bsgs_matvec with double hoisting: the baby-step rotations stay in QP_l (one
+// ModUp, no ModDown: R_j = (P sigma_j(c0) + acc_0, acc_1), R_0 = P v), each
+// giant step's diagonal products are summed over QP_l with the diagonals
+// encoded over QP_l, and the sum is divided by P q_level once (the ModDowns
+// of the baby steps and the rescale of the products in one rounded
+// division), then rotated by g1 i. One input chunk (nch = 1).
+template <class DV>
+Ct bsgs_matvec_double(kan_model& M, int li, int tag, const Plan& p, DV&& dval,
+                      const ckks_keys& keys, const ckks_ct& v) {
+  Ctx& c = *M.ctx;
+  const int S = (int)(c.N / 2);
+  const int lv = v.level, l = lv + 1;
+  if (lv < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+  ConvTables& T = c.tables(lv);
+  const size_t qp_words = v.B * 2 * (size_t)T.rows * c.N;
+  std::vector<DevBuf> R;
+  R.emplace_back(&c, qp_words * 8);
+  k_qp_lift(c, v.d.u64(), v.B, lv, nullptr, R[0].u64());
+  DevBuf ext;
+  for (int j = 1; j < p.g1; j++) {
+    const uint64_t g = c.galois(j);
+    auto it = keys.galois.find(g);
+    if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
+    if (!ext.p) {
+      ext = DevBuf(&c, v.B * T.beta * T.rows * c.N * 8);
+      // c1 of batch element b sits at v + (2b + 1) l N
+      modup(c, v.d.u64() + (size_t)l * c.N, v.B, lv, ext.u64(), 2 * (size_t)l * c.N);
+    }
+    DevBuf acc = keyswitch_qp(c, ext.u64(), v.B, lv, it->second->u64(), g);
+    k_qp_lift(c, v.d.u64(), v.B, lv, c.perm(g), acc.u64());
+    R.push_back(std::move(acc));
+  }
+  ext.reset();
+  const double Spt = plain_scale(c, v.scale, lv);
+  double s = v.scale * Spt / (double)c.mod[lv];
+  if (fabs(s / c.delta[lv - 1] - 1.0) < SNAP) s = c.delta[lv - 1];
+  Ct z;
+  for (int i = 0; i < p.g2; i++) {
+    DevBuf acc(&c, qp_words * 8);
+    for (int j = 0; j < p.g1; j++) {
+      const int t = p.g1 * i + j;
+      const uint64_t* pt = cached_pt_qp(M, li, tag, t * 64, lv, Spt, [&] {
+        std::vector<double> d(S);
+        const int sh = p.g1 * i;
+        for (int q = 0; q < S; q++) d[q] = dval(0, t, ((q - sh) % S + S) % S);
+        return d;
+      });
+      k_qp_mul_pt_acc(c, R[j].u64(), pt, acc.u64(), v.B * 2, lv, j == 0);
+    }
+    Ct inner = ct_alloc(c, v.B, lv - 1, s);
+    div_p_ql(c, acc.u64(), v.B, lv, inner->d.u64());
+    if (i > 0) inner = op_rotate(c, keys, *inner, (int64_t)p.g1 * i);
+    z = z ? op_add(c, *z, *inner, false) : std::move(inner);
+  }
+  for (int f : p.folds) {
+    Ct r = op_rotate(c, keys, *z, f);
+    z = op_add(c, *z, *r, false);
+  }
+  return z;
+}
+
+// the layer's matvec form; double hoisting takes one input chunk
+template <class DV>
+Ct matvec(kan_model& M, int li, int tag, const Plan& p, int nch, DV&& dval, const ckks_keys& keys,
+          const ckks_ct& v) {
+  if (M.layers[li].bsgs == 1) {
+    if (nch != 1) throw Error(CKKS_ERR_UNSUPPORTED, "double hoisting of a chunked layer");
+    return bsgs_matvec_double(M, li, tag, p, dval, keys, v);
+  }
+  return bsgs_matvec(M, li, tag, p, nch, dval, keys, v);
 }
 
 // sum_l cf[l] u^(2l+1) + cst: the coefficients, padded to 2^K, split in
@@ -370,7 +457,7 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
   Ct y = op_add_pt(c, *y0, p_sa);
   if (L.plan_b.npad < S) y = op_add(c, *y, *op_rotate(c, keys, *y, -L.plan_b.npad), false);
   Ct v = eval_cheb(c, keys, *y, L.cheb);
-  Ct yb = bsgs_matvec(M, li, T_DIAG_B, L.plan_b, L.K, stored_diag(L.diag_b, S), keys, *v);
+  Ct yb = matvec(M, li, T_DIAG_B, L.plan_b, L.K, stored_diag(L.diag_b, S), keys, *v);
 
   // Algorithm 1
   const uint64_t* p_mr = cached_pt(M, li, T_MASK_R, 0, x.level, S1,
@@ -470,12 +557,12 @@ Ct layer_eval(kan_model& M, int li, const ckks_keys& keys, const ckks_ct& x) {
       if (r >= n || col >= n) return 0.0;
       return col == (r % nb) * n_i + r / nb ? 1.0 : 0.0;
     };
-    b = bsgs_matvec(M, li, T_DIAG_P, L.plan_p, 1, perm, keys, *b);
+    b = matvec(M, li, T_DIAG_P, L.plan_p, 1, perm, keys, *b);
   }
   // fused linear layer W_f (Eq. 13), or W' after the naive permutation
   if (L.plan_s.npad < S) b = op_add(c, *b, *op_rotate(c, keys, *b, -L.plan_s.npad), false);
-  Ct ys = bsgs_matvec(M, li, L.naive ? T_DIAG_W : T_DIAG_S, L.plan_s, L.K, stored_diag(L.diag_s, S),
-                      keys, *b);
+  Ct ys = matvec(M, li, L.naive ? T_DIAG_W : T_DIAG_S, L.plan_s, L.K, stored_diag(L.diag_s, S),
+                 keys, *b);
   const int lv = std::min(ys->level, yb->level);
   Ct out = op_add(c, *op_level_down(c, *ys, lv), *op_level_down(c, *yb, lv), false);
   if (L.K == 1) return out;
@@ -668,7 +755,8 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
       const kan_layer_desc& d = layers[li];
       if (d.n_in < 1 || d.n_out < 1 || d.G < 1 || d.k < 0 || !d.coef || !d.w_s || !d.w_b ||
           !d.silu_cheb || d.silu_degree < 1 || !(d.R > 0) || !(d.silu_hi > d.silu_lo) ||
-          !(d.grid_hi > d.grid_lo) || (d.b0_form != 0 && d.b0_form != 1))
+          !(d.grid_hi > d.grid_lo) || (d.b0_form != 0 && d.b0_form != 1) ||
+          (d.bsgs_form != 0 && d.bsgs_form != 1))
         throw Error(CKKS_ERR_INVALID_ARG, "invalid layer description");
       Layer L;
       if (d.n_comp_poly > 0) {
@@ -690,6 +778,7 @@ int kan_model_create(ckks_ctx* ctx, const kan_layer_desc* layers, size_t n_layer
         }
       }
       L.b0 = d.b0_form;
+      L.bsgs = d.bsgs_form;
       L.n_in = d.n_in;
       L.n_out = d.n_out;
       L.G = d.G;

@@ -446,9 +446,13 @@ __global__ void rr_finish_kernel(const uint64_t* acc, const uint64_t* d, const u
     const size_t b = bk / 2, k = bk % 2;
     const uint64_t q = mods[i].q;
     const uint64_t a = acc[(bk * rows + i) * N + n];
+    const uint64_t r = mul_shoup(sub_mod(a, conv[idx], q), minv[i], minvs[i], q);
+    if (!d) {
+      out[idx] = r;
+      continue;
+    }
     const uint64_t dv = d[((b * 3 + k) * l + i) * N + n];
-    out[idx] = add_mod(mul_shoup(dv, qlinv[i], qlinvs[i], q),
-                       mul_shoup(sub_mod(a, conv[idx], q), minv[i], minvs[i], q), q);
+    out[idx] = add_mod(mul_shoup(dv, qlinv[i], qlinvs[i], q), r, q);
   }
 }
 
@@ -549,6 +553,48 @@ void wait_selftest(Ctx& c, long long limit) {
   CK_CUDA(cudaGetLastError());
 }
 
+// Division of y = P d + acc over QP_l by M = P q_level (d may be null: y = acc)
+// with the centred conversion of the dropped limbs; acc's D rows are
+// transformed in place.
+static void div_p_ql_impl(Ctx& c, uint64_t* acc, const uint64_t* d, size_t B, int level,
+                          uint64_t* out) {
+  ConvTables& T = c.tables(level);
+  const int rows = T.rows;
+  const double W8 = (double)c.N * 8.0;
+  const int16_t* pat = static_cast<const int16_t*>(T.rr_pattern.p);
+  const size_t active = B * 2 * (size_t)(c.alpha + 1);
+  if (ntt_fused_available(c)) {
+    ntt_inverse_post(c, acc, B * 2 * rows, pat, rows, T.rr_post.u64(), T.rr_post_s.u64(), active);
+    DevBuf ov(&c, B * 2 * c.N);
+    {
+      Launch L_(c, K_OVERFLOW, W8 * B * 2.0 * (c.alpha + 1.0) + B * 2.0 * c.N);
+      overflow_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+          acc, static_cast<uint8_t*>(ov.p), B * 2, c.log_n, level, c.alpha + 1, rows,
+          static_cast<const double*>(T.rr_inv.p), inv_float(T.rr_inv_h));
+      CK_CUDA(cudaGetLastError());
+    }
+    ntt_relin_rescale_fused(c, acc, d, static_cast<const uint8_t*>(ov.p), B, level, out);
+    return;
+  }
+  ntt_inverse(c, acc, B * 2 * rows, pat, rows, active);
+  DevBuf conv(&c, B * 2 * (size_t)level * c.N * 8);
+  {
+    Launch L_(c, K_MD_CONV, W8 * B * 2.0 * (c.alpha + 1.0 + level));
+    rr_conv_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
+        acc, conv.u64(), B * 2, c.log_n, level, c.alpha, rows, c.dmod(), pat, T.rr_yinv.u64(),
+        T.rr_yinv_s.u64(), T.rr_mh.u64(), T.rr_mh_s.u64(), static_cast<const double*>(T.rr_inv.p),
+        T.rr_mq.u64(), T.rr_mq_s.u64());
+    CK_CUDA(cudaGetLastError());
+  }
+  ntt_forward(c, conv.u64(), B * 2 * (size_t)level, c.iota(), level);
+  Launch L2_(c, K_MD_FINISH, W8 * B * 2.0 * ((d ? 4.0 : 3.0) * level));
+  rr_finish_kernel<<<grid_for(B * 2 * (size_t)level * c.N), TPB, 0, c.stream>>>(
+      acc, d, conv.u64(), out, B * 2, c.log_n, level, rows, c.dmod(), T.rr_minv.u64(),
+      T.rr_minv_s.u64(), c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
+      c.d_rs_invs.u64() + (size_t)level * (c.L + 1));
+  CK_CUDA(cudaGetLastError());
+}
+
 void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B, int level,
                        const uint64_t* key, uint64_t* out) {
   if (level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
@@ -563,39 +609,18 @@ void relin_rescale_ext(Ctx& c, const uint64_t* d, const uint64_t* ext, size_t B,
         acc.u64(), d, B, c.log_n, level, rows, c.mod[level], T.rr_pq, T.rr_pq_s);
     CK_CUDA(cudaGetLastError());
   }
-  const int16_t* pat = static_cast<const int16_t*>(T.rr_pattern.p);
-  const size_t active = B * 2 * (size_t)(c.alpha + 1);
-  if (ntt_fused_available(c)) {
-    ntt_inverse_post(c, acc.u64(), B * 2 * rows, pat, rows, T.rr_post.u64(), T.rr_post_s.u64(),
-                     active);
-    DevBuf ov(&c, B * 2 * c.N);
-    {
-      Launch L_(c, K_OVERFLOW, W8 * B * 2.0 * (c.alpha + 1.0) + B * 2.0 * c.N);
-      overflow_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
-          acc.u64(), static_cast<uint8_t*>(ov.p), B * 2, c.log_n, level, c.alpha + 1, rows,
-          static_cast<const double*>(T.rr_inv.p), inv_float(T.rr_inv_h));
-      CK_CUDA(cudaGetLastError());
-    }
-    ntt_relin_rescale_fused(c, acc.u64(), d, static_cast<const uint8_t*>(ov.p), B, level, out);
-    return;
-  }
-  ntt_inverse(c, acc.u64(), B * 2 * rows, pat, rows, active);
-  DevBuf conv(&c, B * 2 * (size_t)level * c.N * 8);
-  {
-    Launch L_(c, K_MD_CONV, W8 * B * 2.0 * (c.alpha + 1.0 + level));
-    rr_conv_kernel<<<grid_for(B * 2 * c.N), TPB, 0, c.stream>>>(
-        acc.u64(), conv.u64(), B * 2, c.log_n, level, c.alpha, rows, c.dmod(), pat,
-        T.rr_yinv.u64(), T.rr_yinv_s.u64(), T.rr_mh.u64(), T.rr_mh_s.u64(),
-        static_cast<const double*>(T.rr_inv.p), T.rr_mq.u64(), T.rr_mq_s.u64());
-    CK_CUDA(cudaGetLastError());
-  }
-  ntt_forward(c, conv.u64(), B * 2 * (size_t)level, c.iota(), level);
-  Launch L2_(c, K_MD_FINISH, W8 * B * 2.0 * 4.0 * level);
-  rr_finish_kernel<<<grid_for(B * 2 * (size_t)level * c.N), TPB, 0, c.stream>>>(
-      acc.u64(), d, conv.u64(), out, B * 2, c.log_n, level, rows, c.dmod(), T.rr_minv.u64(),
-      T.rr_minv_s.u64(), c.d_rs_inv.u64() + (size_t)level * (c.L + 1),
-      c.d_rs_invs.u64() + (size_t)level * (c.L + 1));
-  CK_CUDA(cudaGetLastError());
+  div_p_ql_impl(c, acc.u64(), d, B, level, out);
+}
+
+DevBuf keyswitch_qp(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,
+                    uint64_t galois) {
+  return key_product(c, ext, B, level, key, galois);
+}
+
+void div_p_ql(Ctx& c, uint64_t* acc, size_t B, int level, uint64_t* out) {
+  if (level < 1) throw Error(CKKS_ERR_LEVEL, "level exhausted");
+  if (c.alpha + 1 > MAX_ALPHA + 1) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 16");
+  div_p_ql_impl(c, acc, nullptr, B, level, out);
 }
 
 void keyswitch_ext(Ctx& c, const uint64_t* ext, size_t B, int level, const uint64_t* key,

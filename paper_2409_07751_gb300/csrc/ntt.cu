@@ -39,6 +39,10 @@ template <int N1>
 __host__ __device__ constexpr int fwd_cs() { return N1 >= 4 ? N1 / 2 : 1; }
 template <int N1>
 __host__ __device__ constexpr int inv_cs() { return N1 >= 4 ? N1 / 2 : 1; }
+// CTAs per SM the clustered kernels are compiled for: 2 (64 registers per
+// thread, 32 warps per SM) by default; 1 (up to 128 registers, no spills in
+// the fused descriptors, 16 warps) per tuning slot for N1 >= 8, chosen by
+// ckks_autotune_ntt or ckks_set_ntt_shape (Ctx::ntt_minb).
 constexpr int CTAS_PER_SM = 2;
 
 // 32-bit address of this CTA's shared-memory location p in the cluster window
@@ -59,7 +63,7 @@ __device__ __forceinline__ void st_dsmem(uint32_t addr, uint64_t v) {
 }
 
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
-  return a * w - __umul64hi(a, ws) * q;  // in [0, 2q) for any a < 2^64
+  return mul_sub_q(a, w, __umul64hi(a, ws), q);  // in [0, 2q) for any a < 2^64
 }
 // x, y in [0, 4q) -> [0, 4q)
 __device__ __forceinline__ void ct_lazy(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
@@ -281,6 +285,7 @@ constexpr int MAX_SRC = 16;
 
 // plain forward NTT of pattern-selected rows
 struct DescPlain {
+  static constexpr int SLOT = NTT_SLOT_FWD;
   static constexpr bool FOLD1 = false;  // see DescModUp
   uint64_t* base;
   const int16_t* pattern;
@@ -300,6 +305,7 @@ struct DescPlain {
 
 // ModUp target row: sum_a xs[a][i] * [Dhat_a]_{m} mod m, then NTT; digit rows copy d.
 struct DescModUp {
+  static constexpr int SLOT = NTT_SLOT_MODUP;
   // The forward transform's first stage multiplies the upper half of the
   // row by the single twiddle w = psi^(N/2); the upper half is loaded with
   // the constants [Dhat_a w]_m instead (load_w), so that stage is a plain
@@ -385,6 +391,7 @@ __device__ __forceinline__ uint64_t conv_load(const Row& r, uint32_t i, const ui
 
 // ModDown output row i of (b,k): (acc_i - NTT(sum_a y_a [Phat_a]_{q_i})) * P^-1
 struct DescModDown {
+  static constexpr int SLOT = NTT_SLOT_MODDOWN;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* acc;  // [BK][rows][N]; P rows already inverse-transformed and scaled
   uint64_t* out;        // [BK][l][N]
@@ -426,6 +433,7 @@ struct DescModDown {
 
 // Rescale output row t of poly p: (c_t - NTT(centred(last) mod q_t)) * q_level^-1
 struct DescRescale {
+  static constexpr int SLOT = NTT_SLOT_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* in;    // [polys][level+1][N]
   const uint64_t* last;  // [polys][N] coefficient form of limb `level`
@@ -461,6 +469,7 @@ struct DescRescale {
 // with `last` the coefficient form of k c_level (the inverse transform's post
 // factor carries k) and c read in place (poly p at in + p in_stride).
 struct DescRescaleScaled {
+  static constexpr int SLOT = NTT_SLOT_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* in;
   size_t in_stride;
@@ -580,6 +589,7 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
 // y_m the D rows of acc (level .. level+alpha) already inverse-transformed and
 // scaled by (M/m)^-1, with y_level = P d_k + acc_k on q_level.
 struct DescRelinRescale {
+  static constexpr int SLOT = NTT_SLOT_RELIN_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* acc;    // [BK][rows][N]
   const uint64_t* d;      // [B][3][level+1][N] tensor product
@@ -605,7 +615,7 @@ struct DescRelinRescale {
     r.src = acc + (bk * rows + level) * N;
     r.n_src = alpha + 1;
     r.src2 = acc + (bk * rows + i) * N;
-    r.src3 = d + ((b * 3 + k) * l + i) * N;
+    r.src3 = d ? d + ((b * 3 + k) * l + i) * N : nullptr;  // null: no tensor term
     r.k = minv[i];
     r.ks = minvs[i];
     r.k2 = qlinv[i];
@@ -623,8 +633,8 @@ struct DescRelinRescale {
     return conv_load(r, i, kc, grow, N);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
-    r.mid[i] = add_mod(mul_shoup(r.src3[i], r.k2, r.k2s, q),
-                       mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q), q);
+    const uint64_t y = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+    r.mid[i] = r.src3 ? add_mod(mul_shoup(r.src3[i], r.k2, r.k2s, q), y, q) : y;
   }
 };
 
@@ -636,8 +646,8 @@ struct DescRelinRescale {
 // barrier each CTA runs the radix-8 rounds on its own chunks in place and
 // writes the results through the epilogue. The row never round-trips
 // through global memory.
-template <int N1, class D>
-__global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
+template <int N1, class D, int MINB = CTAS_PER_SM>
+__global__ void __launch_bounds__(ROW_THREADS, MINB)
     ntt_fwd_cl(D d, int log_n, const Mod* mods, const uint64_t* tw, const uint64_t* tws,
                const ulonglong2* tw8, size_t nodes) {
   constexpr int CS = fwd_cs<N1>();
@@ -725,8 +735,8 @@ __device__ __forceinline__ void inv_rows(uint64_t* a, const uint64_t* as, uint64
 // and transforms its own chunks, then (after a cluster barrier) transforms
 // its share of the columns, reading the elements from the owners' shared
 // memory, and writes the row scaled by post[row % P] (default N^-1).
-template <int N1>
-__global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
+template <int N1, int MINB = CTAS_PER_SM>
+__global__ void __launch_bounds__(ROW_THREADS, MINB)
     ntt_inv_cl(uint64_t* base, const uint64_t* src, size_t src_stride, int log_n,
                const int16_t* pattern, int P, const Mod* mods,
                const uint64_t* tw, const uint64_t* tws, const uint64_t* ninv,
@@ -756,7 +766,7 @@ __global__ void __launch_bounds__(ROW_THREADS, CTAS_PER_SM)
     inv_rows<N1, false>(a, as, sm, ctw, t8, log_n, q, pv, pvs, rank);
 }
 
-template <int N1, int CS, class K, class... Args>
+template <int N1, int CS, int MINB, class K, class... Args>
 void launch_cl(Ctx& c, K kernel, size_t n_rows, Args... args) {
   constexpr int CPC = N1 / CS;
   const size_t smem = (size_t)CPC * CHUNK * 8;
@@ -790,11 +800,18 @@ void launch_fwd(Ctx& c, size_t n_rows, const D& d) {
   const size_t nd = c.tw8_nodes;
   const int ln = c.log_n;
   const Mod* md = c.dmod();
+  const bool one = c.ntt_minb[D::SLOT] == 1;
   switch (c.log_n - CHUNK_LOG) {
-    case 1: launch_cl<2, fwd_cs<2>()>(c, ntt_fwd_cl<2, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
-    case 2: launch_cl<4, fwd_cs<4>()>(c, ntt_fwd_cl<4, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
-    case 3: launch_cl<8, fwd_cs<8>()>(c, ntt_fwd_cl<8, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
-    case 4: launch_cl<16, fwd_cs<16>()>(c, ntt_fwd_cl<16, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 1: launch_cl<2, fwd_cs<2>(), 2>(c, ntt_fwd_cl<2, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 2: launch_cl<4, fwd_cs<4>(), 2>(c, ntt_fwd_cl<4, D>, n_rows, d, ln, md, tw, tws, t8, nd); break;
+    case 3:
+      if (one) launch_cl<8, fwd_cs<8>(), 1>(c, ntt_fwd_cl<8, D, 1>, n_rows, d, ln, md, tw, tws, t8, nd);
+      else launch_cl<8, fwd_cs<8>(), 2>(c, ntt_fwd_cl<8, D>, n_rows, d, ln, md, tw, tws, t8, nd);
+      break;
+    case 4:
+      if (one) launch_cl<16, fwd_cs<16>(), 1>(c, ntt_fwd_cl<16, D, 1>, n_rows, d, ln, md, tw, tws, t8, nd);
+      else launch_cl<16, fwd_cs<16>(), 2>(c, ntt_fwd_cl<16, D>, n_rows, d, ln, md, tw, tws, t8, nd);
+      break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
 }
@@ -811,11 +828,18 @@ void launch_inv(Ctx& c, size_t n_rows, uint64_t* base, const int16_t* pattern, i
   const size_t nd = c.tw8_nodes;
   const int ln = c.log_n;
   const Mod* md = c.dmod();
+  const bool one = c.ntt_minb[NTT_SLOT_INV] == 1;
   switch (c.log_n - CHUNK_LOG) {
-    case 1: launch_cl<2, inv_cs<2>()>(c, ntt_inv_cl<2>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 2: launch_cl<4, inv_cs<4>()>(c, ntt_inv_cl<4>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 3: launch_cl<8, inv_cs<8>()>(c, ntt_inv_cl<8>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
-    case 4: launch_cl<16, inv_cs<16>()>(c, ntt_inv_cl<16>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 1: launch_cl<2, inv_cs<2>(), 2>(c, ntt_inv_cl<2>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 2: launch_cl<4, inv_cs<4>(), 2>(c, ntt_inv_cl<4>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd); break;
+    case 3:
+      if (one) launch_cl<8, inv_cs<8>(), 1>(c, ntt_inv_cl<8, 1>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd);
+      else launch_cl<8, inv_cs<8>(), 2>(c, ntt_inv_cl<8>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd);
+      break;
+    case 4:
+      if (one) launch_cl<16, inv_cs<16>(), 1>(c, ntt_inv_cl<16, 1>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd);
+      else launch_cl<16, inv_cs<16>(), 2>(c, ntt_inv_cl<16>, n_rows, base, src, src_stride, ln, pattern, P, md, tw, tws, ni, nis, post, posts, t8, nd);
+      break;
     default: throw Error(CKKS_ERR_UNSUPPORTED, "NTT size");
   }
 }
@@ -897,7 +921,7 @@ void ntt_relin_rescale_fused(Ctx& c, const uint64_t* acc, const uint64_t* d, con
   if (c.alpha + 1 > MAX_SRC) throw Error(CKKS_ERR_UNSUPPORTED, "alpha > 15");
   const double W8 = (double)c.N * 8.0;
   const double BK = 2.0 * (double)B;
-  Launch L_(c, K_RR_NTT, W8 * BK * (c.alpha + 1.0 + 3.0 * level),
+  Launch L_(c, K_RR_NTT, W8 * BK * (c.alpha + 1.0 + (d ? 3.0 : 2.0) * level),
             BK * level * ((double)(c.N / 2) * c.log_n + (c.alpha + 3.0) * c.N));
   DescRelinRescale dsc{acc, d, out, T.rr_mh.u64(), T.rr_mh_s.u64(), T.rr_minv.u64(),
                        T.rr_minv_s.u64(), c.d_rs_inv.u64() + (size_t)level * (c.L + 1),

@@ -46,6 +46,17 @@ DevBuf encode_vec(Ctx& c, const double* host, size_t n, int level, double scale)
   return pt;
 }
 
+DevBuf encode_vec_qp(Ctx& c, const double* host, size_t n, int level, double scale) {
+  ConvTables& T = c.tables(level);
+  DevBuf pt(&c, (size_t)T.rows * c.N * 8);
+  DevBuf v(&c, std::max<size_t>(n, 1) * 8);
+  if (n) CK_CUDA(cudaMemcpyAsync(v.p, host, n * 8, cudaMemcpyHostToDevice, c.stream));
+  const int rc = encode_rows(c, static_cast<const double*>(v.p), 1, n, T.rows,
+                             static_cast<const int16_t*>(T.qp_pattern.p), scale, pt.u64());
+  if (rc != CKKS_OK) throw Error(rc, "plaintext does not fit its scale");
+  return pt;
+}
+
 Ct op_add(Ctx& c, const ckks_ct& a, const ckks_ct& b, bool sub) {
   check_pair(a, b);
   Ct r = ct_alloc(c, a.B, a.level, a.scale);

@@ -25,6 +25,8 @@ double plain_scale(const Ctx& c, double ct_scale, int level);
 
 // plaintext [l][N] (device) of a real vector at `level` and `scale`
 DevBuf encode_vec(Ctx& c, const double* host, size_t n, int level, double scale);
+// the same over QP_level ([l + alpha][N]: Q limbs, then the special primes)
+DevBuf encode_vec_qp(Ctx& c, const double* host, size_t n, int level, double scale);
 
 Ct op_add(Ctx& c, const ckks_ct& a, const ckks_ct& b, bool sub);
 Ct op_mul_int(Ctx& c, const ckks_ct& a, int64_t k);
@@ -68,6 +70,12 @@ void k_mul_pt_acc_grouped(Ctx& c, const uint64_t* a, const std::vector<const uin
                           uint64_t* acc, size_t B, int l);
 void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_t*>& pts,
                       uint64_t* out, size_t B, int l);
+// double-hoisted BSGS over QP_level rows ([polys][l + alpha][N]): acc (=) +=
+// a * pt; a rotation kept in QP (R holds the key product; perm null: the
+// identity, R = P c)
+void k_qp_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, size_t polys,
+                     int level, bool first);
+void k_qp_lift(Ctx& c, const uint64_t* ct, size_t B, int level, const uint32_t* perm, uint64_t* R);
 // out[b] = sum_c in[b K + c]
 void k_chunk_sum(Ctx& c, const uint64_t* in, uint64_t* out, size_t B, int K, int l);
 void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,

@@ -5,14 +5,14 @@
 // (no memory traffic inside the timed loop) of one of:
 //   kind 0: a 64 x 64 -> 128-bit product (the low and high words);
 //   kind 1: the forward transform's lazy butterfly (ct_grow: a three-product
-//           Shoup multiply plus the two 64-bit sums), 16 stages then the full
+//           Shoup multiply plus the two 64-bit sums, as the transforms run
+//           it), 16 stages then the full
 //           reduction of both words, the ratio of butterflies to reductions
 //           of a 2^16-point transform;
 //   kind 2: the three-product Shoup multiply alone (the basis-conversion
 //           product of ModUp and ModDown), accumulated lazily;
-//   kind 3: kind 1 with the remainder y w - Q q formed as y w + Q (2^64 - q)
-//           in one multiply-add chain of 32-bit pieces (two widening
-//           products, four low products);
+//   kind 3: kind 1 with the remainder formed as y w - Q q on 64-bit words
+//           (the form the transforms used before the one-chain remainder);
 //   kind 4: kind 1 where every butterfly takes its partner word from another
 //           lane through two 32-bit warp shuffles (the exchange of a
 //           shuffle-based transform);
@@ -73,13 +73,12 @@ __global__ void __launch_bounds__(PEAK_THREADS) k_int_peak(uint64_t* out, uint64
 #pragma unroll
       for (int j = 0; j < CHAINS; j++) x[j] = reduce_full(x[j], q, w1s);
     } else if (KIND == 3) {
-      const uint64_t nq = 0 - q;
 #pragma unroll
       for (int s = 0; s < 16; s++) {
 #pragma unroll
         for (int j = 0; j < CHAINS; j++) {
           const uint64_t u = x[j];
-          const uint64_t t = shoup_approx_nq(y[j], w, ws, nq);
+          const uint64_t t = shoup_approx_sub(y[j], w, ws, q);
           x[j] = u + t;
           y[j] = u - t + 2 * q2;
         }

@@ -43,8 +43,9 @@ def test_binding_signatures_cover_the_header():
 
 def test_model_descriptor_b0_forms_and_stages():
     """Both forms of the order-0 basis (Algorithm 2's product, the difference
-    of knot comparisons) marshal; another form, or a composite mixing f_n
-    orders with coefficient lists, is refused."""
+    of knot comparisons) and both matvec forms (hoisted, double hoisted)
+    marshal; another form, or a composite mixing f_n orders with coefficient
+    lists, is refused."""
     import numpy as np
     import pytest
     from paper_2409_07751_gb300 import ckks, workloads as W
@@ -60,5 +61,11 @@ def test_model_descriptor_b0_forms_and_stages():
         ckks._descs(m, [])
     m[0]["b0"] = "product"
     m[0]["comp"] = [3, np.array([1.0])]
+    with pytest.raises(ValueError):
+        ckks._descs(m, [])
+    m[0]["comp"] = [3]
+    m[0]["bsgs"] = "double"
+    assert ckks._descs(m, [])[0].bsgs_form == 1
+    m[0]["bsgs"] = "triple"
     with pytest.raises(ValueError):
         ckks._descs(m, [])

@@ -259,3 +259,32 @@ def test_mixed_level_batch_equals_each_alone(G):
         assert (alone.export()[0] == got[b]).all(), b
         oc = O.level_down(octx, O.encrypt(octx, ok, X[b], levels[b], W.SEED_ENC, b), low)
         assert (got[b] == kan_he.infer(octx, ok, oc, m).data).all(), b
+
+
+@pytest.mark.parametrize("b0", ["product", "difference"])
+def test_double_hoisted_bsgs_bit_exact(G, b0):
+    """Double-hoisted BSGS (baby steps kept in QP_l, one division by P q_l
+    per giant step): a layer and the network equal the oracle's double-hoisted
+    schedule word for word, decrypt like the hoisted form, and the words
+    differ from it (a different rounding)."""
+    model = [dict(L, bsgs="double", b0=b0) for L in W.make_model("t", widths=[3, 5, 2], G=3, k=2)]
+    X = W.uniform_inputs(64, 3)
+    m = calibrate.calibrate(model, X, 7, [1])
+    gctx, octx, gm, gk, ok = _setup(G, 7, 17, 2, m)
+    single = G.Model(gctx, [dict(L, bsgs="single") for L in m])
+    oc = O.encrypt(octx, ok, X[0], octx.L, W.SEED_ENC, 0)
+    gc = G.Ciphertext.import_(gctx, oc.data, oc.level, oc.scale)
+    o1 = kan_he.layer_eval(octx, ok, oc, m[0])
+    g1 = G.kan_layer_eval(gctx, gk, gm, 0, gc)
+    assert g1.level == o1.level and g1.scale == o1.scale
+    assert (g1.export()[0] == o1.data).all()
+    gin = G.encrypt(gctx, gk, X[:2], octx.L, W.SEED_ENC, 0)
+    gout = G.kan_infer(gctx, gk, gm, [gin])
+    sout = G.kan_infer(gctx, gk, single, [gin])
+    for b in range(2):
+        oo = kan_he.infer(octx, ok, O.encrypt(octx, ok, X[b], octx.L, W.SEED_ENC, b), m)
+        assert (gout.export()[b] == oo.data).all()
+    assert not (gout.export() == sout.export()).all()
+    hef = kan_plain.forward(m, X[:2], "poly", "poly")
+    dd, ds = G.decrypt(gctx, gk, gout, 2), G.decrypt(gctx, gk, sout, 2)
+    assert np.abs(dd - hef).max() < 1e-5 and np.abs(dd - ds).max() < 1e-5
