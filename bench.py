@@ -764,6 +764,13 @@ def main():
                                                         device=local)
     ctx = G.Context(a.log_n, a.levels, a.alpha, p_bits=a.p_bits, device=local)
     ctx.set_stream(stream.cuda_stream)
+    # CTAs per SM of each NTT kind, by measurement on this context
+    ntt_chosen, ntt_ms = ctx.autotune_ntt(8)
+    ntt_tune = {"chosen_ctas_per_sm": ntt_chosen,
+                "ms_at_2_and_1_ctas_per_sm": {k: [round(v[0], 3), round(v[1], 3)]
+                                              for k, v in ntt_ms.items()},
+                "workload": "HMult, HRot, constant product, rescale, forward NTT; batch 8 "
+                            "at the top level"}
     model, Xcal, X = model_and_inputs(a, rank)
     m = calibrate_for(a, G.calibrate, model, Xcal, gpu_design(G))
     gm = G.Model(ctx, m)
@@ -1030,7 +1037,8 @@ def main():
             "roofline": roofline, "kernel_time_shares": shares, "kernel_rates": rates,
             "gpu_launches": launches,
             "clocks": clocks, "e2e": e2e, "plain_form": plain, "graph_replay": graph_replay,
-            "keyswitch_autotune_ms": tuned, "micro": micro, "int_peaks": int_peaks, "depth": depth,
+            "keyswitch_autotune_ms": tuned, "ntt_autotune": ntt_tune, "micro": micro,
+            "int_peaks": int_peaks, "depth": depth,
             "slack": slack}
     if rank == 0 and world == 1 and not a.no_extras and a.workload == "c2":
         line["configs"] = extras(local)

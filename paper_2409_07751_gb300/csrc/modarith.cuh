@@ -57,7 +57,12 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const Mod& m
 // products added to the high word (the remainder of every Shoup product;
 // the same value as the two 64-bit products and a subtraction, measured 9 %
 // faster in a butterfly)
-__device__ __forceinline__ uint64_t mul_sub_q(uint64_t a, uint64_t w, uint64_t Q, uint64_t q) {
+// CHAIN = false: the same value from two 64-bit products and a subtraction
+// (which of the two forms runs faster depends on the kernel's register
+// pressure; the transforms choose per descriptor by measurement)
+template <bool CHAIN>
+__device__ __forceinline__ uint64_t mul_sub_q_t(uint64_t a, uint64_t w, uint64_t Q, uint64_t q) {
+  if (!CHAIN) return a * w - Q * q;
   const uint64_t nq = 0 - q;
   const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
   const uint32_t Q0 = (uint32_t)Q, Q1 = (uint32_t)(Q >> 32);
@@ -67,9 +72,16 @@ __device__ __forceinline__ uint64_t mul_sub_q(uint64_t a, uint64_t w, uint64_t Q
   const uint32_t hi = (uint32_t)(lo >> 32) + a0 * w1 + a1 * w0 + Q0 * n1 + Q1 * n0;
   return ((uint64_t)hi << 32) | (uint32_t)lo;
 }
-__device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
-  const uint64_t r = mul_sub_q(a, w, __umul64hi(a, ws), q);
+__device__ __forceinline__ uint64_t mul_sub_q(uint64_t a, uint64_t w, uint64_t Q, uint64_t q) {
+  return mul_sub_q_t<true>(a, w, Q, q);
+}
+template <bool CHAIN = true>
+__device__ __forceinline__ uint64_t mul_shoup_t(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+  const uint64_t r = mul_sub_q_t<CHAIN>(a, w, __umul64hi(a, ws), q);
   return r >= q ? r - q : r;
+}
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t ws, uint64_t q) {
+  return mul_shoup_t<true>(a, w, ws, q);
 }
 // Shoup product whose quotient is estimated from three of the four 32-bit
 // partial products of y * ws (the low product and the carries out of the
@@ -77,29 +89,29 @@ __device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t w
 // y0 s0, Q' = y1 s1 + hi(y1 s0) + hi(y0 s1) satisfies Q - 2 <= Q' <= Q for
 // the exact Q = floor(y ws / 2^64), so y w - Q' q lies in [0, 4q) for any
 // y < 2^64 (exact Shoup: [0, 2q)). The remainder by mul_sub_q.
-__device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_t ws, uint64_t q) {
+template <bool CHAIN = true>
+__device__ __forceinline__ uint64_t shoup_approx_t(uint64_t y, uint64_t w, uint64_t ws, uint64_t q) {
   const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
   const uint32_t s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
   const uint64_t Q = (uint64_t)y1 * s1 + __umulhi(y1, s0) + __umulhi(y0, s1);
-  return mul_sub_q(y, w, Q, q);
+  return mul_sub_q_t<CHAIN>(y, w, Q, q);
 }
-
-// The same product with the remainder formed as y w - Q' q on 64-bit words
-// (kept to measure the two forms against each other).
+__device__ __forceinline__ uint64_t shoup_approx(uint64_t y, uint64_t w, uint64_t ws, uint64_t q) {
+  return shoup_approx_t<true>(y, w, ws, q);
+}
+// the subtraction form (kept to measure the two forms against each other)
 __device__ __forceinline__ uint64_t shoup_approx_sub(uint64_t y, uint64_t w, uint64_t ws, uint64_t q) {
-  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
-  const uint32_t s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
-  const uint64_t Q = (uint64_t)y1 * s1 + __umulhi(y1, s0) + __umulhi(y0, s1);
-  return y * w - Q * q;
+  return shoup_approx_t<false>(y, w, ws, q);
 }
 
 // Forward butterfly without the reduction of x, for moduli q < 2^50: with
 // t in [0, 4q) both outputs grow by less than 4q per stage, so 16 stages
 // from inputs below q stay below 65q < 2^57.
+template <bool CHAIN = true>
 __device__ __forceinline__ void ct_grow(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
   const uint64_t u = x;
-  const uint64_t t = shoup_approx(y, w, ws, q);
+  const uint64_t t = shoup_approx_t<CHAIN>(y, w, ws, q);
   x = u + t;
   y = u - t + 2 * q2;
 }

@@ -100,11 +100,11 @@ __device__ __forceinline__ void gs_step(uint64_t& x, uint64_t& y, uint64_t w, ui
   else
     gs_lazy(x, y, w, ws, q, q2);
 }
-template <bool GROW>
+template <bool GROW, bool CHAIN = true>
 __device__ __forceinline__ void ct_step(uint64_t& x, uint64_t& y, uint64_t w, uint64_t ws,
                                         uint64_t q, uint64_t q2) {
   if (GROW)
-    ct_grow(x, y, w, ws, q, q2);
+    ct_grow<CHAIN>(x, y, w, ws, q, q2);
   else
     ct_lazy(x, y, w, ws, q, q2);
 }
@@ -188,18 +188,18 @@ __device__ __forceinline__ uint32_t node_base(uint32_t ls, int log_n) {
 }
 
 // The three butterfly layers of a round on the group's 8 words x.
-template <bool INV, bool GROW>
+template <bool INV, bool GROW, bool CHAIN = true>
 __device__ __forceinline__ void bfly8(uint64_t* x, const ulonglong2* tt, uint32_t ls, uint64_t q,
                                       uint64_t q2) {
   if (!INV) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) ct_step<GROW>(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
-    ct_step<GROW>(x[0], x[2], tt[1].x, tt[1].y, q, q2);
-    ct_step<GROW>(x[1], x[3], tt[1].x, tt[1].y, q, q2);
-    ct_step<GROW>(x[4], x[6], tt[2].x, tt[2].y, q, q2);
-    ct_step<GROW>(x[5], x[7], tt[2].x, tt[2].y, q, q2);
+    for (int k = 0; k < 4; k++) ct_step<GROW, CHAIN>(x[k], x[k + 4], tt[0].x, tt[0].y, q, q2);
+    ct_step<GROW, CHAIN>(x[0], x[2], tt[1].x, tt[1].y, q, q2);
+    ct_step<GROW, CHAIN>(x[1], x[3], tt[1].x, tt[1].y, q, q2);
+    ct_step<GROW, CHAIN>(x[4], x[6], tt[2].x, tt[2].y, q, q2);
+    ct_step<GROW, CHAIN>(x[5], x[7], tt[2].x, tt[2].y, q, q2);
 #pragma unroll
-    for (int k = 0; k < 4; k++) ct_step<GROW>(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
+    for (int k = 0; k < 4; k++) ct_step<GROW, CHAIN>(x[2 * k], x[2 * k + 1], tt[3 + k].x, tt[3 + k].y, q, q2);
   } else {
     // stages ls, ls + 1, ls + 2 of the inverse (bounds 2^s q when growing)
     const uint64_t c0 = GROW ? q << ls : 0;
@@ -222,7 +222,7 @@ __device__ __forceinline__ void load_tw8(ulonglong2* tt, const ulonglong2* t8, u
   for (int k = 0; k < 7; k++) tt[k] = T[k];
 }
 
-template <bool INV, bool GROW = false>
+template <bool INV, bool GROW = false, bool CHAIN = true>
 __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, uint32_t chunk,
                                        int log_n, const ulonglong2* t8, uint64_t q, uint64_t q2) {
   const uint32_t blk8 = g >> ls, r = g & ((1u << ls) - 1);
@@ -232,7 +232,7 @@ __device__ __forceinline__ void round8(uint64_t* sm, uint32_t g, uint32_t ls, ui
   for (int k = 0; k < 8; k++) x[k] = sm[swz(base + ((uint32_t)k << ls))];
   ulonglong2 tt[7];
   load_tw8(tt, t8, ls, (chunk << (CHUNK_LOG - ls - 3)) + blk8, log_n);
-  bfly8<INV, GROW>(x, tt, ls, q, q2);
+  bfly8<INV, GROW, CHAIN>(x, tt, ls, q, q2);
 #pragma unroll
   for (int k = 0; k < 8; k++) sm[swz(base + ((uint32_t)k << ls))] = x[k];
 }
@@ -285,6 +285,7 @@ constexpr int MAX_SRC = 16;
 
 // plain forward NTT of pattern-selected rows
 struct DescPlain {
+  static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_FWD;
   static constexpr bool FOLD1 = false;  // see DescModUp
   uint64_t* base;
@@ -305,6 +306,7 @@ struct DescPlain {
 
 // ModUp target row: sum_a xs[a][i] * [Dhat_a]_{m} mod m, then NTT; digit rows copy d.
 struct DescModUp {
+  static constexpr bool CHAIN = false;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_MODUP;
   // The forward transform's first stage multiplies the upper half of the
   // row by the single twiddle w = psi^(N/2); the upper half is loaded with
@@ -351,18 +353,18 @@ struct DescModUp {
     uint64_t acc = 0;
     if (grow) {  // lazy: each term below 4m, the sum below 4 alpha m (the transform tolerates it)
       for (int a = 0; a < r.n_src; a++)
-        acc += shoup_approx(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
+        acc += shoup_approx_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
       return acc;
     }
     for (int a = 0; a < r.n_src; a++)
-      acc = add_mod(acc, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
+      acc = add_mod(acc, mul_shoup_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
     return acc;
   }
   // the upper-half load times w (moduli below 2^50): below 4 n_src m
   __device__ uint64_t load_w(const Row& r, uint32_t i, const uint64_t* kc) const {
     uint64_t acc = 0;
     for (int a = 0; a < r.n_src; a++)
-      acc += shoup_approx(r.src[(size_t)a * N + i], kc[2 * MAX_SRC + a], kc[3 * MAX_SRC + a], r.aux);
+      acc += shoup_approx_t<CHAIN>(r.src[(size_t)a * N + i], kc[2 * MAX_SRC + a], kc[3 * MAX_SRC + a], r.aux);
     return acc;
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
@@ -375,22 +377,24 @@ struct DescModUp {
 // Exact: in [0, m). Growth-tolerant transforms (m < 2^50) take the lazy form:
 // three-product Shoup terms (each below 4m) plus 256 m - u [M]_m (u <= 255),
 // a value congruent to the exact one and below (4 n_src + 256) m < 2^60.
+template <bool CHAIN>
 __device__ __forceinline__ uint64_t conv_load(const Row& r, uint32_t i, const uint64_t* kc,
                                               bool grow, size_t N) {
   const uint64_t m = r.aux;
   uint64_t s = 0;
   if (grow) {
     for (int a = 0; a < r.n_src; a++)
-      s += shoup_approx(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
+      s += shoup_approx_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
     return s + (256 * m - (uint64_t)r.ov[i] * r.km);
   }
   for (int a = 0; a < r.n_src; a++)
-    s = add_mod(s, mul_shoup(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
-  return sub_mod(s, mul_shoup((uint64_t)r.ov[i], r.km, r.kms, m), m);
+    s = add_mod(s, mul_shoup_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
+  return sub_mod(s, mul_shoup_t<CHAIN>((uint64_t)r.ov[i], r.km, r.kms, m), m);
 }
 
 // ModDown output row i of (b,k): (acc_i - NTT(sum_a y_a [Phat_a]_{q_i})) * P^-1
 struct DescModDown {
+  static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_MODDOWN;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* acc;  // [BK][rows][N]; P rows already inverse-transformed and scaled
@@ -424,7 +428,7 @@ struct DescModDown {
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
-    return conv_load(r, i, kc, grow, N);
+    return conv_load<CHAIN>(r, i, kc, grow, N);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
@@ -433,6 +437,7 @@ struct DescModDown {
 
 // Rescale output row t of poly p: (c_t - NTT(centred(last) mod q_t)) * q_level^-1
 struct DescRescale {
+  static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* in;    // [polys][level+1][N]
@@ -469,6 +474,7 @@ struct DescRescale {
 // with `last` the coefficient form of k c_level (the inverse transform's post
 // factor carries k) and c read in place (poly p at in + p in_stride).
 struct DescRescaleScaled {
+  static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* in;
@@ -548,7 +554,7 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
         const ulonglong2 tv = ctw[m + i];
 #pragma unroll
         for (int jj = 0; jj < t1; jj++)
-          ct_step<GROW>(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
+          ct_step<GROW, D::CHAIN>(x[i * 2 * t1 + jj], x[i * 2 * t1 + jj + t1], tv.x, tv.y, q, q2);
       }
     }
 #pragma unroll
@@ -570,8 +576,8 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
     uint64_t* s = sm + lc * CHUNK;
 #pragma unroll
     for (int ls = 9; ls >= 0; ls -= 3) {
-      round8<false, GROW>(s, g, ls, chunk, log_n, t8, q, q2);
-      round8<false, GROW>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
+      round8<false, GROW, D::CHAIN>(s, g, ls, chunk, log_n, t8, q, q2);
+      round8<false, GROW, D::CHAIN>(s + CHUNK, g, ls, chunk + 1, log_n, t8, q, q2);
       __syncthreads();
     }
     // stored through shared memory so that a warp writes 256 contiguous
@@ -589,6 +595,7 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
 // y_m the D rows of acc (level .. level+alpha) already inverse-transformed and
 // scaled by (M/m)^-1, with y_level = P d_k + acc_k on q_level.
 struct DescRelinRescale {
+  static constexpr bool CHAIN = false;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_RELIN_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
   const uint64_t* acc;    // [BK][rows][N]
@@ -630,11 +637,11 @@ struct DescRelinRescale {
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
-    return conv_load(r, i, kc, grow, N);
+    return conv_load<CHAIN>(r, i, kc, grow, N);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
-    const uint64_t y = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
-    r.mid[i] = r.src3 ? add_mod(mul_shoup(r.src3[i], r.k2, r.k2s, q), y, q) : y;
+    const uint64_t y = mul_shoup_t<CHAIN>(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+    r.mid[i] = r.src3 ? add_mod(mul_shoup_t<CHAIN>(r.src3[i], r.k2, r.k2s, q), y, q) : y;
   }
 };
 
