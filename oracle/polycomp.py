@@ -4,10 +4,12 @@ Algorithm 2 builds the order-0 B-spline indicators from PolyComp(a, 0), which
 the paper evaluates with the composite minimax polynomials of Lee et al.
 (2021) without giving their degrees. The construction here (a reading):
 
-* the composite approximates sign(a) on [-A, -eps] u [eps, A] (A = 1/1.1, the
-  bound of the comparison inputs; eps the width left to the transition);
+* the composite approximates sign(a) on [-1, -eps] u [eps, 1] (eps the width
+  left to the transition): PolyComp's range. The comparison bound R puts
+  the calibration inputs within 1/1.1 of the range, so inputs up to 10 %
+  beyond the calibration set still fall inside it;
 * stage 1 is the odd polynomial of degree d_1 with the smallest maximum error
-  against 1 on [eps, A] (by oddness, against sign on both intervals);
+  against 1 on [eps, 1] (by oddness, against sign on both intervals);
 * stage i + 1 is the odd polynomial of degree d_(i+1) with the smallest
   maximum error against 1 on the image of stage i's interval, which is
   [1 - tau_i, 1 + tau_i] for the stage's error tau_i;
@@ -20,7 +22,7 @@ form the encrypted evaluation takes.
 """
 import numpy as np
 
-A_DEFAULT = 1.0 / 1.1
+A_DEFAULT = 1.0
 
 
 def _basis(x, m, sc):
