@@ -78,6 +78,12 @@ def lib():
         "or_key_product": (None, [vp, vp, i32, vp, u64, vp]),
         "or_qp_mul_plain_acc": (None, [vp, vp, vp, i32, vp]),
         "or_qp_lift": (None, [vp, vp, i32, u64, vp, vp]),
+        "or_encode_complex": (i32, [vp, vp, u64, i32, dbl, vp]),
+        "or_decode_complex": (None, [vp, i32, vp, vp, u64]),
+        "or_encode_plain_complex": (i32, [vp, vp, vp, u64, i32, dbl, vp]),
+        "or_mod_raise": (None, [vp, vp, i32, vp]),
+        "or_sample_sparse_ternary": (None, [u64, i32, i32, vp]),
+        "or_keygen_secret_sparse": (None, [vp, u64, i32, vp, vp]),
         "or_ext_rows": (u64, [vp, i32]),
         "or_galois_elt": (u64, [vp, i64]),
     }

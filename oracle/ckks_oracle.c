@@ -353,8 +353,22 @@ static void dft_radix2(double* xr, double* xi, int log_n, const double* tr,
   }
 }
 
+static int encode_slots(const double* v, const double* vi, uint64_t nv, int log_n, double scale,
+                        int64_t* coeffs);
+
 /* v: nv <= N/2 real slot values (rest zero). coeffs: N int64. */
 int or_encode(const double* v, uint64_t nv, int log_n, double scale, int64_t* coeffs) {
+  return encode_slots(v, NULL, nv, log_n, scale, coeffs);
+}
+
+/* complex slot values re[j] + i im[j] */
+int or_encode_complex(const double* re, const double* im, uint64_t nv, int log_n, double scale,
+                      int64_t* coeffs) {
+  return encode_slots(re, im, nv, log_n, scale, coeffs);
+}
+
+static int encode_slots(const double* v, const double* vi, uint64_t nv, int log_n, double scale,
+                        int64_t* coeffs) {
   const uint64_t n = 1ull << (log_n - 1), M = 2ull << log_n;
   if (nv > n) return OR_ERR_ARG;
   double* tr = malloc(M * sizeof(double));
@@ -364,7 +378,10 @@ int or_encode(const double* v, uint64_t nv, int log_n, double scale, int64_t* co
   uint32_t* kj = malloc(n * sizeof(uint32_t));
   twiddles(log_n, tr, ti);
   slot_index(log_n, kj);
-  for (uint64_t j = 0; j < nv; j++) xr[kj[j]] = v[j];
+  for (uint64_t j = 0; j < nv; j++) {
+    xr[kj[j]] = v[j];
+    if (vi) xi[kj[j]] = vi[j];
+  }
   dft_radix2(xr, xi, log_n, tr, ti, -1);
   const double f = scale / (double)n;
   int rc = OR_OK;
@@ -387,8 +404,19 @@ int or_encode(const double* v, uint64_t nv, int log_n, double scale, int64_t* co
   return rc;
 }
 
+static void decode_slots(const double* m, int log_n, double* out, double* out_im, uint64_t nv);
+
 /* m: N real coefficients already divided by the scale; out: nv slots (real parts) */
 void or_decode(const double* m, int log_n, double* out, uint64_t nv) {
+  decode_slots(m, log_n, out, NULL, nv);
+}
+
+/* the same with the imaginary parts */
+void or_decode_complex(const double* m, int log_n, double* re, double* im, uint64_t nv) {
+  decode_slots(m, log_n, re, im, nv);
+}
+
+static void decode_slots(const double* m, int log_n, double* out, double* out_im, uint64_t nv) {
   const uint64_t n = 1ull << (log_n - 1), M = 2ull << log_n;
   double* tr = malloc(M * sizeof(double));
   double* ti = malloc(M * sizeof(double));
@@ -403,7 +431,10 @@ void or_decode(const double* m, int log_n, double* out, uint64_t nv) {
     xi[i] = mr * ti[i] + mi * tr[i];
   }
   dft_radix2(xr, xi, log_n, tr, ti, +1);
-  for (uint64_t j = 0; j < nv && j < n; j++) out[j] = xr[kj[j]];
+  for (uint64_t j = 0; j < nv && j < n; j++) {
+    out[j] = xr[kj[j]];
+    if (out_im) out_im[j] = xi[kj[j]];
+  }
   free(tr);
   free(ti);
   free(xr);
@@ -580,6 +611,39 @@ void or_ntt_limb(const or_ctx* c, uint64_t* a, int t, int inverse) {
 }
 
 /* secret key in NTT form over all n_qp limbs; also returns the ternary coefficients */
+/*
+ * Sparse ternary secret of Hamming weight h (a bootstrapping key set: the
+ * ModRaise overflow I grows with the secret's weight): positions by a
+ * partial Fisher-Yates shuffle of 0..N-1, step i swapping i with
+ * i + (w mod (N - i)) for the ChaCha20 word w = word32(seed, 4, 0, 2i), the
+ * sign +1 if word32(seed, 4, 0, 2i + 1) is even, else -1.
+ */
+void or_sample_sparse_ternary(uint64_t seed, int log_n, int h, int64_t* s) {
+  const uint64_t N = 1ull << log_n;
+  uint32_t* perm = malloc(N * sizeof(uint32_t));
+  for (uint64_t i = 0; i < N; i++) {
+    perm[i] = (uint32_t)i;
+    s[i] = 0;
+  }
+  for (int i = 0; i < h && (uint64_t)i < N; i++) {
+    const uint64_t j = (uint64_t)i + cc_word32(seed, 4, 0, 2 * (uint64_t)i) % (N - (uint64_t)i);
+    const uint32_t t = perm[i];
+    perm[i] = perm[j];
+    perm[j] = t;
+    s[perm[i]] = (cc_word32(seed, 4, 0, 2 * (uint64_t)i + 1) & 1) ? -1 : 1;
+  }
+  free(perm);
+}
+
+void or_keygen_secret_sparse(const or_ctx* c, uint64_t seed, int h, uint64_t* s_ntt,
+                             int64_t* s_coef) {
+  int64_t* s = malloc(c->N * sizeof(int64_t));
+  or_sample_sparse_ternary(seed, c->log_n, h, s);
+  for (int t = 0; t < c->n_qp; t++) int_to_ntt(c, s, t, s_ntt + (uint64_t)t * c->N);
+  if (s_coef) memcpy(s_coef, s, c->N * sizeof(int64_t));
+  free(s);
+}
+
 void or_keygen_secret(const or_ctx* c, uint64_t seed, uint64_t* s_ntt, int64_t* s_coef) {
   int64_t* s = malloc(c->N * sizeof(int64_t));
   or_sample_ternary(seed, c->log_n, s);
@@ -648,6 +712,37 @@ int or_encode_plain(const or_ctx* c, const double* v, uint64_t nv, int level, do
     for (int t = 0; t <= level; t++) int_to_ntt(c, m, t, pt + (uint64_t)t * c->N);
   free(m);
   return rc;
+}
+
+int or_encode_plain_complex(const or_ctx* c, const double* re, const double* im, uint64_t nv,
+                            int level, double scale, uint64_t* pt) {
+  int64_t* m = malloc(c->N * sizeof(int64_t));
+  int rc = or_encode_complex(re, im, nv, c->log_n, scale, m);
+  if (rc == OR_OK)
+    for (int t = 0; t <= level; t++) int_to_ntt(c, m, t, pt + (uint64_t)t * c->N);
+  free(m);
+  return rc;
+}
+
+/*
+ * ModRaise (bootstrapping): a ciphertext at level 0 ([2][1][N], NTT form
+ * mod q0) read as the centred coefficients of each polynomial, in
+ * (-q0/2, q0/2], and reduced mod q_0 .. q_level: out [2][level+1][N], NTT
+ * form. It decrypts to c0 + c1 s = m + q0 I over the integers, I a small
+ * integer polynomial (|I| below about the secret's Hamming weight).
+ */
+void or_mod_raise(const or_ctx* c, const uint64_t* ct0, int level, uint64_t* out) {
+  const uint64_t N = c->N, q0 = c->mod[0];
+  uint64_t* x = malloc(N * sizeof(uint64_t));
+  int64_t* v = malloc(N * sizeof(int64_t));
+  for (int k = 0; k < 2; k++) {
+    memcpy(x, ct0 + (uint64_t)k * N, N * sizeof(uint64_t));
+    or_ntt_inverse(x, c->log_n, q0, c->psi[0]);
+    for (uint64_t i = 0; i < N; i++) v[i] = x[i] > q0 / 2 ? -(int64_t)(q0 - x[i]) : (int64_t)x[i];
+    for (int t = 0; t <= level; t++) int_to_ntt(c, v, t, out + ((uint64_t)k * (level + 1) + t) * N);
+  }
+  free(x);
+  free(v);
 }
 
 /*

@@ -1,0 +1,174 @@
+"""Pins for the oracle's CKKS bootstrapping (CPU only, N = 2^7).
+
+Each step is checked against what the mathematics fixes rather than against
+itself: the decoding matrix against the canonical embedding (odd powers of a
+primitive 2N-th root of unity), the CoeffToSlot matrices against the
+decoding of random coefficient vectors, ModRaise against the exact
+big-integer identity t = m + q0 I with the Hamming-weight bound on I, the
+conjugation and the dense transform against numpy's complex arithmetic on
+the slots, the modular-reduction interpolant against m / Delta (closed form
+of the scaled sine), and the whole pipeline against the slots it started
+from.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import boot, ckks
+
+H = 16  # Hamming weight of the sparse secret
+
+
+def _setup(q0_bits):
+    ctx = ckks.Ctx(ckks.Params(log_n=7, n_scale=20, n_special=2, q0_bits=q0_bits))
+    return ctx, boot.BootKeys(ctx, 7, h=H)
+
+
+@pytest.fixture(scope="module")
+def c20():
+    """q0 / Delta = 2^20, the gap of the configurations' chains."""
+    return _setup(60)
+
+
+@pytest.fixture(scope="module")
+def c10():
+    return _setup(50)
+
+
+def _complex_ct(ctx, keys, z, level):
+    """A ciphertext at `level` whose slots are the complex z: Re z encrypted,
+    times the plaintext z / Re z, rescaled."""
+    re = np.where(np.abs(z.real) < 0.3, 0.3, z.real)
+    ct = ckks.encrypt(ctx, keys, re, level + 1, 5)
+    S = ckks.plain_scale(ctx, ct.scale, level + 1)
+    pt = boot.encode_complex(ctx, z / re, level + 1, S)
+    prod = np.zeros_like(ct.data)
+    ctx.L_.or_mul_plain(ctx.h, boot.ptr(ct.data), boot.ptr(pt), 2, level + 2, boot.ptr(prod))
+    return ckks.rescale(ctx, ckks.Ct(prod, level + 1, ct.scale * S))
+
+
+def test_sparse_secret_has_weight_h(c20):
+    ctx, keys = c20
+    s = keys.s_coef
+    assert np.count_nonzero(s) == H
+    assert set(np.unique(s[s != 0]).tolist()) <= {-1, 1}
+    s2 = np.zeros(ctx.N, np.int64)
+    ctx.L_.or_sample_sparse_ternary(8, ctx.log_n, H, boot.ptr(s2))
+    assert np.count_nonzero(s2) == H and not np.array_equal(s, s2)
+
+
+def test_decode_matrix_is_canonical_embedding(c20):
+    ctx, _ = c20
+    N, n = ctx.N, ctx.slots
+    E = boot.decode_matrix(ctx)
+    zeta = E[:, 1]
+    # X^i decodes to the i-th powers of the slots' roots
+    for i in (0, 2, 3, 17, N - 1):
+        assert np.abs(E[:, i] - zeta ** i).max() < 1e-12
+    # the roots with their conjugates are exactly the primitive 2N-th roots
+    ang = np.angle(np.concatenate([zeta, zeta.conj()])) / np.pi * N  # odd integers mod 2N
+    k = np.mod(np.rint(ang).astype(int), 2 * N)
+    assert np.abs(np.abs(zeta) - 1).max() < 1e-12
+    assert sorted(k.tolist()) == list(range(1, 2 * N, 2))
+    assert len(set(np.rint(ang[:n]).astype(int).tolist())) == n
+
+
+def test_coeff_to_slot_matrices_invert_decoding(c20):
+    ctx, _ = c20
+    n = ctx.slots
+    E = boot.decode_matrix(ctx)
+    A_lo, B_lo, A_hi, B_hi = boot.coeff_to_slot_matrices(ctx)
+    t = np.random.default_rng(3).normal(size=ctx.N) * 1e3
+    z = E @ t
+    assert np.abs(A_lo @ z + B_lo @ z.conj() - t[:n]).max() < 1e-8
+    assert np.abs(A_hi @ z + B_hi @ z.conj() - t[n:]).max() < 1e-8
+
+
+def test_mod_raise_adds_a_small_multiple_of_q0(c20):
+    ctx, keys = c20
+    z = np.random.default_rng(4).uniform(-1, 1, ctx.slots)
+    ct = ckks.encrypt(ctx, keys, z, 0, 9)
+    raised = boot.mod_raise(ctx, ct)
+    assert raised.level == ctx.L
+    assert np.array_equal(raised.data[:, 0], ct.data[:, 0])
+    q0 = ctx.q[0]
+    m = boot.decrypt_coeffs_crt(ctx, keys, ct)  # centred mod q0
+    t = boot.decrypt_coeffs_crt(ctx, keys, raised)
+    I = [(ti - mi) // q0 for ti, mi in zip(t, m)]
+    assert all((ti - mi) % q0 == 0 for ti, mi in zip(t, m))
+    # |c0 + c1 s| <= (h + 1) q0 / 2 with centred c0, c1 and h entries of s
+    assert max(abs(i) for i in I) <= (H + 1) // 2 + 1
+    assert any(i != 0 for i in I)  # the overflow is really there
+
+
+def test_conjugation_conjugates_the_slots(c20):
+    ctx, keys = c20
+    rng = np.random.default_rng(6)
+    z = rng.uniform(-1, 1, ctx.slots) + 1j * rng.uniform(-1, 1, ctx.slots)
+    ct = _complex_ct(ctx, keys, z, 10)
+    assert np.abs(boot.decrypt_crt(ctx, keys, ct) - z).max() < 1e-6
+    cj = boot.conjugate(ctx, keys, ct)
+    assert np.abs(boot.decrypt_crt(ctx, keys, cj) - z.conj()).max() < 1e-6
+
+
+def test_dense_linear_transform_matches_the_matrix(c20):
+    ctx, keys = c20
+    rng = np.random.default_rng(7)
+    n = ctx.slots
+    U = (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / math.sqrt(2 * n)
+    z = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+    ct = _complex_ct(ctx, keys, z, 12)
+    out = boot.linear_transform(ctx, keys, ct, U)
+    assert out.level == 11
+    assert np.abs(boot.decrypt_crt(ctx, keys, out) - U @ z).max() < 1e-6
+
+
+def test_coeff_to_slot_gives_the_scaled_coefficients(c20):
+    ctx, keys = c20
+    K = 4
+    z = np.random.default_rng(8).uniform(-1, 1, ctx.slots)
+    raised = boot.mod_raise(ctx, ckks.encrypt(ctx, keys, z, 0, 10))
+    t = np.array([float(x) for x in boot.decrypt_coeffs_crt(ctx, keys, raised)])
+    y = t / (raised.scale * 2.0 ** boot.mod_exponent(ctx, K))
+    assert np.abs(y).max() <= 1.0
+    lo, hi = boot.coeff_to_slot(ctx, keys, raised, K)
+    for ct, want in ((lo, y[: ctx.slots]), (hi, y[ctx.slots:])):
+        got = boot.decrypt_crt(ctx, keys, ct)
+        assert np.abs(got.real - want).max() < 1e-9
+        assert np.abs(got.imag).max() < 1e-9
+
+
+@pytest.mark.parametrize("q0_bits,bound", [(60, 1e-8), (50, 1e-9)])
+def test_eval_mod_interpolant_reduces_mod_q0(q0_bits, bound):
+    ctx = ckks.Ctx(ckks.Params(log_n=7, n_scale=20, n_special=2, q0_bits=q0_bits))
+    K, deg = 4, 127
+    coeffs = boot.eval_mod_coeffs(ctx, K, deg)
+    q0, D = float(ctx.q[0]), float(ctx.delta[0])
+    e = boot.mod_exponent(ctx, K)
+    assert 2.0 ** e >= (K + 1) * q0 / D > 2.0 ** (e - 1)
+    c = q0 / D
+    mD = np.linspace(-1, 1, 201)
+    # c / (2 pi) sin(2 pi x / c) = x - (2 pi / c)^2 x^3 / 6 + ...
+    sine_err = (2 * math.pi / c) ** 2 / 6 * np.abs(mD) ** 3
+    for I in range(-K, K + 1):
+        y = (mD * D + q0 * I) / (D * 2.0 ** e)
+        got = np.polynomial.chebyshev.chebval(y, coeffs)
+        assert (np.abs(got - mD) <= sine_err * 1.001 + bound).all(), I
+
+
+@pytest.mark.parametrize("fx,K,bound", [("c10", 4, 1e-4), ("c20", 4, 2e-2)])
+def test_bootstrap_restores_the_slots(fx, K, bound, request):
+    """Precision follows q0 / Delta: EvalMod multiplies the noise of y by
+    about 2^e ~ (K + 1) q0 / Delta, so the configurations' gap of 2^20
+    leaves a few 1e-3 where 2^10 leaves a few 1e-6."""
+    ctx, keys = request.getfixturevalue(fx)
+    z = np.random.default_rng(1).uniform(-1, 1, ctx.slots)
+    ct = ckks.encrypt(ctx, keys, z, 0, 3)
+    out = boot.bootstrap(ctx, keys, ct, K, 127)
+    assert out.level >= 8
+    got = boot.decrypt_crt(ctx, keys, out)
+    assert np.abs(got.real - z).max() < bound
+    assert np.abs(got.imag).max() < bound
+    sq = ckks.mul(ctx, keys, out, out)  # the refreshed levels are usable
+    assert np.abs(ckks.decrypt(ctx, keys, sq) - z * z).max() < 3 * bound
