@@ -9,34 +9,31 @@ Kim and Song 2018, with a polynomial for the modular reduction):
   coefficients decrypt to t = m + q0 I over the integers, I a small integer
   polynomial (|I| bounded by about half the secret's Hamming weight; a
   sparse secret keeps it small).
-* CoeffToSlot: the slots z' = E t / Delta (E the decoding map from N real
-  coefficients to N/2 complex slots) are turned into two ciphertexts whose
-  real slots hold t_j / Delta for the lower and upper halves of the
-  coefficients: [t_lo; t_hi] / Delta = G [z'; conj z'] with G the inverse of
-  [[E_lo, E_hi], [conj E_lo, conj E_hi]], each block applied to z' and to
-  its conjugate (the conjugation automorphism X -> X^-1) as a dense
-  baby-step giant-step linear transform with complex diagonals; then a
-  product by the exact constant 2^-e, 2^e >= (K + 1) c with c = q0 / Delta,
-  gives y = t_j / (Delta 2^e) in [-1, 1]. The diagonals are applied 2^B
-  larger (B = 12) and the constant is 2^-(e + B): the slots after ModRaise
-  reach about 2^27 while y needs about 2^-40 absolute precision, which a
-  diagonal of magnitude 2^-6 rounded at a 2^40 plaintext scale does not
-  give. The constant 2^-(e + B) is applied as a 45-bit integer over two
-  rescales (mul_const_wide): a one-level constant product would realise it
-  as a 5-bit integer. (Folding 1 / ((K + 1) c) into the diagonals instead
-  would leave their encodings about 11 bits.)
+* CoeffToSlot: the slots are z = U w with w = (t_lo + i t_hi) / Delta (the
+  n = N/2 complex coefficients, U the encoder's decoding map). U factors
+  into log2(n) radix-2 stages and a bit reversal (the "special FFT"); the
+  stages' inverses, merged a few at a time into levels of 2^(r+1) - 1
+  cyclic diagonals each and applied by baby-step giant-step with hoisted
+  baby rotations, give n BR(w) (the bit-reversed order is kept: EvalMod is
+  slot-wise and SlotToCoeff undoes it). The conjugation automorphism
+  X -> X^-1 splits real and imaginary parts (the latter times -i, the
+  monomial X^(3N/2)); the exact constant 2^-(e + log2(2n)), applied as a
+  wide integer over two rescales (mul_const_wide), gives
+  y = t_j / (Delta 2^e) in [-1, 1] with 2^e >= (K + 1) c, c = q0 / Delta.
+  The diagonals keep magnitude 1 (the inverse stages' halvings go into the
+  final constant), so their encodings keep the plaintext scale's precision.
 * EvalMod: the Chebyshev interpolant of g(y) = c / (2 pi) sin(2 pi 2^e y / c)
   on [-1, 1] (Paterson-Stockmeyer evaluation, the SiLU evaluator), since
   g(t / (Delta 2^e)) = c / (2 pi) sin(2 pi m / q0) = m / Delta up to a
   relative (2 pi m / q0)^2 / 6.
-* SlotToCoeff: z = E_lo (m_lo / Delta) + E_hi (m_hi / Delta), two dense
-  transforms with complex diagonals on the real-slot ciphertexts.
+* SlotToCoeff: the two real halves joined as m_lo + i m_hi (i = X^(N/2)),
+  then the merged forward stages: U (m / Delta), the original slots.
 
-The dense transforms need N/2 diagonals each, so this form is for small
-rings; a full-size ring takes the factored (FFT-like) transforms instead.
-Every operation is an oracle operation (ciphertext arithmetic of ckks.py and
-the C core), so a GPU schedule of the same steps can be checked word for
-word against it.
+Precision follows q0 / Delta: EvalMod multiplies the absolute noise of y
+(about 2^-30 at 40-bit scale primes) by 2^e, about (K + 1) q0 / Delta. Every
+operation is an oracle operation (ciphertext arithmetic of ckks.py and the
+C core), so a GPU schedule of the same steps can be checked word for word
+against it.
 """
 import math
 
@@ -47,22 +44,14 @@ from ._lib import ptr
 
 
 # ---------------------------------------------------------------- keys
-def boot_steps(ctx):
-    """Rotation steps of the dense transforms: baby steps 1 .. g1 - 1 and
-    giant steps g1 i over the N/2 slots."""
-    n = ctx.slots
-    g1 = 1 << ((n.bit_length() - 1 + 1) // 2)
-    return list(range(1, g1)) + [g1 * i for i in range(1, n // g1)]
-
-
 class BootKeys:
     """The secret (dense ternary, or sparse of Hamming weight h, which keeps
-    the ModRaise overflow small), the relinearisation key, the transforms'
-    rotation keys and the conjugation key (Galois element 2N - 1)."""
+    the ModRaise overflow small), the relinearisation key, rotation keys for
+    `steps` and the conjugation key (Galois element 2N - 1)."""
 
     _switch_key = ckks.Keys._switch_key
 
-    def __init__(self, ctx, seed, h=None):
+    def __init__(self, ctx, seed, steps=(), h=None):
         self.ctx, self.seed, self.h = ctx, seed, h
         self.s = np.zeros((ctx.n_qp, ctx.N), np.uint64)
         self.s_coef = np.zeros(ctx.N, np.int64)
@@ -72,7 +61,7 @@ class BootKeys:
             ctx.L_.or_keygen_secret_sparse(ctx.h, seed, int(h), ptr(self.s), ptr(self.s_coef))
         self.relin = self._switch_key(0)
         self.galois = {}
-        for g in [ctx.galois(t) for t in boot_steps(ctx)] + [2 * ctx.N - 1]:
+        for g in [ctx.galois(t) for t in steps] + [2 * ctx.N - 1]:
             if g != 1 and g not in self.galois:
                 self.galois[g] = self._switch_key(g)
 
@@ -154,37 +143,166 @@ def encode_complex(ctx, z, level, scale):
     return pt
 
 
-def linear_transform(ctx, keys, v, U):
-    """Slots z -> U z (U: N/2 x N/2 complex) by baby-step giant-step over the
-    N/2 cyclic diagonals u_t[s] = U[s][(s + t) mod n], hoisted baby steps;
-    the diagonal products are accumulated and rescaled once per giant step
-    (one level)."""
+def mul_monomial(ctx, a, k):
+    """a X^k (exact, no level): every slot times zeta_j^k; X^(N/2)
+    multiplies every slot by i, since zeta_j^(N/2) = i^(5^j) = i."""
+    k %= 2 * ctx.N
+    l = a.level + 1
+    pt = np.zeros((l, ctx.N), np.uint64)
+    for t in range(l):
+        if k < ctx.N:
+            pt[t, k] = 1
+        else:
+            pt[t, k - ctx.N] = ctx.q[t] - 1
+        ctx.L_.or_ntt_limb(ctx.h, ptr(pt[t]), t, 0)
+    out = np.zeros_like(a.data)
+    ctx.L_.or_mul_plain(ctx.h, ptr(np.ascontiguousarray(a.data)), ptr(pt), 2, l, ptr(out))
+    return ckks.Ct(out, a.level, a.scale)
+
+
+# ---------------------------------------------------------------- the slot transforms
+# Slot j of the encoder holds sum_i w_i zeta_j^i over the n = N/2 complex
+# coefficients w_i = m_i + i m_(i+n), zeta_j = zeta^(5^j mod 2N): z = U w.
+# U factors as F_(log n) ... F_1 BR (decimation in time, BR the bit
+# reversal): stage s pairs slots p and p + h (h = 2^(s-1), blocks of 2h) as
+#   out[p] = x[p] + w_r x[p + h],  out[p + h] = x[p] - w_r x[p + h],
+# r = p mod 2h < h, w_r = exp(2 pi i (5^r mod 8h) / (8h)) (the root of the
+# half-size problem on 2h slots). As cyclic diagonals of the slot vector
+# (offset o: the factor of rot(x, o), rot moving slot p + o to p) a stage has
+# offsets 0, +h, -h; r stages merged have offsets k 2^a, |k| < 2^r.
+def _stage_roots(h):
+    r = np.arange(h)
+    e = np.array([pow(5, int(x), 8 * h) for x in r], dtype=np.float64)
+    ang = 2.0 * math.pi * e / (8.0 * h)
+    return np.cos(ang) + 1j * np.sin(ang)
+
+
+def fft_stage(ctx, s, inverse=False):
+    """{offset: diagonal} of F_s, or of 2 F_s^-1 (inverse): from the pair
+    (u + w v, u - w v) the inverse recovers (2u, 2 conj(w) v)."""
     n = ctx.slots
-    g1 = 1 << ((n.bit_length() - 1 + 1) // 2)
-    g2 = n // g1
-    s = np.arange(n)
-    baby = ckks.rotate_many(ctx, keys, v, list(range(g1)))
+    h = 1 << (s - 1)
+    p = np.arange(n)
+    r = p % (2 * h)
+    lower = r < h
+    w = _stage_roots(h)[np.where(lower, r, r - h)]
+    one, zero = np.ones(n, complex), np.zeros(n, complex)
+    if not inverse:
+        terms = [(0, np.where(lower, one, -w)), (h, np.where(lower, w, zero)),
+                 (-h, np.where(lower, zero, one))]
+    else:
+        terms = [(0, np.where(lower, one, -w.conj())), (h, np.where(lower, one, zero)),
+                 (-h, np.where(lower, zero, w.conj()))]
+    d = {}
+    for o, v in terms:  # offsets mod n: at h = n/2, +h and -h are one rotation
+        d[o % n] = d[o % n] + v if o % n in d else v
+    return d
+
+
+def compose(ctx, A, B):
+    """Diagonals of the product A B (B applied first):
+    (A B)_o = sum over a + b = o (mod n) of A_a (.) rot(B_b, a)."""
+    n = ctx.slots
+    out = {}
+    for a in sorted(A):
+        for b in sorted(B):
+            o = (a + b) % n
+            term = A[a] * np.roll(B[b], -a)
+            out[o] = out[o] + term if o in out else term
+    return out
+
+
+def _groups(n_stages, n_levels, ascending):
+    sizes = [n_stages // n_levels + (1 if i < n_stages % n_levels else 0) for i in range(n_levels)]
+    stages = list(range(1, n_stages + 1)) if ascending else list(range(n_stages, 0, -1))
+    out, k = [], 0
+    for sz in sizes:
+        out.append(stages[k:k + sz])
+        k += sz
+    return out
+
+
+class LinearTransform:
+    """z -> sum_k d_k (.) rot(z, base + k stride), k in [0, len(diags)), by
+    baby-step giant-step: baby steps j stride (j < g1, one hoisted ModUp),
+    giant steps base + g1 i stride; an all-zero diagonal is skipped."""
+
+    def __init__(self, base, stride, diags, g1=None):
+        self.base, self.stride = int(base), int(stride)
+        self.diags = [np.asarray(d, complex) for d in diags]
+        K = len(self.diags)
+        self.g1 = g1 or 1 << max(0, math.ceil(math.log2(math.sqrt(K))))
+        self.g2 = -(-K // self.g1)
+
+    def matrix_apply(self, z):
+        """The transform on plain slots (numpy)."""
+        return sum(d * np.roll(z, -(self.base + k * self.stride)) for k, d in enumerate(self.diags))
+
+    def steps(self, n):
+        st = {(j * self.stride) % n for j in range(1, self.g1)}
+        st |= {(self.base + self.g1 * i * self.stride) % n for i in range(self.g2)}
+        return sorted(st - {0})
+
+
+def transform_levels(ctx, n_levels, inverse):
+    """The merged levels of U's factors: SlotToCoeff (inverse False) applies
+    F_1 .. F_(log n) in that order, CoeffToSlot (inverse True) applies
+    2 F_(log n)^-1 .. 2 F_1^-1. Each level merges consecutive stages with
+    h = 2^a .. 2^(a+r-1): offsets k 2^a, k from -(2^r - 1) to 2^r - 1."""
+    n = ctx.slots
+    log_n = n.bit_length() - 1
+    out = []
+    for grp in _groups(log_n, n_levels, ascending=not inverse):
+        M = None
+        for s in grp:
+            st = fft_stage(ctx, s, inverse)
+            M = st if M is None else compose(ctx, st, M)
+        a, r = min(grp) - 1, len(grp)
+        stride, span = 1 << a, (1 << r) - 1
+        base = -span * stride
+        diags, seen = [], set()
+        for k in range(2 * span + 1):
+            o = (base + k * stride) % n
+            if o in M and o not in seen:
+                diags.append(M[o])
+                seen.add(o)
+            else:
+                diags.append(np.zeros(n, complex))
+        out.append(LinearTransform(base, stride, diags))
+    return out
+
+
+def linear_transform(ctx, keys, v, lt):
+    """The BSGS evaluation of a LinearTransform: per giant step i the
+    products of the baby rotations with the diagonals pre-rotated by
+    -(base + g1 i stride), summed, rescaled once (one level), then rotated
+    by base + g1 i stride."""
+    n = ctx.slots
+    baby = ckks.rotate_many(ctx, keys, v, [j * lt.stride for j in range(lt.g1)])
     lv = v.level
     Spt = ckks.plain_scale(ctx, v.scale, lv)
     z = None
-    for i in range(g2):
+    for i in range(lt.g2):
+        G = lt.base + lt.g1 * i * lt.stride
         acc = None
-        for j in range(g1):
-            t = g1 * i + j
-            d = U[s, (s + t) % n]
-            d = np.roll(d, g1 * i)  # rot(d, -g1 i)
-            pt = encode_complex(ctx, d, lv, Spt)
+        for j in range(lt.g1):
+            k = lt.g1 * i + j
+            if k >= len(lt.diags) or not lt.diags[k].any():
+                continue
+            pt = encode_complex(ctx, np.roll(lt.diags[k], G), lv, Spt)
             prod = np.zeros_like(v.data)
-            ctx.L_.or_mul_plain(ctx.h, ptr(baby[j].data), ptr(pt), 2, lv + 1, ptr(prod))
+            ctx.L_.or_mul_plain(ctx.h, ptr(baby[j * lt.stride].data), ptr(pt), 2, lv + 1, ptr(prod))
             if acc is None:
                 acc = prod
             else:
                 o = np.zeros_like(acc)
                 ctx.L_.or_add(ctx.h, ptr(acc), ptr(prod), 2, lv + 1, 0, ptr(o))
                 acc = o
+        if acc is None:
+            continue
         inner = ckks.rescale(ctx, ckks.Ct(acc, lv, v.scale * Spt))
-        if i > 0:
-            inner = ckks.rotate(ctx, keys, inner, g1 * i)
+        if G % n:
+            inner = ckks.rotate(ctx, keys, inner, G % n)
         z = inner if z is None else ckks.add(ctx, z, inner)
     return z
 
@@ -199,46 +317,52 @@ def mod_raise(ctx, ct, level=None):
     return ckks.Ct(out, level, ct.scale)
 
 
-def coeff_to_slot_matrices(ctx):
-    """(A_lo, B_lo, A_hi, B_hi): t_lo / Delta = A_lo z' + B_lo conj(z'), t_hi
-    likewise."""
-    n = ctx.slots
-    E = decode_matrix(ctx)
-    El, Eh = E[:, :n], E[:, n:]
-    big = np.block([[El, Eh], [El.conj(), Eh.conj()]])
-    Gm = np.linalg.inv(big)
-    return Gm[:n, :n], Gm[:n, n:], Gm[n:, :n], Gm[n:, n:]
-
-
 def mod_exponent(ctx, K):
     """e with 2^e >= (K + 1) q0 / Delta_0: y = t / (Delta 2^e) stays in [-1, 1]."""
     return math.ceil(math.log2((K + 1) * ctx.q[0] / ctx.delta[0]))
 
 
-DIAG_BOOST = 12  # bits by which the CoeffToSlot diagonals are applied larger
+def mul_bigint(ctx, a, k):
+    """a times the integer k of any size: limb t times k mod q_t (the
+    constant polynomial's transform is k in every position)."""
+    l = a.level + 1
+    pt = np.zeros((l, ctx.N), np.uint64)
+    for t in range(l):
+        pt[t, :] = k % ctx.q[t]
+    out = np.zeros_like(a.data)
+    ctx.L_.or_mul_plain(ctx.h, ptr(np.ascontiguousarray(a.data)), ptr(pt), 2, l, ptr(out))
+    return ckks.Ct(out, a.level, a.scale)
 
 
 def mul_const_wide(ctx, a, c):
-    """a * c for a constant far below 1: mul_const realises c as
-    rint(c S) / S with S near Delta, a relative error of 1 / (2 c S) (for
-    c = 2^-35 about 1 %); here c is realised as an integer of about 45 bits,
-    rint(c S2) with S2 = Delta_(l-2) q_l q_(l-1) / scale, and the product is
-    rescaled twice, landing on the canonical scale of level l - 2 (two
-    levels)."""
+    """a * c for a constant far below 1, landing on the canonical scale of
+    level l - 2 (two levels). A one-level constant product realises c as
+    rint(c S) / S with S near the prime size, a relative error 1 / (2 c S)
+    that EvalMod would multiply by about c K q0 / Delta; here c is realised
+    as the integer k = rint(c S2), S2 = Delta_(l-2) q_l q_(l-1) / scale
+    (rounded in double precision, a relative error of 2^-53, the integer
+    exact however large), and the product is rescaled twice."""
     lv = a.level
     S2 = ctx.delta[lv - 2] * float(ctx.q[lv]) * float(ctx.q[lv - 1]) / a.scale
-    k = ckks.round_const(c, S2)
-    once = ckks.rescale(ctx, ckks.Ct(ckks.mul_int(ctx, a, k).data, lv, a.scale * S2))
+    k = int(np.rint(c * S2))
+    once = ckks.rescale(ctx, ckks.Ct(mul_bigint(ctx, a, k).data, lv, a.scale * S2))
     return ckks.rescale(ctx, once)
 
 
-def coeff_to_slot(ctx, keys, ct, K):
-    A_lo, B_lo, A_hi, B_hi = (M * 2.0 ** DIAG_BOOST for M in coeff_to_slot_matrices(ctx))
+def coeff_to_slot(ctx, keys, ct, K, levels):
+    """(y_lo, y_hi): real slots p holding t_(brv(p)) / (Delta 2^e) and
+    t_(n + brv(p)) / (Delta 2^e) for the raised ciphertext's coefficients t.
+    The merged levels of 2 F^-1 give n BR(w), w = (t_lo + i t_hi) / Delta;
+    adding the conjugate gives 2 n Re, subtracting it and multiplying by
+    -i = X^(3N/2) gives 2 n Im; the exact constant 2^-(e + log2(2n)) then
+    brings both into [-1, 1] (two levels)."""
+    for lt in levels:
+        ct = linear_transform(ctx, keys, ct, lt)
     cj = conjugate(ctx, keys, ct)
-    lo = ckks.add(ctx, linear_transform(ctx, keys, ct, A_lo), linear_transform(ctx, keys, cj, B_lo))
-    hi = ckks.add(ctx, linear_transform(ctx, keys, ct, A_hi), linear_transform(ctx, keys, cj, B_hi))
-    f = 2.0 ** -(mod_exponent(ctx, K) + DIAG_BOOST)
-    return mul_const_wide(ctx, lo, f), mul_const_wide(ctx, hi, f)
+    re2 = ckks.add(ctx, ct, cj)
+    im2 = mul_monomial(ctx, ckks.sub(ctx, ct, cj), 3 * ctx.N // 2)
+    f = 2.0 ** -(mod_exponent(ctx, K) + ctx.log_n)
+    return mul_const_wide(ctx, re2, f), mul_const_wide(ctx, im2, f)
 
 
 def eval_mod_coeffs(ctx, K, degree):
@@ -254,19 +378,40 @@ def eval_mod(ctx, keys, ct, K, degree):
     return kan_he.eval_cheb(ctx, keys, ct, eval_mod_coeffs(ctx, K, degree))
 
 
-def slot_to_coeff(ctx, keys, lo, hi):
-    n = ctx.slots
-    E = decode_matrix(ctx)
+def slot_to_coeff(ctx, keys, lo, hi, levels):
+    """z = U (m_lo + i m_hi): the real-slot halves joined by X^(N/2) (times
+    i), then the merged levels of F, which take the bit-reversed order the
+    CoeffToSlot left back to the coefficients' order."""
     lv = min(lo.level, hi.level)
     lo, hi = ckks.level_down(ctx, lo, lv), ckks.level_down(ctx, hi, lv)
-    return ckks.add(ctx, linear_transform(ctx, keys, lo, E[:, :n]),
-                    linear_transform(ctx, keys, hi, E[:, n:]))
+    ct = ckks.add(ctx, lo, mul_monomial(ctx, hi, ctx.N // 2))
+    for lt in levels:
+        ct = linear_transform(ctx, keys, ct, lt)
+    return ct
 
 
-def bootstrap(ctx, keys, ct, K, degree):
+class Plan:
+    """The bootstrapping's fixed parts: the merged transform levels, the
+    overflow bound K (|I| <= K) and the EvalMod polynomial's degree."""
+
+    def __init__(self, ctx, K, degree, cts_levels=2, stc_levels=2):
+        self.K, self.degree = K, degree
+        self.cts = transform_levels(ctx, cts_levels, inverse=True)
+        self.stc = transform_levels(ctx, stc_levels, inverse=False)
+        self.cheb = eval_mod_coeffs(ctx, K, degree)
+
+    def steps(self, ctx):
+        st = set()
+        for lt in self.cts + self.stc:
+            st |= set(lt.steps(ctx.slots))
+        return sorted(st)
+
+
+def bootstrap(ctx, keys, ct, plan):
     """A level-0 ciphertext back at a high level with the same slots (up to
     the precision the modular-reduction polynomial and the noise allow)."""
     raised = mod_raise(ctx, ct)
-    lo, hi = coeff_to_slot(ctx, keys, raised, K)
-    lo, hi = eval_mod(ctx, keys, lo, K, degree), eval_mod(ctx, keys, hi, K, degree)
-    return slot_to_coeff(ctx, keys, lo, hi)
+    lo, hi = coeff_to_slot(ctx, keys, raised, plan.K, plan.cts)
+    lo = kan_he.eval_cheb(ctx, keys, lo, plan.cheb)
+    hi = kan_he.eval_cheb(ctx, keys, hi, plan.cheb)
+    return slot_to_coeff(ctx, keys, lo, hi, plan.stc)

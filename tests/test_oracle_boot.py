@@ -2,8 +2,9 @@
 
 Each step is checked against what the mathematics fixes rather than against
 itself: the decoding matrix against the canonical embedding (odd powers of a
-primitive 2N-th root of unity), the CoeffToSlot matrices against the
-decoding of random coefficient vectors, ModRaise against the exact
+primitive 2N-th root of unity), the factored transforms against that matrix
+and its inverse (numpy), merged levels against their stages, the monomial
+product against multiplication by i, ModRaise against the exact
 big-integer identity t = m + q0 I with the Hamming-weight bound on I, the
 conjugation and the dense transform against numpy's complex arithmetic on
 the slots, the modular-reduction interpolant against m / Delta (closed form
@@ -20,20 +21,29 @@ from oracle import boot, ckks
 H = 16  # Hamming weight of the sparse secret
 
 
-def _setup(q0_bits):
-    ctx = ckks.Ctx(ckks.Params(log_n=7, n_scale=20, n_special=2, q0_bits=q0_bits))
-    return ctx, boot.BootKeys(ctx, 7, h=H)
+def _setup(q0_bits, scale_bits=40, K=4, levels=(2, 2)):
+    ctx = ckks.Ctx(ckks.Params(log_n=7, n_scale=24, n_special=2, q0_bits=q0_bits,
+                               scale_bits=scale_bits))
+    plan = boot.Plan(ctx, K, 127, *levels)
+    lt_steps = [7, 14, 21, 57]  # the generic transform test's rotations
+    return ctx, boot.BootKeys(ctx, 7, plan.steps(ctx) + lt_steps, h=H), plan
 
 
 @pytest.fixture(scope="module")
 def c20():
     """q0 / Delta = 2^20, the gap of the configurations' chains."""
-    return _setup(60)
+    return _setup(60, levels=(3, 3))
 
 
 @pytest.fixture(scope="module")
 def c10():
     return _setup(50)
+
+
+@pytest.fixture(scope="module")
+def s50():
+    """50-bit scale primes under a 60-bit q0: a bootstrappable chain."""
+    return _setup(60, scale_bits=50)
 
 
 def _complex_ct(ctx, keys, z, level):
@@ -49,7 +59,7 @@ def _complex_ct(ctx, keys, z, level):
 
 
 def test_sparse_secret_has_weight_h(c20):
-    ctx, keys = c20
+    ctx, keys, _ = c20
     s = keys.s_coef
     assert np.count_nonzero(s) == H
     assert set(np.unique(s[s != 0]).tolist()) <= {-1, 1}
@@ -59,7 +69,7 @@ def test_sparse_secret_has_weight_h(c20):
 
 
 def test_decode_matrix_is_canonical_embedding(c20):
-    ctx, _ = c20
+    ctx, _, _ = c20
     N, n = ctx.N, ctx.slots
     E = boot.decode_matrix(ctx)
     zeta = E[:, 1]
@@ -74,19 +84,83 @@ def test_decode_matrix_is_canonical_embedding(c20):
     assert len(set(np.rint(ang[:n]).astype(int).tolist())) == n
 
 
-def test_coeff_to_slot_matrices_invert_decoding(c20):
-    ctx, _ = c20
+def _dense(n, d):
+    M = np.zeros((n, n), complex)
+    for o, v in d.items():
+        M[np.arange(n), (np.arange(n) + o) % n] += v
+    return M
+
+
+def _bitrev(n):
+    b = n.bit_length() - 1
+    P = np.zeros((n, n))
+    for i in range(n):
+        P[int(format(i, "0%db" % b)[::-1], 2), i] = 1
+    return P
+
+
+def test_special_fft_factors_the_decoding_map(c20):
+    ctx, _, _ = c20
     n = ctx.slots
+    log_n = n.bit_length() - 1
     E = boot.decode_matrix(ctx)
-    A_lo, B_lo, A_hi, B_hi = boot.coeff_to_slot_matrices(ctx)
-    t = np.random.default_rng(3).normal(size=ctx.N) * 1e3
-    z = E @ t
-    assert np.abs(A_lo @ z + B_lo @ z.conj() - t[:n]).max() < 1e-8
-    assert np.abs(A_hi @ z + B_hi @ z.conj() - t[n:]).max() < 1e-8
+    U = E[:, :n]
+    assert np.abs(E[:, n:] - 1j * U).max() < 1e-12  # zeta_j^n = i: z = U (t_lo + i t_hi)
+    F, Fi = np.eye(n), np.eye(n)
+    for s in range(1, log_n + 1):
+        F = _dense(n, boot.fft_stage(ctx, s)) @ F
+    for s in range(log_n, 0, -1):
+        Fi = _dense(n, boot.fft_stage(ctx, s, inverse=True)) @ Fi
+    BR = _bitrev(n)
+    assert np.abs(F @ BR - U).max() < 1e-12
+    assert np.abs(Fi - n * BR @ np.linalg.inv(U)).max() < 1e-11
+    rng = np.random.default_rng(2)
+    z = rng.normal(size=n) + 1j * rng.normal(size=n)
+    for n_levels in (1, 2, 3, log_n):
+        for inverse, want in ((False, F @ z), (True, Fi @ z)):
+            lts = boot.transform_levels(ctx, n_levels, inverse)
+            assert len(lts) == n_levels
+            w = z
+            for lt in lts:
+                assert len(lt.diags) <= 2 * n
+                w = lt.matrix_apply(w)
+            assert np.abs(w - want).max() < 1e-11 * np.abs(want).max()
+
+
+def test_linear_transform_matches_numpy(c20):
+    ctx, keys, _ = c20
+    rng = np.random.default_rng(7)
+    n = ctx.slots
+    diags = [(rng.normal(size=n) + 1j * rng.normal(size=n)) / 3 for _ in range(7)]
+    diags[4][:] = 0  # skipped
+    lt = boot.LinearTransform(-7, 7, diags, g1=4)  # offsets -7, 0, ..., 35
+    assert lt.steps(n) == [7, 14, 21, 57]  # baby 7, 14, 21; giant -7 = 57 and 21
+    z = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+    ct = _complex_ct(ctx, keys, z, 12)
+    out = boot.linear_transform(ctx, keys, ct, lt)
+    assert out.level == 11
+    assert np.abs(boot.decrypt_crt(ctx, keys, out) - lt.matrix_apply(z)).max() < 1e-6
+
+
+def test_monomial_and_wide_constant(c20):
+    ctx, keys, _ = c20
+    rng = np.random.default_rng(9)
+    z = rng.uniform(-1, 1, ctx.slots) + 1j * rng.uniform(-1, 1, ctx.slots)
+    ct = _complex_ct(ctx, keys, z, 10)
+    for k, f in ((ctx.N // 2, 1j), (3 * ctx.N // 2, -1j), (ctx.N, -1), (1, None)):
+        got = boot.decrypt_crt(ctx, keys, boot.mul_monomial(ctx, ct, k))
+        if f is None:  # X multiplies slot j by zeta_j = E[j, 1]
+            f = boot.decode_matrix(ctx)[:, 1]
+        assert np.abs(got - f * z).max() < 1e-6
+    big = ckks.encrypt(ctx, keys, rng.uniform(-1, 1, ctx.slots) * 2.0 ** 20, 12, 4)
+    vals = boot.decrypt_crt(ctx, keys, big).real
+    out = boot.mul_const_wide(ctx, big, 2.0 ** -30)
+    assert out.level == 10 and abs(out.scale / ctx.delta[10] - 1) < 2 ** -30
+    assert np.abs(boot.decrypt_crt(ctx, keys, out).real - vals * 2.0 ** -30).max() < 1e-10
 
 
 def test_mod_raise_adds_a_small_multiple_of_q0(c20):
-    ctx, keys = c20
+    ctx, keys, _ = c20
     z = np.random.default_rng(4).uniform(-1, 1, ctx.slots)
     ct = ckks.encrypt(ctx, keys, z, 0, 9)
     raised = boot.mod_raise(ctx, ct)
@@ -103,7 +177,7 @@ def test_mod_raise_adds_a_small_multiple_of_q0(c20):
 
 
 def test_conjugation_conjugates_the_slots(c20):
-    ctx, keys = c20
+    ctx, keys, _ = c20
     rng = np.random.default_rng(6)
     z = rng.uniform(-1, 1, ctx.slots) + 1j * rng.uniform(-1, 1, ctx.slots)
     ct = _complex_ct(ctx, keys, z, 10)
@@ -112,28 +186,17 @@ def test_conjugation_conjugates_the_slots(c20):
     assert np.abs(boot.decrypt_crt(ctx, keys, cj) - z.conj()).max() < 1e-6
 
 
-def test_dense_linear_transform_matches_the_matrix(c20):
-    ctx, keys = c20
-    rng = np.random.default_rng(7)
-    n = ctx.slots
-    U = (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / math.sqrt(2 * n)
-    z = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
-    ct = _complex_ct(ctx, keys, z, 12)
-    out = boot.linear_transform(ctx, keys, ct, U)
-    assert out.level == 11
-    assert np.abs(boot.decrypt_crt(ctx, keys, out) - U @ z).max() < 1e-6
-
-
 def test_coeff_to_slot_gives_the_scaled_coefficients(c20):
-    ctx, keys = c20
-    K = 4
-    z = np.random.default_rng(8).uniform(-1, 1, ctx.slots)
+    ctx, keys, plan = c20
+    n = ctx.slots
+    z = np.random.default_rng(8).uniform(-1, 1, n)
     raised = boot.mod_raise(ctx, ckks.encrypt(ctx, keys, z, 0, 10))
     t = np.array([float(x) for x in boot.decrypt_coeffs_crt(ctx, keys, raised)])
-    y = t / (raised.scale * 2.0 ** boot.mod_exponent(ctx, K))
+    y = t / (raised.scale * 2.0 ** boot.mod_exponent(ctx, plan.K))
     assert np.abs(y).max() <= 1.0
-    lo, hi = boot.coeff_to_slot(ctx, keys, raised, K)
-    for ct, want in ((lo, y[: ctx.slots]), (hi, y[ctx.slots:])):
+    lo, hi = boot.coeff_to_slot(ctx, keys, raised, plan.K, plan.cts)
+    br = _bitrev(n).argmax(axis=1)  # slot p holds coefficient brv(p)
+    for ct, want in ((lo, y[:n][br]), (hi, y[n:][br])):
         got = boot.decrypt_crt(ctx, keys, ct)
         assert np.abs(got.real - want).max() < 1e-9
         assert np.abs(got.imag).max() < 1e-9
@@ -157,15 +220,16 @@ def test_eval_mod_interpolant_reduces_mod_q0(q0_bits, bound):
         assert (np.abs(got - mD) <= sine_err * 1.001 + bound).all(), I
 
 
-@pytest.mark.parametrize("fx,K,bound", [("c10", 4, 1e-4), ("c20", 4, 2e-2)])
-def test_bootstrap_restores_the_slots(fx, K, bound, request):
-    """Precision follows q0 / Delta: EvalMod multiplies the noise of y by
-    about 2^e ~ (K + 1) q0 / Delta, so the configurations' gap of 2^20
-    leaves a few 1e-3 where 2^10 leaves a few 1e-6."""
-    ctx, keys = request.getfixturevalue(fx)
+@pytest.mark.parametrize("fx,bound", [("c20", 2e-2), ("c10", 1e-4), ("s50", 1e-6)])
+def test_bootstrap_restores_the_slots(fx, bound, request):
+    """Precision follows q0 / Delta and the scale: EvalMod multiplies the
+    noise of y by about 2^e ~ (K + 1) q0 / Delta, so 40-bit scale primes
+    under a 60-bit q0 (the configurations' chains) leave a few 1e-3, a
+    50-bit q0 a few 1e-6 and 50-bit scale primes under a 60-bit q0 1e-7."""
+    ctx, keys, plan = request.getfixturevalue(fx)
     z = np.random.default_rng(1).uniform(-1, 1, ctx.slots)
     ct = ckks.encrypt(ctx, keys, z, 0, 3)
-    out = boot.bootstrap(ctx, keys, ct, K, 127)
+    out = boot.bootstrap(ctx, keys, ct, plan)
     assert out.level >= 8
     got = boot.decrypt_crt(ctx, keys, out)
     assert np.abs(got.real - z).max() < bound
