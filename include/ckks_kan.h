@@ -48,6 +48,8 @@ typedef struct ckks_ctx ckks_ctx;
 typedef struct ckks_keys ckks_keys;
 typedef struct ckks_ct ckks_ct;
 typedef struct kan_model kan_model;
+typedef struct ckks_lt ckks_lt;
+typedef struct ckks_boot ckks_boot;
 
 const char* ckks_strerror(int code);
 const char* ckks_last_error(void);
@@ -248,6 +250,105 @@ int ckks_rotate(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, int32_t
  * outs[i] receives the rotation by steps[i]; bit-identical to ckks_rotate. */
 int ckks_rotate_hoisted(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in,
                         const int32_t* steps, size_t n_steps, ckks_ct** outs);
+
+/* ------------------------------------------------------------ bootstrapping
+ * The paper's parameter sets bootstrap as in Lee et al. 2022 (Experiment
+ * Setup): ModRaise, CoeffToSlot, EvalMod, SlotToCoeff. Slot j of the
+ * encoder holds sum_i w_i zeta_j^i, w_i = m_i + i m_(i+N/2),
+ * zeta_j = exp(i pi 5^j / N); rot(x, t) moves slot j + t to slot j.
+ *
+ * Keys with a sparse ternary secret of Hamming weight `hamming_weight`
+ * (0: the dense ternary secret of ckks_keygen, identical keys) and, if
+ * `conjugation`, the key of the Galois element 2N - 1 (X -> X^-1, the
+ * slots' complex conjugates). Sparse draw: partial Fisher-Yates shuffle on
+ * the ChaCha20 stream (seed, domain 4, id 0), step i swapping position i
+ * with i + w32[2i] mod (N - i) and giving the drawn position the sign -1 if
+ * w32[2i+1] is odd, else +1. */
+int ckks_keygen_ex(ckks_ctx* ctx, uint64_t seed, int hamming_weight, const int32_t* rot_steps,
+                   size_t n_steps, int conjugation, ckks_keys** out);
+/* ModRaise: a level-0 batch read over limbs 0..level (the centred residues
+ * mod q0 of each coefficient reduced mod every q_t); same scale.
+ * CKKS_ERR_LEVEL unless `in` is at level 0 and level <= L. */
+int ckks_mod_raise(ckks_ctx* ctx, const ckks_ct* in, int level, ckks_ct** out);
+/* X -> X^(2N-1) (the conjugation key is needed): slots conjugated. */
+int ckks_conjugate(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, ckks_ct** out);
+/* Times the monomial X^k (k taken mod 2N): exact, no level. Slot j is
+ * multiplied by zeta_j^k; X^(N/2) multiplies every slot by i. */
+int ckks_mul_monomial(ckks_ctx* ctx, const ckks_ct* in, int64_t k, ckks_ct** out);
+/* Times a constant far below 1 (two levels, canonical scale of level - 2):
+ * the integer rint(value S2), S2 = Delta_(l-2) q_l q_(l-1) / scale, of any
+ * size, applied by its residues, then two rescales. CKKS_ERR_LEVEL below
+ * level 2. */
+int ckks_mul_const_wide(ckks_ctx* ctx, const ckks_ct* in, double value, ckks_ct** out);
+
+/* A slot linear transform z -> sum_k d_k (.) rot(z, base + k stride),
+ * k < n_diag, for inputs at `level` with scale `in_scale` (0: Delta_level);
+ * re / im: host [n_diag][N/2] real and imaginary parts of the diagonals (an
+ * all-zero diagonal is skipped), copied and encoded at creation (device
+ * plaintexts [nonzero][level+1][N]). Applied by baby-step giant-step with g1
+ * baby steps (0: the least power of two whose square is >= n_diag): it takes
+ * one level and lands on the canonical scale. Rotation keys: see
+ * ckks_lt_rotations. */
+int ckks_lt_create(ckks_ctx* ctx, int level, double in_scale, int64_t base, int64_t stride,
+                   size_t n_diag, const double* re, const double* im, int g1, ckks_lt** out);
+int ckks_lt_destroy(ckks_lt* lt);
+/* Rotation steps the transform uses (baby steps j stride, giant steps
+ * base + g1 i stride, mod N/2, without 0); *n receives their count. */
+int ckks_lt_rotations(const ckks_lt* lt, int32_t* steps, size_t cap, size_t* n);
+/* CKKS_ERR_LEVEL / CKKS_ERR_SCALE if `in` is not at the transform's level
+ * and input scale; CKKS_ERR_MISSING_KEY for a missing rotation key. */
+int ckks_lt_apply(ckks_ctx* ctx, const ckks_keys* keys, const ckks_lt* lt, const ckks_ct* in,
+                  ckks_ct** out);
+
+/* A bootstrapping plan computed by the library: overflow bound K (the
+ * ModRaise multiple |I| <= K), EvalMod by the Chebyshev interpolant of
+ * degree `degree` of (c / 2 pi) sin(2 pi 2^e y / c), c = q0 / Delta_0,
+ * 2^e >= (K + 1) c; CoeffToSlot and SlotToCoeff as cts_levels and
+ * stc_levels merged levels of the special-FFT stages (log2(N/2) stages in
+ * near-equal groups). CoeffToSlot starts at level L on inputs of scale
+ * Delta_0; the output comes out at L - cts_levels - 2 - depth(degree) -
+ * stc_levels. CKKS_ERR_LEVEL if the chain is too short. */
+int ckks_boot_create(ckks_ctx* ctx, int K, int degree, int cts_levels, int stc_levels,
+                     ckks_boot** out);
+/* The same from given parts: exponent e, EvalMod's Chebyshev coefficients,
+ * the CoeffToSlot and SlotToCoeff transforms in application order (borrowed:
+ * they must outlive the plan). */
+int ckks_boot_create_ex(ckks_ctx* ctx, int e, const double* cheb, size_t n_cheb,
+                        const ckks_lt* const* cts, size_t n_cts, const ckks_lt* const* stc,
+                        size_t n_stc, ckks_boot** out);
+int ckks_boot_destroy(ckks_boot* boot);
+/* e, the level CoeffToSlot and SlotToCoeff start at, the number of
+ * Chebyshev coefficients (each pointer may be NULL). */
+int ckks_boot_info(const ckks_boot* boot, int* e, int* cts_level, int* stc_level,
+                   size_t* n_cheb);
+int ckks_boot_coefficients(const ckks_boot* boot, double* cheb, size_t cap);
+/* base, stride and diagonal count of transform `index` (inverse != 0:
+ * CoeffToSlot). */
+int ckks_boot_diagonals(const ckks_boot* boot, int inverse, size_t index, int64_t* base,
+                        int64_t* stride, size_t* n_diag);
+/* The library's merged levels for n_levels groups (inverse != 0: the
+ * CoeffToSlot factors 2 F^-1): level `index`'s base, stride, count and, if
+ * re and im are given, its diagonals ([n_diag][N/2], cap doubles each). */
+int ckks_boot_levels(ckks_ctx* ctx, int n_levels, int inverse, size_t index, double* re,
+                     double* im, size_t cap, int64_t* base, int64_t* stride, size_t* n_diag);
+/* Every rotation step of the plan's transforms (keys for ckks_keygen_ex,
+ * with conjugation). */
+int ckks_boot_rotations(const ckks_boot* boot, int32_t* steps, size_t cap, size_t* n);
+/* The steps one by one: CoeffToSlot of a raised batch into the two real-slot
+ * halves y_lo, y_hi (slot p holding t_(brv(p)) / (Delta_0 2^e) and
+ * t_(N/2 + brv(p)) / (Delta_0 2^e)); EvalMod of one half; SlotToCoeff of the
+ * two reduced halves. */
+int ckks_boot_coeff_to_slot(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* boot,
+                            const ckks_ct* raised, ckks_ct** lo, ckks_ct** hi);
+int ckks_boot_eval_mod(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* boot,
+                       const ckks_ct* in, ckks_ct** out);
+int ckks_boot_slot_to_coeff(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* boot,
+                            const ckks_ct* lo, const ckks_ct* hi, ckks_ct** out);
+/* The whole refresh of a level-0 batch: ModRaise to the CoeffToSlot level,
+ * CoeffToSlot, EvalMod of both halves, SlotToCoeff; the slots come back up
+ * to the plan's precision at the level ckks_boot_create states. */
+int ckks_bootstrap(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* boot,
+                   const ckks_ct* in, ckks_ct** out);
 
 /* ------------------------------------------------------------ encrypted KAN
  * One KAN layer (paper, Method): n_in -> n_out with a uniform grid of G

@@ -53,6 +53,31 @@ SIGNATURES = {
     "ckks_autotune_ntt": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "ckks_set_ntt_shape": (c_i32, [c_vp, c_i32, c_i32]),
     "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
+    "ckks_keygen_ex": (c_i32, [c_vp, c_u64, c_i32, c_vp, c_sz, c_i32, PP]),
+    "ckks_mod_raise": (c_i32, [c_vp, c_vp, c_i32, PP]),
+    "ckks_conjugate": (c_i32, [c_vp, c_vp, c_vp, PP]),
+    "ckks_mul_monomial": (c_i32, [c_vp, c_vp, c_i64, PP]),
+    "ckks_mul_const_wide": (c_i32, [c_vp, c_vp, c_dbl, PP]),
+    "ckks_lt_create": (c_i32, [c_vp, c_i32, c_dbl, c_i64, c_i64, c_sz, c_vp, c_vp, c_i32, PP]),
+    "ckks_lt_destroy": (c_i32, [c_vp]),
+    "ckks_lt_rotations": (c_i32, [c_vp, c_vp, c_sz, ctypes.POINTER(c_sz)]),
+    "ckks_lt_apply": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
+    "ckks_boot_create": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_i32, PP]),
+    "ckks_boot_create_ex": (c_i32, [c_vp, c_i32, c_vp, c_sz, c_vp, c_sz, c_vp, c_sz, PP]),
+    "ckks_boot_destroy": (c_i32, [c_vp]),
+    "ckks_boot_info": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
+                               ctypes.POINTER(c_i32), ctypes.POINTER(c_sz)]),
+    "ckks_boot_coefficients": (c_i32, [c_vp, c_vp, c_sz]),
+    "ckks_boot_diagonals": (c_i32, [c_vp, c_i32, c_sz, ctypes.POINTER(c_i64),
+                                    ctypes.POINTER(c_i64), ctypes.POINTER(c_sz)]),
+    "ckks_boot_levels": (c_i32, [c_vp, c_i32, c_i32, c_sz, c_vp, c_vp, c_sz,
+                                 ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                                 ctypes.POINTER(c_sz)]),
+    "ckks_boot_rotations": (c_i32, [c_vp, c_vp, c_sz, ctypes.POINTER(c_sz)]),
+    "ckks_boot_coeff_to_slot": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP, PP]),
+    "ckks_boot_eval_mod": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
+    "ckks_boot_slot_to_coeff": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, PP]),
+    "ckks_bootstrap": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
     "ckks_keys_export_switch": (c_i32, [c_vp, c_u64, c_vp, c_sz]),
@@ -231,11 +256,19 @@ class Context:
 
 
 class Keys:
-    def __init__(self, ctx, seed, rot_steps=()):
+    """Secret, relinearisation and Galois keys. hamming_weight > 0 draws a
+    sparse secret of that weight; conjugation adds the key of X -> X^-1."""
+
+    def __init__(self, ctx, seed, rot_steps=(), hamming_weight=0, conjugation=False):
         steps = np.ascontiguousarray(list(rot_steps), dtype=np.int32)
         h = c_vp()
-        check(lib().ckks_keygen(ctx.h, seed, _p(steps) if len(steps) else None, len(steps),
-                                ctypes.byref(h)))
+        if hamming_weight or conjugation:
+            check(lib().ckks_keygen_ex(ctx.h, seed, int(hamming_weight),
+                                       _p(steps) if len(steps) else None, len(steps),
+                                       int(bool(conjugation)), ctypes.byref(h)))
+        else:
+            check(lib().ckks_keygen(ctx.h, seed, _p(steps) if len(steps) else None, len(steps),
+                                    ctypes.byref(h)))
         self.h, self.ctx = h, ctx
 
     def close(self):
@@ -398,6 +431,137 @@ def rotate_hoisted(ctx, keys, a, steps):
     hs = (c_vp * len(s))()
     check(lib().ckks_rotate_hoisted(ctx.h, keys.h, a.h, _p(s), len(s), hs))
     return [Ciphertext(ctx, c_vp(h)) for h in hs]
+
+
+# ---------------------------------------------------------------- bootstrapping
+def mod_raise(ctx, a, level=None):
+    return _out(ctx, lib().ckks_mod_raise, ctx.h, a.h, ctx.L if level is None else level)
+
+
+def conjugate(ctx, keys, a):
+    return _out(ctx, lib().ckks_conjugate, ctx.h, keys.h, a.h)
+
+
+def mul_monomial(ctx, a, k):
+    return _out(ctx, lib().ckks_mul_monomial, ctx.h, a.h, int(k))
+
+
+def mul_const_wide(ctx, a, value):
+    return _out(ctx, lib().ckks_mul_const_wide, ctx.h, a.h, float(value))
+
+
+def _steps(fn, h):
+    n = c_sz()
+    check(fn(h, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, np.int32)
+    if n.value:
+        check(fn(h, _p(out), n.value, ctypes.byref(n)))
+    return [int(x) for x in out]
+
+
+class LinearTransform:
+    """z -> sum_k d_k (.) rot(z, base + k stride): diags [n_diag][N/2]
+    complex, encoded for inputs at `level` with scale in_scale (0: canonical)."""
+
+    def __init__(self, ctx, level, base, stride, diags, g1=0, in_scale=0.0):
+        d = np.asarray(diags, dtype=complex)
+        if d.ndim != 2 or d.shape[1] != ctx.slots:
+            raise ValueError("diagonals must be [n_diag][N/2]")
+        re = np.ascontiguousarray(d.real, dtype=np.float64)
+        im = np.ascontiguousarray(d.imag, dtype=np.float64)
+        h = c_vp()
+        check(lib().ckks_lt_create(ctx.h, level, float(in_scale), int(base), int(stride), d.shape[0],
+                                   _p(re), _p(im), int(g1), ctypes.byref(h)))
+        self.h, self.ctx, self.level = h, ctx, level
+
+    def rotations(self):
+        return _steps(lib().ckks_lt_rotations, self.h)
+
+    def apply(self, keys, a):
+        return _out(self.ctx, lib().ckks_lt_apply, self.ctx.h, keys.h, self.h, a.h)
+
+    def close(self):
+        if self.h:
+            lib().ckks_lt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BootPlan:
+    """A bootstrapping plan: BootPlan(ctx, K, degree, cts_levels, stc_levels)
+    computed by the library, or BootPlan.from_parts(ctx, e, cheb, cts, stc)
+    from given transforms (kept alive by the plan object)."""
+
+    def __init__(self, ctx, K=None, degree=None, cts_levels=3, stc_levels=3, _h=None, _keep=()):
+        if _h is None:
+            _h = c_vp()
+            check(lib().ckks_boot_create(ctx.h, K, degree, cts_levels, stc_levels, ctypes.byref(_h)))
+        self.h, self.ctx, self._keep = _h, ctx, list(_keep)
+        e, lc, ls, nc = c_i32(), c_i32(), c_i32(), c_sz()
+        check(lib().ckks_boot_info(self.h, ctypes.byref(e), ctypes.byref(lc), ctypes.byref(ls),
+                                   ctypes.byref(nc)))
+        self.e, self.cts_level, self.stc_level, self.n_cheb = e.value, lc.value, ls.value, nc.value
+
+    @classmethod
+    def from_parts(cls, ctx, e, cheb, cts, stc):
+        cf = np.ascontiguousarray(cheb, dtype=np.float64)
+        a = (c_vp * len(cts))(*[t.h for t in cts])
+        b = (c_vp * len(stc))(*[t.h for t in stc])
+        h = c_vp()
+        check(lib().ckks_boot_create_ex(ctx.h, int(e), _p(cf), len(cf), a, len(cts), b, len(stc),
+                                        ctypes.byref(h)))
+        return cls(ctx, _h=h, _keep=list(cts) + list(stc))
+
+    def rotations(self):
+        return _steps(lib().ckks_boot_rotations, self.h)
+
+    def coefficients(self):
+        out = np.zeros(self.n_cheb)
+        check(lib().ckks_boot_coefficients(self.h, _p(out), len(out)))
+        return out
+
+    def coeff_to_slot(self, keys, raised):
+        lo, hi = c_vp(), c_vp()
+        check(lib().ckks_boot_coeff_to_slot(self.ctx.h, keys.h, self.h, raised.h,
+                                            ctypes.byref(lo), ctypes.byref(hi)))
+        return Ciphertext(self.ctx, lo), Ciphertext(self.ctx, hi)
+
+    def eval_mod(self, keys, a):
+        return _out(self.ctx, lib().ckks_boot_eval_mod, self.ctx.h, keys.h, self.h, a.h)
+
+    def slot_to_coeff(self, keys, lo, hi):
+        return _out(self.ctx, lib().ckks_boot_slot_to_coeff, self.ctx.h, keys.h, self.h, lo.h, hi.h)
+
+    def bootstrap(self, keys, a):
+        return _out(self.ctx, lib().ckks_bootstrap, self.ctx.h, keys.h, self.h, a.h)
+
+    def close(self):
+        if self.h:
+            lib().ckks_boot_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def boot_levels(ctx, n_levels, inverse, index):
+    """The library's merged transform level: (base, stride, diags)."""
+    b, s, n = c_i64(), c_i64(), c_sz()
+    check(lib().ckks_boot_levels(ctx.h, n_levels, int(inverse), index, None, None, 0,
+                                 ctypes.byref(b), ctypes.byref(s), ctypes.byref(n)))
+    re = np.zeros((n.value, ctx.N // 2))
+    im = np.zeros_like(re)
+    check(lib().ckks_boot_levels(ctx.h, n_levels, int(inverse), index, _p(re), _p(im), re.size,
+                                 ctypes.byref(b), ctypes.byref(s), ctypes.byref(n)))
+    return b.value, s.value, re + 1j * im
 
 
 def _descs(layers, keep):

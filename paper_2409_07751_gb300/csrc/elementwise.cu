@@ -361,6 +361,21 @@ void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows,
   CK_CUDA(cudaGetLastError());
 }
 
+void k_mul_limbs(Ctx& c, const uint64_t* a, const std::vector<uint64_t>& res, uint64_t* out,
+                 size_t rows, int l) {
+  if (l > MAX_LIMBS || (int)res.size() < l) throw Error(CKKS_ERR_UNSUPPORTED, "limb constants");
+  LimbRes r{};
+  for (int t = 0; t < l; t++) {
+    r.v[t] = res[t];
+    r.s[t] = shoup_h(res[t], c.mod[t]);
+  }
+  const size_t total = rows * c.N;
+  Launch L_(c, K_MUL_INT, 2.0 * total * 8);
+  mul_int_kernel<<<grid_for(total), TPB, 0, c.stream>>>(a, r, out, total, c.log_n, divu(l),
+                                                        c.dmod());
+  CK_CUDA(cudaGetLastError());
+}
+
 void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l) {
   Launch L_(c, K_ADD, 2.0 * B * l * c.N * 8);
   add_int_c0_kernel<<<grid_for(B * l * c.N), TPB, 0, c.stream>>>(a, limb_res(c, k, l), B, c.log_n,

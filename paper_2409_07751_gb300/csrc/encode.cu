@@ -28,12 +28,14 @@ inline unsigned grid_for(size_t total) {
 
 __device__ __forceinline__ uint32_t brv(uint32_t x, int bits) { return __brev(x) >> (32 - bits); }
 
-__global__ void place_kernel(const double* v, size_t nv, double* xr, size_t B, int log_n,
-                             const uint32_t* slot) {
+__global__ void place_kernel(const double* v, const double* vi, size_t nv, double* xr, double* xi,
+                             size_t B, int log_n, const uint32_t* slot) {
   const size_t n = (size_t)1 << (log_n - 1);
   GRID_LOOP(idx, B * nv) {
     const size_t b = idx / nv, j = idx % nv;
-    xr[b * n + brv(slot[j], log_n - 1)] = v[idx];
+    const size_t p = b * n + brv(slot[j], log_n - 1);
+    xr[p] = v[idx];
+    if (vi) xi[p] = vi[idx];
   }
 }
 
@@ -128,7 +130,7 @@ int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double sca
 }
 
 int encode_rows(Ctx& c, const double* d_v, size_t B, size_t nv, int rows, const int16_t* pattern,
-                double scale, uint64_t* pt) {
+                double scale, uint64_t* pt, const double* d_im) {
   const size_t n = c.N / 2;
   if (nv > n) throw Error(CKKS_ERR_INVALID_ARG, "more values than slots");
   DevBuf xr(&c, B * n * 8), xi(&c, B * n * 8), coef(&c, B * c.N * 8);
@@ -137,8 +139,9 @@ int encode_rows(Ctx& c, const double* d_v, size_t B, size_t nv, int rows, const 
   CK_CUDA(cudaMemsetAsync(c.d_flag.p, 0, 4, c.stream));
   if (nv) {
     Launch L_(c, K_ENCODE, 2.0 * B * nv * 8);
-    place_kernel<<<grid_for(B * nv), TPB, 0, c.stream>>>(d_v, nv, static_cast<double*>(xr.p), B,
-                                                         c.log_n, static_cast<const uint32_t*>(c.d_slot.p));
+    place_kernel<<<grid_for(B * nv), TPB, 0, c.stream>>>(
+        d_v, d_im, nv, static_cast<double*>(xr.p), static_cast<double*>(xi.p), B, c.log_n,
+        static_cast<const uint32_t*>(c.d_slot.p));
   }
   run_stages(c, static_cast<double*>(xr.p), static_cast<double*>(xi.p), B, -1);
   const double f = scale / (double)n;

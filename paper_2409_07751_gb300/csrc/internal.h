@@ -283,14 +283,16 @@ void div_p_ql(Ctx& c, uint64_t* acc, size_t B, int level, uint64_t* out);
 // CKKS_ERR_OVERFLOW if a coefficient does not fit int64.
 int encode(Ctx& c, const double* d_v, size_t B, size_t nv, int level, double scale, uint64_t* pt);
 // the same integer coefficients reduced mod the moduli pattern[0 .. rows-1]
-// (e.g. a QP_l plaintext): pt [B][rows][N], NTT form
+// (e.g. a QP_l plaintext): pt [B][rows][N], NTT form; d_im (optional):
+// the slots' imaginary parts, [B][nv] like d_v
 int encode_rows(Ctx& c, const double* d_v, size_t B, size_t nv, int rows, const int16_t* pattern,
-                double scale, uint64_t* pt);
+                double scale, uint64_t* pt, const double* d_im = nullptr);
 // m: [B][N] limb-0 coefficient values (uint64 mod q0); out: device doubles [B][nv]
 void decode_limb0(Ctx& c, const uint64_t* m, size_t B, double scale, double* d_out, size_t nv);
 
 // ---- sampling (sample.cu)
 void sample_ternary(Ctx& c, uint64_t seed, int64_t* out);
+void sample_sparse_ternary(Ctx& c, uint64_t seed, int h, int64_t* out);
 void sample_cbd(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int64_t* out);
 void sample_uniform(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int rows,
                     const int16_t* pattern, uint64_t* out);

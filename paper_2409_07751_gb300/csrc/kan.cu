@@ -740,6 +740,10 @@ int kan_total_depth(const kan_model& M) {
   for (const Layer& L : M.layers) d += layer_depth(L);
   return d;
 }
+Ct cheb_eval(Ctx& c, const ckks_keys& keys, const ckks_ct& y, const std::vector<double>& a) {
+  return eval_cheb(c, keys, y, a);
+}
+int cheb_levels(int degree) { return cheb_depth(degree); }
 }  // namespace ck
 
 extern "C" {

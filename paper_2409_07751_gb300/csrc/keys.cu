@@ -1,6 +1,7 @@
 // Key generation, encryption and decryption.
 //
-// Secret s: ternary, NTT form over every QP modulus. Switching key from s'
+// Secret s: ternary (dense, or sparse of a given Hamming weight), NTT form
+// over every QP modulus. Switching key from s'
 // to s for digit j and modulus t: b = e - a s + [t in D_j] [P]_{q_t} s',
 // a uniform; s' = s^2 (relinearisation) or sigma_g(s) (Galois element g);
 // randomness from object id 2^40 | g << 8 | j. Encryption at level l:
@@ -104,12 +105,16 @@ std::unique_ptr<DevBuf> switch_key(Ctx& c, const ckks_keys& k, uint64_t seed, ui
 
 }  // namespace
 
-std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps) {
+std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps,
+                                  int hamming, bool conjugation) {
   auto k = std::make_unique<ckks_keys>();
   k->ctx = &c;
   const size_t N = c.N;
   DevBuf sc(&c, N * 8);
-  sample_ternary(c, seed, static_cast<int64_t*>(sc.p));
+  if (hamming > 0)
+    sample_sparse_ternary(c, seed, hamming, static_cast<int64_t*>(sc.p));
+  else
+    sample_ternary(c, seed, static_cast<int64_t*>(sc.p));
   k->s = DevBuf(&c, (size_t)c.n_qp * N * 8);
   k_int_to_rns(c, static_cast<int64_t*>(sc.p), k->s.u64(), 1, c.n_qp, c.iota());
   ntt_forward(c, k->s.u64(), c.n_qp, c.iota(), c.n_qp);
@@ -119,6 +124,7 @@ std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64
     if (g == 1 || k->galois.count(g)) continue;
     k->galois[g] = switch_key(c, *k, seed, g, nullptr);
   }
+  if (conjugation) k->galois[2 * N - 1] = switch_key(c, *k, seed, 2 * N - 1, nullptr);
   CK_CUDA(cudaStreamSynchronize(c.stream));
   return k;
 }

@@ -296,12 +296,18 @@ Ct op_mul_sum(Ctx& c, const ckks_keys& keys,
 
 std::vector<Ct> op_rotate_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
                                const std::vector<int64_t>& steps) {
+  std::vector<uint64_t> g;
+  for (int64_t t : steps) g.push_back(c.galois(t));
+  return op_galois_many(c, keys, a, g);
+}
+
+std::vector<Ct> op_galois_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
+                               const std::vector<uint64_t>& galois) {
   std::vector<Ct> out;
   const int l = a.level + 1;
   ConvTables& T = c.tables(a.level);
   DevBuf ext;
-  for (int64_t t : steps) {
-    const uint64_t g = c.galois(t);
+  for (uint64_t g : galois) {
     if (g == 1) {
       out.push_back(ct_copy(c, a));
       continue;

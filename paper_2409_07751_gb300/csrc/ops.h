@@ -47,10 +47,15 @@ Ct op_mul_sum(Ctx& c, const ckks_keys& keys,
 std::vector<Ct> op_rotate_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
                                const std::vector<int64_t>& steps);
 Ct op_rotate(Ctx& c, const ckks_keys& keys, const ckks_ct& a, int64_t step);
+// the automorphisms X -> X^g (g odd) of a, sharing one ModUp
+std::vector<Ct> op_galois_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
+                               const std::vector<uint64_t>& galois);
 Ct op_concat(Ctx& c, const std::vector<const ckks_ct*>& in);
 
-// keys.cu
-std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps);
+// keys.cu: hamming > 0 draws a sparse secret of that weight; conjugation
+// adds the key of the Galois element 2N - 1
+std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps,
+                                  int hamming = 0, bool conjugation = false);
 Ct encrypt(Ctx& c, const ckks_keys& keys, const double* values, size_t B, size_t n, int level,
            uint64_t seed, uint64_t first_index);
 void decrypt(Ctx& c, const ckks_keys& keys, const ckks_ct& ct, double* out, size_t n);
@@ -58,6 +63,9 @@ void decrypt(Ctx& c, const ckks_keys& keys, const ckks_ct& ct, double* out, size
 // elementwise.cu (extra entry points)
 void k_mul_int(Ctx& c, const uint64_t* a, int64_t k, uint64_t* out, size_t rows, int l);
 void k_add_int_c0(Ctx& c, uint64_t* a, int64_t k, size_t B, int l);
+// limb t of every row times res[t] (an integer of any size, by its residues)
+void k_mul_limbs(Ctx& c, const uint64_t* a, const std::vector<uint64_t>& res, uint64_t* out,
+                 size_t rows, int l);
 void k_lincomb_int(Ctx& c, const std::vector<const uint64_t*>& in, const std::vector<int64_t>& k,
                    uint64_t* out, size_t rows, int l);
 void k_rotate_finish(Ctx& c, const uint64_t* a, const uint64_t* ks, const uint32_t* perm,
@@ -80,6 +88,11 @@ void k_qp_lift(Ctx& c, const uint64_t* ct, size_t B, int level, const uint32_t* 
 void k_chunk_sum(Ctx& c, const uint64_t* in, uint64_t* out, size_t B, int K, int l);
 void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,
                       int level, const uint64_t* inv, const uint64_t* invs);
+
+// kan.cu: sum_j a_j T_j(y) (Paterson-Stockmeyer over the Chebyshev basis)
+// and the levels it takes
+Ct cheb_eval(Ctx& c, const ckks_keys& keys, const ckks_ct& y, const std::vector<double>& a);
+int cheb_levels(int degree);
 
 // capi.cu: translates the exception being handled into an error code and
 // records its message for ckks_last_error; call only inside a catch block

@@ -6,6 +6,10 @@
 // centred binomial e_i = popcount(w64[i] & (2^21-1)) - popcount((w64[i]>>21) &
 // (2^21-1)) (domain 2); uniform a_t[i] = (w64[2i+1] 2^64 + w64[2i]) mod q_t
 // (domain 3, id = object << 8 | t), w64[i] = w32[2i] | w32[2i+1] << 32.
+// Sparse ternary of Hamming weight h (domain 4, id 0): a partial
+// Fisher-Yates shuffle of 0..N-1, step i swapping position i with
+// i + w32[2i] mod (N - i) and giving the coefficient at the position drawn
+// the sign -1 if w32[2i+1] is odd, else +1.
 #include "modarith.cuh"
 
 namespace ck {
@@ -106,7 +110,50 @@ __global__ void uniform_kernel(uint64_t seed, const uint64_t* ids, size_t count,
   }
 }
 
+__global__ void sparse_init_kernel(int64_t* s, uint32_t* perm, size_t N) {
+  GRID_LOOP(i, N) {
+    s[i] = 0;
+    perm[i] = (uint32_t)i;
+  }
+}
+
+// sequential by definition (each draw depends on the previous swaps); one thread
+__global__ void sparse_shuffle_kernel(uint64_t seed, int h, int64_t* s, uint32_t* perm, size_t N) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  uint32_t w[16];
+  uint32_t have = 0xFFFFFFFFu;
+  for (int i = 0; i < h; i++) {
+    uint32_t v[2];
+    for (int k = 0; k < 2; k++) {
+      const uint64_t idx = 2 * (uint64_t)i + k;
+      if ((uint32_t)(idx / 16) != have) {
+        have = (uint32_t)(idx / 16);
+        chacha_block(seed, 4, 0, have, w);
+      }
+      v[k] = w[idx % 16];
+    }
+    const size_t j = (size_t)i + (size_t)(v[0] % (uint32_t)(N - (size_t)i));
+    const uint32_t t = perm[i];
+    perm[i] = perm[j];
+    perm[j] = t;
+    s[perm[i]] = (v[1] & 1u) ? -1 : 1;
+  }
+}
+
 }  // namespace
+
+void sample_sparse_ternary(Ctx& c, uint64_t seed, int h, int64_t* out) {
+  if (h < 1 || (uint64_t)h > c.N) throw Error(CKKS_ERR_INVALID_ARG, "Hamming weight out of range");
+  DevBuf perm(&c, c.N * 4);
+  {
+  Launch L_(c, K_SAMPLE, c.N * 12.0);
+  sparse_init_kernel<<<grid_for(c.N), TPB, 0, c.stream>>>(out, static_cast<uint32_t*>(perm.p), c.N);
+  CK_CUDA(cudaGetLastError());
+  }
+  Launch L_(c, K_SAMPLE, h * 24.0);
+  sparse_shuffle_kernel<<<1, 32, 0, c.stream>>>(seed, h, out, static_cast<uint32_t*>(perm.p), c.N);
+  CK_CUDA(cudaGetLastError());
+}
 
 void sample_ternary(Ctx& c, uint64_t seed, int64_t* out) {
   if (c.N < 16) throw Error(CKKS_ERR_UNSUPPORTED, "N < 16");

@@ -1,0 +1,185 @@
+"""GPU parity of CKKS bootstrapping with the oracle (oracle/boot.py): the
+CUDA ModRaise, monomial and wide-constant products, conjugation, slot
+linear transforms, CoeffToSlot, EvalMod, SlotToCoeff and the whole refresh
+must equal the oracle's ciphertexts word for word (same seeded sparse-secret
+keys, input ciphertext, transform diagonals and EvalMod coefficients).
+Sizes: N = 2^7 (the small transform kernels) and N = 2^13 (the clustered
+transforms, a batch of 2 against two oracle runs). The library's own plan
+(merged diagonals, exponent, Chebyshev coefficients) is checked against the
+oracle's by value, and a full-size refresh (N = 2^16, sparse secret of
+weight 192) against the slots it started from."""
+import numpy as np
+import pytest
+
+from oracle import boot as OB, ckks as O
+
+pytestmark = pytest.mark.gpu
+
+SEED = 7
+H = 16
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2409_07751_gb300 import build, ckks
+    build.build()
+    return ckks
+
+
+def _setup(G, log_n, L, alpha, K, degree, levels, extra=()):
+    params = dict(q0_bits=60, scale_bits=50)
+    octx = O.Ctx(O.Params(log_n, L, alpha, **params))
+    plan = OB.Plan(octx, K, degree, *levels)
+    steps = sorted(set(plan.steps(octx)) | set(extra))
+    okeys = OB.BootKeys(octx, SEED, steps, h=H)
+    gctx = G.Context(log_n, L, alpha, **params)
+    gkeys = G.Keys(gctx, SEED, steps, hamming_weight=H, conjugation=True)
+    return octx, plan, okeys, gctx, gkeys
+
+
+def _gpu_plan(G, gctx, octx, plan, stc_level):
+    cts = [G.LinearTransform(gctx, octx.L - i, lt.base, lt.stride, lt.diags, g1=lt.g1,
+                             in_scale=octx.delta[0] if i == 0 else 0.0)
+           for i, lt in enumerate(plan.cts)]
+    stc = [G.LinearTransform(gctx, stc_level - i, lt.base, lt.stride, lt.diags, g1=lt.g1)
+           for i, lt in enumerate(plan.stc)]
+    return G.BootPlan.from_parts(gctx, OB.mod_exponent(octx, plan.K), plan.cheb, cts, stc)
+
+
+def _same(g, o, b=0):
+    assert g.level == o.level and g.scale == o.scale
+    assert (g.export()[b] == o.data).all()
+
+
+@pytest.fixture(scope="module")
+def small(G):
+    return _setup(G, 7, 24, 2, 6, 127, (2, 2), extra=(5, 10, 15, 59))
+
+
+def test_sparse_keys_bit_exact(G, small):
+    octx, plan, okeys, gctx, gkeys = small
+    assert (gkeys.export_secret() == okeys.s).all()
+    assert (gkeys.export_switch(0) == okeys.relin).all()
+    g = 2 * octx.N - 1
+    assert (gkeys.export_switch(g) == okeys.galois[g]).all()
+    g5 = octx.galois(plan.steps(octx)[0])
+    assert (gkeys.export_switch(g5) == okeys.galois[g5]).all()
+
+
+def test_boot_primitives_bit_exact(G, small):
+    octx, plan, okeys, gctx, gkeys = small
+    z = np.random.default_rng(2).uniform(-1, 1, octx.slots)
+    oc = O.encrypt(octx, okeys, z, 0, 3, 0)
+    gc = G.Ciphertext.import_(gctx, oc.data, oc.level, oc.scale)
+    for level in (octx.L, 5):
+        _same(G.mod_raise(gctx, gc, level), OB.mod_raise(octx, oc, level))
+    o12 = O.encrypt(octx, okeys, z * 2.0 ** 8, 12, 3, 1)
+    g12 = G.Ciphertext.import_(gctx, o12.data, o12.level, o12.scale)
+    for k in (1, octx.N // 2, 3 * octx.N // 2, octx.N, 2 * octx.N - 1):
+        _same(G.mul_monomial(gctx, g12, k), OB.mul_monomial(octx, o12, k))
+    _same(G.conjugate(gctx, gkeys, g12), OB.conjugate(octx, okeys, o12))
+    for c in (2.0 ** -25, 3.0 ** -20):
+        _same(G.mul_const_wide(gctx, g12, c), OB.mul_const_wide(octx, o12, c))
+
+
+def test_linear_transform_bit_exact(G, small):
+    octx, plan, okeys, gctx, gkeys = small
+    rng = np.random.default_rng(5)
+    n = octx.slots
+    diags = [(rng.normal(size=n) + 1j * rng.normal(size=n)) / 3 for _ in range(6)]
+    diags[2][:] = 0
+    lt = OB.LinearTransform(-5, 5, diags, g1=4)  # offsets -5 .. 20
+    glt = G.LinearTransform(gctx, 10, lt.base, lt.stride, lt.diags, g1=lt.g1)
+    assert glt.rotations() == lt.steps(n)
+    z = rng.uniform(-1, 1, n)
+    oc = O.encrypt(octx, okeys, z, 10, 3, 2)
+    gc = G.Ciphertext.import_(gctx, oc.data, oc.level, oc.scale)
+    _same(glt.apply(gkeys, gc), OB.linear_transform(octx, okeys, oc, lt))
+    with pytest.raises(G.CkksError):
+        glt.apply(gkeys, G.Ciphertext.import_(gctx, oc.data[:, :10], 9, octx.delta[9]))
+
+
+def _stages_bit_exact(G, setup, batch):
+    octx, plan, okeys, gctx, gkeys = setup
+    rng = np.random.default_rng(11)
+    zs = rng.uniform(-1, 1, (batch, octx.slots))
+    ocs = [O.encrypt(octx, okeys, zs[b], 0, 3, b) for b in range(batch)]
+    gc = G.Ciphertext.import_(gctx, np.stack([c.data for c in ocs]), 0, ocs[0].scale)
+    o_raised = [OB.mod_raise(octx, c) for c in ocs]
+    o_cts = [OB.coeff_to_slot(octx, okeys, r, plan.K, plan.cts) for r in o_raised]
+    o_mod = [(OB.kan_he.eval_cheb(octx, okeys, lo, plan.cheb),
+              OB.kan_he.eval_cheb(octx, okeys, hi, plan.cheb)) for lo, hi in o_cts]
+    o_out = [OB.slot_to_coeff(octx, okeys, lo, hi, plan.stc) for lo, hi in o_mod]
+    gp = _gpu_plan(G, gctx, octx, plan, min(o_mod[0][0].level, o_mod[0][1].level))
+    g_raised = G.mod_raise(gctx, gc, octx.L)
+    glo, ghi = gp.coeff_to_slot(gkeys, g_raised)
+    gmlo, gmhi = gp.eval_mod(gkeys, glo), gp.eval_mod(gkeys, ghi)
+    gout = gp.slot_to_coeff(gkeys, gmlo, gmhi)
+    gfull = gp.bootstrap(gkeys, gc)
+    for b in range(batch):
+        _same(g_raised, o_raised[b], b)
+        _same(glo, o_cts[b][0], b)
+        _same(ghi, o_cts[b][1], b)
+        _same(gmlo, o_mod[b][0], b)
+        _same(gmhi, o_mod[b][1], b)
+        _same(gout, o_out[b], b)
+        _same(gfull, o_out[b], b)
+    got = G.decrypt(gctx, gkeys, gfull, octx.slots)
+    assert np.abs(got - zs).max() < 1e-6
+
+
+def test_bootstrap_stages_bit_exact_small(G, small):
+    _stages_bit_exact(G, small, 1)
+
+
+def test_bootstrap_stages_bit_exact_clustered_transforms(G):
+    setup = _setup(G, 13, 18, 3, 6, 127, (3, 3))
+    _stages_bit_exact(G, setup, 2)
+
+
+def test_library_plan_matches_oracle(G, small):
+    octx, plan, okeys, gctx, gkeys = small
+    for n_levels in (1, 2, 3):
+        for inverse in (False, True):
+            for i, lt in enumerate(OB.transform_levels(octx, n_levels, inverse)):
+                base, stride, d = G.boot_levels(gctx, n_levels, inverse, i)
+                assert (base, stride) == (lt.base, lt.stride)
+                assert np.abs(d - np.array(lt.diags)).max() < 1e-12
+    gp = G.BootPlan(gctx, 6, 127, 2, 2)
+    assert gp.e == OB.mod_exponent(octx, 6) == 13
+    assert np.abs(gp.coefficients() - plan.cheb).max() < 1e-9 * np.abs(plan.cheb).max()
+    assert gp.cts_level == octx.L
+    assert sorted(gp.rotations()) == plan.steps(octx)
+
+
+def test_library_plan_bootstraps(G, small):
+    octx, plan, okeys, gctx, gkeys = small
+    gp = G.BootPlan(gctx, 6, 127, 2, 2)
+    z = np.random.default_rng(4).uniform(-1, 1, (2, octx.slots))
+    gc = G.encrypt(gctx, gkeys, z, 0, 9, 0)
+    out = gp.bootstrap(gkeys, gc)
+    assert out.level == gp.stc_level - 2
+    assert np.abs(G.decrypt(gctx, gkeys, out, octx.slots) - z).max() < 1e-6
+
+
+def test_bootstrap_full_size(G):
+    """N = 2^16, 60-bit q0 under 28 primes of 50 bits, 5 special primes of 60
+    bits (log QP = 1760), sparse secret of weight 192 (|I| <= 30: 31 q0 / Delta
+    stays below 2^15, so the sine has 32 periods on [-1, 1]), EvalMod of
+    degree 255, three merged levels each way, 11 levels left. Precision: every
+    rescale at a 2^50 scale leaves about 2^-41.5 in each slot of y; EvalMod
+    multiplies it by 2^15 (and the Paterson-Stockmeyer basis by about 13),
+    SlotToCoeff sums N/2 such coefficient errors: a few 1e-4 (the oracle at
+    N = 2^13 with these parameters: 2.3e-5)."""
+    gctx = G.Context(16, 28, 5, q0_bits=60, scale_bits=50)
+    gp = G.BootPlan(gctx, 30, 255, 3, 3)
+    assert gp.e == 15
+    keys = G.Keys(gctx, SEED, gp.rotations(), hamming_weight=192, conjugation=True)
+    z = np.random.default_rng(6).uniform(-1, 1, (2, gctx.slots))
+    gc = G.encrypt(gctx, keys, z, 0, 9, 0)
+    out = gp.bootstrap(keys, gc)
+    assert out.level == 11
+    err = np.abs(G.decrypt(gctx, keys, out, gctx.slots) - z).max()
+    assert err < 1e-3, err
+    sq = G.mul(gctx, keys, out, out)
+    assert np.abs(G.decrypt(gctx, keys, sq, gctx.slots) - z * z).max() < 3e-3
