@@ -102,6 +102,9 @@ def args_():
     p.add_argument("--oracle-micro", action="store_true",
                    help="with --impl reference: also time the oracle's NTT per limb, HMult and "
                         "HRot at the top level (single thread; about a minute)")
+    p.add_argument("--boot", action="store_true", help="time CKKS bootstrapping at N=2^16")
+    p.add_argument("--boot-batch", type=int, default=8)
+    p.add_argument("--boot-form", default="double", choices=["single", "double"])
     p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
     p.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals for --serve")
     return p.parse_args()
@@ -330,6 +333,102 @@ def kernel_arm(a):
     print(json.dumps({"kernel": a.kernel, "rows": a.rows, "n_poly": N, "ms_per_launch": ms,
                       "limbs_per_s": a.rows / (ms / 1000.0), "algorithmic_GBps": by / (ms / 1000.0) / 1e9}),
           flush=True)
+
+
+BOOT_DESC = ("CKKS bootstrapping (ModRaise, CoeffToSlot, EvalMod, SlotToCoeff) of full-slot "
+             "ciphertexts, N=2^16, 60-bit q0 + 28 x 50-bit primes, 5 x 60-bit special primes "
+             "(log QP 1760), sparse secret h=192, |I| <= 30, EvalMod degree 255, 3 + 3 merged "
+             "transform levels, double-hoisted transforms")
+
+
+def boot_arm(a):
+    """--boot: bootstraps/s of a batch of `boot_batch` level-0 ciphertexts
+    refreshed in one call (inputs resident), the batch-1 latency, the
+    refreshed slots' error, and the live roofline of the dominant kernel kind
+    (per-launch CUDA events over a profiled repeat)."""
+    import numpy as np
+    import torch
+    from paper_2409_07751_gb300 import build
+    build.build()
+    from paper_2409_07751_gb300 import ckks as G
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = G.Context(16, 28, 5, q0_bits=60, scale_bits=50)
+    ctx.set_stream(stream.cuda_stream)
+    t0 = time.perf_counter()
+    plan = G.BootPlan(ctx, 30, 255, 3, 3, form=a.boot_form)
+    keys = G.Keys(ctx, 7, plan.rotations(), hamming_weight=192, conjugation=True)
+    ctx.synchronize()
+    setup_s = time.perf_counter() - t0
+    B = a.boot_batch
+    z = np.random.default_rng(6).uniform(-1, 1, (B, ctx.slots))
+    ct = G.encrypt(ctx, keys, z, 0, 9, 0)
+    out = plan.bootstrap(keys, ct)
+    err = float(np.abs(G.decrypt(ctx, keys, out, ctx.slots) - z).max())
+    level = out.level
+    out.close()
+    for _ in range(a.warmup):
+        plan.bootstrap(keys, ct).close()
+    torch.cuda.synchronize()
+    before = ctx.launch_counts()
+    clk = Clocks(torch.cuda.current_device())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    ev[0].record(stream)
+    for i in range(a.steps):
+        plan.bootstrap(keys, ct).close()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    after = ctx.launch_counts()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
+    ms = ev[0].elapsed_time(ev[-1]) / a.steps
+    launches = sum(after[k] - before[k] for k in after if k != "copy") // a.steps
+    ctx.profile(True)
+    plan.bootstrap(keys, ct).close()
+    torch.cuda.synchronize()
+    prof = ctx.profile_collect()
+    ctx.profile(False)
+    kinds = {k: v for k, v in prof.items() if k != "copy"}
+    total = sum(v[0] for v in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    kms, kby, kn, kmm = kinds[dom]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = kby / (kms / 1000.0) / 1e9
+    bpk = ctx.int_peak(1) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": kby / kn, "avg_launch_ms": kms / kn,
+                "share_of_kernel_time": kms / total}
+    if kmm > 0:
+        alu = kmm / (kms / 1000.0) / 1e9
+        roofline["alu"] = {"achieved": alu, "unit": "G modmul/s", "peak": bpk, "frac": alu / bpk,
+                           "peak_source": "measured: register-only lazy forward butterflies"}
+    lat = []
+    one = G.encrypt(ctx, keys, z[:1], 0, 9, 0)
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.bootstrap(keys, one).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    print(json.dumps({
+        "metric": "CKKS bootstraps/s", "value": B / (ms / 1000.0), "unit": "bootstraps/s",
+        "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup, "batch": B,
+        "latency_ms_batch1": min(lat), "max_abs_error": err, "output_level": level,
+        "gpu_launches_per_step": launches, "setup_s": round(setup_s, 2),
+        "step_ms": [round(x, 2) for x in step_ms], "roofline": roofline,
+        "kernel_time_shares": {k: round(v[0] / total, 4)
+                               for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][0])[:8]},
+        "clocks": clocks, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": BOOT_DESC, "form": a.boot_form, "rotation_keys": len(plan.rotations()),
+                   "l2": "inputs and keys (several GB) far above L2"}}), flush=True)
 
 
 def config(a):
@@ -664,6 +763,7 @@ EXTRA_RUNS = [
     ("c4", ["--workload", "c4", "--steps", "3", "--warmup", "3"], 600),
     ("c5_serve", ["--serve", "--rate", "20", "--duration", "30"], 900),
     ("table3", ["--table3"], 600),
+    ("boot", ["--boot", "--steps", "3", "--warmup", "2"], 600),
 ]
 
 
@@ -675,6 +775,11 @@ def _summary(name, line):
                                            "latency_ms", "depth", "clocks")} | {
             "batch": line["config"]["batch_per_gpu"], "workload": line["config"]["workload"],
             "alpha": line["config"]["alpha"], "p_bits": line["config"]["p_bits"],
+            "dominant_kernel": {k: line["roofline"].get(k) for k in ("kernel", "frac", "unit")}}
+    if name == "boot":
+        return {k: line.get(k) for k in ("value", "unit", "ms_per_step", "batch", "latency_ms_batch1",
+                                           "max_abs_error", "output_level", "gpu_launches_per_step",
+                                           "kernel_time_shares", "clocks", "config")} | {
             "dominant_kernel": {k: line["roofline"].get(k) for k in ("kernel", "frac", "unit")}}
     if name == "c5_serve":
         return {k: line.get(k) for k in ("value", "unit", "latency_ms", "requests", "wall_s",
@@ -730,6 +835,8 @@ def main():
         return serve_arm(a)
     if a.table3:
         return table3_arm(a)
+    if a.boot:
+        return boot_arm(a)
     import numpy as np
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

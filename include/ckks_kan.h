@@ -285,12 +285,16 @@ int ckks_mul_const_wide(ckks_ctx* ctx, const ckks_ct* in, double value, ckks_ct*
  * k < n_diag, for inputs at `level` with scale `in_scale` (0: Delta_level);
  * re / im: host [n_diag][N/2] real and imaginary parts of the diagonals (an
  * all-zero diagonal is skipped), copied and encoded at creation (device
- * plaintexts [nonzero][level+1][N]). Applied by baby-step giant-step with g1
- * baby steps (0: the least power of two whose square is >= n_diag): it takes
- * one level and lands on the canonical scale. Rotation keys: see
- * ckks_lt_rotations. */
+ * plaintexts [nonzero][level+1][N], over QP_level for form 1). Applied by
+ * baby-step giant-step with g1 baby steps (0: the least power of two whose
+ * square is >= n_diag): it takes one level and lands on the canonical
+ * scale. form 0: hoisted baby rotations, one rescale per giant step; form 1:
+ * double hoisting, the baby rotations kept in QP_level and each giant step's
+ * products divided by P q_level once (the rounding differs from form 0).
+ * Rotation keys: see ckks_lt_rotations. */
 int ckks_lt_create(ckks_ctx* ctx, int level, double in_scale, int64_t base, int64_t stride,
-                   size_t n_diag, const double* re, const double* im, int g1, ckks_lt** out);
+                   size_t n_diag, const double* re, const double* im, int g1, int form,
+                   ckks_lt** out);
 int ckks_lt_destroy(ckks_lt* lt);
 /* Rotation steps the transform uses (baby steps j stride, giant steps
  * base + g1 i stride, mod N/2, without 0); *n receives their count. */
@@ -305,10 +309,11 @@ int ckks_lt_apply(ckks_ctx* ctx, const ckks_keys* keys, const ckks_lt* lt, const
  * degree `degree` of (c / 2 pi) sin(2 pi 2^e y / c), c = q0 / Delta_0,
  * 2^e >= (K + 1) c; CoeffToSlot and SlotToCoeff as cts_levels and
  * stc_levels merged levels of the special-FFT stages (log2(N/2) stages in
- * near-equal groups). CoeffToSlot starts at level L on inputs of scale
+ * near-equal groups), in the transform form `form` (ckks_lt_create).
+ * CoeffToSlot starts at level L on inputs of scale
  * Delta_0; the output comes out at L - cts_levels - 2 - depth(degree) -
  * stc_levels. CKKS_ERR_LEVEL if the chain is too short. */
-int ckks_boot_create(ckks_ctx* ctx, int K, int degree, int cts_levels, int stc_levels,
+int ckks_boot_create(ckks_ctx* ctx, int K, int degree, int cts_levels, int stc_levels, int form,
                      ckks_boot** out);
 /* The same from given parts: exponent e, EvalMod's Chebyshev coefficients,
  * the CoeffToSlot and SlotToCoeff transforms in application order (borrowed:

@@ -225,10 +225,15 @@ def _groups(n_stages, n_levels, ascending):
 class LinearTransform:
     """z -> sum_k d_k (.) rot(z, base + k stride), k in [0, len(diags)), by
     baby-step giant-step: baby steps j stride (j < g1, one hoisted ModUp),
-    giant steps base + g1 i stride; an all-zero diagonal is skipped."""
+    giant steps base + g1 i stride; an all-zero diagonal is skipped. form
+    "single": hoisted baby rotations, one rescale per giant step; "double":
+    the baby rotations kept in QP_l and each giant step's products divided by
+    P q_l once (double hoisting)."""
 
-    def __init__(self, base, stride, diags, g1=None):
-        self.base, self.stride = int(base), int(stride)
+    def __init__(self, base, stride, diags, g1=None, form="single"):
+        if form not in ("single", "double"):
+            raise ValueError(form)
+        self.base, self.stride, self.form = int(base), int(stride), form
         self.diags = [np.asarray(d, complex) for d in diags]
         K = len(self.diags)
         self.g1 = g1 or 1 << max(0, math.ceil(math.log2(math.sqrt(K))))
@@ -244,7 +249,7 @@ class LinearTransform:
         return sorted(st - {0})
 
 
-def transform_levels(ctx, n_levels, inverse):
+def transform_levels(ctx, n_levels, inverse, form="single"):
     """The merged levels of U's factors: SlotToCoeff (inverse False) applies
     F_1 .. F_(log n) in that order, CoeffToSlot (inverse True) applies
     2 F_(log n)^-1 .. 2 F_1^-1. Each level merges consecutive stages with
@@ -268,7 +273,24 @@ def transform_levels(ctx, n_levels, inverse):
                 seen.add(o)
             else:
                 diags.append(np.zeros(n, complex))
-        out.append(LinearTransform(base, stride, diags))
+        out.append(LinearTransform(base, stride, diags, form=form))
+    return out
+
+
+def encode_qp_complex(ctx, z, level, scale):
+    """Plaintext of the complex slots z over QP_level ([l + alpha][N], NTT
+    form): the encoding's integer coefficients reduced mod each Q limb and
+    special prime (the Q rows equal encode_complex's)."""
+    z = np.asarray(z, complex)
+    re, im = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+    co = np.zeros(ctx.N, np.int64)
+    if ctx.L_.or_encode_complex(ptr(re), ptr(im), len(z), ctx.log_n, scale, ptr(co)) != 0:
+        raise OverflowError("oracle: encoding overflow")
+    rows = list(range(level + 1)) + [ctx.L + 1 + k for k in range(ctx.alpha)]
+    out = np.zeros((len(rows), ctx.N), np.uint64)
+    for r, t in enumerate(rows):
+        out[r] = np.mod(co, np.int64(ctx.moduli[t])).astype(np.uint64)
+        ctx.L_.or_ntt_limb(ctx.h, ptr(out[r]), t, 0)
     return out
 
 
@@ -276,7 +298,11 @@ def linear_transform(ctx, keys, v, lt):
     """The BSGS evaluation of a LinearTransform: per giant step i the
     products of the baby rotations with the diagonals pre-rotated by
     -(base + g1 i stride), summed, rescaled once (one level), then rotated
-    by base + g1 i stride."""
+    by base + g1 i stride. In the double form the baby rotations stay in
+    QP_l, the products and sum are taken over QP_l and the rescale is the
+    division of the sum by P q_l."""
+    if lt.form == "double":
+        return _linear_transform_double(ctx, keys, v, lt)
     n = ctx.slots
     baby = ckks.rotate_many(ctx, keys, v, [j * lt.stride for j in range(lt.g1)])
     lv = v.level
@@ -301,6 +327,31 @@ def linear_transform(ctx, keys, v, lt):
         if acc is None:
             continue
         inner = ckks.rescale(ctx, ckks.Ct(acc, lv, v.scale * Spt))
+        if G % n:
+            inner = ckks.rotate(ctx, keys, inner, G % n)
+        z = inner if z is None else ckks.add(ctx, z, inner)
+    return z
+
+
+def _linear_transform_double(ctx, keys, v, lt):
+    n = ctx.slots
+    R = ckks.rotate_many_qp(ctx, keys, v, [j * lt.stride for j in range(lt.g1)])
+    lv = v.level
+    Spt = ckks.plain_scale(ctx, v.scale, lv)
+    z = None
+    for i in range(lt.g2):
+        G = lt.base + lt.g1 * i * lt.stride
+        acc, any_ = np.zeros_like(R[0]), False
+        for j in range(lt.g1):
+            k = lt.g1 * i + j
+            if k >= len(lt.diags) or not lt.diags[k].any():
+                continue
+            pt = encode_qp_complex(ctx, np.roll(lt.diags[k], G), lv, Spt)
+            ckks.qp_mul_plain_acc(ctx, R[j * lt.stride], pt, lv, acc)
+            any_ = True
+        if not any_:
+            continue
+        inner = ckks.div_p_ql(ctx, acc, lv, v.scale * Spt)
         if G % n:
             inner = ckks.rotate(ctx, keys, inner, G % n)
         z = inner if z is None else ckks.add(ctx, z, inner)
@@ -394,10 +445,10 @@ class Plan:
     """The bootstrapping's fixed parts: the merged transform levels, the
     overflow bound K (|I| <= K) and the EvalMod polynomial's degree."""
 
-    def __init__(self, ctx, K, degree, cts_levels=2, stc_levels=2):
+    def __init__(self, ctx, K, degree, cts_levels=2, stc_levels=2, form="single"):
         self.K, self.degree = K, degree
-        self.cts = transform_levels(ctx, cts_levels, inverse=True)
-        self.stc = transform_levels(ctx, stc_levels, inverse=False)
+        self.cts = transform_levels(ctx, cts_levels, inverse=True, form=form)
+        self.stc = transform_levels(ctx, stc_levels, inverse=False, form=form)
         self.cheb = eval_mod_coeffs(ctx, K, degree)
 
     def steps(self, ctx):

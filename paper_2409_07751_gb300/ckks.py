@@ -58,11 +58,12 @@ SIGNATURES = {
     "ckks_conjugate": (c_i32, [c_vp, c_vp, c_vp, PP]),
     "ckks_mul_monomial": (c_i32, [c_vp, c_vp, c_i64, PP]),
     "ckks_mul_const_wide": (c_i32, [c_vp, c_vp, c_dbl, PP]),
-    "ckks_lt_create": (c_i32, [c_vp, c_i32, c_dbl, c_i64, c_i64, c_sz, c_vp, c_vp, c_i32, PP]),
+    "ckks_lt_create": (c_i32, [c_vp, c_i32, c_dbl, c_i64, c_i64, c_sz, c_vp, c_vp, c_i32, c_i32,
+                               PP]),
     "ckks_lt_destroy": (c_i32, [c_vp]),
     "ckks_lt_rotations": (c_i32, [c_vp, c_vp, c_sz, ctypes.POINTER(c_sz)]),
     "ckks_lt_apply": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
-    "ckks_boot_create": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_i32, PP]),
+    "ckks_boot_create": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_i32, c_i32, PP]),
     "ckks_boot_create_ex": (c_i32, [c_vp, c_i32, c_vp, c_sz, c_vp, c_sz, c_vp, c_sz, PP]),
     "ckks_boot_destroy": (c_i32, [c_vp]),
     "ckks_boot_info": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
@@ -461,9 +462,12 @@ def _steps(fn, h):
 
 class LinearTransform:
     """z -> sum_k d_k (.) rot(z, base + k stride): diags [n_diag][N/2]
-    complex, encoded for inputs at `level` with scale in_scale (0: canonical)."""
+    complex, encoded for inputs at `level` with scale in_scale (0: canonical);
+    form "single" (hoisted) or "double" (double hoisting)."""
 
-    def __init__(self, ctx, level, base, stride, diags, g1=0, in_scale=0.0):
+    FORMS = ("single", "double")
+
+    def __init__(self, ctx, level, base, stride, diags, g1=0, in_scale=0.0, form="single"):
         d = np.asarray(diags, dtype=complex)
         if d.ndim != 2 or d.shape[1] != ctx.slots:
             raise ValueError("diagonals must be [n_diag][N/2]")
@@ -471,7 +475,8 @@ class LinearTransform:
         im = np.ascontiguousarray(d.imag, dtype=np.float64)
         h = c_vp()
         check(lib().ckks_lt_create(ctx.h, level, float(in_scale), int(base), int(stride), d.shape[0],
-                                   _p(re), _p(im), int(g1), ctypes.byref(h)))
+                                   _p(re), _p(im), int(g1), self.FORMS.index(form),
+                                   ctypes.byref(h)))
         self.h, self.ctx, self.level = h, ctx, level
 
     def rotations(self):
@@ -497,10 +502,12 @@ class BootPlan:
     computed by the library, or BootPlan.from_parts(ctx, e, cheb, cts, stc)
     from given transforms (kept alive by the plan object)."""
 
-    def __init__(self, ctx, K=None, degree=None, cts_levels=3, stc_levels=3, _h=None, _keep=()):
+    def __init__(self, ctx, K=None, degree=None, cts_levels=3, stc_levels=3, form="double",
+                 _h=None, _keep=()):
         if _h is None:
             _h = c_vp()
-            check(lib().ckks_boot_create(ctx.h, K, degree, cts_levels, stc_levels, ctypes.byref(_h)))
+            check(lib().ckks_boot_create(ctx.h, K, degree, cts_levels, stc_levels,
+                                         LinearTransform.FORMS.index(form), ctypes.byref(_h)))
         self.h, self.ctx, self._keep = _h, ctx, list(_keep)
         e, lc, ls, nc = c_i32(), c_i32(), c_i32(), c_sz()
         check(lib().ckks_boot_info(self.h, ctypes.byref(e), ctypes.byref(lc), ctypes.byref(ls),

@@ -25,8 +25,10 @@
 // baby-step giant-step: one hoisted ModUp for the baby rotations j stride
 // (j < g1), per giant step the products with the diagonals pre-rotated by
 // -(base + g1 i stride) accumulated, rescaled once and rotated by
-// base + g1 i stride. Its plaintexts are encoded once, at creation, for the
-// level and input scale it is applied at.
+// base + g1 i stride; with double hoisting the baby rotations stay in QP_l
+// and each giant step's products are summed over QP_l and divided by P q_l
+// once. Its plaintexts are encoded once, at creation, for the level and
+// input scale it is applied at.
 #include <math.h>
 
 #include <algorithm>
@@ -152,8 +154,9 @@ struct ckks_lt {
   double in_scale, pt_scale;
   int64_t base, stride;
   int n_diag, g1, g2;
+  int form;               // 0: hoisted baby steps; 1: double hoisting (QP_l)
   std::vector<int> slot;  // [n_diag]: plaintext index, -1 = zero diagonal
-  ck::DevBuf pts;         // [nonzero][level + 1][N]
+  ck::DevBuf pts;         // [nonzero][rows][N], rows = level + 1 (+ alpha if form 1)
 };
 
 struct ckks_boot {
@@ -180,10 +183,11 @@ int64_t mod_n(int64_t x, int64_t n) { return ((x % n) + n) % n; }
 
 std::unique_ptr<ckks_lt> lt_create(Ctx& c, int level, double in_scale, int64_t base,
                                    int64_t stride, int n_diag, const double* re, const double* im,
-                                   int g1) {
+                                   int g1, int form) {
   if (level < 1 || level > c.L) throw Error(CKKS_ERR_LEVEL, "level out of range");
   if (n_diag < 1 || !re || !im) throw Error(CKKS_ERR_INVALID_ARG, "no diagonals");
   if (g1 < 0) throw Error(CKKS_ERR_INVALID_ARG, "negative baby-step count");
+  if (form != 0 && form != 1) throw Error(CKKS_ERR_INVALID_ARG, "unknown transform form");
   const int64_t n = (int64_t)c.N / 2;
   auto lt = std::make_unique<ckks_lt>();
   lt->ctx = &c;
@@ -195,6 +199,7 @@ std::unique_ptr<ckks_lt> lt_create(Ctx& c, int level, double in_scale, int64_t b
   lt->n_diag = n_diag;
   lt->g1 = g1 ? g1 : default_g1(n_diag);
   lt->g2 = (n_diag + lt->g1 - 1) / lt->g1;
+  lt->form = form;
   // pre-rotate the nonzero diagonals by -(base + g1 i stride): np.roll(d, G)
   std::vector<double> hr, hi;
   int nz = 0;
@@ -213,13 +218,15 @@ std::unique_ptr<ckks_lt> lt_create(Ctx& c, int level, double in_scale, int64_t b
       hi.push_back(di[src]);
     }
   }
-  const int l = level + 1;
-  lt->pts = DevBuf(&c, std::max<size_t>((size_t)nz * l * c.N * 8, 8));
+  ConvTables& T = c.tables(level);
+  const int rows = form == 1 ? T.rows : level + 1;
+  const int16_t* pattern = form == 1 ? static_cast<const int16_t*>(T.qp_pattern.p) : c.iota();
+  lt->pts = DevBuf(&c, std::max<size_t>((size_t)nz * rows * c.N * 8, 8));
   if (nz) {
     DevBuf dr(&c, hr.size() * 8), di(&c, hi.size() * 8);
     CK_CUDA(cudaMemcpyAsync(dr.p, hr.data(), hr.size() * 8, cudaMemcpyHostToDevice, c.stream));
     CK_CUDA(cudaMemcpyAsync(di.p, hi.data(), hi.size() * 8, cudaMemcpyHostToDevice, c.stream));
-    const int rc = encode_rows(c, static_cast<const double*>(dr.p), nz, n, l, c.iota(),
+    const int rc = encode_rows(c, static_cast<const double*>(dr.p), nz, n, rows, pattern,
                                lt->pt_scale, lt->pts.u64(), static_cast<const double*>(di.p));
     if (rc != CKKS_OK) throw Error(rc, "diagonal does not fit its scale");
   }
@@ -238,9 +245,59 @@ std::vector<int64_t> lt_steps(const Ctx& c, const ckks_lt& lt) {
   return st;
 }
 
+// double hoisting: baby rotations kept in QP_l (R_0 = P v, R_j the key
+// product of sigma_j(ModUp(c1)) plus P sigma_j(c0)), each giant step's
+// products summed over QP_l and divided by P q_l once
+Ct lt_apply_double(Ctx& c, const ckks_keys& keys, const ckks_lt& lt, const ckks_ct& v) {
+  const int64_t n = (int64_t)c.N / 2;
+  const int lv = v.level, l = lv + 1;
+  ConvTables& T = c.tables(lv);
+  const size_t qp_words = v.B * 2 * (size_t)T.rows * c.N;
+  std::vector<DevBuf> R;
+  R.emplace_back(&c, qp_words * 8);
+  k_qp_lift(c, v.d.u64(), v.B, lv, nullptr, R[0].u64());
+  DevBuf ext;
+  for (int j = 1; j < lt.g1; j++) {
+    const uint64_t g = c.galois(j * lt.stride);
+    auto it = keys.galois.find(g);
+    if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
+    if (!ext.p) {
+      ext = DevBuf(&c, v.B * T.beta * T.rows * c.N * 8);
+      modup(c, v.d.u64() + (size_t)l * c.N, v.B, lv, ext.u64(), 2 * (size_t)l * c.N);
+    }
+    DevBuf acc = keyswitch_qp(c, ext.u64(), v.B, lv, it->second->u64(), g);
+    k_qp_lift(c, v.d.u64(), v.B, lv, c.perm(g), acc.u64());
+    R.push_back(std::move(acc));
+  }
+  ext.reset();
+  double s = v.scale * lt.pt_scale / (double)c.mod[lv];
+  if (fabs(s / c.delta[lv - 1] - 1.0) < SNAP) s = c.delta[lv - 1];
+  Ct z;
+  DevBuf acc(&c, qp_words * 8);
+  for (int i = 0; i < lt.g2; i++) {
+    const int64_t G = lt.base + (int64_t)lt.g1 * i * lt.stride;
+    bool first = true;
+    for (int j = 0; j < lt.g1; j++) {
+      const int k = lt.g1 * i + j;
+      if (k >= lt.n_diag || lt.slot[k] < 0) continue;
+      const uint64_t* pt = lt.pts.u64() + (size_t)lt.slot[k] * T.rows * c.N;
+      k_qp_mul_pt_acc(c, R[j].u64(), pt, acc.u64(), v.B * 2, lv, first);
+      first = false;
+    }
+    if (first) continue;
+    Ct inner = ct_alloc(c, v.B, lv - 1, s);
+    div_p_ql(c, acc.u64(), v.B, lv, inner->d.u64());
+    if (mod_n(G, n)) inner = op_rotate(c, keys, *inner, mod_n(G, n));
+    z = z ? op_add(c, *z, *inner, false) : std::move(inner);
+  }
+  if (!z) throw Error(CKKS_ERR_INVALID_ARG, "transform with only zero diagonals");
+  return z;
+}
+
 Ct lt_apply(Ctx& c, const ckks_keys& keys, const ckks_lt& lt, const ckks_ct& v) {
   if (v.level != lt.level) throw Error(CKKS_ERR_LEVEL, "transform built for another level");
   if (fabs(v.scale / lt.in_scale - 1.0) > SNAP) throw Error(CKKS_ERR_SCALE, "transform built for another scale");
+  if (lt.form == 1) return lt_apply_double(c, keys, lt, v);
   const int64_t n = (int64_t)c.N / 2;
   const int l = v.level + 1;
   const size_t rows = v.B * 2 * l;
@@ -301,10 +358,18 @@ Ct bootstrap(Ctx& c, const ckks_keys& keys, const ckks_boot& b, const ckks_ct& i
   Ct lo, hi;
   boot_coeff_to_slot(c, keys, b, *raised, lo, hi);
   raised.reset();
-  Ct mlo = cheb_eval(c, keys, *lo, b.cheb);
+  // both halves through EvalMod as one batch of 2B (every step is per element)
+  Ct both = op_concat(c, {lo.get(), hi.get()});
   lo.reset();
-  Ct mhi = cheb_eval(c, keys, *hi, b.cheb);
   hi.reset();
+  Ct m = cheb_eval(c, keys, *both, b.cheb);
+  both.reset();
+  const size_t half = m->words() / 2;
+  Ct mlo = ct_alloc(c, in.B, m->level, m->scale), mhi = ct_alloc(c, in.B, m->level, m->scale);
+  CK_CUDA(cudaMemcpyAsync(mlo->d.p, m->d.p, half * 8, cudaMemcpyDeviceToDevice, c.stream));
+  CK_CUDA(cudaMemcpyAsync(mhi->d.p, m->d.u64() + half, half * 8, cudaMemcpyDeviceToDevice,
+                          c.stream));
+  m.reset();
   return boot_slot_to_coeff(c, keys, b, *mlo, *mhi);
 }
 
@@ -514,11 +579,13 @@ int ckks_mul_const_wide(ckks_ctx* ctx, const ckks_ct* in, double value, ckks_ct*
 }
 
 int ckks_lt_create(ckks_ctx* ctx, int level, double in_scale, int64_t base, int64_t stride,
-                   size_t n_diag, const double* re, const double* im, int g1, ckks_lt** out) {
+                   size_t n_diag, const double* re, const double* im, int g1, int form,
+                   ckks_lt** out) {
   return guard([&] {
     need(ctx && re && im && out, "NULL argument");
     need(n_diag >= 1 && n_diag <= ctx->c.N, "diagonal count out of range");
-    *out = lt_create(ctx->c, level, in_scale, base, stride, (int)n_diag, re, im, g1).release();
+    *out = lt_create(ctx->c, level, in_scale, base, stride, (int)n_diag, re, im, g1, form)
+               .release();
   });
 }
 
@@ -545,7 +612,7 @@ int ckks_lt_apply(ckks_ctx* ctx, const ckks_keys* keys, const ckks_lt* lt, const
   });
 }
 
-int ckks_boot_create(ckks_ctx* ctx, int K, int degree, int cts_levels, int stc_levels,
+int ckks_boot_create(ckks_ctx* ctx, int K, int degree, int cts_levels, int stc_levels, int form,
                      ckks_boot** out) {
   return guard([&] {
     need(ctx && out, "NULL argument");
@@ -566,7 +633,7 @@ int ckks_boot_create(ckks_ctx* ctx, int K, int degree, int cts_levels, int stc_l
       for (size_t g = 0; g < base.size(); g++) {
         const double in_scale = inverse && g == 0 ? c.delta[0] : c.delta[level];
         auto lt = lt_create(c, level, in_scale, base[g], stride[g], (int)(re[g].size() / n),
-                            re[g].data(), im[g].data(), 0);
+                            re[g].data(), im[g].data(), 0, form);
         (inverse ? b->cts : b->stc).push_back(lt.get());
         b->owned.push_back(std::move(lt));
         level -= 1;

@@ -3,8 +3,9 @@ CUDA ModRaise, monomial and wide-constant products, conjugation, slot
 linear transforms, CoeffToSlot, EvalMod, SlotToCoeff and the whole refresh
 must equal the oracle's ciphertexts word for word (same seeded sparse-secret
 keys, input ciphertext, transform diagonals and EvalMod coefficients).
-Sizes: N = 2^7 (the small transform kernels) and N = 2^13 (the clustered
-transforms, a batch of 2 against two oracle runs). The library's own plan
+Sizes: N = 2^7 (the small transform kernels; hoisted and double-hoisted
+transforms) and N = 2^13 (the clustered transforms, double hoisting, a batch
+of 2 against two oracle runs). The library's own plan
 (merged diagonals, exponent, Chebyshev coefficients) is checked against the
 oracle's by value, and a full-size refresh (N = 2^16, sparse secret of
 weight 192) against the slots it started from."""
@@ -26,10 +27,10 @@ def G():
     return ckks
 
 
-def _setup(G, log_n, L, alpha, K, degree, levels, extra=()):
+def _setup(G, log_n, L, alpha, K, degree, levels, extra=(), form="single"):
     params = dict(q0_bits=60, scale_bits=50)
     octx = O.Ctx(O.Params(log_n, L, alpha, **params))
-    plan = OB.Plan(octx, K, degree, *levels)
+    plan = OB.Plan(octx, K, degree, *levels, form=form)
     steps = sorted(set(plan.steps(octx)) | set(extra))
     okeys = OB.BootKeys(octx, SEED, steps, h=H)
     gctx = G.Context(log_n, L, alpha, **params)
@@ -39,9 +40,10 @@ def _setup(G, log_n, L, alpha, K, degree, levels, extra=()):
 
 def _gpu_plan(G, gctx, octx, plan, stc_level):
     cts = [G.LinearTransform(gctx, octx.L - i, lt.base, lt.stride, lt.diags, g1=lt.g1,
-                             in_scale=octx.delta[0] if i == 0 else 0.0)
+                             in_scale=octx.delta[0] if i == 0 else 0.0, form=lt.form)
            for i, lt in enumerate(plan.cts)]
-    stc = [G.LinearTransform(gctx, stc_level - i, lt.base, lt.stride, lt.diags, g1=lt.g1)
+    stc = [G.LinearTransform(gctx, stc_level - i, lt.base, lt.stride, lt.diags, g1=lt.g1,
+                             form=lt.form)
            for i, lt in enumerate(plan.stc)]
     return G.BootPlan.from_parts(gctx, OB.mod_exponent(octx, plan.K), plan.cheb, cts, stc)
 
@@ -82,14 +84,16 @@ def test_boot_primitives_bit_exact(G, small):
         _same(G.mul_const_wide(gctx, g12, c), OB.mul_const_wide(octx, o12, c))
 
 
-def test_linear_transform_bit_exact(G, small):
+@pytest.mark.parametrize("form", ["single", "double"])
+def test_linear_transform_bit_exact(G, small, form):
     octx, plan, okeys, gctx, gkeys = small
     rng = np.random.default_rng(5)
     n = octx.slots
     diags = [(rng.normal(size=n) + 1j * rng.normal(size=n)) / 3 for _ in range(6)]
     diags[2][:] = 0
-    lt = OB.LinearTransform(-5, 5, diags, g1=4)  # offsets -5 .. 20
-    glt = G.LinearTransform(gctx, 10, lt.base, lt.stride, lt.diags, g1=lt.g1)
+    diags[4][:] = 0  # the first diagonal of the second giant step
+    lt = OB.LinearTransform(-5, 5, diags, g1=4, form=form)  # offsets -5 .. 20
+    glt = G.LinearTransform(gctx, 10, lt.base, lt.stride, lt.diags, g1=lt.g1, form=form)
     assert glt.rotations() == lt.steps(n)
     z = rng.uniform(-1, 1, n)
     oc = O.encrypt(octx, okeys, z, 10, 3, 2)
@@ -132,8 +136,14 @@ def test_bootstrap_stages_bit_exact_small(G, small):
     _stages_bit_exact(G, small, 1)
 
 
+def test_bootstrap_stages_bit_exact_small_double_hoisted(G, small):
+    octx, plan, okeys, gctx, gkeys = small
+    dplan = OB.Plan(octx, plan.K, plan.degree, len(plan.cts), len(plan.stc), form="double")
+    _stages_bit_exact(G, (octx, dplan, okeys, gctx, gkeys), 2)
+
+
 def test_bootstrap_stages_bit_exact_clustered_transforms(G):
-    setup = _setup(G, 13, 18, 3, 6, 127, (3, 3))
+    setup = _setup(G, 13, 18, 3, 6, 127, (3, 3), form="double")
     _stages_bit_exact(G, setup, 2)
 
 
@@ -145,7 +155,7 @@ def test_library_plan_matches_oracle(G, small):
                 base, stride, d = G.boot_levels(gctx, n_levels, inverse, i)
                 assert (base, stride) == (lt.base, lt.stride)
                 assert np.abs(d - np.array(lt.diags)).max() < 1e-12
-    gp = G.BootPlan(gctx, 6, 127, 2, 2)
+    gp = G.BootPlan(gctx, 6, 127, 2, 2, form="single")
     assert gp.e == OB.mod_exponent(octx, 6) == 13
     assert np.abs(gp.coefficients() - plan.cheb).max() < 1e-9 * np.abs(plan.cheb).max()
     assert gp.cts_level == octx.L

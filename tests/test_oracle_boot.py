@@ -46,6 +46,13 @@ def s50():
     return _setup(60, scale_bits=50)
 
 
+@pytest.fixture(scope="module")
+def s50d(s50):
+    """The same keys with double-hoisted transforms."""
+    ctx, keys, plan = s50
+    return ctx, keys, boot.Plan(ctx, plan.K, plan.degree, len(plan.cts), len(plan.stc), "double")
+
+
 def _complex_ct(ctx, keys, z, level):
     """A ciphertext at `level` whose slots are the complex z: Re z encrypted,
     times the plaintext z / Re z, rescaled."""
@@ -127,13 +134,14 @@ def test_special_fft_factors_the_decoding_map(c20):
             assert np.abs(w - want).max() < 1e-11 * np.abs(want).max()
 
 
-def test_linear_transform_matches_numpy(c20):
+@pytest.mark.parametrize("form", ["single", "double"])
+def test_linear_transform_matches_numpy(c20, form):
     ctx, keys, _ = c20
     rng = np.random.default_rng(7)
     n = ctx.slots
     diags = [(rng.normal(size=n) + 1j * rng.normal(size=n)) / 3 for _ in range(7)]
     diags[4][:] = 0  # skipped
-    lt = boot.LinearTransform(-7, 7, diags, g1=4)  # offsets -7, 0, ..., 35
+    lt = boot.LinearTransform(-7, 7, diags, g1=4, form=form)  # offsets -7, 0, ..., 35
     assert lt.steps(n) == [7, 14, 21, 57]  # baby 7, 14, 21; giant -7 = 57 and 21
     z = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
     ct = _complex_ct(ctx, keys, z, 12)
@@ -220,7 +228,7 @@ def test_eval_mod_interpolant_reduces_mod_q0(q0_bits, bound):
         assert (np.abs(got - mD) <= sine_err * 1.001 + bound).all(), I
 
 
-@pytest.mark.parametrize("fx,bound", [("c20", 2e-2), ("c10", 1e-4), ("s50", 1e-6)])
+@pytest.mark.parametrize("fx,bound", [("c20", 2e-2), ("c10", 1e-4), ("s50", 1e-6), ("s50d", 1e-6)])
 def test_bootstrap_restores_the_slots(fx, bound, request):
     """Precision follows q0 / Delta and the scale: EvalMod multiplies the
     noise of y by about 2^e ~ (K + 1) q0 / Delta, so 40-bit scale primes
