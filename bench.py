@@ -35,10 +35,9 @@ sys.path.insert(0, ROOT)
 # fused ModUp forward NTT, measured on a 13-limb, batch-8 HMult (the bench's
 # launch is too large for a full capture); traffic scales with the units
 # processed, so a full launch's traffic is this ratio times its algorithmic
-# bytes: 408.1 MB of DRAM traffic for 394.3 MB algorithmic (13 limbs, 4
-# digits of 17 rows, batch 8; the kernel with the first stage folded into
-# its conversion constants).
-MODUP_TRAFFIC_RATIO = 408.1 / 394.3
+# bytes: 393.2 MB of DRAM traffic (148.2 read, 245.0 written) for 394.3 MB
+# algorithmic (13 limbs, 4 digits of 17 rows, batch 8), current kernel build.
+MODUP_TRAFFIC_RATIO = 393.19 / 394.26
 
 METRIC = "encrypted KAN inferences/s"
 UNIT = "inferences/s"
@@ -103,6 +102,8 @@ def args_():
                    help="with --impl reference: also time the oracle's NTT per limb, HMult and "
                         "HRot at the top level (single thread; about a minute)")
     p.add_argument("--boot", action="store_true", help="time CKKS bootstrapping at N=2^16")
+    p.add_argument("--deep", action="store_true",
+                   help="time a five-layer KAN refreshed by bootstrapping between layers")
     p.add_argument("--boot-batch", type=int, default=8)
     p.add_argument("--boot-form", default="double", choices=["single", "double"])
     p.add_argument("--rate", type=float, default=20.0, help="requests/s for --serve")
@@ -429,6 +430,80 @@ def boot_arm(a):
         "clocks": clocks, "dtype": "u64", "data": "synthetic",
         "config": {"workload": BOOT_DESC, "form": a.boot_form, "rotation_keys": len(plan.rotations()),
                    "l2": "inputs and keys (several GB) far above L2"}}), flush=True)
+
+
+DEEP_DESC = ("encrypted KAN [4,8,8,8,4,1] G=5 k=3 (SiLU degree 27, minimax comparison degrees 7 "
+             "and 15, eps 0.12, difference form: 12 levels per layer, 60 in all), CKKS N=2^16, "
+             "60-bit q0 + 29 x 50-bit primes, 4 x 60-bit special primes (log QP 1750), refreshed "
+             "by bootstrapping before layers 3, 4 and 5")
+
+
+def deep_arm(a):
+    """--deep: a KAN deeper than any leveled chain inside the security budget,
+    run by kan_infer with a bootstrapping plan set (refresh when the next
+    layer needs more levels than are left); inferences/s of a batch, and the
+    time one refresh of the batch takes alone."""
+    import numpy as np
+    import torch
+    from paper_2409_07751_gb300 import build
+    build.build()
+    from paper_2409_07751_gb300 import ckks as G, workloads as W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = G.Context(16, 29, 4, q0_bits=60, scale_bits=50)
+    ctx.set_stream(stream.cuda_stream)
+    t0 = time.perf_counter()
+    model = [dict(L, b0="difference") for L in W.make_model("t", widths=[4, 8, 8, 8, 4, 1], G=5, k=3)]
+    Xcal = W.uniform_inputs(256, 4, seed=W.SEED_INPUTS + 1000)
+    m = G.calibrate(model, Xcal, 27, G.comp_minimax(0.12, (7, 15))[0])
+    gm = G.Model(ctx, m)
+    depths = [gm.layer_depth(i) for i in range(len(m))]
+    plan = G.BootPlan(ctx, 30, 255, 3, 3)
+    keys = G.Keys(ctx, 7, sorted(set(gm.rotations()) | set(plan.rotations())),
+                  hamming_weight=192, conjugation=True)
+    gm.set_bootstrap(plan)
+    x = W.uniform_inputs(a.batch, 4)
+    ct = G.encrypt(ctx, keys, x, ctx.L, W.SEED_ENC, 0)
+    ctx.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = G.kan_infer(ctx, keys, gm, [ct])
+    level = out.level
+    out.close()
+    for _ in range(a.warmup):
+        G.kan_infer(ctx, keys, gm, [ct]).close()
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    ev[0].record(stream)
+    for i in range(a.steps):
+        G.kan_infer(ctx, keys, gm, [ct]).close()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev[0].elapsed_time(ev[-1]) / a.steps
+    # one refresh of the whole batch alone
+    low = G.level_down(ctx, ct, 0)
+    plan.bootstrap(keys, low).close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.bootstrap(keys, low).close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    refresh_ms = e0.elapsed_time(e1)
+    lv, refreshes = ctx.L, 0
+    for i, d in enumerate(depths):
+        if i > 0 and lv < d:
+            lv, refreshes = plan.stc_level - 3, refreshes + 1
+        lv -= d
+    print(json.dumps({
+        "metric": "encrypted KAN inferences/s (bootstrapped)", "value": a.batch / (ms / 1000.0),
+        "unit": "inferences/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
+        "batch": a.batch, "layer_depths": depths, "refreshes_per_inference": refreshes,
+        "refresh_ms_per_batch": refresh_ms,
+        "refresh_share": refreshes * refresh_ms / ms, "output_level": level,
+        "setup_s": round(setup_s, 1), "clocks": clocks, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": DEEP_DESC, "batch_per_gpu": a.batch,
+                   "l2": "inputs and keys (tens of GB) far above L2"}}), flush=True)
 
 
 def config(a):
@@ -764,6 +839,7 @@ EXTRA_RUNS = [
     ("c5_serve", ["--serve", "--rate", "20", "--duration", "30"], 900),
     ("table3", ["--table3"], 600),
     ("boot", ["--boot", "--steps", "3", "--warmup", "2"], 600),
+    ("deep_kan", ["--deep", "--batch", "32", "--steps", "2", "--warmup", "1"], 900),
 ]
 
 
@@ -776,6 +852,10 @@ def _summary(name, line):
             "batch": line["config"]["batch_per_gpu"], "workload": line["config"]["workload"],
             "alpha": line["config"]["alpha"], "p_bits": line["config"]["p_bits"],
             "dominant_kernel": {k: line["roofline"].get(k) for k in ("kernel", "frac", "unit")}}
+    if name == "deep_kan":
+        return {k: line.get(k) for k in ("value", "unit", "ms_per_step", "batch", "layer_depths",
+                                           "refreshes_per_inference", "refresh_ms_per_batch",
+                                           "refresh_share", "clocks", "config")}
     if name == "boot":
         return {k: line.get(k) for k in ("value", "unit", "ms_per_step", "batch", "latency_ms_batch1",
                                            "max_abs_error", "output_level", "gpu_launches_per_step",
@@ -837,6 +917,8 @@ def main():
         return table3_arm(a)
     if a.boot:
         return boot_arm(a)
+    if a.deep:
+        return deep_arm(a)
     import numpy as np
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -470,6 +470,12 @@ int kan_model_layer_chunks(const kan_model* model, int layer, int* K, int* n_c);
  * graph-owned buffers. Results are identical word for word to the eager
  * schedule. */
 int kan_model_set_graphs(kan_model* model, int enabled);
+/* Deeper networks than the chain holds: with a bootstrapping plan set
+ * (borrowed; NULL clears it), kan_infer brings the batch to level 0 and
+ * refreshes it (ckks_bootstrap) before any layer after the first whose depth
+ * (kan_model_layer_depth) exceeds the batch's level. The keys passed to
+ * kan_infer then need the plan's rotations and the conjugation key too. */
+int kan_model_set_bootstrap(kan_model* model, const ckks_boot* boot);
 /* One layer on a batch: repeat packing (Algorithm 1), B-spline basis
  * (Algorithm 2), fused linear layer W_f = W'P (Algorithm 3, Eq. 13) and the
  * polynomial SiLU branch, both linear maps by BSGS diagonal matvec with

@@ -466,3 +466,18 @@ def bootstrap(ctx, keys, ct, plan):
     lo = kan_he.eval_cheb(ctx, keys, lo, plan.cheb)
     hi = kan_he.eval_cheb(ctx, keys, hi, plan.cheb)
     return slot_to_coeff(ctx, keys, lo, hi, plan.stc)
+
+
+def infer_deep(ctx, keys, x, model, plan, refresh_before):
+    """An encrypted KAN deeper than the chain: before each layer index in
+    refresh_before the batch is brought to level 0 and bootstrapped, then the
+    layers run as in kan_he.infer."""
+    h = x
+    for i, layer in enumerate(model):
+        if i in refresh_before:
+            h = bootstrap(ctx, keys, ckks.level_down(ctx, h, 0), plan)
+        if isinstance(h, (list, tuple)):
+            h = kan_he.layer_eval_chunked(ctx, keys, list(h), layer)
+        else:
+            h = kan_he.layer_eval(ctx, keys, h, layer)
+    return h

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ckks_boot_eval_mod": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
     "ckks_boot_slot_to_coeff": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, PP]),
     "ckks_bootstrap": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
+    "kan_model_set_bootstrap": (c_i32, [c_vp, c_vp]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
     "ckks_keys_export_switch": (c_i32, [c_vp, c_u64, c_vp, c_sz]),
@@ -692,6 +693,12 @@ class Model:
         d = ctypes.c_int()
         check(lib().kan_model_layer_depth(self.h, layer, ctypes.byref(d)))
         return d.value
+
+    def set_bootstrap(self, plan):
+        """Refresh the batch between layers with `plan` (a BootPlan) when
+        the next layer needs more levels than are left; None clears it."""
+        check(lib().kan_model_set_bootstrap(self.h, plan.h if plan is not None else None))
+        self._boot = plan
 
     def set_graphs(self, enabled):
         check(lib().kan_model_set_graphs(self.h, 1 if enabled else 0))

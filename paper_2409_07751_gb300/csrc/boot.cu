@@ -276,15 +276,16 @@ Ct lt_apply_double(Ctx& c, const ckks_keys& keys, const ckks_lt& lt, const ckks_
   DevBuf acc(&c, qp_words * 8);
   for (int i = 0; i < lt.g2; i++) {
     const int64_t G = lt.base + (int64_t)lt.g1 * i * lt.stride;
-    bool first = true;
+    std::vector<const uint64_t*> as, ps;
     for (int j = 0; j < lt.g1; j++) {
       const int k = lt.g1 * i + j;
       if (k >= lt.n_diag || lt.slot[k] < 0) continue;
-      const uint64_t* pt = lt.pts.u64() + (size_t)lt.slot[k] * T.rows * c.N;
-      k_qp_mul_pt_acc(c, R[j].u64(), pt, acc.u64(), v.B * 2, lv, first);
-      first = false;
+      as.push_back(R[j].u64());
+      ps.push_back(lt.pts.u64() + (size_t)lt.slot[k] * T.rows * c.N);
     }
-    if (first) continue;
+    if (as.empty()) continue;
+    k_mul_pt_sum(c, as, ps, acc.u64(), v.B * 2, T.rows, static_cast<const int16_t*>(T.qp_pattern.p),
+                 true);
     Ct inner = ct_alloc(c, v.B, lv - 1, s);
     div_p_ql(c, acc.u64(), v.B, lv, inner->d.u64());
     if (mod_n(G, n)) inner = op_rotate(c, keys, *inner, mod_n(G, n));
@@ -300,26 +301,22 @@ Ct lt_apply(Ctx& c, const ckks_keys& keys, const ckks_lt& lt, const ckks_ct& v) 
   if (lt.form == 1) return lt_apply_double(c, keys, lt, v);
   const int64_t n = (int64_t)c.N / 2;
   const int l = v.level + 1;
-  const size_t rows = v.B * 2 * l;
   std::vector<int64_t> bsteps;
   for (int j = 0; j < lt.g1; j++) bsteps.push_back(j * lt.stride);
   std::vector<Ct> baby = op_rotate_many(c, keys, v, bsteps);
   Ct z;
   for (int i = 0; i < lt.g2; i++) {
     const int64_t G = lt.base + (int64_t)lt.g1 * i * lt.stride;
-    Ct acc;
+    std::vector<const uint64_t*> as, ps;
     for (int j = 0; j < lt.g1; j++) {
       const int k = lt.g1 * i + j;
       if (k >= lt.n_diag || lt.slot[k] < 0) continue;
-      const uint64_t* pt = lt.pts.u64() + (size_t)lt.slot[k] * l * c.N;
-      if (!acc) {
-        acc = ct_alloc(c, v.B, v.level, v.scale * lt.pt_scale);
-        k_mul_pt(c, baby[j]->d.u64(), pt, acc->d.u64(), rows, l);
-      } else {
-        k_mul_pt_acc(c, baby[j]->d.u64(), pt, acc->d.u64(), rows, l);
-      }
+      as.push_back(baby[j]->d.u64());
+      ps.push_back(lt.pts.u64() + (size_t)lt.slot[k] * l * c.N);
     }
-    if (!acc) continue;
+    if (as.empty()) continue;
+    Ct acc = ct_alloc(c, v.B, v.level, v.scale * lt.pt_scale);
+    k_mul_pt_sum(c, as, ps, acc->d.u64(), v.B * 2, l, c.iota(), true);
     Ct inner = op_rescale(c, *acc);
     if (mod_n(G, n)) inner = op_rotate(c, keys, *inner, mod_n(G, n));
     z = z ? op_add(c, *z, *inner, false) : std::move(inner);

@@ -60,6 +60,26 @@ __global__ void qp_mul_pt_acc_kernel(const uint64_t* a, const uint64_t* pt, uint
   }
 }
 
+// acc = (first ? 0 : acc) + sum_j a_j * pt_j (one pass over K diagonal
+// products; row t of every polynomial uses modulus pat[t])
+constexpr int PT_TERMS = 16;
+struct PtPairs {
+  const uint64_t* a[PT_TERMS];
+  const uint64_t* pt[PT_TERMS];
+};
+__global__ void mul_pt_sum_kernel(PtPairs P, int K, uint64_t* acc, size_t total, int log_n,
+                                  DivU32 rows, const int16_t* pat, const Mod* mods, bool first) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, total) {
+    const int t = (int)umod((uint32_t)(i >> log_n), rows);
+    const Mod& m = mods[pat[t]];
+    const size_t off = (size_t)t * N + (i & (N - 1));
+    uint64_t v = first ? 0 : acc[i];
+    for (int j = 0; j < K; j++) v = add_mod(v, mul_mod(P.a[j][i], P.pt[j][off], m), m.q);
+    acc[i] = v;
+  }
+}
+
 // A rotation kept in QP_l: on the Q rows t < l of polynomial 0,
 // R += P sigma(c0) (sigma by the NTT-domain permutation perm); the key
 // product already in R. identity (perm null): R_k = P c_k on the Q rows and
@@ -341,6 +361,27 @@ void k_qp_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* ac
       a, pt, acc, total, c.log_n, divu(T.rows), static_cast<const int16_t*>(T.qp_pattern.p),
       c.dmod(), first);
   CK_CUDA(cudaGetLastError());
+}
+
+void k_mul_pt_sum(Ctx& c, const std::vector<const uint64_t*>& a,
+                  const std::vector<const uint64_t*>& pt, uint64_t* acc, size_t polys, int rows,
+                  const int16_t* pattern, bool first) {
+  if (a.size() != pt.size() || a.empty()) throw Error(CKKS_ERR_INVALID_ARG, "diagonal products");
+  const size_t total = polys * rows * c.N;
+  for (size_t s = 0; s < a.size(); s += PT_TERMS) {
+    const int K = (int)std::min(a.size() - s, (size_t)PT_TERMS);
+    PtPairs P{};
+    for (int j = 0; j < K; j++) {
+      P.a[j] = a[s + j];
+      P.pt[j] = pt[s + j];
+    }
+    const bool f = first && s == 0;
+    Launch L_(c, K_MUL_PT, (K + (f ? 1.0 : 2.0)) * total * 8 + K * (double)rows * c.N * 8,
+              (double)K * total);
+    mul_pt_sum_kernel<<<grid_for(total), TPB, 0, c.stream>>>(P, K, acc, total, c.log_n, divu(rows),
+                                                             pattern, c.dmod(), f);
+    CK_CUDA(cudaGetLastError());
+  }
 }
 
 void k_qp_lift(Ctx& c, const uint64_t* ct, size_t B, int level, const uint32_t* perm, uint64_t* R) {

@@ -118,6 +118,7 @@ struct kan_model {
   std::vector<Layer> layers;
   std::map<std::tuple<int, int, int, int, uint64_t>, std::unique_ptr<DevBuf>> pts;
   bool graphs = false;
+  const ckks_boot* boot = nullptr;  // refresh between layers when levels run short (borrowed)
   std::map<GraphKey, std::unique_ptr<GraphEntry>> graph_cache;  // destroyed before pts
 };
 
@@ -867,6 +868,12 @@ int kan_model_layer_depth(const kan_model* model, int layer, int* depth) {
   return CKKS_OK;
 }
 
+int kan_model_set_bootstrap(kan_model* model, const ckks_boot* boot) {
+  if (!model) return CKKS_ERR_INVALID_ARG;
+  model->boot = boot;
+  return CKKS_OK;
+}
+
 int kan_model_set_graphs(kan_model* model, int enabled) {
   try {
     if (!model) return CKKS_ERR_INVALID_ARG;
@@ -918,7 +925,15 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, const ckks
     }
     Ct h = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
     aligned.clear();
-    for (size_t li = 0; li < model->layers.size(); li++) h = layer_run(*model, (int)li, *keys, *h);
+    for (size_t li = 0; li < model->layers.size(); li++) {
+      // a layer after the first that needs more levels than are left runs on
+      // the refreshed batch: brought to level 0, bootstrapped
+      if (li > 0 && model->boot && h->level < layer_depth(model->layers[li])) {
+        h = op_level_down(c, *h, 0);
+        h = bootstrap(c, *keys, *model->boot, *h);
+      }
+      h = layer_run(*model, (int)li, *keys, *h);
+    }
     *out = h.release();
     return CKKS_OK;
   } catch (...) {

@@ -84,6 +84,12 @@ void k_mul_pt_grouped(Ctx& c, const uint64_t* a, const std::vector<const uint64_
 void k_qp_mul_pt_acc(Ctx& c, const uint64_t* a, const uint64_t* pt, uint64_t* acc, size_t polys,
                      int level, bool first);
 void k_qp_lift(Ctx& c, const uint64_t* ct, size_t B, int level, const uint32_t* perm, uint64_t* R);
+// acc = (first ? 0 : acc) + sum_j a[j] * pt[j] over polys polynomials of
+// `rows` rows (row t modulus pattern[t]; pt[j]: [rows][N]), one pass per 16
+// products
+void k_mul_pt_sum(Ctx& c, const std::vector<const uint64_t*>& a,
+                  const std::vector<const uint64_t*>& pt, uint64_t* acc, size_t polys, int rows,
+                  const int16_t* pattern, bool first);
 // out[b] = sum_c in[b K + c]
 void k_chunk_sum(Ctx& c, const uint64_t* in, uint64_t* out, size_t B, int K, int l);
 void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* out, size_t polys,
@@ -93,6 +99,9 @@ void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* o
 // and the levels it takes
 Ct cheb_eval(Ctx& c, const ckks_keys& keys, const ckks_ct& y, const std::vector<double>& a);
 int cheb_levels(int degree);
+
+// boot.cu: the whole refresh of a level-0 batch with a plan
+Ct bootstrap(Ctx& c, const ckks_keys& keys, const ckks_boot& b, const ckks_ct& in);
 
 // capi.cu: translates the exception being handled into an error code and
 // records its message for ckks_last_error; call only inside a catch block
