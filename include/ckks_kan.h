@@ -471,11 +471,22 @@ int kan_model_layer_chunks(const kan_model* model, int layer, int* K, int* n_c);
  * schedule. */
 int kan_model_set_graphs(kan_model* model, int enabled);
 /* Deeper networks than the chain holds: with a bootstrapping plan set
- * (borrowed; NULL clears it), kan_infer brings the batch to level 0 and
- * refreshes it (ckks_bootstrap) before any layer after the first whose depth
- * (kan_model_layer_depth) exceeds the batch's level. The keys passed to
- * kan_infer then need the plan's rotations and the conjugation key too. */
+ * (borrowed; NULL clears it), kan_infer refreshes the batch before any layer
+ * after the first whose depth (kan_model_layer_depth) exceeds the batch's
+ * level. A batch of several ciphertexts with a level to spare is refreshed
+ * packed: each ciphertext masked to the previous layer's n_out leading slots
+ * (one level), packed by a rotation tree into one ciphertext per N/2 / nb
+ * (nb the least power of two >= n_out; ciphertext b at slots b nb..),
+ * brought to level 0 and bootstrapped, and unpacked by a rotation tree (the
+ * next layer masks its input, so the other blocks do no harm); otherwise
+ * each ciphertext is brought to level 0 and bootstrapped. The keys passed to
+ * kan_infer then need the plan's rotations, the conjugation key and, for
+ * packing, kan_model_refresh_rotations. */
 int kan_model_set_bootstrap(kan_model* model, const ckks_boot* boot);
+/* The rotation steps packed refreshes of a batch of `batch` take (+-s nb,
+ * s = 1, 2, 4, .. below the ciphertexts per packed one, mod N/2). */
+int kan_model_refresh_rotations(const kan_model* model, size_t batch, int32_t* steps, size_t cap,
+                                size_t* n);
 /* One layer on a batch: repeat packing (Algorithm 1), B-spline basis
  * (Algorithm 2), fused linear layer W_f = W'P (Algorithm 3, Eq. 13) and the
  * polynomial SiLU branch, both linear maps by BSGS diagonal matvec with

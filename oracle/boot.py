@@ -468,16 +468,64 @@ def bootstrap(ctx, keys, ct, plan):
     return slot_to_coeff(ctx, keys, lo, hi, plan.stc)
 
 
-def infer_deep(ctx, keys, x, model, plan, refresh_before):
-    """An encrypted KAN deeper than the chain: before each layer index in
-    refresh_before the batch is brought to level 0 and bootstrapped, then the
-    layers run as in kan_he.infer."""
-    h = x
+def pack_tree(ctx, keys, cts, nb):
+    """One ciphertext holding ciphertext b's slots [0, nb) at [b nb, b nb + nb)
+    (the inputs already zero outside [0, nb)): pairs (c_2k, c_2k+1) become
+    c_2k + rot(c_2k+1, -nb), then pairs of pairs with -2 nb, and so on."""
+    cur, step = list(cts), nb
+    while len(cur) > 1:
+        nxt = []
+        for k in range(0, len(cur), 2):
+            if k + 1 < len(cur):
+                nxt.append(ckks.add(ctx, cur[k], ckks.rotate(ctx, keys, cur[k + 1], -step)))
+            else:
+                nxt.append(cur[k])
+        cur, step = nxt, step * 2
+    return cur[0]
+
+
+def unpack_tree(ctx, keys, packed, count, nb):
+    """[rot(packed, b nb) for b < count], each by one rotation of an earlier
+    one: u_(x + s) = rot(u_x, s nb) for s = top/2, top/4, .., 1."""
+    out = {0: packed}
+    s = 1 << max(0, (count - 1).bit_length() - 1) if count > 1 else 0
+    while s >= 1:
+        for x in sorted(out):
+            if x + s < count and x + s not in out:
+                out[x + s] = ckks.rotate(ctx, keys, out[x], s * nb)
+        s //= 2
+    return [out[b] for b in range(count)]
+
+
+def refresh_packed(ctx, keys, hs, n_out, plan):
+    """A batch refreshed with one bootstrap per S / nb ciphertexts (nb the
+    least power of two >= n_out): each output masked to its slots [0, n_out)
+    (one level), packed, brought to level 0, bootstrapped, unpacked."""
+    nb = 1 << max(0, (n_out - 1).bit_length())
+    per = ctx.slots // nb
+    mask = np.ones(n_out)
+    masked = [ckks.mul_plain(ctx, h, mask) for h in hs]
+    out = []
+    for g in range(0, len(masked), per):
+        grp = masked[g:g + per]
+        packed = pack_tree(ctx, keys, grp, nb)
+        fresh = bootstrap(ctx, keys, ckks.level_down(ctx, packed, 0), plan)
+        out.extend(unpack_tree(ctx, keys, fresh, len(grp), nb))
+    return out
+
+
+def infer_deep(ctx, keys, xs, model, plan, refresh_before, packed=False):
+    """An encrypted KAN deeper than the chain, on the batch xs (a list of
+    ciphertexts): before each layer index in refresh_before the batch is
+    refreshed, each ciphertext brought to level 0 and bootstrapped, or, with
+    packed, the whole batch through refresh_packed; the layers run as in
+    kan_he.infer."""
+    hs = list(xs)
     for i, layer in enumerate(model):
         if i in refresh_before:
-            h = bootstrap(ctx, keys, ckks.level_down(ctx, h, 0), plan)
-        if isinstance(h, (list, tuple)):
-            h = kan_he.layer_eval_chunked(ctx, keys, list(h), layer)
-        else:
-            h = kan_he.layer_eval(ctx, keys, h, layer)
-    return h
+            if packed:
+                hs = refresh_packed(ctx, keys, hs, model[i - 1]["n_out"], plan)
+            else:
+                hs = [bootstrap(ctx, keys, ckks.level_down(ctx, h, 0), plan) for h in hs]
+        hs = [kan_he.layer_eval(ctx, keys, h, layer) for h in hs]
+    return hs

@@ -80,6 +80,7 @@ SIGNATURES = {
     "ckks_boot_slot_to_coeff": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, PP]),
     "ckks_bootstrap": (c_i32, [c_vp, c_vp, c_vp, c_vp, PP]),
     "kan_model_set_bootstrap": (c_i32, [c_vp, c_vp]),
+    "kan_model_refresh_rotations": (c_i32, [c_vp, c_sz, c_vp, c_sz, ctypes.POINTER(c_sz)]),
     "ckks_keys_destroy": (c_i32, [c_vp]),
     "ckks_keys_export_secret": (c_i32, [c_vp, c_vp, c_sz]),
     "ckks_keys_export_switch": (c_i32, [c_vp, c_u64, c_vp, c_sz]),
@@ -699,6 +700,15 @@ class Model:
         the next layer needs more levels than are left; None clears it."""
         check(lib().kan_model_set_bootstrap(self.h, plan.h if plan is not None else None))
         self._boot = plan
+
+    def refresh_rotations(self, batch):
+        """Rotation steps the packed refresh of a batch of `batch` takes."""
+        n = c_sz()
+        check(lib().kan_model_refresh_rotations(self.h, batch, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, np.int32)
+        if n.value:
+            check(lib().kan_model_refresh_rotations(self.h, batch, _p(out), n.value, ctypes.byref(n)))
+        return [int(x) for x in out]
 
     def set_graphs(self, enabled):
         check(lib().kan_model_set_graphs(self.h, 1 if enabled else 0))

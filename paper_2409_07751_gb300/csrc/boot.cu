@@ -370,6 +370,70 @@ Ct bootstrap(Ctx& c, const ckks_keys& keys, const ckks_boot& b, const ckks_ct& i
   return boot_slot_to_coeff(c, keys, b, *mlo, *mhi);
 }
 
+// A batch refreshed with one bootstrap per S / nb ciphertexts (nb the least
+// power of two >= n_out): each ciphertext masked to its slots [0, n_out)
+// (one level), packed by a rotation tree (ciphertext b at slots b nb..),
+// brought to level 0 and bootstrapped, unpacked by a rotation tree
+// (u_(x + s) = rot(u_x, s nb) for s = top/2 .. 1); the unpacked ciphertexts
+// hold the others' blocks beyond [0, n_out), which the next layer's input
+// mask removes.
+Ct refresh_packed(Ctx& c, const ckks_keys& keys, const ckks_boot& b, const ckks_ct& in,
+                  int n_out) {
+  if (in.level < 1) throw Error(CKKS_ERR_LEVEL, "packing needs one level");
+  const size_t S = c.N / 2;
+  size_t nb = 1;
+  while (nb < (size_t)n_out) nb *= 2;
+  if (nb > S) throw Error(CKKS_ERR_INVALID_ARG, "block larger than the slots");
+  const size_t per = S / nb;
+  std::vector<double> mask((size_t)n_out, 1.0);
+  const double Spt = plain_scale(c, in.scale, in.level);
+  DevBuf pt = encode_vec(c, mask.data(), mask.size(), in.level, Spt);
+  Ct masked = op_mul_pt(c, in, pt.u64(), Spt);
+  const size_t words = masked->words() / masked->B;
+  std::vector<Ct> outs;
+  for (size_t g = 0; g < in.B; g += per) {
+    const size_t cnt = std::min(per, in.B - g);
+    std::vector<Ct> cur;
+    for (size_t k = 0; k < cnt; k++) {
+      Ct one = ct_alloc(c, 1, masked->level, masked->scale);
+      CK_CUDA(cudaMemcpyAsync(one->d.p, masked->d.u64() + (g + k) * words, words * 8,
+                              cudaMemcpyDeviceToDevice, c.stream));
+      cur.push_back(std::move(one));
+    }
+    int64_t step = (int64_t)nb;
+    while (cur.size() > 1) {
+      std::vector<Ct> nxt;
+      for (size_t k = 0; k < cur.size(); k += 2) {
+        if (k + 1 < cur.size())
+          nxt.push_back(op_add(c, *cur[k], *op_rotate(c, keys, *cur[k + 1], -step), false));
+        else
+          nxt.push_back(std::move(cur[k]));
+      }
+      cur = std::move(nxt);
+      step *= 2;
+    }
+    Ct fresh = bootstrap(c, keys, b, *op_level_down(c, *cur[0], 0));
+    std::map<size_t, Ct> u;
+    u[0] = std::move(fresh);
+    size_t s = 0;
+    if (cnt > 1) {
+      s = 1;
+      while (2 * s <= cnt - 1) s *= 2;
+    }
+    for (; s >= 1; s /= 2) {
+      std::vector<size_t> have;
+      for (auto& kv : u) have.push_back(kv.first);
+      for (size_t x : have)
+        if (x + s < cnt && !u.count(x + s)) u[x + s] = op_rotate(c, keys, *u[x], (int64_t)(s * nb));
+    }
+    for (size_t k = 0; k < cnt; k++) outs.push_back(std::move(u[k]));
+  }
+  if (outs.size() == 1) return std::move(outs[0]);
+  std::vector<const ckks_ct*> parts;
+  for (auto& o : outs) parts.push_back(o.get());
+  return op_concat(c, parts);
+}
+
 // ---------------------------------------------------------------- the plan
 namespace {
 

@@ -874,6 +874,28 @@ int kan_model_set_bootstrap(kan_model* model, const ckks_boot* boot) {
   return CKKS_OK;
 }
 
+int kan_model_refresh_rotations(const kan_model* model, size_t batch, int32_t* steps, size_t cap,
+                                size_t* n) {
+  if (!model || !n || (cap && !steps)) return CKKS_ERR_INVALID_ARG;
+  const int64_t S = (int64_t)model->ctx->N / 2;
+  std::set<int64_t> st;
+  for (size_t li = 1; li < model->layers.size(); li++) {
+    int64_t nb = 1;
+    while (nb < model->layers[li - 1].n_out) nb *= 2;
+    const int64_t per = std::min<int64_t>(S / nb, (int64_t)batch);
+    for (int64_t s = 1; s < per; s *= 2) {
+      st.insert((s * nb) % S);
+      st.insert(((-s * nb) % S + S) % S);
+    }
+  }
+  st.erase(0);
+  *n = st.size();
+  size_t i = 0;
+  for (int64_t v : st)
+    if (i < cap) steps[i++] = (int32_t)v;
+  return CKKS_OK;
+}
+
 int kan_model_set_graphs(kan_model* model, int enabled) {
   try {
     if (!model) return CKKS_ERR_INVALID_ARG;
@@ -927,10 +949,16 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, const ckks
     aligned.clear();
     for (size_t li = 0; li < model->layers.size(); li++) {
       // a layer after the first that needs more levels than are left runs on
-      // the refreshed batch: brought to level 0, bootstrapped
+      // the refreshed batch: packed into as few ciphertexts as the slots
+      // allow when there are several and a level is left for the mask, else
+      // each brought to level 0 and bootstrapped
       if (li > 0 && model->boot && h->level < layer_depth(model->layers[li])) {
-        h = op_level_down(c, *h, 0);
-        h = bootstrap(c, *keys, *model->boot, *h);
+        if (h->B > 1 && h->level >= 1) {
+          h = refresh_packed(c, *keys, *model->boot, *h, model->layers[li - 1].n_out);
+        } else {
+          h = op_level_down(c, *h, 0);
+          h = bootstrap(c, *keys, *model->boot, *h);
+        }
       }
       h = layer_run(*model, (int)li, *keys, *h);
     }

@@ -100,8 +100,11 @@ void k_rescale_finish(Ctx& c, const uint64_t* in, const uint64_t* r, uint64_t* o
 Ct cheb_eval(Ctx& c, const ckks_keys& keys, const ckks_ct& y, const std::vector<double>& a);
 int cheb_levels(int degree);
 
-// boot.cu: the whole refresh of a level-0 batch with a plan
+// boot.cu: the whole refresh of a level-0 batch with a plan, and the
+// packed refresh of a batch whose ciphertexts carry n_out leading slots
 Ct bootstrap(Ctx& c, const ckks_keys& keys, const ckks_boot& b, const ckks_ct& in);
+Ct refresh_packed(Ctx& c, const ckks_keys& keys, const ckks_boot& b, const ckks_ct& in,
+                  int n_out);
 
 // capi.cu: translates the exception being handled into an error code and
 // records its message for ckks_last_error; call only inside a catch block

@@ -195,40 +195,42 @@ def test_bootstrap_full_size(G):
     assert np.abs(G.decrypt(gctx, keys, sq, gctx.slots) - z * z).max() < 3e-3
 
 
-def test_deep_kan_refreshed_between_layers_bit_exact(G):
+@pytest.mark.parametrize("batch", [1, 2])
+def test_deep_kan_refreshed_between_layers_bit_exact(G, batch):
     """Four layers of depth 7 on a 24-level chain: the library refreshes the
-    batch before the fourth layer (levels 24 -> 17 -> 10 -> 3, then 10 after
-    the refresh); the outputs equal the oracle's with the refresh at the same
-    place, word for word, and the HE-friendly FP64 KAN within 1e-4."""
+    batch before the fourth layer (levels 24 -> 17 -> 10 -> 3); a batch of
+    two is refreshed packed (masked to the 5 output slots, one level, packed
+    into one ciphertext, one bootstrap, unpacked: 10 levels after), a single
+    ciphertext alone. The outputs equal the oracle's with the same refresh,
+    word for word, and the HE-friendly FP64 KAN within 1e-4."""
     from oracle import calibrate, kan_he, kan_plain
     from paper_2409_07751_gb300 import workloads as W
     octx, plan, okeys, gctx, gkeys = _setup(G, 7, 24, 2, 6, 127, (2, 2), form="double")
     model = W.make_model("t", widths=[3, 5, 5, 5, 2], G=3, k=2)
     X = W.uniform_inputs(64, 3)
     m = calibrate.calibrate(model, X, 7, [1])
-    rots = sorted(set(kan_he.model_rotations(m, octx.slots)) | set(plan.steps(octx)))
+    gm = G.Model(gctx, m)
+    assert [gm.layer_depth(i) for i in range(len(m))] == [7, 7, 7, 7]
+    assert gm.refresh_rotations(2) == [8, 56]  # +-8: the block of the 5 output slots
+    rots = sorted(set(kan_he.model_rotations(m, octx.slots)) | set(plan.steps(octx))
+                  | set(gm.refresh_rotations(batch)))
     okeys = OB.BootKeys(octx, SEED, rots, h=H)
     gkeys = G.Keys(gctx, SEED, rots, hamming_weight=H, conjugation=True)
-    gm = G.Model(gctx, m)
-    depths = [gm.layer_depth(i) for i in range(len(m))]
-    assert depths == [7, 7, 7, 7]
     probe = OB.kan_he.layer_eval(octx, okeys, O.encrypt(octx, okeys, X[0], octx.L, 1, 0), m[0])
     assert octx.L - probe.level == 7
-    x = X[:2]
-    ocs = [O.encrypt(octx, okeys, x[b], octx.L, W.SEED_ENC, b) for b in range(2)]
+    x = X[:batch]
+    ocs = [O.encrypt(octx, okeys, x[b], octx.L, W.SEED_ENC, b) for b in range(batch)]
     gc = G.Ciphertext.import_(gctx, np.stack([c.data for c in ocs]), octx.L, ocs[0].scale)
-    # the oracle's refresh point, from the levels the layers leave
     stc_level = octx.L - len(plan.cts) - 2 - 8
     gp = _gpu_plan(G, gctx, octx, plan, stc_level)
     gm.set_bootstrap(gp)
     gout = G.kan_infer(gctx, gkeys, gm, [gc])
-    hef = kan_plain.forward(m, x, "poly", "poly")
-    for b in range(2):
-        oo = OB.infer_deep(octx, okeys, ocs[b], m, plan, refresh_before={3})
-        _same(gout, oo, b)
+    oo = OB.infer_deep(octx, okeys, ocs, m, plan, refresh_before={3}, packed=batch > 1)
+    for b in range(batch):
+        _same(gout, oo[b], b)
     assert gout.level == stc_level - len(plan.stc) - 7
-    dec = G.decrypt(gctx, gkeys, gout, 2)
-    assert np.abs(dec - hef).max() < 1e-4
+    hef = kan_plain.forward(m, x, "poly", "poly")
+    assert np.abs(G.decrypt(gctx, gkeys, gout, 2) - hef).max() < 1e-4
     with pytest.raises(G.CkksError):  # without the plan the fourth layer runs out of levels
         gm.set_bootstrap(None)
         G.kan_infer(gctx, gkeys, gm, [gc])
@@ -237,10 +239,11 @@ def test_deep_kan_refreshed_between_layers_bit_exact(G):
 def test_deep_kan_full_size(G):
     """A five-layer [4,8,8,8,4,1] KAN (G=5, k=3, SiLU degree 27, the degree-7
     and 15 minimax comparison with eps 0.12 in the difference form: 12
-    levels per layer) at N = 2^16 on a 29-level 50-bit chain (alpha = 4, log
-    QP = 1750): no leveled chain inside the security budget holds its 60
-    levels; kan_infer refreshes the batch before layers 3, 4 and 5 (12
-    levels left after each refresh). Outputs against the FP64 KAN."""
+    levels per layer, 60 in all) at N = 2^16 on a 29-level 50-bit chain
+    (alpha = 4, log QP = 1750): no leveled chain inside the security budget
+    holds it. Two merged CoeffToSlot levels leave 13 levels per refresh (12
+    for a layer, one for the packing mask); kan_infer refreshes the batch of
+    8 packed before layers 3, 4 and 5. Outputs against the FP64 KAN."""
     from oracle import calibrate, kan_plain, polycomp
     from paper_2409_07751_gb300 import workloads as W
     gctx = G.Context(16, 29, 4, q0_bits=60, scale_bits=50)
@@ -249,15 +252,16 @@ def test_deep_kan_full_size(G):
     m = calibrate.calibrate(model, Xcal, 27, polycomp.composite(0.12, (7, 15))[0])
     gm = G.Model(gctx, m)
     assert [gm.layer_depth(i) for i in range(5)] == [12] * 5
-    gp = G.BootPlan(gctx, 30, 255, 3, 3)
-    assert gp.stc_level - 3 == 12
-    keys = G.Keys(gctx, SEED, sorted(set(gm.rotations()) | set(gp.rotations())),
+    gp = G.BootPlan(gctx, 30, 255, 2, 3)
+    assert gp.stc_level - 3 == 13
+    keys = G.Keys(gctx, SEED, sorted(set(gm.rotations()) | set(gp.rotations())
+                                     | set(gm.refresh_rotations(8))),
                   hamming_weight=192, conjugation=True)
     gm.set_bootstrap(gp)
     x = W.uniform_inputs(8, 4)
     gc = G.encrypt(gctx, keys, x, 29, W.SEED_ENC, 0)
     out = G.kan_infer(gctx, keys, gm, [gc])
-    assert out.level == 0
+    assert out.level == 1
     dec = G.decrypt(gctx, keys, out, 1)
     hef = kan_plain.forward(m, x, "poly", "poly")
     exact = kan_plain.forward(m, x, "exact", "exact")
