@@ -1145,6 +1145,26 @@ def main():
             micro["%s_limbs_per_s" % ("intt" if inv else "ntt")] = rows / s
         del buf
 
+    # ---------------- seed-compressed keys: the same batched step and the
+    # top-level HMult / HRot with the switching keys' uniform halves
+    # regenerated before each key switch
+    compressed = None
+    if not a.no_micro:
+        ck = G.Keys(ctx, W.SEED_KEYS, gm.rotations(), public_seed=W.SEED_KEYS + 0x5EED)
+        full_bytes = ck.nbytes()
+        ck.compress()
+        compressed = {"key_bytes_full": full_bytes, "key_bytes_compressed": ck.nbytes()}
+        s = timed(lambda: G.kan_infer(ctx, ck, gm, cts), 2)
+        compressed["inferences_per_s"] = world * a.batch / s
+        compressed["over_full_keys"] = compressed["inferences_per_s"] / value
+        for B in (1, 64):
+            x = G.encrypt(ctx, ck, X[:B], a.levels, 9, 0)
+            for name, fn in (("hmult", lambda: G.mul(ctx, ck, x, x)),
+                             ("hrot", lambda: G.rotate(ctx, ck, x, 1))):
+                compressed["%s_per_s_l%d_b%d" % (name, a.levels + 1, B)] = B / timed(fn, 3 if B < 64 else 2)
+            x.close()
+        ck.close()
+
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e = None
     if not a.no_e2e:
@@ -1231,6 +1251,7 @@ def main():
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": float(np.percentile(step_ms, 99)), "per": "batch of %d" % a.batch},
             "roofline": roofline, "kernel_time_shares": shares, "kernel_rates": rates,
+            "compressed_keys": compressed,
             "gpu_launches": launches,
             "clocks": clocks, "e2e": e2e, "plain_form": plain, "graph_replay": graph_replay,
             "keyswitch_autotune_ms": tuned, "ntt_autotune": ntt_tune, "micro": micro,

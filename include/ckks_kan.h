@@ -263,9 +263,25 @@ int ckks_rotate_hoisted(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in,
  * slots' complex conjugates). Sparse draw: partial Fisher-Yates shuffle on
  * the ChaCha20 stream (seed, domain 4, id 0), step i swapping position i
  * with i + w32[2i] mod (N - i) and giving the drawn position the sign -1 if
- * w32[2i+1] is odd, else +1. */
+ * w32[2i+1] is odd, else +1. public_seed != 0 (and != seed) draws the
+ * switching keys' uniform halves from that public seed instead of `seed`
+ * (needed by ckks_keys_compress); 0 keeps ckks_keygen's keys. */
 int ckks_keygen_ex(ckks_ctx* ctx, uint64_t seed, int hamming_weight, const int32_t* rot_steps,
-                   size_t n_steps, int conjugation, ckks_keys** out);
+                   size_t n_steps, int conjugation, uint64_t public_seed, ckks_keys** out);
+/* Seed-compressed switching keys (the BSGS section's keys; NEXT-4): a key
+ * pair (b, a) keeps only b, and a is regenerated on the device before each
+ * key switch from the public seed (ChaCha20 stream (public_seed, domain 3,
+ * object 2^40 | g << 8 | j), as at key generation), so every result is
+ * word for word the uncompressed keys'. The resident switching-key bytes
+ * halve; each key switch pays the regeneration (beta_max n_qp limbs of
+ * ChaCha20 output and two copies) in scratch device memory. Only keys made
+ * by ckks_keygen_ex with a public_seed (nonzero, different from the seed)
+ * can be compressed: otherwise the uniform halves come from the secret's
+ * seed, and handing that out would reveal the secret (CKKS_ERR_INVALID_ARG).
+ * Irreversible; ckks_keys_export_switch then exports the regenerated key. */
+int ckks_keys_compress(ckks_keys* keys);
+/* Device bytes the key set holds (secret and switching keys). */
+int ckks_keys_bytes(const ckks_keys* keys, size_t* bytes);
 /* ModRaise: a level-0 batch read over limbs 0..level (the centred residues
  * mod q0 of each coefficient reduced mod every q_t); same scale.
  * CKKS_ERR_LEVEL unless `in` is at level 0 and level <= L. */

@@ -61,6 +61,7 @@ def lib():
         "or_keygen_secret": (None, [vp, u64, vp, vp]),
         "or_target_secret": (None, [vp, vp, u64, vp]),
         "or_keygen_switch": (None, [vp, u64, vp, vp, u64, vp]),
+        "or_keygen_switch_pub": (None, [vp, u64, u64, vp, vp, u64, vp]),
         "or_encode_plain": (i32, [vp, vp, u64, i32, dbl, vp]),
         "or_encrypt": (i32, [vp, vp, vp, u64, i32, u64, u64, vp]),
         "or_decrypt": (None, [vp, vp, vp, i32, dbl, vp, u64]),

@@ -69,12 +69,15 @@ class Ctx:
 
 
 class Keys:
-    """Secret key, relinearisation key and Galois keys, all generated from one seed."""
+    """Secret key, relinearisation key and Galois keys, all generated from one
+    seed; a_seed (optional) draws the switching keys' uniform halves from a
+    separate public seed instead."""
 
-    def __init__(self, ctx, seed, rot_steps=(), relin=True):
+    def __init__(self, ctx, seed, rot_steps=(), relin=True, a_seed=None):
         L = ctx.L_
         self.ctx = ctx
         self.seed = seed
+        self.a_seed = a_seed
         N = ctx.N
         self.s = np.zeros((ctx.n_qp, N), np.uint64)
         self.s_coef = np.zeros(N, np.int64)
@@ -91,7 +94,9 @@ class Keys:
         sp = np.zeros_like(self.s)
         ctx.L_.or_target_secret(ctx.h, ptr(self.s), g, ptr(sp))
         key = np.zeros((ctx.beta_max, 2, ctx.n_qp, ctx.N), np.uint64)
-        ctx.L_.or_keygen_switch(ctx.h, self.seed, ptr(self.s), ptr(sp), g, ptr(key))
+        a_seed = getattr(self, "a_seed", None)
+        ctx.L_.or_keygen_switch_pub(ctx.h, self.seed, self.seed if a_seed is None else a_seed,
+                                    ptr(self.s), ptr(sp), g, ptr(key))
         return key
 
 

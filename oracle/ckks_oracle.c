@@ -672,8 +672,21 @@ void or_target_secret(const or_ctx* c, const uint64_t* s_ntt, uint64_t g, uint64
  * Layout: key[j][0 = b, 1 = a][t][N]. Randomness: seed, object id
  * X = 2^40 | g<<8 | j (g = 0 for relinearisation).
  */
+void or_keygen_switch_pub(const or_ctx* c, uint64_t seed, uint64_t a_seed,
+                          const uint64_t* s_ntt, const uint64_t* sp_ntt, uint64_t g,
+                          uint64_t* key);
+
 void or_keygen_switch(const or_ctx* c, uint64_t seed, const uint64_t* s_ntt,
                       const uint64_t* sp_ntt, uint64_t g, uint64_t* key) {
+  or_keygen_switch_pub(c, seed, seed, s_ntt, sp_ntt, g, key);
+}
+
+/* The same with the uniform halves a drawn from a_seed instead of seed: a
+ * public seed, independent of the secret's, from which a holder of the key
+ * can regenerate a (seed-compressed keys) without learning anything of s. */
+void or_keygen_switch_pub(const or_ctx* c, uint64_t seed, uint64_t a_seed,
+                          const uint64_t* s_ntt, const uint64_t* sp_ntt, uint64_t g,
+                          uint64_t* key) {
   const uint64_t N = c->N;
   int64_t* e = malloc(N * sizeof(int64_t));
   uint64_t* et = malloc(N * sizeof(uint64_t));
@@ -684,7 +697,7 @@ void or_keygen_switch(const or_ctx* c, uint64_t seed, const uint64_t* s_ntt,
       const uint64_t q = c->mod[t];
       uint64_t* b = key + (((uint64_t)j * 2 + 0) * c->n_qp + t) * N;
       uint64_t* a = key + (((uint64_t)j * 2 + 1) * c->n_qp + t) * N;
-      or_sample_uniform(seed, X, (uint32_t)t, q, c->log_n, a);
+      or_sample_uniform(a_seed, X, (uint32_t)t, q, c->log_n, a);
       int_to_ntt(c, e, t, et);
       const int in_digit = (t <= c->L) && (t / c->alpha == j);
       uint64_t Pmod = 1 % q;

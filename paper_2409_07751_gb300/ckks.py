@@ -53,7 +53,9 @@ SIGNATURES = {
     "ckks_autotune_ntt": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "ckks_set_ntt_shape": (c_i32, [c_vp, c_i32, c_i32]),
     "ckks_keygen": (c_i32, [c_vp, c_u64, c_vp, c_sz, PP]),
-    "ckks_keygen_ex": (c_i32, [c_vp, c_u64, c_i32, c_vp, c_sz, c_i32, PP]),
+    "ckks_keygen_ex": (c_i32, [c_vp, c_u64, c_i32, c_vp, c_sz, c_i32, c_u64, PP]),
+    "ckks_keys_compress": (c_i32, [c_vp]),
+    "ckks_keys_bytes": (c_i32, [c_vp, ctypes.POINTER(c_sz)]),
     "ckks_mod_raise": (c_i32, [c_vp, c_vp, c_i32, PP]),
     "ckks_conjugate": (c_i32, [c_vp, c_vp, c_vp, PP]),
     "ckks_mul_monomial": (c_i32, [c_vp, c_vp, c_i64, PP]),
@@ -262,13 +264,14 @@ class Keys:
     """Secret, relinearisation and Galois keys. hamming_weight > 0 draws a
     sparse secret of that weight; conjugation adds the key of X -> X^-1."""
 
-    def __init__(self, ctx, seed, rot_steps=(), hamming_weight=0, conjugation=False):
+    def __init__(self, ctx, seed, rot_steps=(), hamming_weight=0, conjugation=False,
+                 public_seed=0):
         steps = np.ascontiguousarray(list(rot_steps), dtype=np.int32)
         h = c_vp()
-        if hamming_weight or conjugation:
+        if hamming_weight or conjugation or public_seed:
             check(lib().ckks_keygen_ex(ctx.h, seed, int(hamming_weight),
                                        _p(steps) if len(steps) else None, len(steps),
-                                       int(bool(conjugation)), ctypes.byref(h)))
+                                       int(bool(conjugation)), int(public_seed), ctypes.byref(h)))
         else:
             check(lib().ckks_keygen(ctx.h, seed, _p(steps) if len(steps) else None, len(steps),
                                     ctypes.byref(h)))
@@ -284,6 +287,15 @@ class Keys:
             self.close()
         except Exception:
             pass
+
+    def compress(self):
+        """Keep only the switching keys' b halves (seed-compressed keys)."""
+        check(lib().ckks_keys_compress(self.h))
+
+    def nbytes(self):
+        n = c_sz()
+        check(lib().ckks_keys_bytes(self.h, ctypes.byref(n)))
+        return n.value
 
     def export_secret(self):
         out = np.zeros((self.ctx.n_qp, self.ctx.N), np.uint64)

@@ -259,13 +259,13 @@ Ct lt_apply_double(Ctx& c, const ckks_keys& keys, const ckks_lt& lt, const ckks_
   DevBuf ext;
   for (int j = 1; j < lt.g1; j++) {
     const uint64_t g = c.galois(j * lt.stride);
-    auto it = keys.galois.find(g);
-    if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
+    DevBuf kt;
+    const uint64_t* key = switch_key_words(c, keys, g, kt);
     if (!ext.p) {
       ext = DevBuf(&c, v.B * T.beta * T.rows * c.N * 8);
       modup(c, v.d.u64() + (size_t)l * c.N, v.B, lv, ext.u64(), 2 * (size_t)l * c.N);
     }
-    DevBuf acc = keyswitch_qp(c, ext.u64(), v.B, lv, it->second->u64(), g);
+    DevBuf acc = keyswitch_qp(c, ext.u64(), v.B, lv, key, g);
     k_qp_lift(c, v.d.u64(), v.B, lv, c.perm(g), acc.u64());
     R.push_back(std::move(acc));
   }
@@ -601,13 +601,14 @@ void need(bool cond, const char* what) {
 extern "C" {
 
 int ckks_keygen_ex(ckks_ctx* ctx, uint64_t seed, int hamming_weight, const int32_t* rot_steps,
-                   size_t n_steps, int conjugation, ckks_keys** out) {
+                   size_t n_steps, int conjugation, uint64_t public_seed, ckks_keys** out) {
   return guard([&] {
     need(ctx && out, "NULL argument");
     need(n_steps == 0 || rot_steps, "rot_steps is NULL");
     need(hamming_weight >= 0, "negative Hamming weight");
+    need(public_seed == 0 || public_seed != seed, "the public seed must differ from the seed");
     std::vector<int64_t> steps(rot_steps, rot_steps + n_steps);
-    *out = keygen(ctx->c, seed, steps, hamming_weight, conjugation != 0).release();
+    *out = keygen(ctx->c, seed, steps, hamming_weight, conjugation != 0, public_seed).release();
   });
 }
 

@@ -205,6 +205,22 @@ int ckks_keygen(ckks_ctx* ctx, uint64_t seed, const int32_t* rot_steps, size_t n
   });
 }
 
+int ckks_keys_compress(ckks_keys* keys) {
+  return guard([&] {
+    need(keys != nullptr, "NULL argument");
+    keys_compress(*keys->ctx, *keys);
+  });
+}
+
+int ckks_keys_bytes(const ckks_keys* keys, size_t* bytes) {
+  return guard([&] {
+    need(keys && bytes, "NULL argument");
+    size_t b = keys->s.bytes + keys->relin.bytes;
+    for (auto& kv : keys->galois) b += kv.second->bytes;
+    *bytes = b;
+  });
+}
+
 int ckks_keys_destroy(ckks_keys* keys) {
   return guard([&] { delete keys; });
 }
@@ -223,17 +239,12 @@ int ckks_keys_export_switch(const ckks_keys* keys, uint64_t galois, uint64_t* ho
                             size_t cap_words) {
   return guard([&] {
     need(keys && host, "NULL argument");
-    const DevBuf* b = nullptr;
-    if (galois == 0) {
-      b = &keys->relin;
-    } else {
-      auto it = keys->galois.find(galois);
-      if (it == keys->galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "no such Galois key");
-      b = it->second.get();
-    }
-    need(cap_words * 8 >= b->bytes, "buffer too small");
     Ctx& c = *keys->ctx;
-    CK_CUDA(cudaMemcpyAsync(host, b->p, b->bytes, cudaMemcpyDeviceToHost, c.stream));
+    const size_t bytes = (size_t)c.beta_max * 2 * c.n_qp * c.N * 8;
+    need(cap_words * 8 >= bytes, "buffer too small");
+    DevBuf tmp;
+    const uint64_t* w = switch_key_words(c, *keys, galois, tmp);
+    CK_CUDA(cudaMemcpyAsync(host, w, bytes, cudaMemcpyDeviceToHost, c.stream));
     CK_CUDA(cudaStreamSynchronize(c.stream));
   });
 }

@@ -177,6 +177,12 @@ struct ckks_keys {
   ck::DevBuf s;                                   // [n_qp][N] NTT form
   ck::DevBuf relin;                               // [beta_max][2][n_qp][N]
   std::map<uint64_t, std::unique_ptr<ck::DevBuf>> galois;
+  // the switching keys' uniform halves come from this public seed (the
+  // secret's seed when none was given); seed-compressed keys keep only the
+  // b halves ([beta_max][n_qp][N]) and regenerate a from it on use
+  uint64_t a_seed = 0;
+  bool own_a_seed = false;
+  bool compressed = false;
 };
 
 struct ckks_ct {
@@ -292,6 +298,10 @@ void decode_limb0(Ctx& c, const uint64_t* m, size_t B, double scale, double* d_o
 
 // ---- sampling (sample.cu)
 void sample_ternary(Ctx& c, uint64_t seed, int64_t* out);
+// uniform residues of objects id_base .. id_base + count - 1, object o at
+// out + o obj_rows N (rows rows each, moduli pattern[r])
+void sample_uniform_seq(Ctx& c, uint64_t seed, uint64_t id_base, size_t count, int rows,
+                        const int16_t* pattern, uint64_t* out, size_t obj_rows);
 void sample_sparse_ternary(Ctx& c, uint64_t seed, int h, int64_t* out);
 void sample_cbd(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int64_t* out);
 void sample_uniform(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int rows,

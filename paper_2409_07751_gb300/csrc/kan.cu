@@ -267,14 +267,14 @@ Ct bsgs_matvec_double(kan_model& M, int li, int tag, const Plan& p, DV&& dval,
   DevBuf ext;
   for (int j = 1; j < p.g1; j++) {
     const uint64_t g = c.galois(j);
-    auto it = keys.galois.find(g);
-    if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
+    DevBuf kt;
+    const uint64_t* key = switch_key_words(c, keys, g, kt);
     if (!ext.p) {
       ext = DevBuf(&c, v.B * T.beta * T.rows * c.N * 8);
       // c1 of batch element b sits at v + (2b + 1) l N
       modup(c, v.d.u64() + (size_t)l * c.N, v.B, lv, ext.u64(), 2 * (size_t)l * c.N);
     }
-    DevBuf acc = keyswitch_qp(c, ext.u64(), v.B, lv, it->second->u64(), g);
+    DevBuf acc = keyswitch_qp(c, ext.u64(), v.B, lv, key, g);
     k_qp_lift(c, v.d.u64(), v.B, lv, c.perm(g), acc.u64());
     R.push_back(std::move(acc));
   }

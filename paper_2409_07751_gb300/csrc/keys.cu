@@ -71,6 +71,7 @@ __global__ void decrypt_limb0_kernel(const uint64_t* ct, const uint64_t* s, uint
 
 std::unique_ptr<DevBuf> switch_key(Ctx& c, const ckks_keys& k, uint64_t seed, uint64_t g,
                                    const int64_t* s_coef_dev) {
+  const uint64_t a_seed = k.own_a_seed ? k.a_seed : seed;
   (void)s_coef_dev;
   const size_t N = c.N;
   const int beta = c.beta_max, n_qp = c.n_qp;
@@ -89,7 +90,7 @@ std::unique_ptr<DevBuf> switch_key(Ctx& c, const ckks_keys& k, uint64_t seed, ui
   ntt_forward(c, er.u64(), (size_t)beta * n_qp, c.iota(), n_qp);
   auto key = std::make_unique<DevBuf>(&c, (size_t)beta * 2 * n_qp * N * 8);
   DevBuf a(&c, (size_t)beta * n_qp * N * 8);
-  sample_uniform(c, seed, d_ids.u64(), beta, n_qp, c.iota(), a.u64());
+  sample_uniform(c, a_seed, d_ids.u64(), beta, n_qp, c.iota(), a.u64());
   CK_CUDA(cudaMemcpy2DAsync(key->u64() + (size_t)n_qp * N, 2 * (size_t)n_qp * N * 8, a.p,
                             (size_t)n_qp * N * 8, (size_t)n_qp * N * 8, beta,
                             cudaMemcpyDeviceToDevice, c.stream));
@@ -106,9 +107,11 @@ std::unique_ptr<DevBuf> switch_key(Ctx& c, const ckks_keys& k, uint64_t seed, ui
 }  // namespace
 
 std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps,
-                                  int hamming, bool conjugation) {
+                                  int hamming, bool conjugation, uint64_t a_seed) {
   auto k = std::make_unique<ckks_keys>();
   k->ctx = &c;
+  k->a_seed = a_seed ? a_seed : seed;
+  k->own_a_seed = a_seed != 0;
   const size_t N = c.N;
   DevBuf sc(&c, N * 8);
   if (hamming > 0)
@@ -127,6 +130,44 @@ std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64
   if (conjugation) k->galois[2 * N - 1] = switch_key(c, *k, seed, 2 * N - 1, nullptr);
   CK_CUDA(cudaStreamSynchronize(c.stream));
   return k;
+}
+
+const uint64_t* switch_key_words(Ctx& c, const ckks_keys& keys, uint64_t g, DevBuf& tmp) {
+  const DevBuf* b = nullptr;
+  if (g == 0) {
+    b = &keys.relin;
+  } else {
+    auto it = keys.galois.find(g);
+    if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
+    b = it->second.get();
+  }
+  if (!keys.compressed) return b->u64();
+  const size_t N = c.N, rows = (size_t)c.n_qp, beta = (size_t)c.beta_max;
+  tmp = DevBuf(&c, beta * 2 * rows * N * 8);
+  CK_CUDA(cudaMemcpy2DAsync(tmp.p, 2 * rows * N * 8, b->p, rows * N * 8, rows * N * 8, beta,
+                            cudaMemcpyDeviceToDevice, c.stream));
+  sample_uniform_seq(c, keys.a_seed, (1ull << 40) | (g << 8), beta, c.n_qp, c.iota(),
+                     tmp.u64() + rows * N, 2 * rows);
+  return tmp.u64();
+}
+
+void keys_compress(Ctx& c, ckks_keys& keys) {
+  if (keys.compressed) return;
+  if (!keys.own_a_seed)
+    throw Error(CKKS_ERR_INVALID_ARG,
+                "keys drew their uniform halves from the secret's seed; generate them with a "
+                "public seed to compress them");
+  const size_t N = c.N, rows = (size_t)c.n_qp, beta = (size_t)c.beta_max;
+  auto halve = [&](DevBuf& full) {
+    DevBuf b(&c, beta * rows * N * 8);
+    CK_CUDA(cudaMemcpy2DAsync(b.p, rows * N * 8, full.p, 2 * rows * N * 8, rows * N * 8, beta,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    full = std::move(b);
+  };
+  halve(keys.relin);
+  for (auto& kv : keys.galois) halve(*kv.second);
+  keys.compressed = true;
+  CK_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 Ct encrypt(Ctx& c, const ckks_keys& keys, const double* values, size_t B, size_t n, int level,

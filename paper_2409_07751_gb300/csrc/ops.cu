@@ -233,7 +233,8 @@ static Ct relinearise(Ctx& c, const ckks_keys& keys, const DevBuf& d, size_t B, 
   modup(c, d2.u64(), B, level, ext.u64());
   d2.reset();
   Ct ks = ct_alloc(c, B, level, scale);
-  keyswitch_ext(c, ext.u64(), B, level, keys.relin.u64(), 0, ks->d.u64());
+  DevBuf kt;
+  keyswitch_ext(c, ext.u64(), B, level, switch_key_words(c, keys, 0, kt), 0, ks->d.u64());
   ext.reset();
   // (d0, d1) of each batch element sit at the start of its 3-poly block
   Ct r = ct_alloc(c, B, level, scale);
@@ -257,7 +258,9 @@ static Ct relin_rescale(Ctx& c, const ckks_keys& keys, const DevBuf& d, size_t B
   const double dl = c.delta[level - 1];
   if (fabs(s / dl - 1.0) < SNAP) s = dl;
   Ct r = ct_alloc(c, B, level - 1, s);
-  relin_rescale_ext(c, d.u64(), ext.u64(), B, level, keys.relin.u64(), r->d.u64());
+  DevBuf kt;
+  relin_rescale_ext(c, d.u64(), ext.u64(), B, level, switch_key_words(c, keys, 0, kt),
+                    r->d.u64());
   return r;
 }
 
@@ -312,15 +315,15 @@ std::vector<Ct> op_galois_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
       out.push_back(ct_copy(c, a));
       continue;
     }
-    auto it = keys.galois.find(g);
-    if (it == keys.galois.end()) throw Error(CKKS_ERR_MISSING_KEY, "missing Galois key");
+    DevBuf kt;
+    const uint64_t* key = switch_key_words(c, keys, g, kt);
     if (!ext.p) {
       ext = DevBuf(&c, a.B * T.beta * T.rows * c.N * 8);
       // c1 of batch element b sits at a + (2b + 1) l N
       modup(c, a.d.u64() + (size_t)l * c.N, a.B, a.level, ext.u64(), 2 * (size_t)l * c.N);
     }
     Ct ks = ct_alloc(c, a.B, a.level, a.scale);
-    keyswitch_ext(c, ext.u64(), a.B, a.level, it->second->u64(), g, ks->d.u64());
+    keyswitch_ext(c, ext.u64(), a.B, a.level, key, g, ks->d.u64());
     Ct r = ct_alloc(c, a.B, a.level, a.scale);
     // c0' = sigma(c0) + ks0, c1' = ks1
     k_rotate_finish(c, a.d.u64(), ks->d.u64(), c.perm(g), r->d.u64(), a.B, l);

@@ -53,9 +53,17 @@ std::vector<Ct> op_galois_many(Ctx& c, const ckks_keys& keys, const ckks_ct& a,
 Ct op_concat(Ctx& c, const std::vector<const ckks_ct*>& in);
 
 // keys.cu: hamming > 0 draws a sparse secret of that weight; conjugation
-// adds the key of the Galois element 2N - 1
+// adds the key of the Galois element 2N - 1; a_seed != 0 draws the switching
+// keys' uniform halves from that public seed
 std::unique_ptr<ckks_keys> keygen(Ctx& c, uint64_t seed, const std::vector<int64_t>& steps,
-                                  int hamming = 0, bool conjugation = false);
+                                  int hamming = 0, bool conjugation = false, uint64_t a_seed = 0);
+// the switching key of Galois element g (0: relinearisation) as
+// [beta_max][2][n_qp][N] words: the stored key, or for seed-compressed keys
+// the b halves with the a halves regenerated into `tmp`
+// (CKKS_ERR_MISSING_KEY if there is none)
+const uint64_t* switch_key_words(Ctx& c, const ckks_keys& keys, uint64_t g, DevBuf& tmp);
+// drop the uniform halves of every switching key (keys with a public seed)
+void keys_compress(Ctx& c, ckks_keys& keys);
 Ct encrypt(Ctx& c, const ckks_keys& keys, const double* values, size_t B, size_t n, int level,
            uint64_t seed, uint64_t first_index);
 void decrypt(Ctx& c, const ckks_keys& keys, const ckks_ct& ct, double* out, size_t n);

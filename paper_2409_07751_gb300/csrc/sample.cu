@@ -110,6 +110,32 @@ __global__ void uniform_kernel(uint64_t seed, const uint64_t* ids, size_t count,
   }
 }
 
+// the same stream as uniform_kernel for objects id_base + o; object o
+// written at out + o * obj_rows * N (rows of another layout between objects)
+__global__ void uniform_seq_kernel(uint64_t seed, uint64_t id_base, size_t count, int rows,
+                                   const int16_t* pattern, const Mod* mods, uint64_t* out,
+                                   size_t obj_rows, size_t N) {
+  const size_t per = N / 4;
+  GRID_LOOP(idx, count * rows * per) {
+    const size_t blk = idx % per;
+    const size_t orow = idx / per;
+    const int r = (int)(orow % rows);
+    const size_t o = orow / rows;
+    const int t = pattern[r];
+    const Mod m = mods[t];
+    uint32_t w[16];
+    chacha_block(seed, 3, ((id_base + o) << 8) | (uint64_t)t, (uint32_t)blk, w);
+    const uint64_t two64 = (0 - m.q) % m.q;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint64_t lo = (uint64_t)w[4 * k] | ((uint64_t)w[4 * k + 1] << 32);
+      const uint64_t hi = (uint64_t)w[4 * k + 2] | ((uint64_t)w[4 * k + 3] << 32);
+      const uint64_t v = add_mod(mul_mod(hi % m.q, two64, m), lo % m.q, m.q);
+      out[(o * obj_rows + r) * N + blk * 4 + k] = v;
+    }
+  }
+}
+
 __global__ void sparse_init_kernel(int64_t* s, uint32_t* perm, size_t N) {
   GRID_LOOP(i, N) {
     s[i] = 0;
@@ -165,6 +191,14 @@ void sample_ternary(Ctx& c, uint64_t seed, int64_t* out) {
 void sample_cbd(Ctx& c, uint64_t seed, const uint64_t* ids, size_t count, int64_t* out) {
   Launch L_(c, K_SAMPLE, count * c.N * 8.0);
   cbd_kernel<<<grid_for(count * c.N / 8), TPB, 0, c.stream>>>(seed, ids, count, out, c.N);
+  CK_CUDA(cudaGetLastError());
+}
+
+void sample_uniform_seq(Ctx& c, uint64_t seed, uint64_t id_base, size_t count, int rows,
+                        const int16_t* pattern, uint64_t* out, size_t obj_rows) {
+  Launch L_(c, K_SAMPLE, count * rows * c.N * 8.0);
+  uniform_seq_kernel<<<grid_for(count * rows * c.N / 4), TPB, 0, c.stream>>>(
+      seed, id_base, count, rows, pattern, c.dmod(), out, obj_rows, c.N);
   CK_CUDA(cudaGetLastError());
 }
 

@@ -550,3 +550,39 @@ def test_keyswitch_rounding_is_unbiased():
     e_mul = ckks.decrypt(ctx, keys, ckks.mul(ctx, keys, cx, cy)) - x * y
     assert np.abs(e_rot).max() < 1e-7 and abs(e_rot.mean()) < 1e-10
     assert np.abs(e_mul).max() < 1e-7 and abs(e_mul.mean()) < 1e-10
+
+
+def test_switch_keys_with_a_public_seed():
+    """Switching keys whose uniform halves come from a public seed: the
+    default (public seed = seed) gives the same keys word for word; another
+    public seed changes every a half, leaves the secret alone, and every
+    digit row t still satisfies the key equation b + a s = e + [t in digit j]
+    [P]_q s' mod q_t with e the small centred-binomial error (checked in the
+    coefficient domain, |e| <= 21)."""
+    ctx = ckks.Ctx(ckks.Params(log_n=6, n_scale=5, n_special=2))
+    L = lib()
+    k0 = ckks.Keys(ctx, 11, rot_steps=[1])
+    k1 = ckks.Keys(ctx, 11, rot_steps=[1], a_seed=11)
+    k2 = ckks.Keys(ctx, 11, rot_steps=[1], a_seed=12345)
+    assert (k0.relin == k1.relin).all() and (k0.s == k2.s).all()
+    g = ctx.galois(1)
+    for key0, key, gg in ((k0.relin, k2.relin, 0), (k0.galois[g], k2.galois[g], g)):
+        assert not (key0[:, 1] == key[:, 1]).any(axis=-1).all()
+        sp = np.zeros_like(k2.s)
+        L.or_target_secret(ctx.h, ptr(k2.s), gg, ptr(sp))
+        P = 1
+        for p in ctx.pm:
+            P *= p
+        for j in range(ctx.beta_max):
+            for t in range(ctx.n_qp):
+                q = int(ctx.moduli[t])
+                b = key[j, 0, t].astype(object)
+                a = key[j, 1, t].astype(object)
+                s = k2.s[t].astype(object)
+                e = (b + a * s) % q
+                if t <= ctx.L and t // ctx.alpha == j:
+                    e = (e - (P % q) * sp[t].astype(object)) % q
+                row = np.array([int(v) for v in e], dtype=np.uint64)
+                L.or_ntt_limb(ctx.h, ptr(row), t, 1)
+                c = np.array([int(v) if int(v) <= q // 2 else int(v) - q for v in row])
+                assert np.abs(c).max() <= 21, (j, t)
