@@ -101,6 +101,8 @@ def args_():
     p.add_argument("--oracle-micro", action="store_true",
                    help="with --impl reference: also time the oracle's NTT per limb, HMult and "
                         "HRot at the top level (single thread; about a minute)")
+    p.add_argument("--bsgs", default="single", choices=["single", "double"],
+                   help="BSGS form of the KAN layers' matvecs (hoisted or double-hoisted)")
     p.add_argument("--boot", action="store_true", help="time CKKS bootstrapping at N=2^16")
     p.add_argument("--deep", action="store_true",
                    help="time a five-layer KAN refreshed by bootstrapping between layers")
@@ -521,6 +523,7 @@ def config(a):
             "parallelism": "replicas (request sharding)",
             "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)",
             "schedule": "CUDA graph per layer" if getattr(a, "graphs", False) else "eager",
+            "bsgs": getattr(a, "bsgs", "single"),
             "alpha": getattr(a, "alpha", 4), "p_bits": getattr(a, "p_bits", 60),
             "log_qp": 60 + 40 * a.levels + getattr(a, "alpha", 4) * getattr(a, "p_bits", 60)}
 
@@ -550,7 +553,7 @@ def workload(a):
 def model_and_inputs(a, rank):
     from paper_2409_07751_gb300 import workloads as W
     wl = workload(a)
-    model = [dict(L, b0=wl["b0"]) for L in W.make_model(wl["model"])]
+    model = [dict(L, b0=wl["b0"], bsgs=a.bsgs) for L in W.make_model(wl["model"])]
     n_in = model[0]["n_in"]
     gen = {"uniform": lambda n, s: W.uniform_inputs(n, n_in, seed=s),
            "blob": lambda n, s: W.blob_images(n, seed=s),
