@@ -841,7 +841,7 @@ def oracle_micro(a):
 
 # ------------------------------------------------------------------ other configurations
 EXTRA_RUNS = [
-    ("c1", ["--workload", "c1", "--steps", "20", "--warmup", "3"], 300),
+    ("c1", ["--workload", "c1", "--steps", "20", "--warmup", "3", "--graphs"], 300),
     ("c3", ["--workload", "c3", "--steps", "3", "--warmup", "3"], 600),
     ("c4", ["--workload", "c4", "--steps", "3", "--warmup", "3"], 600),
     ("c5_serve", ["--serve", "--rate", "20", "--duration", "30"], 900),

@@ -170,11 +170,75 @@ def mul_monomial(ctx, a, k):
 # half-size problem on 2h slots). As cyclic diagonals of the slot vector
 # (offset o: the factor of rot(x, o), rot moving slot p + o to p) a stage has
 # offsets 0, +h, -h; r stages merged have offsets k 2^a, |k| < 2^r.
+ROOT_LOG = 17  # every stage root is a 2^17-th root of unity (N <= 2^16)
+
+
+def _cos_sin_decimal(k, log_m):
+    """(cos, sin)(2 pi k / 2^log_m) for 0 <= k <= 2^log_m / 8, correctly
+    rounded to double from a 40-digit Taylor series (the same bits on every
+    machine, unlike a platform math library)."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 40
+    pi = Decimal("3.141592653589793238462643383279502884197169399375")
+    x = 2 * pi * k / (Decimal(2) ** log_m)
+    c = s = Decimal(0)
+    term = Decimal(1)  # x^n / n!
+    for n in range(0, 60):
+        if n % 4 == 0:
+            c += term
+        elif n % 4 == 1:
+            s += term
+        elif n % 4 == 2:
+            c -= term
+        else:
+            s -= term
+        term = term * x / (n + 1)
+    return float(c), float(s)
+
+
+_ROOTS = {}
+
+
+def _root_table(log_m):
+    """(cos, sin)(2 pi k / 2^log_m) for every k, from the first octant by the
+    exact symmetries cos(pi/2 - t) = sin t and quarter turns."""
+    if log_m in _ROOTS:
+        return _ROOTS[log_m]
+    M = 1 << log_m
+    o = M // 8
+    base = [_cos_sin_decimal(k, log_m) for k in range(o + 1)]
+    cs = np.zeros(M)
+    sn = np.zeros(M)
+    for k in range(M // 4 + 1):  # first quadrant
+        if k <= o:
+            c, s_ = base[k]
+        else:
+            s_, c = base[M // 4 - k]
+        cs[k % M], sn[k % M] = c, s_
+    for k in range(M // 4 + 1, M):
+        q, r = divmod(k, M // 4)
+        c, s_ = cs[r], sn[r]
+        for _ in range(q):  # times i: (c, s) -> (-s, c)
+            c, s_ = -s_, c
+        cs[k], sn[k] = c, s_
+    _ROOTS[log_m] = (cs, sn)
+    return _ROOTS[log_m]
+
+
 def _stage_roots(h):
-    r = np.arange(h)
-    e = np.array([pow(5, int(x), 8 * h) for x in r], dtype=np.float64)
-    ang = 2.0 * math.pi * e / (8.0 * h)
-    return np.cos(ang) + 1j * np.sin(ang)
+    """w_r = exp(2 pi i (5^r mod 8h) / (8h)) for r < h: the 2^17-th roots
+    of unity at k = (5^r mod 8h) 2^17 / (8h)."""
+    cs, sn = _root_table(ROOT_LOG)
+    k = np.array([pow(5, int(x), 8 * h) for x in range(h)], dtype=np.int64) * ((1 << ROOT_LOG) // (8 * h))
+    return cs[k] + 1j * sn[k]
+
+
+def _cmul(a, b):
+    """a * b elementwise with each real product and sum rounded once (the
+    same bits on every machine)."""
+    re = np.subtract(np.multiply(a.real, b.real), np.multiply(a.imag, b.imag))
+    im = np.add(np.multiply(a.real, b.imag), np.multiply(a.imag, b.real))
+    return re + 1j * im
 
 
 def fft_stage(ctx, s, inverse=False):
@@ -207,7 +271,7 @@ def compose(ctx, A, B):
     for a in sorted(A):
         for b in sorted(B):
             o = (a + b) % n
-            term = A[a] * np.roll(B[b], -a)
+            term = _cmul(A[a], np.roll(B[b], -a))
             out[o] = out[o] + term if o in out else term
     return out
 

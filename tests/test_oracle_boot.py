@@ -244,3 +244,19 @@ def test_bootstrap_restores_the_slots(fx, bound, request):
     assert np.abs(got.imag).max() < bound
     sq = ckks.mul(ctx, keys, out, out)  # the refreshed levels are usable
     assert np.abs(ckks.decrypt(ctx, keys, sq) - z * z).max() < 3 * bound
+
+
+def test_stage_roots_are_correctly_rounded():
+    """The transforms' roots of unity (the 2^17-th roots) equal mpmath's
+    50-digit cos and sin rounded to double, bit for bit, at a spread of
+    indices in every octant: the plan's diagonals are the same on every
+    machine."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    cs, sn = boot._root_table(boot.ROOT_LOG)
+    M = 1 << boot.ROOT_LOG
+    for k in list(range(1, M, 997)) + [M // 8, 3 * M // 8, M - 1]:
+        t = 2 * mpmath.pi * k / M
+        assert cs[k] == float(mpmath.cos(t)) and sn[k] == float(mpmath.sin(t)), k
+    for q, (c, s_) in enumerate(((1, 0), (0, 1), (-1, 0), (0, -1))):  # quarter turns exactly
+        assert cs[q * M // 4] == c and sn[q * M // 4] == s_
