@@ -303,7 +303,8 @@ int ckks_mul_const_wide(ckks_ctx* ctx, const ckks_ct* in, double value, ckks_ct*
  * all-zero diagonal is skipped), copied and encoded at creation (device
  * plaintexts [nonzero][level+1][N], over QP_level for form 1). Applied by
  * baby-step giant-step with g1 baby steps (0: the least power of two whose
- * square is >= n_diag): it takes one level and lands on the canonical
+ * square is >= n_diag for form 0, >= 4 n_diag for form 1, whose baby steps
+ * cost no ModDown): it takes one level and lands on the canonical
  * scale. form 0: hoisted baby rotations, one rescale per giant step; form 1:
  * double hoisting, the baby rotations kept in QP_level and each giant step's
  * products divided by P q_level once (the rounding differs from form 0).

@@ -197,7 +197,10 @@ std::unique_ptr<ckks_lt> lt_create(Ctx& c, int level, double in_scale, int64_t b
   lt->base = base;
   lt->stride = stride;
   lt->n_diag = n_diag;
-  lt->g1 = g1 ? g1 : default_g1(n_diag);
+  // a double-hoisted baby step is a key product only (no ModDown) while a
+  // giant step is a whole rotation: twice the square-root rule's baby steps
+  // measured fastest for the refresh's levels (63 diagonals: 16 against 8)
+  lt->g1 = g1 ? g1 : (form == 1 ? default_g1(4 * n_diag) : default_g1(n_diag));
   lt->g2 = (n_diag + lt->g1 - 1) / lt->g1;
   lt->form = form;
   // pre-rotate the nonzero diagonals by -(base + g1 i stride): np.roll(d, G)

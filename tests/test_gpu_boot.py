@@ -164,7 +164,8 @@ def test_library_plan_matches_oracle(G, small):
 
 def test_library_plan_bootstraps(G, small):
     octx, plan, okeys, gctx, gkeys = small
-    gp = G.BootPlan(gctx, 6, 127, 2, 2)
+    gp = G.BootPlan(gctx, 6, 127, 2, 2)  # double hoisting: its own baby-step count
+    gkeys = G.Keys(gctx, SEED, gp.rotations(), hamming_weight=H, conjugation=True)
     z = np.random.default_rng(4).uniform(-1, 1, (2, octx.slots))
     gc = G.encrypt(gctx, gkeys, z, 0, 9, 0)
     out = gp.bootstrap(gkeys, gc)
