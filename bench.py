@@ -54,11 +54,11 @@ WORKLOADS = {
     "c3": dict(desc="encrypted KAN [784,64,10] G=5 k=3 on synthetic 28x28 blob images, CKKS "
                     "N=2^16, 36 levels, batch 32",
                model="kan_784_64_10", inputs="blob", log_n=16, levels=36, alpha=0, batch=32,
-               degree=15, comp=((7, 7, 7, 7), 0.02), b0="product", fixed=None, uneven=False),
+               degree=15, comp=((7, 7, 7), 0.05), b0="product", fixed=None, uneven=False),
     "c4": dict(desc="encrypted KAN [3072,64,10] G=10 k=3 on synthetic 3x32x32 images (two "
                     "ciphertexts per image), CKKS N=2^16, 36 levels, batch 16",
                model="kan_3072_64_10", inputs="cifar", log_n=16, levels=36, alpha=0, batch=16,
-               degree=15, comp=((7, 7, 7, 7), 0.02), b0="product", fixed=None, uneven=False),
+               degree=15, comp=((7, 7, 15), 0.03), b0="product", fixed=None, uneven=False),
 }
 WORKLOAD = WORKLOADS["c2"]["desc"]
 
@@ -519,7 +519,8 @@ def config(a):
             "levels": a.levels, "batch_per_gpu": a.batch, "silu_degree": wl["degree"],
             "comparison": "minimax composite, stage degrees %s, eps %g, B_{m,0} %s form"
                           % ("-".join(str(d) for d in wl["comp"][0]), wl["comp"][1], wl["b0"]),
-            "input_levels": "uniform over [L - slack, L]" if wl["uneven"] else "all at L",
+            "input_levels": "uniform over [L - slack, L]" if wl["uneven"]
+                            else "all at the network's depth (<= L)",
             "parallelism": "replicas (request sharding)",
             "l2": "inputs larger than L2 (ciphertexts + keys per step >> 129 MB)",
             "schedule": "CUDA graph per layer" if getattr(a, "graphs", False) else "eager",
@@ -979,8 +980,8 @@ def main():
     plan = shard_plan(rank, a.batch)
     if wl["uneven"]:
         levels = W.uneven_levels(a.batch, a.levels, slack, seed=plan["level_seed"])
-    else:
-        levels = np.full(a.batch, a.levels)
+    else:  # encrypted at the level the network needs (the chain's spare levels unused)
+        levels = np.full(a.batch, min(a.levels, depth))
     keys = G.Keys(ctx, W.SEED_KEYS, gm.rotations())
     K = gm.layer_chunks(0)[0]
 
