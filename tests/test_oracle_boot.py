@@ -260,3 +260,26 @@ def test_stage_roots_are_correctly_rounded():
         assert cs[k] == float(mpmath.cos(t)) and sn[k] == float(mpmath.sin(t)), k
     for q, (c, s_) in enumerate(((1, 0), (0, 1), (-1, 0), (0, -1))):  # quarter turns exactly
         assert cs[q * M // 4] == c and sn[q * M // 4] == s_
+
+
+@pytest.mark.parametrize("count", [1, 3, 4, 7])
+def test_pack_and_unpack_trees(count):
+    """The packed refresh's rotation trees on encrypted vectors: pack_tree
+    puts ciphertext b's block [0, nb) at slots [b nb, b nb + nb) (numpy
+    concatenation, the rest zero), and unpack_tree returns rot(packed, b nb)
+    for every b (numpy roll), for a ragged and a power-of-two count."""
+    ctx = ckks.Ctx(ckks.Params(log_n=7, n_scale=6, n_special=2))
+    n, nb = ctx.slots, 8
+    steps = sorted({(s * nb) % n for s in (1, 2, 4)} | {(-s * nb) % n for s in (1, 2, 4)})
+    keys = ckks.Keys(ctx, 3, rot_steps=steps)
+    rng = np.random.default_rng(count)
+    vals = [np.concatenate([rng.uniform(-1, 1, 5), np.zeros(n - 5)]) for _ in range(count)]
+    cts = [ckks.encrypt(ctx, keys, v, 5, 4, b) for b, v in enumerate(vals)]
+    packed = boot.pack_tree(ctx, keys, cts, nb)
+    want = np.zeros(n)
+    for b, v in enumerate(vals):
+        want[b * nb:(b + 1) * nb] = v[:nb]
+    got = ckks.decrypt(ctx, keys, packed)
+    assert np.abs(got - want).max() < 1e-6
+    for b, u in enumerate(boot.unpack_tree(ctx, keys, packed, count, nb)):
+        assert np.abs(ckks.decrypt(ctx, keys, u) - np.roll(want, -b * nb)).max() < 1e-6
