@@ -534,7 +534,12 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model,
  * kan_server_step evaluates one layer for every active request, batching
  * requests of the same model, layer and level into one evaluation; requests
  * submitted meanwhile join at the next step. Results are word-for-word those
- * of evaluating each request alone. kan_server_take returns CKKS_PENDING
+ * of evaluating each request alone, or, for a model with a bootstrapping
+ * plan (kan_model_set_bootstrap), those of kan_infer on the batch the
+ * requests shared: a group whose level is below the next layer's depth is
+ * refreshed as kan_infer refreshes a batch (packed when it holds several
+ * requests), and the keys then need kan_model_refresh_rotations for the
+ * largest group. kan_server_take returns CKKS_PENDING
  * while a request is still queued or running. The server does not own the
  * models or keys, which must outlive it. */
 #define CKKS_PENDING 1
@@ -542,7 +547,8 @@ typedef struct kan_server kan_server;
 int kan_server_create(ckks_ctx* ctx, size_t hbm_budget_bytes, kan_server** out);
 int kan_server_destroy(kan_server* server);
 /* Runs the model twice on the device to measure its footprint (above);
- * LEVEL if the model is deeper than the chain. */
+ * LEVEL if the model is deeper than the chain and has no bootstrapping plan
+ * (with one, the first layer must fit). */
 int kan_server_add_model(kan_server* server, kan_model* model, const ckks_keys* keys,
                          int* model_id);
 /* The measured footprint of one request of the model, in bytes. */

@@ -741,6 +741,23 @@ int kan_total_depth(const kan_model& M) {
   for (const Layer& L : M.layers) d += layer_depth(L);
   return d;
 }
+// the level an input needs: the whole network's depth, or with a
+// bootstrapping plan the first layer's (later layers run on refreshes)
+int kan_input_depth(const kan_model& M) {
+  return M.boot ? layer_depth(M.layers[0]) : kan_total_depth(M);
+}
+// A layer after the first that needs more levels than are left runs on the
+// refreshed batch: packed into as few ciphertexts as the slots allow when
+// there are several and a level is left for the mask, else each brought to
+// level 0 and bootstrapped; without a plan, or with levels enough, x as is.
+Ct kan_refresh_for_layer(kan_model& M, int layer, const ckks_keys& keys, Ct x) {
+  if (layer == 0 || !M.boot || x->level >= layer_depth(M.layers[layer])) return x;
+  Ctx& c = *M.ctx;
+  if (x->B > 1 && x->level >= 1)
+    return refresh_packed(c, keys, *M.boot, *x, M.layers[layer - 1].n_out);
+  Ct low = op_level_down(c, *x, 0);
+  return bootstrap(c, keys, *M.boot, *low);
+}
 Ct cheb_eval(Ctx& c, const ckks_keys& keys, const ckks_ct& y, const std::vector<double>& a) {
   return eval_cheb(c, keys, y, a);
 }
@@ -948,18 +965,7 @@ int kan_infer(ckks_ctx* ctx, const ckks_keys* keys, kan_model* model, const ckks
     Ct h = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
     aligned.clear();
     for (size_t li = 0; li < model->layers.size(); li++) {
-      // a layer after the first that needs more levels than are left runs on
-      // the refreshed batch: packed into as few ciphertexts as the slots
-      // allow when there are several and a level is left for the mask, else
-      // each brought to level 0 and bootstrapped
-      if (li > 0 && model->boot && h->level < layer_depth(model->layers[li])) {
-        if (h->B > 1 && h->level >= 1) {
-          h = refresh_packed(c, *keys, *model->boot, *h, model->layers[li - 1].n_out);
-        } else {
-          h = op_level_down(c, *h, 0);
-          h = bootstrap(c, *keys, *model->boot, *h);
-        }
-      }
+      h = kan_refresh_for_layer(*model, (int)li, *keys, std::move(h));
       h = layer_run(*model, (int)li, *keys, *h);
     }
     *out = h.release();

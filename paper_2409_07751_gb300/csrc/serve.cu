@@ -29,9 +29,11 @@
 
 namespace ck {
 Ct kan_eval_layer(kan_model& M, int layer, const ckks_keys& keys, const ckks_ct& x);
+Ct kan_refresh_for_layer(kan_model& M, int layer, const ckks_keys& keys, Ct x);
 int kan_num_layers(const kan_model& M);
 int kan_layer_chunks(const kan_model& M, int layer);
 int kan_total_depth(const kan_model& M);
+int kan_input_depth(const kan_model& M);
 }  // namespace ck
 
 using namespace ck;
@@ -102,6 +104,8 @@ void run_group(Ctx& c, kan_model& M, const ckks_keys& K, int layer, std::vector<
   for (Ct* p : cts) parts.push_back(p->get());
   Ct in = parts.size() == 1 ? ct_copy(c, *parts[0]) : op_concat(c, parts);
   const int chunks = kan_layer_chunks(M, layer);
+  // a model with a bootstrapping plan refreshes the group as kan_infer does
+  in = kan_refresh_for_layer(M, layer, K, std::move(in));
   Ct out = kan_eval_layer(M, layer, K, *in);
   in.reset();
   const size_t per = out->words() / out->B;
@@ -207,8 +211,8 @@ int kan_server_destroy(kan_server* s) {
 int kan_server_add_model(kan_server* s, kan_model* model, const ckks_keys* keys, int* model_id) {
   return guard([&] {
     if (!s || !model || !keys || !model_id) throw Error(CKKS_ERR_INVALID_ARG, "bad argument");
-    if (s->ctx->L < kan_total_depth(*model))
-      throw Error(CKKS_ERR_LEVEL, "the model is deeper than the chain");
+    if (s->ctx->L < kan_input_depth(*model))
+      throw Error(CKKS_ERR_LEVEL, "the model is deeper than the chain (and has no bootstrapping plan)");
     s->models.emplace_back(model, keys);
     const int m = (int)s->models.size() - 1;
     s->footprint.push_back(0);
@@ -221,7 +225,7 @@ int kan_server_submit(kan_server* s, int model_id, const ckks_ct* in, uint64_t* 
   return guard([&] {
     if (!s || !in || !request_id || model_id < 0 || model_id >= (int)s->models.size())
       throw Error(CKKS_ERR_INVALID_ARG, "bad argument");
-    if (in->level < kan_total_depth(*s->models[model_id].first))
+    if (in->level < kan_input_depth(*s->models[model_id].first))
       throw Error(CKKS_ERR_LEVEL, "input level below the model's depth");
     auto r = std::make_unique<Request>();
     r->id = s->next_id++;

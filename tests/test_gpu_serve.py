@@ -86,3 +86,43 @@ def test_admission_respects_budget(env):
     with pytest.raises(G.CkksError) as e:
         small.submit(m2, one)
     assert e.value.code == -5  # CKKS_ERR_OUT_OF_MEMORY
+
+
+def test_deep_model_served_with_refreshes():
+    """A four-layer model of depth 7 per layer on a 24-level chain with a
+    bootstrapping plan: the server refreshes a group before the fourth layer
+    as kan_infer does. Two requests submitted together share every group
+    (packed refresh) and equal kan_infer on the pair word for word; a request
+    submitted one step later runs alone (refreshed by itself) and equals
+    kan_infer on it alone."""
+    from paper_2409_07751_gb300 import build, ckks as G
+    from oracle import kan_plain
+    build.build()
+    ctx = G.Context(7, 24, 2, q0_bits=60, scale_bits=50)
+    m = calibrate.calibrate(W.make_model("t", widths=[3, 5, 5, 5, 2], G=3, k=2),
+                            W.uniform_inputs(64, 3), 7, [1])
+    M = G.Model(ctx, m)
+    plan = G.BootPlan(ctx, 6, 127, 2, 2)
+    M.set_bootstrap(plan)
+    keys = G.Keys(ctx, 7, sorted(set(M.rotations()) | set(plan.rotations()) | set(M.refresh_rotations(2))),
+                  hamming_weight=16, conjugation=True)
+    X = W.uniform_inputs(3, 3, seed=77)
+    cts = [G.encrypt(ctx, keys, X[i], 24, W.SEED_ENC, i) for i in range(3)]
+    srv = G.Server(ctx, 1 << 40)
+    mid = srv.add_model(M, keys)
+    r0, r1 = srv.submit(mid, cts[0]), srv.submit(mid, cts[1])
+    srv.step()
+    r2 = srv.submit(mid, cts[2])
+    for _ in range(6):
+        srv.step()
+    pair = G.kan_infer(ctx, keys, M, [G.Ciphertext.import_(ctx, np.concatenate(
+        [cts[0].export(), cts[1].export()]), 24, cts[0].scale)])
+    outs = [srv.take(r) for r in (r0, r1, r2)]
+    assert all(o is not None for o in outs)
+    assert (outs[0].export()[0] == pair.export()[0]).all()
+    assert (outs[1].export()[0] == pair.export()[1]).all()
+    alone = G.kan_infer(ctx, keys, M, [cts[2]])
+    assert (outs[2].export() == alone.export()).all()
+    hef = kan_plain.forward(m, X, "poly", "poly")
+    for i, o in enumerate(outs):
+        assert np.abs(G.decrypt(ctx, keys, o, 2)[0] - hef[i]).max() < 1e-4
