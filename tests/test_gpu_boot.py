@@ -269,3 +269,38 @@ def test_deep_kan_full_size(G):
     err_hef, err_exact = np.abs(dec - hef).max(), np.abs(dec - exact).max()
     print("deep KAN: vs HE-friendly %.2e, vs exact %.2e" % (err_hef, err_exact))
     assert err_hef < 2e-3, err_hef
+
+
+def test_entry_points_reject_invalid_input(G, small):
+    """The bootstrapping and key entry points refuse what they document as
+    invalid (and the context keeps working): ModRaise of a ciphertext above
+    level 0, a transform of only zero diagonals, diagonals of the wrong
+    width, a plan with K = 0 or a chain too short, a public seed equal to
+    the seed; compressing twice is harmless."""
+    octx, plan, okeys, gctx, gkeys = small
+    z = np.linspace(-1, 1, gctx.slots)
+    c3 = G.encrypt(gctx, gkeys, z, 3, 1, 0)
+    with pytest.raises(G.CkksError) as e:
+        G.mod_raise(gctx, c3, gctx.L)
+    assert e.value.code == -2
+    zero = G.LinearTransform(gctx, 3, 0, 1, np.zeros((2, gctx.slots)))
+    with pytest.raises(G.CkksError):
+        zero.apply(gkeys, c3)
+    with pytest.raises(ValueError):
+        G.LinearTransform(gctx, 3, 0, 1, np.zeros((2, gctx.slots + 1)))
+    with pytest.raises(G.CkksError):
+        G.BootPlan(gctx, 0, 127, 2, 2)
+    short = G.Context(7, 8, 2, q0_bits=60, scale_bits=50)
+    with pytest.raises(G.CkksError) as e:
+        G.BootPlan(short, 6, 127, 2, 2)  # 17 levels needed
+    assert e.value.code == -2
+    with pytest.raises(G.CkksError):
+        G.Keys(gctx, 5, [1], public_seed=5)
+    k = G.Keys(gctx, 5, [1], public_seed=6)
+    k.compress()
+    k.compress()
+    assert np.abs(G.decrypt(gctx, k, G.rotate(gctx, k, G.encrypt(gctx, k, z, 3, 1, 0), 1), gctx.slots)[0]
+                  - np.roll(z, -1)).max() < 1e-6
+    # the context still computes after the refusals
+    out = G.mul(gctx, gkeys, c3, c3)
+    assert np.abs(G.decrypt(gctx, gkeys, out, gctx.slots)[0] - z * z).max() < 1e-6
