@@ -93,7 +93,6 @@ uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t q) {
 }
 uint64_t invmod_h(uint64_t a, uint64_t q) { return powmod_h(a % q, q - 2, q); }
 uint64_t shoup_h(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
-uint64_t split25_h(uint64_t v) { return (v & ((1ull << 25) - 1)) | ((v >> 25) << 32); }
 Mod make_mod(uint64_t q) {
   Mod m;
   m.q = q;
@@ -273,9 +272,6 @@ void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p
   c.d_itws = upload(&c, itws);
   c.d_ninv = upload(&c, ninv);
   c.d_ninvs = upload(&c, ninvs);
-  std::vector<uint64_t> sh25(c.n_qp);
-  for (int t = 0; t < c.n_qp; t++) sh25[t] = c.mod[t] > (1ull << 25) ? shoup_h(1ull << 25, c.mod[t]) : 0;
-  c.d_sh25 = upload(&c, sh25);
   std::vector<int16_t> iota(c.n_qp);
   for (int t = 0; t < c.n_qp; t++) iota[t] = (int16_t)t;
   c.d_iota = upload(&c, iota);
@@ -298,7 +294,6 @@ void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p
   // ModDown constants (independent of the level)
   const int A = c.alpha;
   std::vector<uint64_t> yinv(A), yinvs(A), ph((size_t)A * (c.L + 1)), phs((size_t)A * (c.L + 1));
-  std::vector<uint64_t> phsp((size_t)A * (c.L + 1)), phesp((size_t)A * (c.L + 1));
   for (int a = 0; a < A; a++) {
     const uint64_t pa = c.mod[c.L + 1 + a];
     uint64_t h = 1;
@@ -313,16 +308,12 @@ void ctx_init(Ctx& c, int log_n, int q0_bits, int scale_bits, int n_scale, int p
         if (b != a) hq = mulmod_h(hq, c.mod[c.L + 1 + b] % q, q);
       ph[(size_t)a * (c.L + 1) + i] = hq;
       phs[(size_t)a * (c.L + 1) + i] = shoup_h(hq, q);
-      phsp[(size_t)a * (c.L + 1) + i] = split25_h(hq);
-      phesp[(size_t)a * (c.L + 1) + i] = split25_h(mulmod_h(hq, (1ull << 32) % q, q));
     }
   }
   c.d_md_yinv = upload(&c, yinv);
   c.d_md_yinv_s = upload(&c, yinvs);
   c.d_md_ph = upload(&c, ph);
   c.d_md_ph_s = upload(&c, phs);
-  c.d_md_ph_sp = upload(&c, phsp);
-  c.d_md_phe_sp = upload(&c, phesp);
   std::vector<uint64_t> rs((size_t)(c.L + 1) * (c.L + 1), 0), rss((size_t)(c.L + 1) * (c.L + 1), 0);
   for (int l = 1; l <= c.L; l++)
     for (int t = 0; t < l; t++) {
@@ -369,9 +360,6 @@ Ctx::~Ctx() {
   d_md_yinv_s.reset();
   d_md_ph.reset();
   d_md_ph_s.reset();
-  d_md_ph_sp.reset();
-  d_md_phe_sp.reset();
-  d_sh25.reset();
   d_flag.reset();
   d_rs_inv.reset();
   d_rs_invs.reset();
@@ -393,8 +381,6 @@ ConvTables& Ctx::tables(int level) {
   std::vector<uint64_t> dhinv((size_t)beta * A, 0), dhinvs((size_t)beta * A, 0);
   std::vector<uint64_t> dh((size_t)beta * A * rows, 0), dhs((size_t)beta * A * rows, 0);
   std::vector<uint64_t> dhw((size_t)beta * A * rows, 0), dhws((size_t)beta * A * rows, 0);
-  std::vector<uint64_t> dhsp((size_t)beta * A * rows, 0), dhesp((size_t)beta * A * rows, 0);
-  std::vector<uint64_t> dhwsp((size_t)beta * A * rows, 0), dhwesp((size_t)beta * A * rows, 0);
   std::vector<int16_t> pat((size_t)beta * rows);
   auto row_mod = [&](int r) { return r < l ? r : L + 1 + (r - l); };
   for (int j = 0; j < beta; j++) {
@@ -417,11 +403,6 @@ ConvTables& Ctx::tables(int level) {
         const uint64_t hw = mulmod_h(hm, powmod_h(psi[row_mod(r)], N / 2, m), m);
         dhw[((size_t)j * A + (i - lo)) * rows + r] = hw;
         dhws[((size_t)j * A + (i - lo)) * rows + r] = shoup_h(hw, m);
-        const uint64_t t32 = (1ull << 32) % m;
-        dhsp[((size_t)j * A + (i - lo)) * rows + r] = split25_h(hm);
-        dhesp[((size_t)j * A + (i - lo)) * rows + r] = split25_h(mulmod_h(hm, t32, m));
-        dhwsp[((size_t)j * A + (i - lo)) * rows + r] = split25_h(hw);
-        dhwesp[((size_t)j * A + (i - lo)) * rows + r] = split25_h(mulmod_h(hw, t32, m));
       }
     }
     for (int r = 0; r < rows; r++)
@@ -442,10 +423,6 @@ ConvTables& Ctx::tables(int level) {
   T->dh_s = upload(this, dhs);
   T->dhw = upload(this, dhw);
   T->dhw_s = upload(this, dhws);
-  T->dh_sp = upload(this, dhsp);
-  T->dhe_sp = upload(this, dhesp);
-  T->dhw_sp = upload(this, dhwsp);
-  T->dhwe_sp = upload(this, dhwesp);
   T->ext_pattern = upload(this, pat);
   T->pq_pattern = upload(this, pq);
   std::vector<int16_t> qp(rows);

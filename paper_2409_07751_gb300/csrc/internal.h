@@ -60,9 +60,6 @@ struct ConvTables {
   DevBuf dhinv, dhinv_s;   // [beta][alpha]
   DevBuf dh, dh_s;         // [beta][alpha][rows]
   DevBuf dhw, dhw_s;       // [beta][alpha][rows]: dh times psi^(N/2) of the row's modulus
-  // split forms (split25_h) of dh, [2^32 dh]_m, dhw and [2^32 dhw]_m: ModUp's
-  // conversion sums in the growth-tolerant fused transforms (moduli below 2^50)
-  DevBuf dh_sp, dhe_sp, dhw_sp, dhwe_sp;  // [beta][alpha][rows]
   DevBuf ext_pattern;      // int16 [beta*rows]: modulus index of the row, -1 = digit row
   DevBuf pq_pattern;       // int16 [rows]: -1 for Q rows, special modulus for P rows
   DevBuf qp_pattern;       // int16 [rows]: the modulus of every QP_l row (Q limbs, then P)
@@ -136,8 +133,6 @@ struct Ctx {
   DevBuf d_slot;            // uint32 [N/2]: k_j = (5^j mod 2N - 1) / 4
   DevBuf d_md_yinv, d_md_yinv_s;  // [alpha]: Phat_a^-1 mod p_a
   DevBuf d_md_ph, d_md_ph_s;      // [alpha][L+1]: Phat_a mod q_i
-  DevBuf d_md_ph_sp, d_md_phe_sp; // [alpha][L+1]: split forms of Phat_a and [2^32 Phat_a]_{q_i}
-  DevBuf d_sh25;                  // [n_qp]: floor(2^89 / q), Shoup companion of 2^25 (0 if q <= 2^25)
   std::map<int, std::unique_ptr<ConvTables>> conv;
   std::map<uint64_t, std::unique_ptr<DevBuf>> perms;  // galois -> uint32[N]
   // rescale of k c by q_r: (r, k) -> [N^-1 k mod q_r, Shoup, k q_r^-1 mod q_t (t < r), Shoup]
@@ -217,8 +212,6 @@ uint64_t mulmod_h(uint64_t a, uint64_t b, uint64_t q);
 uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t q);
 uint64_t invmod_h(uint64_t a, uint64_t q);
 uint64_t shoup_h(uint64_t w, uint64_t q);
-// v < 2^57 as 25-bit halves packed lo | hi << 32 (v = lo + 2^25 hi)
-uint64_t split25_h(uint64_t v);
 Mod make_mod(uint64_t q);
 bool is_prime_h(uint64_t n);
 int gen_chain(int log_n, int q0_bits, int scale_bits, int n_scale, int p_bits, int n_special,

@@ -282,45 +282,13 @@ struct Row {
 };
 
 constexpr int MAX_SRC = 16;
-// shared constants of a fused row (kc): [0, 4 MAX_SRC) the descriptor's Shoup
-// pairs; then the split forms of the conversion constants and the Shoup
-// companion of 2^25 (split_conv_sum)
-constexpr int KC_SPLIT = 4 * MAX_SRC;     // split c_a
-constexpr int KC_SPLIT_E = 5 * MAX_SRC;   // split [2^32 c_a]_m
-constexpr int KC_SPLIT_W = 6 * MAX_SRC;   // split c_a psi^(N/2) (ModUp's folded stage)
-constexpr int KC_SPLIT_WE = 7 * MAX_SRC;  // split [2^32 c_a psi^(N/2)]_m
-constexpr int KC_SH25 = 8 * MAX_SRC;      // floor(2^89 / m)
-constexpr int KC_WORDS = 8 * MAX_SRC + 2;
-
-// Conversion sum sum_a y_a c_a mod m for m < 2^50 (growth-tolerant rows) with
-// no reduction per term. With the 32-bit halves y = y0 + 2^32 y1 and the
-// 25-bit halves c = c0 + 2^25 c1, e = [2^32 c]_m = e0 + 2^25 e1 (packed
-// lo | hi << 32 in pc, pe), y c is congruent to (y0 c0 + y1 e0) +
-// 2^25 (y0 c1 + y1 e1). Residues below 2^61 make each bracket's term less
-// than 2^57 + 2^54, so both sums of up to 16 terms are exact in 64 bits
-// (four widening 32-bit products per term); the second is multiplied by 2^25
-// with one lazy Shoup product (companion floor(2^89 / m), below 4m). The
-// value returned is congruent to the sum and below 2^61.2.
-template <bool CHAIN>
-__device__ __forceinline__ uint64_t split_conv_sum(const uint64_t* src, size_t N, uint32_t i,
-                                                   int n, const uint64_t* pc, const uint64_t* pe,
-                                                   uint64_t sh25, uint64_t m) {
-  uint64_t s0 = 0, s1 = 0;
-  for (int a = 0; a < n; a++) {
-    const uint64_t y = src[(size_t)a * N + i];
-    const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
-    const uint64_t c = pc[a], e = pe[a];
-    s0 += (uint64_t)y0 * (uint32_t)c + (uint64_t)y1 * (uint32_t)e;
-    s1 += (uint64_t)y0 * (uint32_t)(c >> 32) + (uint64_t)y1 * (uint32_t)(e >> 32);
-  }
-  return s0 + shoup_approx_t<CHAIN>(s1, 1ull << 25, sh25, m);
-}
 
 // plain forward NTT of pattern-selected rows
 struct DescPlain {
   static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_FWD;
   static constexpr bool FOLD1 = false;  // see DescModUp
+  static constexpr bool COL_LOADS = false;  // see DescModDown
   uint64_t* base;
   const int16_t* pattern;
   int P;
@@ -339,13 +307,14 @@ struct DescPlain {
 
 // ModUp target row: sum_a xs[a][i] * [Dhat_a]_{m} mod m, then NTT; digit rows copy d.
 struct DescModUp {
-  static constexpr bool CHAIN = true;  // remainder form (modarith.cuh; -1.2 % here with split sums)
+  static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_MODUP;
   // The forward transform's first stage multiplies the upper half of the
   // row by the single twiddle w = psi^(N/2); the upper half is loaded with
   // the constants [Dhat_a w]_m instead (load_w), so that stage is a plain
   // sum and difference (moduli below 2^50).
   static constexpr bool FOLD1 = true;
+  static constexpr bool COL_LOADS = false;  // growth-tolerant rows: load_cols through FOLD1
   const uint64_t* xs;  // [B][l][N] coefficients already scaled by N^-1 Dhat^-1 (the iNTT post factor)
   const uint64_t* d;   // batch element b at d + b dstride: [l][N] NTT form
   uint64_t* ext;       // [B][beta][rows][N]
@@ -356,11 +325,6 @@ struct DescModUp {
   size_t N;
   const uint64_t* dhw;  // [beta][alpha][rows]: [Dhat_a psi^(N/2)]_m
   const uint64_t* dhws;
-  const uint64_t* dhsp;   // [beta][alpha][rows]: split forms (split_conv_sum) of dh,
-  const uint64_t* dhesp;  // [2^32 dh]_m,
-  const uint64_t* dhwsp;  // dhw
-  const uint64_t* dhwesp; // and [2^32 dhw]_m
-  const uint64_t* sh25;   // [n_qp]: floor(2^89 / q)
   __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
     const int rr = (int)(blk % rows);
     const int j = (int)((blk / rows) % beta);
@@ -383,28 +347,37 @@ struct DescModUp {
       kc[MAX_SRC + threadIdx.x] = dhs[ti];
       kc[2 * MAX_SRC + threadIdx.x] = dhw[ti];
       kc[3 * MAX_SRC + threadIdx.x] = dhws[ti];
-      kc[KC_SPLIT + threadIdx.x] = dhsp[ti];
-      kc[KC_SPLIT_E + threadIdx.x] = dhesp[ti];
-      kc[KC_SPLIT_W + threadIdx.x] = dhwsp[ti];
-      kc[KC_SPLIT_WE + threadIdx.x] = dhwesp[ti];
     }
-    if (threadIdx.x == 0) kc[KC_SH25] = sh25[r.mi];
     return true;
   }
-  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
+  // exact conversion sum of one element (rows with m >= 2^50; load_cols otherwise)
+  __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool) const {
     const uint64_t m = r.aux;
-    if (grow)  // lazy: congruent, below 2^61.2 (the transform tolerates it)
-      return split_conv_sum<CHAIN>(r.src, N, i, r.n_src, kc + KC_SPLIT, kc + KC_SPLIT_E,
-                                   kc[KC_SH25], m);
     uint64_t acc = 0;
     for (int a = 0; a < r.n_src; a++)
       acc = add_mod(acc, mul_shoup_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
     return acc;
   }
-  // the upper-half load times w (moduli below 2^50): congruent, below 2^61.2
-  __device__ uint64_t load_w(const Row& r, uint32_t i, const uint64_t* kc) const {
-    return split_conv_sum<CHAIN>(r.src, N, i, r.n_src, kc + KC_SPLIT_W, kc + KC_SPLIT_WE,
-                                 kc[KC_SH25], r.aux);
+  // Growth-tolerant rows (m < 2^50): the column's N1 conversion sums at once,
+  // source row outermost, so a thread has N1 independent loads in flight per
+  // source row (per-element sums issue one at a time and were bound by their
+  // load latency); the upper half takes the constants times w = psi^(N/2)
+  // (the folded first stage). Lazy three-product Shoup terms: each sum below
+  // 4 n_src m.
+  template <int N1>
+  __device__ void load_cols(const Row& r, uint32_t c, const uint64_t* kc, uint64_t* x) const {
+    const uint64_t m = r.aux;
+#pragma unroll
+    for (int s = 0; s < N1; s++) x[s] = 0;
+    for (int a = 0; a < r.n_src; a++) {
+      const uint64_t* p = r.src + (size_t)a * N + c;
+      const uint64_t w0 = kc[a], w0s = kc[MAX_SRC + a];
+      const uint64_t w1 = kc[2 * MAX_SRC + a], w1s = kc[3 * MAX_SRC + a];
+#pragma unroll
+      for (int s = 0; s < N1 / 2; s++) x[s] += shoup_approx_t<CHAIN>(p[(size_t)s * CHUNK], w0, w0s, m);
+#pragma unroll
+      for (int s = N1 / 2; s < N1; s++) x[s] += shoup_approx_t<CHAIN>(p[(size_t)s * CHUNK], w1, w1s, m);
+    }
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
     r.mid[i] = v;
@@ -413,27 +386,33 @@ struct DescModUp {
 
 // Centred basis conversion of the n_src rows at r.src into modulus m = r.aux:
 // sum_a y_a kc[a] - u [M]_m, with u = r.ov[i] (ModDown, merged division).
-// Exact: in [0, m). Growth-tolerant transforms (m < 2^50) take a lazy form
-// plus 256 m - u [M]_m (u <= 255): the split sum (SPLIT, split_conv_sum;
-// below 2^61.3 in all) or three-product Shoup terms (each below 4m; below
-// (4 n_src + 256) m < 2^60 in all), both congruent to the exact value. Which
-// is faster depends on the kernel (measured per descriptor).
-template <bool CHAIN, bool SPLIT>
+// Exact, in [0, m), one element (rows with m >= 2^50).
+template <bool CHAIN>
 __device__ __forceinline__ uint64_t conv_load(const Row& r, uint32_t i, const uint64_t* kc,
-                                              bool grow, size_t N) {
+                                              size_t N) {
   const uint64_t m = r.aux;
   uint64_t s = 0;
-  if (grow) {
-    if (SPLIT)
-      s = split_conv_sum<CHAIN>(r.src, N, i, r.n_src, kc + KC_SPLIT, kc + KC_SPLIT_E, kc[KC_SH25], m);
-    else
-      for (int a = 0; a < r.n_src; a++)
-        s += shoup_approx_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m);
-    return s + (256 * m - (uint64_t)r.ov[i] * r.km);
-  }
   for (int a = 0; a < r.n_src; a++)
     s = add_mod(s, mul_shoup_t<CHAIN>(r.src[(size_t)a * N + i], kc[a], kc[MAX_SRC + a], m), m);
   return sub_mod(s, mul_shoup_t<CHAIN>((uint64_t)r.ov[i], r.km, r.kms, m), m);
+}
+// The same for the N1 elements c + s N2 of a column, for the growth-tolerant
+// transforms (m < 2^50), source row outermost (N1 independent loads in flight
+// per row, see DescModUp::load_cols): lazy three-product Shoup terms (each
+// below 4m) plus 256 m - u [M]_m (u <= 255), values congruent to the exact
+// ones and below (4 n_src + 256) m < 2^60.
+template <int N1, bool CHAIN>
+__device__ __forceinline__ void conv_cols(const Row& r, uint32_t c, const uint64_t* kc, size_t N,
+                                          uint64_t* x) {
+  const uint64_t m = r.aux;
+#pragma unroll
+  for (int s = 0; s < N1; s++) x[s] = 256 * m - (uint64_t)r.ov[c + (size_t)s * CHUNK] * r.km;
+  for (int a = 0; a < r.n_src; a++) {
+    const uint64_t* p = r.src + (size_t)a * N + c;
+    const uint64_t w = kc[a], ws = kc[MAX_SRC + a];
+#pragma unroll
+    for (int s = 0; s < N1; s++) x[s] += shoup_approx_t<CHAIN>(p[(size_t)s * CHUNK], w, ws, m);
+  }
 }
 
 // ModDown output row i of (b,k): (acc_i - NTT(sum_a y_a [Phat_a]_{q_i})) * P^-1
@@ -441,6 +420,8 @@ struct DescModDown {
   static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_MODDOWN;
   static constexpr bool FOLD1 = false;  // see DescModUp
+  // growth-tolerant rows load whole columns (conv_cols)
+  static constexpr bool COL_LOADS = true;
   const uint64_t* acc;  // [BK][rows][N]; P rows already inverse-transformed and scaled
   uint64_t* out;        // [BK][l][N]
   const uint64_t* ph;   // [alpha][L+1]
@@ -452,9 +433,6 @@ struct DescModDown {
   const uint64_t* pqs;
   int l, rows, alpha, L;
   size_t N;
-  const uint64_t* phsp;   // [alpha][L+1]: split forms of ph and [2^32 ph]_{q_i}
-  const uint64_t* phesp;
-  const uint64_t* sh25;   // [n_qp]: floor(2^89 / q)
   __device__ bool setup(uint32_t blk, Row& r, uint64_t* kc, uint32_t part, uint32_t nparts) const {
     const int i = (int)(blk % l);
     const size_t bk = blk / l;
@@ -471,14 +449,15 @@ struct DescModDown {
     if (threadIdx.x < (unsigned)alpha) {
       kc[threadIdx.x] = ph[(size_t)threadIdx.x * (L + 1) + i];
       kc[MAX_SRC + threadIdx.x] = phs[(size_t)threadIdx.x * (L + 1) + i];
-      kc[KC_SPLIT + threadIdx.x] = phsp[(size_t)threadIdx.x * (L + 1) + i];
-      kc[KC_SPLIT_E + threadIdx.x] = phesp[(size_t)threadIdx.x * (L + 1) + i];
     }
-    if (threadIdx.x == 0) kc[KC_SH25] = sh25[i];
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
-    return conv_load<CHAIN, true>(r, i, kc, grow, N);
+    return conv_load<CHAIN>(r, i, kc, N);
+  }
+  template <int N1>
+  __device__ void load_cols(const Row& r, uint32_t c, const uint64_t* kc, uint64_t* x) const {
+    conv_cols<N1, CHAIN>(r, c, kc, N, x);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
@@ -490,6 +469,7 @@ struct DescRescale {
   static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
+  static constexpr bool COL_LOADS = false;  // see DescModDown
   const uint64_t* in;    // [polys][level+1][N]
   const uint64_t* last;  // [polys][N] coefficient form of limb `level`
   uint64_t* out;         // [polys][level][N]
@@ -527,6 +507,7 @@ struct DescRescaleScaled {
   static constexpr bool CHAIN = true;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
+  static constexpr bool COL_LOADS = false;  // see DescModDown
   const uint64_t* in;
   size_t in_stride;
   const uint64_t* last;   // [polys][N]
@@ -580,19 +561,20 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
     uint64_t x[N1];
     int m0 = 1;  // first column stage still to run
     if constexpr (D::FOLD1 && GROW) {
-      // first stage folded into the loads: t = w y comes from load_w, and
-      // u - t + cw with cw = q 2^(clz(q) - 1) in [2^62, 2^63) (a multiple of q
-      // above t < 2^61.2) stays >= 0; the 15 further stages add less than
-      // 60 q < 2^56, so every value stays below 2^64
-      const uint64_t cw = q << (__clzll(q) - 1);
+      // first stage folded into the loads: the upper half's t = w y comes
+      // with the loads, and u - t + cw with cw = 4 n_src q (a multiple of q
+      // above t) stays >= 0
+      const uint64_t cw = 4 * (uint64_t)r.n_src * q;
+      d.template load_cols<N1>(r, c, kc, x);
 #pragma unroll
       for (int s = 0; s < N1 / 2; s++) {
-        const uint64_t u = d.load(r, c + (uint32_t)s * CHUNK, kc, true);
-        const uint64_t t = d.load_w(r, c + (uint32_t)(s + N1 / 2) * CHUNK, kc);
+        const uint64_t u = x[s], t = x[s + N1 / 2];
         x[s] = u + t;
         x[s + N1 / 2] = u - t + cw;
       }
       m0 = 2;
+    } else if constexpr (D::COL_LOADS && GROW) {
+      d.template load_cols<N1>(r, c, kc, x);
     } else {
 #pragma unroll
       for (int s = 0; s < N1; s++) x[s] = d.load(r, c + (uint32_t)s * CHUNK, kc, GROW);
@@ -650,6 +632,7 @@ struct DescRelinRescale {
   static constexpr bool CHAIN = false;  // remainder form (modarith.cuh)
   static constexpr int SLOT = NTT_SLOT_RELIN_RESCALE;
   static constexpr bool FOLD1 = false;  // see DescModUp
+  static constexpr bool COL_LOADS = true;
   const uint64_t* acc;    // [BK][rows][N]
   const uint64_t* d;      // [B][3][level+1][N] tensor product
   uint64_t* out;          // [BK][level][N]
@@ -689,8 +672,11 @@ struct DescRelinRescale {
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t* kc, bool grow) const {
-    // Shoup terms: the split sum measured 4.8 % slower in this kind
-    return conv_load<CHAIN, false>(r, i, kc, grow, N);
+    return conv_load<CHAIN>(r, i, kc, N);
+  }
+  template <int N1>
+  __device__ void load_cols(const Row& r, uint32_t c, const uint64_t* kc, uint64_t* x) const {
+    conv_cols<N1, CHAIN>(r, c, kc, N, x);
   }
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
     const uint64_t y = mul_shoup_t<CHAIN>(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
@@ -712,7 +698,7 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB)
                const ulonglong2* tw8, size_t nodes) {
   constexpr int CS = fwd_cs<N1>();
   extern __shared__ uint64_t sm[];  // CPC = N1 / CS chunks
-  __shared__ uint64_t kc[KC_WORDS];
+  __shared__ uint64_t kc[4 * MAX_SRC];
   __shared__ ulonglong2 ctw[N1];  // column-stage twiddles (nodes 1 .. N1-1)
   const uint32_t rank = CS > 1 ? (uint32_t)cg::this_cluster().block_rank() : 0;
   const uint32_t row = blockIdx.x / CS;
@@ -960,8 +946,7 @@ void ntt_modup_fused(Ctx& c, const uint64_t* xs, const uint64_t* d, size_t d_str
   Launch L_(c, K_MODUP_NTT, W8 * (double)B * (2.0 * T.l + (double)T.beta * T.rows),
             out_rows * ((double)(c.N / 2) * c.log_n + (double)c.alpha * c.N));
   DescModUp dsc{xs, d, ext, T.dh.u64(), T.dh_s.u64(), d_stride, T.l, T.beta, T.rows, c.alpha, c.L,
-                c.N, T.dhw.u64(), T.dhw_s.u64(), T.dh_sp.u64(), T.dhe_sp.u64(), T.dhw_sp.u64(),
-                T.dhwe_sp.u64(), c.d_sh25.u64()};
+                c.N, T.dhw.u64(), T.dhw_s.u64()};
   launch_fwd(c, B * T.beta * T.rows, dsc);
 }
 
@@ -972,8 +957,7 @@ void ntt_moddown_fused(Ctx& c, const uint64_t* acc, const uint8_t* ov, size_t BK
   Launch L_(c, K_MODDOWN_NTT, W8 * (double)BK * (c.alpha + 2.0 * T.l),
             (double)BK * T.l * ((double)(c.N / 2) * c.log_n + (c.alpha + 1.0) * c.N));
   DescModDown dsc{acc, out, c.d_md_ph.u64(), c.d_md_ph_s.u64(), T.md_pinv.u64(), T.md_pinv_s.u64(),
-                  ov, T.md_pq.u64(), T.md_pq_s.u64(), T.l, T.rows, c.alpha, c.L, c.N,
-                  c.d_md_ph_sp.u64(), c.d_md_phe_sp.u64(), c.d_sh25.u64()};
+                  ov, T.md_pq.u64(), T.md_pq_s.u64(), T.l, T.rows, c.alpha, c.L, c.N};
   launch_fwd(c, BK * T.l, dsc);
 }
 
