@@ -300,6 +300,8 @@ struct DescPlain {
     return true;
   }
   __device__ uint64_t load(const Row& r, uint32_t i, const uint64_t*, bool) const { return r.mid[i]; }
+  static constexpr int EPI = 0;  // epilogue operand rows (see fwd_rows)
+  __device__ void epi_load(const Row&, uint32_t, uint64_t*) const {}
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
     r.mid[i] = v;
   }
@@ -379,6 +381,8 @@ struct DescModUp {
       for (int s = N1 / 2; s < N1; s++) x[s] += shoup_approx_t<CHAIN>(p[(size_t)s * CHUNK], w1, w1s, m);
     }
   }
+  static constexpr int EPI = 0;  // epilogue operand rows (see fwd_rows)
+  __device__ void epi_load(const Row&, uint32_t, uint64_t*) const {}
   __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t, const uint64_t*) const {
     r.mid[i] = v;
   }
@@ -459,8 +463,10 @@ struct DescModDown {
   __device__ void load_cols(const Row& r, uint32_t c, const uint64_t* kc, uint64_t* x) const {
     conv_cols<N1, CHAIN>(r, c, kc, N, x);
   }
-  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
-    r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+  static constexpr int EPI = 1;
+  __device__ void epi_load(const Row& r, uint32_t i, uint64_t* o) const { o[0] = r.src2[i]; }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t* o) const {
+    r.mid[i] = mul_shoup(sub_mod(o[0], v, q), r.k, r.ks, q);
   }
 };
 
@@ -494,8 +500,10 @@ struct DescRescale {
     const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
     return smod64(v, r.aux);
   }
-  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
-    r.mid[i] = mul_shoup(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
+  static constexpr int EPI = 1;
+  __device__ void epi_load(const Row& r, uint32_t i, uint64_t* o) const { o[0] = r.src2[i]; }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t* o) const {
+    r.mid[i] = mul_shoup(sub_mod(o[0], v, q), r.k, r.ks, q);
   }
 };
 
@@ -537,8 +545,10 @@ struct DescRescaleScaled {
     const int64_t v = x > ql / 2 ? -(int64_t)(ql - x) : (int64_t)x;
     return smod64(v, r.aux);
   }
-  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
-    r.mid[i] = sub_mod(mul_shoup(r.src2[i], r.k2, r.k2s, q), mul_shoup(v, r.k, r.ks, q), q);
+  static constexpr int EPI = 1;
+  __device__ void epi_load(const Row& r, uint32_t i, uint64_t* o) const { o[0] = r.src2[i]; }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t* o) const {
+    r.mid[i] = sub_mod(mul_shoup(o[0], r.k2, r.k2s, q), mul_shoup(v, r.k, r.ks, q), q);
   }
 };
 
@@ -616,10 +626,26 @@ __device__ __forceinline__ void fwd_rows(const D& d, Row& r, int log_n, const ul
     }
     // stored through shared memory so that a warp writes 256 contiguous
     // bytes per instruction (the last round's groups are 8 consecutive
-    // words per thread, which would make every store instruction strided)
-    for (uint32_t i = g; i < 2 * CHUNK; i += ROW_THREADS) {
-      const uint64_t v = s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))];
-      d.store(r, chunk * CHUNK + i, GROW ? reduce_full(v, q, w1s) : reduce4(v, q, q2), q, kc);
+    // words per thread, which would make every store instruction strided).
+    // The epilogue's global operands (D::EPI rows) are loaded for a group of
+    // G elements before any of them is stored: a load cannot be moved above
+    // a store the compiler cannot tell apart from it, so element by element
+    // a thread would have one load in flight.
+    constexpr int SPT = 2 * CHUNK / ROW_THREADS;
+    constexpr int G = D::EPI > 1 ? 4 : 8;
+    constexpr int NE = D::EPI > 0 ? D::EPI : 1;
+#pragma unroll
+    for (int k0 = 0; k0 < SPT; k0 += G) {
+      uint64_t o[G][NE];
+#pragma unroll
+      for (int k = 0; k < G; k++)
+        d.epi_load(r, chunk * CHUNK + g + (uint32_t)(k0 + k) * ROW_THREADS, o[k]);
+#pragma unroll
+      for (int k = 0; k < G; k++) {
+        const uint32_t i = g + (uint32_t)(k0 + k) * ROW_THREADS;
+        const uint64_t v = s[(i & ~(CHUNK - 1)) + swz(i & (CHUNK - 1))];
+        d.store(r, chunk * CHUNK + i, GROW ? reduce_full(v, q, w1s) : reduce4(v, q, q2), q, o[k]);
+      }
     }
   }
 }
@@ -678,9 +704,14 @@ struct DescRelinRescale {
   __device__ void load_cols(const Row& r, uint32_t c, const uint64_t* kc, uint64_t* x) const {
     conv_cols<N1, CHAIN>(r, c, kc, N, x);
   }
-  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t*) const {
-    const uint64_t y = mul_shoup_t<CHAIN>(sub_mod(r.src2[i], v, q), r.k, r.ks, q);
-    r.mid[i] = r.src3 ? add_mod(mul_shoup_t<CHAIN>(r.src3[i], r.k2, r.k2s, q), y, q) : y;
+  static constexpr int EPI = 2;
+  __device__ void epi_load(const Row& r, uint32_t i, uint64_t* o) const {
+    o[0] = r.src2[i];
+    o[1] = r.src3 ? r.src3[i] : 0;
+  }
+  __device__ void store(const Row& r, uint32_t i, uint64_t v, uint64_t q, const uint64_t* o) const {
+    const uint64_t y = mul_shoup_t<CHAIN>(sub_mod(o[0], v, q), r.k, r.ks, q);
+    r.mid[i] = r.src3 ? add_mod(mul_shoup_t<CHAIN>(o[1], r.k2, r.k2s, q), y, q) : y;
   }
 };
 
