@@ -313,7 +313,7 @@ struct DescModUp {
   static constexpr int SLOT = NTT_SLOT_MODUP;
   // The forward transform's first stage multiplies the upper half of the
   // row by the single twiddle w = psi^(N/2); the upper half is loaded with
-  // the constants [Dhat_a w]_m instead (load_w), so that stage is a plain
+  // the constants [Dhat_a w]_m instead (load_cols), so that stage is a plain
   // sum and difference (moduli below 2^50).
   static constexpr bool FOLD1 = true;
   static constexpr bool COL_LOADS = false;  // growth-tolerant rows: load_cols through FOLD1
